@@ -1,0 +1,1010 @@
+/*
+ * grmhd_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, double-precision CPU statement of one IMEX Runge-Kutta step of
+ * resistive (general-relativistic) MHD on a uniform Cartesian grid with a fixed,
+ * conformally flat background metric (gamma_ij = psi^4 delta_ij, beta^i = 0),
+ * staggered face magnetic fields and upwind constrained transport, following
+ * arXiv 2110.03732 (Cheong et al., "Gmunu: ... resistive GRMHD").
+ *
+ * Only tests, __graft_entry__.smoke() and bench.py's cpu_baseline leg may use this
+ * file.  It shares no code with the CUDA path: it has its own structs, its own
+ * index arithmetic and its own statement of every formula, written in the
+ * paper's coordinate-component notation (indices raised/lowered with
+ * gamma_ij = psi^4 delta_ij explicitly), with every intermediate stored in full
+ * arrays and no fusion.
+ *
+ * Paper passages followed (section / equation):
+ *   conserved variables, fluxes, sources          Sec. 2.1 (q, f^i, s; Gauss law for rho_e)
+ *   Ohm's law (xi = 0 only)                       Sec. 2.2
+ *   IMEX-RK stages, SSP2(2,2,2) tableau           Sec. 2.3 (Table "IMEX-SSP2(2,2,2)")
+ *   implicit E + velocity Newton, A_k, Jacobian   Sec. 2.4 (eq. im_E, f_i, J_ij)
+ *   characteristic speeds (maximal diffusivity)   Sec. 2.5
+ *   constrained transport, UCT-HLL edge EMF       Sec. 3.2 (steps i-vii)
+ *   B from an edge vector potential               Sec. 4
+ *   MC limiter + HLL defaults                     Sec. 5 (opening paragraph)
+ *
+ * Readings where the paper is silent or garbled (each also listed in the design doc):
+ *   - IMEX sum limits: q(i) = q^n + dt sum_{j<i} at_ij L(j) + dt sum_{j<=i} a_ij R(j),
+ *     q^{n+1} = q^n + dt sum_i (wt_i L(i) + w_i R(i))  (Pareschi-Russo form).
+ *   - eta_tilde = eta / (alpha a_ii dt) inside stage i.
+ *   - the implicit E equation carries a minus sign in front of W/eta_tilde; the
+ *     A_k printed in Sec. 2.4 are consistent with that sign.
+ *   - d(U_EM)/du^j = E_i dE^i/du^j in the derivative of w_tilde.
+ *   - HLL speeds c+ = max(0, lambda+), c- = max(0, -lambda-) with lambda from Sec. 2.5,
+ *     the metric averaged linearly to faces; at an edge each direction takes the
+ *     larger speed of its two adjacent faces.
+ *   - reconstructed: rho, u^i (= W v^i), p, E^i and the two transverse cell-centred B^i;
+ *     the normal B at a face is the staggered value.  For the edge EMF the covariant
+ *     E_c = psi^4 E^c is reconstructed (face, then edge) and multiplied by the lapse
+ *     averaged to the edge.
+ *   - cell-centred B = mean of the two staggered faces.
+ *   - rho_e from a central difference of cell-centred q_E (Gauss law).
+ *   - ghost cells: periodic, outflow (copy of the nearest interior cell) or fixed
+ *     (left as given).
+ *   - Newton: analytic Jacobian, backtracking line search on 0.5|f|^2 with the Armijo
+ *     condition and a bounded step (Press et al., "globally convergent Newton");
+ *     initial guess = the previous stage's velocity, from rest as the fallback.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NQ 8         /* cell-centred conserved: D, S_1..3, tau, E^1..3 */
+#define NPR 8        /* cell-centred primitives: rho, u^1..3, p, E^1..3 */
+#define NREC 11      /* reconstructed: the 8 primitives + B^1..3 (normal one unused) */
+#define MAXS 4
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_FIXED = 2 };
+
+typedef struct {
+    int ndim;
+    int n[3], ng[3], N[3], act[3], bc[3];
+    double dx[3];
+    double Gam;        /* ideal-gas adiabatic index Gamma */
+    long ncell;        /* padded cells */
+} OGrid;
+
+static void grid_setup(OGrid* g, const int* gi, const double* gd)
+{
+    g->ndim = gi[0];
+    for (int d = 0; d < 3; d++) {
+        g->n[d] = gi[1 + d];
+        g->bc[d] = gi[4 + d];
+        g->act[d] = (d < g->ndim) ? 1 : 0;
+        g->ng[d] = g->act[d] ? 2 : 0;
+        g->N[d] = g->n[d] + 2 * g->ng[d];
+        g->dx[d] = gd[d];
+    }
+    g->Gam = gd[3];
+    g->ncell = (long)g->N[0] * g->N[1] * g->N[2];
+}
+
+static long at(const OGrid* g, int i, int j, int k) { return i + (long)g->N[0] * (j + (long)g->N[1] * k); }
+
+static long shift(const OGrid* g, long c, int d, int s)
+{
+    long st = (d == 0) ? 1 : (d == 1) ? g->N[0] : (long)g->N[0] * g->N[1];
+    return c + s * st;
+}
+
+static void coords(const OGrid* g, long c, int* ijk)
+{
+    ijk[0] = (int)(c % g->N[0]);
+    ijk[1] = (int)((c / g->N[0]) % g->N[1]);
+    ijk[2] = (int)(c / ((long)g->N[0] * g->N[1]));
+}
+
+static int is_interior(const OGrid* g, const int* ijk)
+{
+    for (int d = 0; d < 3; d++)
+        if (ijk[d] < g->ng[d] || ijk[d] >= g->ng[d] + g->n[d]) return 0;
+    return 1;
+}
+
+static double* dalloc(long n) { return (double*)calloc((size_t)n, sizeof(double)); }
+
+/* ------------------------------------------------------------------ */
+/* ghost cells                                                          */
+/* ------------------------------------------------------------------ */
+
+/* cell-centred array: fill the ghost layers of each active direction in turn */
+static void fill_cell_ghosts(const OGrid* g, double* a)
+{
+    for (int d = 0; d < 3; d++) {
+        if (!g->act[d] || g->bc[d] == BC_FIXED) continue;
+        int ijk[3];
+        for (long c = 0; c < g->ncell; c++) {
+            coords(g, c, ijk);
+            int m = ijk[d], lo = g->ng[d], hi = g->ng[d] + g->n[d] - 1;
+            if (m >= lo && m <= hi) continue;
+            int src;
+            if (g->bc[d] == BC_PERIODIC) {
+                src = lo + (((m - lo) % g->n[d]) + g->n[d]) % g->n[d];
+            } else {
+                src = m < lo ? lo : hi;
+            }
+            int s3[3] = {ijk[0], ijk[1], ijk[2]};
+            s3[d] = src;
+            a[c] = a[at(g, s3[0], s3[1], s3[2])];
+        }
+    }
+}
+
+/* face array of direction fd: along fd the faces ng..ng+n are real (ng+n is a copy
+ * of ng when periodic); across fd it behaves like a cell array */
+static void fill_face_ghosts(const OGrid* g, double* a, int fd)
+{
+    for (int d = 0; d < 3; d++) {
+        if (!g->act[d] || g->bc[d] == BC_FIXED) continue;
+        int ijk[3];
+        for (long c = 0; c < g->ncell; c++) {
+            coords(g, c, ijk);
+            int m = ijk[d], lo = g->ng[d];
+            int hi = (d == fd) ? g->ng[d] + g->n[d] : g->ng[d] + g->n[d] - 1;
+            int src;
+            if (g->bc[d] == BC_PERIODIC) {
+                if (d == fd) {
+                    if (m >= lo && m < lo + g->n[d]) continue;
+                } else if (m >= lo && m <= hi) {
+                    continue;
+                }
+                src = lo + (((m - lo) % g->n[d]) + g->n[d]) % g->n[d];
+            } else {
+                if (m >= lo && m <= hi) continue;
+                src = m < lo ? lo : hi;
+            }
+            int s3[3] = {ijk[0], ijk[1], ijk[2]};
+            s3[d] = src;
+            a[c] = a[at(g, s3[0], s3[1], s3[2])];
+        }
+    }
+}
+
+/* cell-centred conserved q_B from the staggered faces: mean of the two faces of the
+ * cell in each active direction (the upper face taken alone where it is outside the
+ * padded array), the face value itself in an inactive direction; then ghost fill */
+static void cell_qB(const OGrid* g, double* const* bf, double** qBc)
+{
+    int ijk[3];
+    for (int d = 0; d < 3; d++) {
+        for (long c = 0; c < g->ncell; c++) {
+            if (!g->act[d]) { qBc[d][c] = bf[d][c]; continue; }
+            coords(g, c, ijk);
+            if (ijk[d] + 1 < g->N[d])
+                qBc[d][c] = 0.5 * (bf[d][c] + bf[d][shift(g, c, d, 1)]);
+            else
+                qBc[d][c] = bf[d][c];
+        }
+        fill_cell_ghosts(g, qBc[d]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* metric helpers: gamma_ij = psi^4 delta_ij, sqrt(gamma) = psi^6        */
+/* ------------------------------------------------------------------ */
+
+static double psi_at(const double* psi, long c) { return psi ? psi[c] : 1.0; }
+static double alp_at(const double* alp, long c) { return alp ? alp[c] : 1.0; }
+
+/* Levi-Civita symbol eta^{ijk} */
+static double levi(int i, int j, int k)
+{
+    if (i == j || j == k || i == k) return 0.0;
+    if ((i == 0 && j == 1 && k == 2) || (i == 1 && j == 2 && k == 0) || (i == 2 && j == 0 && k == 1)) return 1.0;
+    return -1.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* prim -> cons (Sec. 2.1 definitions of q)                              */
+/* ------------------------------------------------------------------ */
+
+/* prim: rho, u^i (=W v^i, contravariant), p, E^i; B^i contravariant; out: densitised q */
+static void prim2con_point(const double* pr, const double* B, double psi, double Gam, double* q)
+{
+    double g = psi * psi * psi * psi, sg = g * psi * psi;
+    double rho = pr[0], p = pr[4];
+    double uu = 0, E2 = 0, B2 = 0;
+    for (int i = 0; i < 3; i++) {
+        uu += g * pr[1 + i] * pr[1 + i];
+        E2 += g * pr[5 + i] * pr[5 + i];
+        B2 += g * B[i] * B[i];
+    }
+    double W = sqrt(1.0 + uu);
+    double h = 1.0 + Gam / (Gam - 1.0) * p / rho;
+    double D = rho * W;
+    double v_lo[3], E_lo[3], B_lo[3];
+    for (int i = 0; i < 3; i++) { v_lo[i] = g * pr[1 + i] / W; E_lo[i] = g * pr[5 + i]; B_lo[i] = g * B[i]; }
+    (void)E_lo; (void)B_lo;
+    double S[3];
+    for (int j = 0; j < 3; j++) {
+        double exb = 0;
+        for (int k = 0; k < 3; k++)
+            for (int l = 0; l < 3; l++) exb += levi(j, k, l) * pr[5 + k] * B[l];
+        S[j] = rho * h * W * W * v_lo[j] + sg * exb;     /* S_j = rho h W^2 v_j + sqrt(gamma) eta_jkl E^k B^l */
+    }
+    double tau = rho * h * W * W - p + 0.5 * (E2 + B2) - D;
+    q[0] = sg * D;
+    for (int j = 0; j < 3; j++) q[1 + j] = sg * S[j];
+    q[4] = sg * tau;
+    for (int j = 0; j < 3; j++) q[5 + j] = sg * pr[5 + j];
+}
+
+/* ------------------------------------------------------------------ */
+/* implicit step (Sec. 2.4), xi = 0                                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    double D, S[3], tau, Es[3], B[3];  /* undensitised; S covariant, Es, B contravariant */
+    double g;                          /* psi^4 */
+    double sg;                         /* psi^6 */
+    double etat;                       /* eta_tilde; < 0 means E held fixed (E = E*) */
+    double Gh;                         /* Gamma_hat_1 = Gamma/(Gamma-1) */
+} OCell;
+
+/* E(u) from eq. im_E with xi = 0 (A_2 = A_3 = A_4 = 0, A_5 = -1):
+ *   A_0 E^i = eta_t E*^i + A_1 (E*_k u^k) u^i + A_5 eps^{ijk} u_j B_k
+ * and its derivative dE^i/du^j from the Sec. 2.4 expression.  Returns W. */
+static double efield(const OCell* c, const double* u, double* E, double dE[3][3])
+{
+    double g = c->g, sg = c->sg;
+    double uu = 0;
+    for (int i = 0; i < 3; i++) uu += g * u[i] * u[i];
+    double W = sqrt(1.0 + uu);
+    double u_lo[3], B_lo[3], Es_lo[3];
+    for (int i = 0; i < 3; i++) { u_lo[i] = g * u[i]; B_lo[i] = g * c->B[i]; Es_lo[i] = g * c->Es[i]; }
+    if (c->etat < 0) {
+        for (int i = 0; i < 3; i++) {
+            E[i] = c->Es[i];
+            if (dE) for (int j = 0; j < 3; j++) dE[i][j] = 0.0;
+        }
+        return W;
+    }
+    double et = c->etat;
+    double A0 = W + et;
+    double A1 = et / (1.0 + et * W);
+    double A5 = -1.0;
+    double A0d = 1.0;
+    double A1d = -et * et / ((1.0 + W * et) * (1.0 + W * et));
+    double Esu = 0, eps_uB[3];
+    for (int k = 0; k < 3; k++) Esu += Es_lo[k] * u[k];
+    for (int i = 0; i < 3; i++) {
+        double s = 0;
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++) s += levi(i, j, k) / sg * u_lo[j] * B_lo[k];
+        eps_uB[i] = s;
+    }
+    for (int i = 0; i < 3; i++)
+        E[i] = (et * c->Es[i] + A1 * Esu * u[i] + A5 * eps_uB[i]) / A0;
+    if (dE) {
+        /* A_0 W dE^i/du^j = -A0' E^i u_j + A_1 W u^i E*_j + (A_1 W delta^i_j + A1' u^i u_j)(E*_k u^k)
+         *                   + eps^{ilm} (A_5 W gamma_lj + A5' u_l u_j) B_m,   A5' = 0 */
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double t = -A0d * E[i] * u_lo[j] + A1 * W * u[i] * Es_lo[j]
+                           + (A1 * W * (i == j ? 1.0 : 0.0) + A1d * u[i] * u_lo[j]) * Esu;
+                double s = 0;
+                for (int l = 0; l < 3; l++)
+                    for (int m = 0; m < 3; m++)
+                        s += levi(i, l, m) / sg * (A5 * W * (l == j ? g : 0.0)) * B_lo[m];
+                dE[i][j] = (t + s) / (A0 * W);
+            }
+    }
+    return W;
+}
+
+/* residual f_i(u) = w_t gamma_ij u^j - (S_i - eps_ilm E^l B^m) and, if J != NULL, J_ij */
+static void residual(const OCell* c, const double* u, double* f, double J[3][3], double* E, double* W_out, double* wt_out)
+{
+    double g = c->g, sg = c->sg, Gh = c->Gh;
+    double dE[3][3];
+    double W = efield(c, u, E, J ? dE : NULL);
+    double E2 = 0, B2 = 0;
+    for (int i = 0; i < 3; i++) { E2 += g * E[i] * E[i]; B2 += g * c->B[i] * c->B[i]; }
+    double U = 0.5 * (E2 + B2);
+    double den = W * W - 1.0 / Gh;
+    double wt = (W * (c->tau + c->D - U) - c->D / Gh) / den;
+    double u_lo[3];
+    for (int i = 0; i < 3; i++) u_lo[i] = g * u[i];
+    double eEB[3];
+    for (int i = 0; i < 3; i++) {
+        double s = 0;
+        for (int l = 0; l < 3; l++)
+            for (int m = 0; m < 3; m++) s += sg * levi(i, l, m) * E[l] * c->B[m];
+        eEB[i] = s;
+        f[i] = wt * u_lo[i] - (c->S[i] - eEB[i]);
+    }
+    if (J) {
+        double dwt[3];
+        for (int j = 0; j < 3; j++) {
+            double dU = 0;
+            for (int i = 0; i < 3; i++) dU += g * E[i] * dE[i][j];
+            dwt[j] = ((c->tau + c->D - U) * u_lo[j] / W - 2.0 * wt * u_lo[j] - W * dU) / den;
+        }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double s = 0;
+                for (int l = 0; l < 3; l++)
+                    for (int m = 0; m < 3; m++) s += sg * levi(i, l, m) * dE[l][j] * c->B[m];
+                J[i][j] = wt * (i == j ? g : 0.0) + u_lo[i] * dwt[j] + s;
+            }
+    }
+    if (W_out) *W_out = W;
+    if (wt_out) *wt_out = wt;
+}
+
+/* Gaussian elimination with partial pivoting: solves M x = b (M, b copied) */
+static int solve3(double M[3][3], const double* b, double* x)
+{
+    double a[3][4];
+    for (int i = 0; i < 3; i++) { for (int j = 0; j < 3; j++) a[i][j] = M[i][j]; a[i][3] = b[i]; }
+    for (int col = 0; col < 3; col++) {
+        int piv = col;
+        for (int r = col + 1; r < 3; r++) if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (a[piv][col] == 0.0) return -1;
+        if (piv != col) for (int j = 0; j < 4; j++) { double t = a[col][j]; a[col][j] = a[piv][j]; a[piv][j] = t; }
+        for (int r = col + 1; r < 3; r++) {
+            double fct = a[r][col] / a[col][col];
+            for (int j = col; j < 4; j++) a[r][j] -= fct * a[col][j];
+        }
+    }
+    for (int i = 2; i >= 0; i--) {
+        double s = a[i][3];
+        for (int j = i + 1; j < 3; j++) s -= a[i][j] * x[j];
+        x[i] = s / a[i][i];
+    }
+    return 0;
+}
+
+static double half_norm2(const double* f) { return 0.5 * (f[0] * f[0] + f[1] * f[1] + f[2] * f[2]); }
+
+/* globally convergent Newton on f(u) = 0; returns iterations (>0) or -1 on failure.
+ * in: u = initial guess; out: u (contravariant), E (contravariant), rho, p */
+static int newton_cell(const OCell* c, double* u, double* E, double* rho, double* p, int kmax, double tol)
+{
+    double f[3], J[3][3], W, wt;
+    /* u holds the initial guess on entry (the caller's previous-stage velocity, or
+     * rest: at u = 0, E(0) = eta_t E_star / (1 + eta_t) stays finite in both the
+     * stiff and the non-stiff limits) */
+    int it;
+    for (it = 1; it <= kmax; it++) {
+        residual(c, u, f, J, E, &W, &wt);
+        double g0 = half_norm2(f);
+        double dx[3], mf[3] = {-f[0], -f[1], -f[2]};
+        if (solve3(J, mf, dx) != 0) return -1;
+        /* step bound (Press et al.): |dx| <= 100 max(|u|, 1) */
+        {
+            double nx = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+            double nu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            double mx = 100.0 * (nu > 1.0 ? nu : 1.0);
+            if (nx > mx) for (int i = 0; i < 3; i++) dx[i] *= mx / nx;
+        }
+        /* backtracking: Armijo condition with slope grad(g).dx = -|f|^2 */
+        double slope = -2.0 * g0, lam = 1.0, un[3], fn[3], En[3];
+        for (int ls = 0; ls < 40; ls++) {
+            for (int i = 0; i < 3; i++) un[i] = u[i] + lam * dx[i];
+            residual(c, un, fn, NULL, En, NULL, NULL);
+            double g1 = half_norm2(fn);
+            if (g1 <= g0 + 1e-4 * lam * slope || !(g0 > 0)) break;
+            double lq = -slope * lam * lam / (2.0 * (g1 - g0 - slope * lam));
+            if (!(lq == lq)) lq = 0.5 * lam;
+            if (lq < 0.1 * lam) lq = 0.1 * lam;
+            if (lq > 0.5 * lam) lq = 0.5 * lam;
+            lam = lq;
+        }
+        double dn = 0, un2 = 0;
+        for (int i = 0; i < 3; i++) {
+            double s = lam * dx[i];
+            dn += s * s; un2 += u[i] * u[i];
+            u[i] = un[i];
+        }
+        if (sqrt(dn) <= tol * (1.0 + sqrt(un2))) {
+            /* a small step is convergence only where the residual is small too */
+            residual(c, u, f, NULL, E, &W, &wt);
+            double fs = 0;
+            for (int i = 0; i < 3; i++) fs += fabs(c->S[i]);
+            if (sqrt(2.0 * half_norm2(f)) <= 1e-9 * (fs + c->tau + c->D)) break;
+        }
+    }
+    if (it > kmax) return -1;
+    residual(c, u, f, NULL, E, &W, &wt);
+    if (!(wt > 0) || !(W < 1e10)) return -1;
+    *rho = c->D / W;
+    *p = (wt / W - *rho) / c->Gh;
+    return it;
+}
+
+/* ------------------------------------------------------------------ */
+/* MC limited reconstruction (Sec. 5: "2nd order MC limiter")            */
+/* ------------------------------------------------------------------ */
+
+static double minmod3(double a, double b, double c)
+{
+    if (a > 0 && b > 0 && c > 0) return fmin(a, fmin(b, c));
+    if (a < 0 && b < 0 && c < 0) return fmax(a, fmax(b, c));
+    return 0.0;
+}
+
+static double mc_slope(double um, double u0, double up)
+{
+    return minmod3(2.0 * (u0 - um), 0.5 * (up - um), 2.0 * (up - u0));
+}
+
+/* ------------------------------------------------------------------ */
+/* physical flux and conserved state at a face (Sec. 2.1)                */
+/* ------------------------------------------------------------------ */
+
+/* pr: rho, u^1..3, p, E^1..3 ; B^1..3 ; direction d; metric psi, alpha at the face.
+ * q: densitised conserved D, S_j, tau, E^j ;  F: flux of the same, in direction d */
+static void face_flux(const double* pr, const double* B, int d, double psi, double alp, double Gam, double* q, double* F)
+{
+    double g = psi * psi * psi * psi, sg = g * psi * psi, ginv = 1.0 / g;
+    prim2con_point(pr, B, psi, Gam, q);
+    double rho = pr[0], p = pr[4];
+    double uu = 0, E2 = 0, B2 = 0;
+    for (int i = 0; i < 3; i++) { uu += g * pr[1 + i] * pr[1 + i]; E2 += g * pr[5 + i] * pr[5 + i]; B2 += g * B[i] * B[i]; }
+    double W = sqrt(1.0 + uu), h = 1.0 + Gam / (Gam - 1.0) * p / rho;
+    double v[3], v_lo[3], E_lo[3], B_lo[3];
+    for (int i = 0; i < 3; i++) { v[i] = pr[1 + i] / W; v_lo[i] = g * v[i]; E_lo[i] = g * pr[5 + i]; B_lo[i] = g * B[i]; }
+    double D = q[0] / sg, tau = q[4] / sg, S_lo[3];
+    for (int j = 0; j < 3; j++) S_lo[j] = q[1 + j] / sg;
+    /* (f_D)^d = sqrt(gamma) D vhat^d, vhat^d = alpha v^d - beta^d */
+    F[0] = sg * D * alp * v[d];
+    /* (f_S_j)^d = sqrt(gamma) alpha S^d_j */
+    for (int j = 0; j < 3; j++)
+        F[1 + j] = sg * alp * ((p + 0.5 * (E2 + B2)) * (d == j ? 1.0 : 0.0) + rho * h * W * W * v[d] * v_lo[j]
+                               - pr[5 + d] * E_lo[j] - B[d] * B_lo[j]);
+    /* (f_tau)^d = sqrt(gamma) alpha (S^d - v^d D) */
+    F[4] = sg * alp * (ginv * S_lo[d] - v[d] * D);
+    /* (f_E^j)^d = sqrt(gamma) (1/sqrt(gamma)) eta^{djk} alpha B_k */
+    for (int j = 0; j < 3; j++) {
+        double s = 0;
+        for (int k = 0; k < 3; k++) s += levi(d, j, k) * alp * B_lo[k];
+        F[5 + j] = s;
+    }
+    (void)tau;
+}
+
+/* ------------------------------------------------------------------ */
+/* the explicit operator L (cell-centred fluxes + sources, CT for faces)  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const OGrid* g;
+    const double* alp;
+    const double* psi;
+} OCtx;
+
+/* prim: 8 padded arrays with ghosts filled; qBc: cell-centred q_B (3, filled);
+ * bf: face q_B (3, ghosts filled); out L: 8 cell-centred + 3 face (interior) */
+static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, double* const* bf, double** L)
+{
+    const OGrid* g = X->g;
+    long nc = g->ncell;
+    int ijk[3];
+    /* cell-centred primitive B and covariant E_c for the EMF */
+    double* Bc[3];
+    double* Ecov[3];
+    for (int d = 0; d < 3; d++) {
+        Bc[d] = dalloc(nc); Ecov[d] = dalloc(nc);
+        for (long c = 0; c < nc; c++) {
+            double ps = psi_at(X->psi, c), gg = ps * ps * ps * ps;
+            Bc[d][c] = qBc[d][c] / (gg * ps * ps);
+            Ecov[d][c] = gg * prim[5 + d][c];
+        }
+    }
+    /* face states and HLL fluxes, direction by direction; the flux for the 8
+     * cell-centred variables lives at face index f (between cells f-1 and f) */
+    double* F[3][NQ];
+    for (int d = 0; d < 3; d++) for (int v = 0; v < NQ; v++) F[d][v] = NULL;
+    for (int d = 0; d < 3; d++) {
+        if (!g->act[d]) continue;
+        for (int v = 0; v < NQ; v++) F[d][v] = dalloc(nc);
+        for (long c = 0; c < nc; c++) {
+            coords(g, c, ijk);
+            int f = ijk[d];
+            if (f < 2 || f > g->N[d] - 2) continue;
+            long cm2 = shift(g, c, d, -2), cm1 = shift(g, c, d, -1), cp1 = shift(g, c, d, 1);
+            double recL[NREC], recR[NREC];
+            for (int v = 0; v < NREC; v++) {
+                const double* a = v < NPR ? prim[v] : Bc[v - NPR];
+                double sl = mc_slope(a[cm2], a[cm1], a[c]);
+                double sr = mc_slope(a[cm1], a[c], a[cp1]);
+                recL[v] = a[cm1] + 0.5 * sl;
+                recR[v] = a[c] - 0.5 * sr;
+            }
+            double psf = 0.5 * (psi_at(X->psi, cm1) + psi_at(X->psi, c));
+            double alf = 0.5 * (alp_at(X->alp, cm1) + alp_at(X->alp, c));
+            double gf = psf * psf * psf * psf;
+            double BL[3], BR[3];
+            for (int k = 0; k < 3; k++) { BL[k] = recL[NPR + k]; BR[k] = recR[NPR + k]; }
+            BL[d] = BR[d] = bf[d][c] / (gf * psf * psf);   /* normal B: the staggered face value */
+            double qL[NQ], qR[NQ], FL[NQ], FR[NQ];
+            face_flux(recL, BL, d, psf, alf, g->Gam, qL, FL);
+            face_flux(recR, BR, d, psf, alf, g->Gam, qR, FR);
+            /* Sec. 2.5: lambda_pm = alpha (pm sqrt(gamma^dd)) - beta^d, beta = 0 */
+            double lp = alf * sqrt(1.0 / gf), lm = -alf * sqrt(1.0 / gf);
+            double cp = fmax(0.0, lp), cm = fmax(0.0, -lm);
+            for (int v = 0; v < NQ; v++)
+                F[d][v][c] = (cp * FL[v] + cm * FR[v] - cp * cm * (qR[v] - qL[v])) / (cp + cm);
+        }
+    }
+    /* cell-centred L: flux divergence + non-stiff sources */
+    for (long c = 0; c < nc; c++) {
+        coords(g, c, ijk);
+        if (!is_interior(g, ijk)) continue;
+        double Lc[NQ];
+        for (int v = 0; v < NQ; v++) Lc[v] = 0.0;
+        for (int d = 0; d < 3; d++) {
+            if (!g->act[d]) continue;
+            long cp1 = shift(g, c, d, 1);
+            for (int v = 0; v < NQ; v++) Lc[v] -= (F[d][v][cp1] - F[d][v][c]) / g->dx[d];
+        }
+        double ps = psi_at(X->psi, c), al = alp_at(X->alp, c);
+        double gg = ps * ps * ps * ps, sg = gg * ps * ps;
+        double uu = 0;
+        for (int i = 0; i < 3; i++) uu += gg * prim[1 + i][c] * prim[1 + i][c];
+        double W = sqrt(1.0 + uu);
+        double v_up[3];
+        for (int i = 0; i < 3; i++) v_up[i] = prim[1 + i][c] / W;
+        /* Gauss law: sqrt(gamma) rho_e = div q_E (central difference) */
+        double divqE = 0;
+        for (int d = 0; d < 3; d++) {
+            if (!g->act[d]) continue;
+            long cp1 = shift(g, c, d, 1), cm1 = shift(g, c, d, -1);
+            double qEp = pow(psi_at(X->psi, cp1), 6) * prim[5 + d][cp1];
+            double qEm = pow(psi_at(X->psi, cm1), 6) * prim[5 + d][cm1];
+            divqE += (qEp - qEm) / (2.0 * g->dx[d]);
+        }
+        double rhoe = divqE / sg;
+        /* s_E non-stiff part: sqrt(gamma) (rho_e beta^i - alpha rho_e v^i), beta = 0 */
+        for (int i = 0; i < 3; i++) Lc[5 + i] += -sg * al * rhoe * v_up[i];
+        if (X->alp || X->psi) {
+            /* s_S_i and s_tau with beta = 0, K_ij = 0 (Sec. 2.1):
+             *   s_S_i = alpha sqrt(gamma) { -T^00 alpha d_i alpha + 1/2 T^jk d_i gamma_jk }
+             *   s_tau = alpha sqrt(gamma) { -T^0j d_j alpha }
+             * T^00 = (tau + D)/alpha^2, alpha T^0j = S^j, T^jk = stress (spatial) */
+            double rho = prim[0][c], p = prim[4][c], h = 1.0 + g->Gam / (g->Gam - 1.0) * p / rho;
+            double E2 = 0, B2 = 0;
+            for (int i = 0; i < 3; i++) { E2 += gg * prim[5 + i][c] * prim[5 + i][c]; B2 += gg * Bc[i][c] * Bc[i][c]; }
+            double pr8[NPR], q8[NQ], Bp[3];
+            for (int v = 0; v < NPR; v++) pr8[v] = prim[v][c];
+            for (int k = 0; k < 3; k++) Bp[k] = Bc[k][c];
+            prim2con_point(pr8, Bp, ps, g->Gam, q8);
+            double D = q8[0] / sg, tau = q8[4] / sg, S_lo[3];
+            for (int j = 0; j < 3; j++) S_lo[j] = q8[1 + j] / sg;
+            double T00 = (tau + D) / (al * al);
+            double Tjk[3][3];
+            for (int j = 0; j < 3; j++)
+                for (int k = 0; k < 3; k++)
+                    Tjk[j][k] = rho * h * W * W * v_up[j] * v_up[k] + p * (j == k ? 1.0 / gg : 0.0)
+                                + 0.5 * (E2 + B2) * (j == k ? 1.0 / gg : 0.0)
+                                - prim[5 + j][c] * prim[5 + k][c] - Bc[j][c] * Bc[k][c];
+            for (int i = 0; i < 3; i++) {
+                if (!g->act[i]) continue;
+                long cp1 = shift(g, c, i, 1), cm1 = shift(g, c, i, -1);
+                double dal = (alp_at(X->alp, cp1) - alp_at(X->alp, cm1)) / (2.0 * g->dx[i]);
+                double dps = (psi_at(X->psi, cp1) - psi_at(X->psi, cm1)) / (2.0 * g->dx[i]);
+                double dgam = 4.0 * ps * ps * ps * dps;     /* d_i gamma_jj (j = k) */
+                double tr = 0;
+                for (int j = 0; j < 3; j++) tr += Tjk[j][j] * dgam;
+                Lc[1 + i] += al * sg * (-T00 * al * dal + 0.5 * tr);
+                Lc[4] += al * sg * (-(S_lo[i] / gg) / al * dal);
+            }
+        }
+        for (int v = 0; v < NQ; v++) L[v][c] = Lc[v];
+    }
+    /* upwind constrained transport: edge EMF hat{E}_c for c = 0,1,2 with the pair
+     * (a, b) = (c+1, c+2) mod 3; stored at the lower-a, lower-b corner index */
+    double* Eh[3];
+    for (int cc = 0; cc < 3; cc++) {
+        Eh[cc] = dalloc(nc);
+        int a = (cc + 1) % 3, b = (cc + 2) % 3;
+        /* step (ii): E_c to a-faces, L/R (cell values where a is inactive) */
+        double* EaL = dalloc(nc);
+        double* EaR = dalloc(nc);
+        for (long c = 0; c < nc; c++) {
+            coords(g, c, ijk);
+            if (!g->act[a]) { EaL[c] = EaR[c] = Ecov[cc][c]; continue; }
+            int f = ijk[a];
+            if (f < 2 || f > g->N[a] - 2) continue;
+            long m2 = shift(g, c, a, -2), m1 = shift(g, c, a, -1), p1 = shift(g, c, a, 1);
+            EaL[c] = Ecov[cc][m1] + 0.5 * mc_slope(Ecov[cc][m2], Ecov[cc][m1], Ecov[cc][c]);
+            EaR[c] = Ecov[cc][c] - 0.5 * mc_slope(Ecov[cc][m1], Ecov[cc][c], Ecov[cc][p1]);
+        }
+        for (long c = 0; c < nc; c++) {
+            coords(g, c, ijk);
+            /* the edge must be reachable by both stencils */
+            if (g->act[a] && (ijk[a] < 2 || ijk[a] > g->N[a] - 2)) continue;
+            if (g->act[b] && (ijk[b] < 2 || ijk[b] > g->N[b] - 2)) continue;
+            if (!g->act[a] && !g->act[b]) {
+                Eh[cc][c] = alp_at(X->alp, c) * Ecov[cc][c];
+                continue;
+            }
+            /* step (iii): along b to the edge: E_c^{XY}, X = a-side, Y = b-side */
+            double EXY[2][2];
+            const double* src[2] = {EaL, EaR};
+            for (int X2 = 0; X2 < 2; X2++) {
+                if (!g->act[b]) { EXY[X2][0] = EXY[X2][1] = src[X2][c]; continue; }
+                long m2 = shift(g, c, b, -2), m1 = shift(g, c, b, -1), p1 = shift(g, c, b, 1);
+                const double* s = src[X2];
+                EXY[X2][0] = s[m1] + 0.5 * mc_slope(s[m2], s[m1], s[c]);
+                EXY[X2][1] = s[c] - 0.5 * mc_slope(s[m1], s[c], s[p1]);
+            }
+            /* step (iv): q_B^b (b-faces) along a -> L/R in a; q_B^a (a-faces) along b -> L/R in b */
+            double qBbL, qBbR, qBaL, qBaR;
+            if (g->act[a]) {
+                long m2 = shift(g, c, a, -2), m1 = shift(g, c, a, -1), p1 = shift(g, c, a, 1);
+                qBbL = bf[b][m1] + 0.5 * mc_slope(bf[b][m2], bf[b][m1], bf[b][c]);
+                qBbR = bf[b][c] - 0.5 * mc_slope(bf[b][m1], bf[b][c], bf[b][p1]);
+            } else {
+                qBbL = qBbR = bf[b][c];
+            }
+            if (g->act[b]) {
+                long m2 = shift(g, c, b, -2), m1 = shift(g, c, b, -1), p1 = shift(g, c, b, 1);
+                qBaL = bf[a][m1] + 0.5 * mc_slope(bf[a][m2], bf[a][m1], bf[a][c]);
+                qBaR = bf[a][c] - 0.5 * mc_slope(bf[a][m1], bf[a][c], bf[a][p1]);
+            } else {
+                qBaL = qBaR = bf[a][c];
+            }
+            /* lapse at the edge: mean of the cells around it; speeds of the faces */
+            long cells[4];
+            int nce = 0;
+            long am = g->act[a] ? shift(g, c, a, -1) : c;
+            cells[nce++] = c;
+            if (g->act[a]) cells[nce++] = am;
+            if (g->act[b]) {
+                cells[nce++] = shift(g, c, b, -1);
+                if (g->act[a]) cells[nce++] = shift(g, am, b, -1);
+            }
+            double ale = 0;
+            for (int t = 0; t < nce; t++) ale += alp_at(X->alp, cells[t]);
+            ale /= nce;
+            double ca = 1.0, cb = 1.0;
+            if (g->act[a]) {
+                /* a-faces adjacent to the edge: at b-cells e-1 and e */
+                ca = 0.0;
+                for (int t = 0; t < (g->act[b] ? 2 : 1); t++) {
+                    long cf = t == 0 ? c : shift(g, c, b, -1);
+                    long cfm = shift(g, cf, a, -1);
+                    double psf = 0.5 * (psi_at(X->psi, cfm) + psi_at(X->psi, cf));
+                    double alf = 0.5 * (alp_at(X->alp, cfm) + alp_at(X->alp, cf));
+                    double sp = alf / (psf * psf);
+                    if (sp > ca) ca = sp;
+                }
+            }
+            if (g->act[b]) {
+                cb = 0.0;
+                for (int t = 0; t < (g->act[a] ? 2 : 1); t++) {
+                    long cf = t == 0 ? c : shift(g, c, a, -1);
+                    long cfm = shift(g, cf, b, -1);
+                    double psf = 0.5 * (psi_at(X->psi, cfm) + psi_at(X->psi, cf));
+                    double alf = 0.5 * (alp_at(X->alp, cfm) + alp_at(X->alp, cf));
+                    double sp = alf / (psf * psf);
+                    if (sp > cb) cb = sp;
+                }
+            }
+            double cap = ca, cam = ca, cbp = cb, cbm = cb;
+            /* step (v): hat{E}^{XY} = alpha E_c^{XY} (beta = 0) */
+            double hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
+            /* step (vii): Londrillo & Del Zanna (2004) */
+            Eh[cc][c] = (cap * cbp * hLL + cap * cbm * hLR + cam * cbp * hRL + cam * cbm * hRR) / ((cap + cam) * (cbp + cbm))
+                        + cap * cam / (cap + cam) * (qBbR - qBbL)
+                        - cbp * cbm / (cbp + cbm) * (qBaR - qBaL);
+        }
+        free(EaL); free(EaR);
+    }
+    /* CT (Sec. 3.2): d(q_B^a)/dt on a-faces, Delta A = product of the two transverse
+     * widths: -d_b hat{E}_c + d_c hat{E}_b with (a, b, c) cyclic */
+    for (int fa = 0; fa < 3; fa++) {
+        int fb = (fa + 1) % 3, fc = (fa + 2) % 3;
+        for (long c = 0; c < nc; c++) {
+            coords(g, c, ijk);
+            int ok = 1;
+            for (int d = 0; d < 3; d++) {
+                int lo = g->ng[d], hi = g->ng[d] + g->n[d] - 1;
+                if (d == fa && g->act[d] && g->bc[d] != BC_PERIODIC) hi += 1;
+                if (ijk[d] < lo || ijk[d] > hi) ok = 0;
+            }
+            if (!ok) continue;
+            double r = 0;
+            /* hat{E}_c lives on edges along c, i.e. varies in a and b */
+            if (g->act[fb]) r -= (Eh[fc][shift(g, c, fb, 1)] - Eh[fc][c]) / g->dx[fb];
+            if (g->act[fc]) r += (Eh[fb][shift(g, c, fc, 1)] - Eh[fb][c]) / g->dx[fc];
+            L[NQ + fa][c] = r;
+        }
+    }
+    for (int d = 0; d < 3; d++) {
+        free(Bc[d]); free(Ecov[d]); free(Eh[d]);
+        for (int v = 0; v < NQ; v++) free(F[d][v]);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* exported API                                                         */
+/* ------------------------------------------------------------------ */
+
+/* gi: ndim, n0, n1, n2, bc0, bc1, bc2 ; gd: dx0, dx1, dx2, Gamma.  All arrays padded. */
+
+/* staggered q_B from an edge vector potential (Sec. 4, q_B^i = eta^{ijk} d_j A_k with
+ * sqrt(gamma_hat) = 1).  A[c] lives on edges along c (lower corner index). Faces whose
+ * stencil leaves the array are left untouched. */
+void orc_curl_A(const int* gi, const double* gd, double* const* A, double** bf)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    int ijk[3];
+    for (int fa = 0; fa < 3; fa++) {
+        int fb = (fa + 1) % 3, fc = (fa + 2) % 3;
+        for (long c = 0; c < G.ncell; c++) {
+            coords(&G, c, ijk);
+            if ((G.act[fb] && ijk[fb] + 1 >= G.N[fb]) || (G.act[fc] && ijk[fc] + 1 >= G.N[fc])) continue;
+            double r = 0;
+            if (G.act[fb]) r += (A[fc][shift(&G, c, fb, 1)] - A[fc][c]) / G.dx[fb];
+            if (G.act[fc]) r -= (A[fb][shift(&G, c, fc, 1)] - A[fb][c]) / G.dx[fc];
+            bf[fa][c] = r;
+        }
+    }
+}
+
+/* prim (8 padded) + face q_B (3 padded) -> densitised conserved q (8 padded, all cells) */
+void orc_prim2con(const int* gi, const double* gd, double* const* prim, double* const* bf, const double* psi, double** q)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    double* qBc[3];
+    double* bfc[3];
+    for (int d = 0; d < 3; d++) {
+        qBc[d] = dalloc(G.ncell);
+        bfc[d] = dalloc(G.ncell);
+        memcpy(bfc[d], bf[d], sizeof(double) * G.ncell);
+        fill_face_ghosts(&G, bfc[d], d);
+    }
+    cell_qB(&G, bfc, qBc);
+    for (long c = 0; c < G.ncell; c++) {
+        double pr[NPR], B[3], qq[NQ];
+        double ps = psi_at(psi, c), sg = pow(ps, 6);
+        for (int v = 0; v < NPR; v++) pr[v] = prim[v][c];
+        for (int d = 0; d < 3; d++) B[d] = qBc[d][c] / sg;
+        prim2con_point(pr, B, ps, G.Gam, qq);
+        for (int v = 0; v < NQ; v++) q[v][c] = qq[v];
+    }
+    for (int d = 0; d < 3; d++) { free(qBc[d]); free(bfc[d]); }
+}
+
+/* single-cell implicit solve, exposed for the pins.  in: D, S_i, tau, E*^i, B^i
+ * (undensitised), psi, eta_tilde (< 0: E fixed), Gamma, initial guess (NULL: rest).
+ * out: u^i, E^i, rho, p.  returns Newton iterations or -1 */
+int orc_solve_cell(const double* in, double psi, double etat, double Gam, const double* guess, double* u, double* E,
+                   double* rho_p)
+{
+    OCell c;
+    c.D = in[0];
+    for (int i = 0; i < 3; i++) { c.S[i] = in[1 + i]; c.Es[i] = in[5 + i]; c.B[i] = in[8 + i]; }
+    c.tau = in[4];
+    c.g = pow(psi, 4); c.sg = pow(psi, 6);
+    c.etat = etat; c.Gh = Gam / (Gam - 1.0);
+    for (int i = 0; i < 3; i++) u[i] = guess ? guess[i] : 0.0;
+    return newton_cell(&c, u, E, &rho_p[0], &rho_p[1], 100, 1e-14);
+}
+
+/* residual + analytic Jacobian at a given u (for the finite-difference pin) */
+void orc_residual_cell(const double* in, double psi, double etat, double Gam, const double* u, double* f, double* J9, double* E)
+{
+    OCell c;
+    c.D = in[0];
+    for (int i = 0; i < 3; i++) { c.S[i] = in[1 + i]; c.Es[i] = in[5 + i]; c.B[i] = in[8 + i]; }
+    c.tau = in[4];
+    c.g = pow(psi, 4); c.sg = pow(psi, 6);
+    c.etat = etat; c.Gh = Gam / (Gam - 1.0);
+    double J[3][3];
+    residual(&c, u, f, J, E, NULL, NULL);
+    for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) J9[3 * i + j] = J[i][j];
+}
+
+/* implicit stage solve over interior cells (Sec. 2.4): base q (8 padded) and face
+ * q_B (3) in; q_E of the base replaced by the solution; prims out (8, interior);
+ * R = (q_E - q_E,base)/(a_ii dt) (3, interior).  eta: per-cell or NULL -> eta_u.
+ * a_dt = a_ii * dt; a_dt <= 0 means E held fixed (plain con2prim).
+ * stats[0] += failures, stats[1] = max iterations.  Returns failures. */
+int orc_implicit(const int* gi, const double* gd, double a_dt, double** q, double* const* bf,
+                 const double* alp, const double* psi, const double* eta, double eta_u,
+                 double** prim, double** R, int* stats)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    double* qBc[3];
+    double* bfc[3];
+    for (int d = 0; d < 3; d++) {
+        qBc[d] = dalloc(G.ncell);
+        bfc[d] = dalloc(G.ncell);
+        memcpy(bfc[d], bf[d], sizeof(double) * G.ncell);
+        fill_face_ghosts(&G, bfc[d], d);
+    }
+    cell_qB(&G, bfc, qBc);
+    int fails = 0, maxit = 0, ijk[3];
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        double ps = psi_at(psi, c), sg = pow(ps, 6);
+        OCell cl;
+        cl.g = pow(ps, 4); cl.sg = sg; cl.Gh = G.Gam / (G.Gam - 1.0);
+        cl.D = q[0][c] / sg; cl.tau = q[4][c] / sg;
+        for (int i = 0; i < 3; i++) { cl.S[i] = q[1 + i][c] / sg; cl.Es[i] = q[5 + i][c] / sg; cl.B[i] = qBc[i][c] / sg; }
+        double et = eta ? eta[c] : eta_u;
+        cl.etat = a_dt > 0 ? et / (alp_at(alp, c) * a_dt) : -1.0;
+        /* initial guess: the velocity of the previous stage held in prim (the paper
+         * does not fix one); from rest if that is not finite or does not converge */
+        double u[3], E[3], rho, p;
+        int fin = 1;
+        for (int i = 0; i < 3; i++) { u[i] = prim[1 + i][c]; if (!(fabs(u[i]) < 1e30)) fin = 0; }
+        if (!fin) for (int i = 0; i < 3; i++) u[i] = 0.0;
+        int it = newton_cell(&cl, u, E, &rho, &p, 100, 1e-14);
+        if (it < 0 && fin) {
+            for (int i = 0; i < 3; i++) u[i] = 0.0;
+            it = newton_cell(&cl, u, E, &rho, &p, 100, 1e-14);
+        }
+        if (it < 0) { fails++; continue; }
+        if (it > maxit) maxit = it;
+        prim[0][c] = rho;
+        for (int i = 0; i < 3; i++) prim[1 + i][c] = u[i];
+        prim[4][c] = p;
+        for (int i = 0; i < 3; i++) prim[5 + i][c] = E[i];
+        for (int i = 0; i < 3; i++) {
+            double qEn = sg * E[i];
+            if (R) R[i][c] = a_dt > 0 ? (qEn - q[5 + i][c]) / a_dt : 0.0;
+            q[5 + i][c] = qEn;
+        }
+    }
+    for (int d = 0; d < 3; d++) { free(qBc[d]); free(bfc[d]); }
+    if (stats) { stats[0] += fails; if (maxit > stats[1]) stats[1] = maxit; }
+    return fails;
+}
+
+/* explicit operator L for given stage prims (8 padded; interior set, ghosts: fixed-BC
+ * values) and face q_B (3 padded).  L out: 8 cell-centred + 3 face arrays. */
+void orc_explicit_L(const int* gi, const double* gd, double* const* prim_in, double* const* bf_in,
+                    const double* alp, const double* psi, double** L)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    OCtx X = {&G, alp, psi};
+    double* prim[NPR];
+    double* bf[3];
+    double* qBc[3];
+    for (int v = 0; v < NPR; v++) {
+        prim[v] = dalloc(G.ncell);
+        memcpy(prim[v], prim_in[v], sizeof(double) * G.ncell);
+        fill_cell_ghosts(&G, prim[v]);
+    }
+    for (int d = 0; d < 3; d++) {
+        bf[d] = dalloc(G.ncell);
+        qBc[d] = dalloc(G.ncell);
+        memcpy(bf[d], bf_in[d], sizeof(double) * G.ncell);
+        fill_face_ghosts(&G, bf[d], d);
+    }
+    cell_qB(&G, bf, qBc);
+    explicit_L(&X, prim, qBc, bf, L);
+    for (int v = 0; v < NPR; v++) free(prim[v]);
+    for (int d = 0; d < 3; d++) { free(bf[d]); free(qBc[d]); }
+}
+
+/* one IMEX step with a DIRK-type tableau (a_ii > 0 for every stage).
+ * At, A: s*s row-major; wt, w: s.  q (8) and bf (3) updated in place (interior).
+ * prim (8 padded): in = fixed-BC ghost values, out = last stage primitives.
+ * stats: [0] failures, [1] max Newton iterations. Returns 0 or -1 (bad tableau). */
+int orc_step(const int* gi, const double* gd, int s, const double* At, const double* A,
+             const double* wt, const double* w, double dt, double** q, double** bf,
+             const double* alp, const double* psi, const double* eta, double eta_u,
+             double** prim, int* stats)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    if (s < 1 || s > MAXS) return -1;
+    for (int i = 0; i < s; i++) if (!(A[i * s + i] > 0)) return -1;
+    long nc = G.ncell;
+    double* Ls[MAXS][NQ + 3];
+    double* Rs[MAXS][3];
+    double* qs[NQ];
+    double* bs[3];
+    for (int i = 0; i < s; i++) {
+        for (int v = 0; v < NQ + 3; v++) Ls[i][v] = dalloc(nc);
+        for (int v = 0; v < 3; v++) Rs[i][v] = dalloc(nc);
+    }
+    for (int v = 0; v < NQ; v++) qs[v] = dalloc(nc);
+    for (int d = 0; d < 3; d++) bs[d] = dalloc(nc);
+    int ijk[3];
+    for (int i = 0; i < s; i++) {
+        /* stage base: q^n + dt sum_{j<i} (at_ij L(j) + a_ij R(j)) -- ghosts keep q^n */
+        for (int v = 0; v < NQ; v++) memcpy(qs[v], q[v], sizeof(double) * nc);
+        for (int d = 0; d < 3; d++) memcpy(bs[d], bf[d], sizeof(double) * nc);
+        for (int j = 0; j < i; j++) {
+            double at_ = At[i * s + j], a_ = A[i * s + j];
+            for (long c = 0; c < nc; c++) {
+                coords(&G, c, ijk);
+                for (int v = 0; v < NQ; v++) {
+                    if (!is_interior(&G, ijk)) continue;
+                    qs[v][c] += dt * at_ * Ls[j][v][c];
+                    if (v >= 5) qs[v][c] += dt * a_ * Rs[j][v - 5][c];
+                }
+                for (int d = 0; d < 3; d++) bs[d][c] += dt * at_ * Ls[j][NQ + d][c];
+            }
+        }
+        orc_implicit(gi, gd, A[i * s + i] * dt, qs, bs, alp, psi, eta, eta_u, prim, Rs[i], stats);
+        orc_explicit_L(gi, gd, prim, bs, alp, psi, Ls[i]);
+    }
+    for (long c = 0; c < nc; c++) {
+        coords(&G, c, ijk);
+        int inter = is_interior(&G, ijk);
+        for (int i = 0; i < s; i++) {
+            if (inter) {
+                for (int v = 0; v < NQ; v++) {
+                    q[v][c] += dt * wt[i] * Ls[i][v][c];
+                    if (v >= 5) q[v][c] += dt * w[i] * Rs[i][v - 5][c];
+                }
+            }
+            for (int d = 0; d < 3; d++) bf[d][c] += dt * wt[i] * Ls[i][NQ + d][c];
+        }
+    }
+    for (int i = 0; i < s; i++) {
+        for (int v = 0; v < NQ + 3; v++) free(Ls[i][v]);
+        for (int v = 0; v < 3; v++) free(Rs[i][v]);
+    }
+    for (int v = 0; v < NQ; v++) free(qs[v]);
+    for (int d = 0; d < 3; d++) free(bs[d]);
+    return 0;
+}
+
+/* Delta t = CFL / max_cells sum_d (alpha sqrt(gamma^dd) + |beta^d|)/dx_d  (Sec. 2.5) */
+double orc_dt(const int* gi, const double* gd, const double* alp, const double* psi, double cfl)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    int ijk[3];
+    double mx = 0;
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        double ps = psi_at(psi, c), s = 0;
+        for (int d = 0; d < 3; d++)
+            if (G.act[d]) s += alp_at(alp, c) * sqrt(1.0 / pow(ps, 4)) / G.dx[d];
+        if (s > mx) mx = s;
+    }
+    return cfl / mx;
+}
+
+/* discrete div q_B per interior cell (Sec. 3.2 / Eq. divb_0 with sqrt(gamma_hat) = 1):
+ * out[0] = mean |div|, out[1] = sqrt(mean div^2), out[2] = max |div| */
+void orc_divb(const int* gi, const double* gd, double* const* bf_in, double* out)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    double* bf[3];
+    for (int d = 0; d < 3; d++) {
+        bf[d] = dalloc(G.ncell);
+        memcpy(bf[d], bf_in[d], sizeof(double) * G.ncell);
+        fill_face_ghosts(&G, bf[d], d);
+    }
+    int ijk[3];
+    double s1 = 0, s2 = 0, mx = 0;
+    long n = 0;
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        double dv = 0;
+        for (int d = 0; d < 3; d++)
+            if (G.act[d]) dv += (bf[d][shift(&G, c, d, 1)] - bf[d][c]) / G.dx[d];
+        s1 += fabs(dv); s2 += dv * dv; if (fabs(dv) > mx) mx = fabs(dv);
+        n++;
+    }
+    out[0] = s1 / n; out[1] = sqrt(s2 / n); out[2] = mx;
+    for (int d = 0; d < 3; d++) free(bf[d]);
+}
+
+/* volume totals of the 8 cell-centred conserved variables over the interior */
+void orc_totals(const int* gi, const double* gd, double* const* q, double* out)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    int ijk[3];
+    double dV = 1;
+    for (int d = 0; d < 3; d++) if (G.act[d]) dV *= G.dx[d];
+    for (int v = 0; v < NQ; v++) out[v] = 0;
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        for (int v = 0; v < NQ; v++) out[v] += q[v][c] * dV;
+    }
+}
