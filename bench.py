@@ -1,0 +1,325 @@
+"""Benchmark: zone-updates per second per IMEX stage of the resistive relativistic
+MHD step (arXiv 2110.03732) on one GB300, FP64.
+
+Workload: the 2-D resistive relativistic Orszag-Tang vortex, periodic [0, 2 pi]^2,
+512 x 512 cells, Gamma = 4/3, eta = 1e-4, synthetic initial data from
+paper_2110_03732_gb300.problems.  One timed step = one full IMEX-SSP2(2,2,2) step:
+two stages, each an implicit E + velocity solve and the explicit MC/HLL/UCT/CT
+operator, with the final combination folded into the last stage.  The time step is
+fixed for a fixed metric and is computed once before timing.
+
+value = interior cells x stages per step / seconds per step, whole job (N ranks each
+advance an independent replica: weak scaling, no data-path collective).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "zone-updates/s per IMEX stage (FP64 vs mixed, 1 GB300, % HBM roofline); p50/p99 run latency"
+UNIT = "zone-updates/s"
+N_OT = 512
+STAGES = 2
+
+# Algorithmic HBM bytes per zone-stage of one IMEX stage (FP64, flat metric, uniform
+# eta): each datum once; stage 1 reads q^n (11 doubles) and writes its increments
+# (11 + 3), stage 2 reads q^n, the increments and writes q^{n+1} (37 doubles): mean
+# 31.5 doubles = 252 B per zone-stage (uniform eta saves the 8 B per-cell field).
+ALG_BYTES_PER_ZONE_STAGE = 252.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_OT, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 ALU peak: the nominal GB300 dense FP64 rate of the profiling recipe
+# (1.25 TFLOP/s); a register-only FMA probe on this machine measured 1.19-1.20 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(n_sample, steps):
+    """The CPU oracle as it stands (single thread) on a bounded sample of the same
+    workload: `steps` IMEX steps of the Orszag-Tang problem at n_sample^2 cells."""
+    import oracle
+    from paper_2110_03732_gb300 import problems as P
+    pr = P.orszag_tang(n_sample)
+    st = oracle.from_problem(pr)
+    dt = oracle.cfl_dt(st.grid, pr.cfl)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.step(dt)
+    el = time.perf_counter() - t0
+    return n_sample * n_sample * STAGES * steps / el, el
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, same metric and workload family,
+    each step a bounded sample (one IMEX step at 256^2 of the same initial data)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2110_03732_gb300 import problems as P
+    n_s = 256
+    pr = P.orszag_tang(n_s)
+    st = oracle.from_problem(pr)
+    dt = oracle.cfl_dt(st.grid, pr.cfl)
+    for _ in range(args.warmup):
+        st.step(dt)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st.step(dt)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n_s * n_s * STAGES / (ms / 1e3)
+    sample = f"orszag_tang_2d {n_s}x{n_s} (quarter-size sample of the 512^2 workload), one IMEX-SSP2 step per timed step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"orszag_tang_2d_{N_OT}x{N_OT}_fp64", "cells": N_OT * N_OT,
+                       "stages_per_step": STAGES, "sample_cells": n_s * n_s},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2110_03732_gb300 import build as _b
+    from paper_2110_03732_gb300 import grmhd
+    from paper_2110_03732_gb300 import problems as P
+    _b.build()
+
+    n = args.n
+    pr = P.orszag_tang(n)
+    S = grmhd.Solver.from_problem(pr, device=dev)
+    dt = S.compute_dt()
+    cells = S.cells
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    for _ in range(max(args.warmup, 3)):
+        S.step(dt)
+    torch.cuda.synchronize()
+    S.set_timing(True)
+    S.kernel_times()
+    launches0 = S.launch_count()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    if rank == 0:
+        clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        S.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ktimes = S.kernel_times()   # fold this step's per-kernel events
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    ktimes = S.kernel_times()
+    launches = S.launch_count() - launches0
+
+    total_s = sum(step_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    ms_per_step = 1e3 * total_s / args.steps
+    value = ws * cells * STAGES * args.steps / total_s
+
+    # end to end: the same step through the public API with the state in pinned host
+    # memory, host->device copy of the inputs and device->host copy of the result
+    # inside the timed region
+    host_q = [t.detach().cpu().pin_memory() for t in S.q]
+    host_b = [t.detach().cpu().pin_memory() for t in S.bf]
+    h2d = sum(t.numel() * t.element_size() for t in host_q + host_b)
+    e2e_ms = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for dst, src in zip(S.q + S.bf, host_q + host_b):
+            dst.copy_(src, non_blocking=True)
+        S.step(dt)
+        for src, dst in zip(S.q + S.bf, host_q + host_b):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = ws * cells * STAGES / (float(np.mean(e2e_ms)) / 1e3)
+
+    divb, tot, nfail = S.diagnostics()
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    pk, pk_src = peaks()
+    # dominant kernel by measured time inside the timed region
+    kname = max(ktimes, key=lambda k: ktimes[k][0])
+    kms, kn = ktimes[kname]
+    k_avg_ms = kms / max(kn, 1)
+    tot_kernel_ms = sum(v[0] for v in ktimes.values())
+    roof = roofline_entry(kname, k_avg_ms, cells, pk, pk_src)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"orszag_tang_2d_{n}x{n}_fp64", "cells": cells, "stages_per_step": STAGES,
+                   "eta": pr.eta_u, "gamma": pr.gamma, "cfl": pr.cfl, "dt": dt,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "p50_ms_per_step": float(np.percentile(step_ms, 50)), "p99_ms_per_step": float(np.percentile(step_ms, 99)),
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
+        "kernel_share": {k: v[0] / tot_kernel_ms for k, v in ktimes.items()},
+        "roofline": roof,
+        "hbm_fraction_of_step": ALG_BYTES_PER_ZONE_STAGE * cells * STAGES / (ms_per_step / 1e3) / (pk["hbm_gbs"] * 1e9),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "divb_max": divb[2], "newton_failures": nfail,
+    }
+    if not args.no_cpu_baseline:
+        rate, el = cpu_oracle_rate(256, 2)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"orszag_tang_2d 256x256, 2 IMEX-SSP2 steps ({el:.1f} s, single thread)"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+# FP64 flops per zone-stage executed by each kernel kind, counted by ncu on the
+# 512^2 workload (2 * DFMA + DADD + DMUL instructions per launch / cells); see
+# profiles/.  None until counted.
+FP64_FLOPS_PER_CELL = {"implicit": None, "flux": None, "emf": None, "update": None}
+
+
+def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):
+    fl = FP64_FLOPS_PER_CELL.get(kname)
+    if fl is None:
+        return {"bound": "alu", "kernel": kname, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "avg_launch_ms": k_avg_ms,
+                "note": "FP64 flop count per cell not yet measured"}
+    ach = fl * cells / (k_avg_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": k_avg_ms,
+            "peak_source": "nominal FP64 (profiling recipe)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * grmhd.h -- C ABI of the GB300 (sm_103a) implementation of one implicit-explicit
+ * Runge-Kutta stage of resistive (general-relativistic) MHD on a uniform Cartesian
+ * grid with a fixed background metric, after arXiv 2110.03732 (Cheong et al.).
+ *
+ * Problem statement (what the calls take):
+ *   - grid: uniform Cartesian, 1-3 active directions, Sec. 5 boundary kinds
+ *   - 3+1 metric (Sec. 2.1): lapse alpha, zero shift, spatial metric
+ *     gamma_ij = psi^4 delta_ij (conformally flat, reference metric Cartesian)
+ *   - state (Sec. 2.1): densitised cell-centred conserved variables
+ *     q = psi^6 (D, S_1, S_2, S_3, tau, E^1, E^2, E^3) and staggered face fields
+ *     q_B^d = psi^6 B^d on the lower d-face of each cell (Sec. 3.2)
+ *   - primitives (Sec. 2.4/2.6): rho, u^i = W v^i (contravariant), p, E^i
+ *   - resistivity eta (Sec. 2.2, xi = 0), per cell or uniform
+ *   - IMEX tableau (Sec. 2.3), diagonally implicit with a_ii > 0; IMEX-SSP2(2,2,2)
+ *     is provided by grmhd_tableau_ssp2
+ *   - ideal-gas equation of state p = (Gamma - 1) rho eps (Sec. 2.4)
+ *
+ * Layout: every array is a padded grid of N0 * N1 * N2 doubles, x fastest, with
+ * N_d = n_d + 4 in an active direction (two ghost cells per side) and N_d = 1 in an
+ * inactive one.  Face arrays hold the value on the lower face of each cell; edge
+ * arrays (vector potential) hold the value on the edge that is lower in both
+ * transverse directions.  Directions become active in the order x, y, z.
+ *
+ * Ownership: the caller owns every buffer (device memory unless stated).  The
+ * library allocates no device memory: grmhd_scratch_bytes says how much scratch the
+ * caller must pass to grmhd_bind.  Pointers must stay valid while bound.
+ *
+ * Streams: all work is ordered on the stream passed in.  Only grmhd_compute_dt and
+ * grmhd_diagnostics synchronise that stream (they return host scalars).
+ *
+ * Errors: every call returns a grmhd_status; negative values are errors, positive
+ * values warnings.  grmhd_last_error() gives a message for the calling thread.  A
+ * context is not thread-safe; use one per thread/stream.
+ */
+#ifndef GRMHD_H
+#define GRMHD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* grmhd_stream_t; /* same type as cudaStream_t */
+typedef struct grmhd_ctx_s grmhd_ctx;
+
+typedef enum {
+    GRMHD_OK = 0,
+    GRMHD_WARN_C2P_FAILED = 1, /* some cells' Newton solves did not converge (see diagnostics) */
+    GRMHD_ERR_ARG = -1,        /* invalid argument (message in grmhd_last_error) */
+    GRMHD_ERR_CUDA = -2,       /* a CUDA call failed */
+    GRMHD_ERR_SCRATCH = -3,    /* scratch buffer too small or misaligned */
+    GRMHD_ERR_STATE = -5       /* call out of order (e.g. step before bind) */
+} grmhd_status;
+
+enum { GRMHD_BC_PERIODIC = 0, GRMHD_BC_OUTFLOW = 1, GRMHD_BC_FIXED = 2 };
+
+/* Uniform Cartesian grid (Sec. 5 test set-ups).  bc: per direction; FIXED keeps the
+ * ghost values that init wrote (Sec. 5, "values at the outer boundaries are kept
+ * fixed").  lo/hi give the physical extent; dx = (hi - lo)/n. */
+typedef struct {
+    int ndim;      /* 1, 2 or 3 active directions */
+    int n[3];      /* interior cells; ignored (taken as 1) for inactive directions */
+    double lo[3];
+    double hi[3];
+    int bc[3];
+} grmhd_grid;
+
+/* IMEX Butcher pair (Sec. 2.3): explicit At (strictly lower), implicit A (lower,
+ * a_ii > 0), weights wt, w; row-major s x s in the first s*s entries. */
+typedef struct {
+    int s; /* 1..4 stages */
+    double At[16];
+    double A[16];
+    double wt[4];
+    double w[4];
+} grmhd_tableau;
+
+typedef struct {
+    double gamma_eos;  /* ideal-gas Gamma (> 1) */
+    double cfl;        /* Courant number for grmhd_compute_dt */
+    double newton_tol; /* Newton residual tolerance, relative to the momentum terms of
+                          f_i (Sec. 2.4); 0 -> 1e-13 */
+    int newton_kmax;   /* Newton iteration cap; 0 -> 50 */
+    int reserved;
+    double rho_atm;    /* atmosphere (not in the paper): a cell with D < 10 rho_atm, or
+                          whose solve fails, is set to rest at (rho_atm, p_atm) with E
+                          kept; 0 disables it (failures then keep their primitives) */
+    double p_atm;
+} grmhd_params;
+
+/* IMEX-SSP2(2,2,2) of Sec. 2.3 (Pareschi & Russo), gamma = 1 - 1/sqrt(2). */
+grmhd_status grmhd_tableau_ssp2(grmhd_tableau* out);
+
+/* Bytes of device scratch the caller must provide for this grid and tableau
+ * (256-byte aligned base). */
+grmhd_status grmhd_scratch_bytes(const grmhd_grid* grid, const grmhd_tableau* tab, size_t* bytes);
+
+/* Create a context on the current CUDA device.  No device memory is allocated. */
+grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const grmhd_tableau* tab,
+                          grmhd_ctx** out);
+grmhd_status grmhd_destroy(grmhd_ctx* ctx);
+
+/* Bind the caller's state and scratch.  q: 8 padded cell arrays (D, S_1..3, tau,
+ * E^1..3, densitised); bface: 3 padded face arrays (q_B^x, q_B^y, q_B^z); scratch:
+ * at least grmhd_scratch_bytes bytes, 256-byte aligned. */
+grmhd_status grmhd_bind(grmhd_ctx* ctx, double* const* q, double* const* bface, void* scratch, size_t scratch_bytes);
+
+/* Fixed background metric (Sec. 2.1): alpha and psi as padded cell arrays read at
+ * every padded cell (ghosts included, no boundary condition applied); NULL = flat
+ * (alpha = psi = 1).  The shift is zero. */
+grmhd_status grmhd_set_metric(grmhd_ctx* ctx, const double* alpha, const double* psi);
+
+/* Resistivity (Sec. 2.2): eta_cc a padded cell array, or NULL for the uniform eta. */
+grmhd_status grmhd_set_eta(grmhd_ctx* ctx, const double* eta_cc, double eta_uniform);
+
+/* Initial state (Sec. 4 + Sec. 2.1): if A_edge is not NULL the face fields become
+ * the discrete curl q_B^i = eta^{ijk} d_j A_k of the three padded edge arrays (faces
+ * whose stencil leaves the array are zero); otherwise the bound face arrays are used
+ * as they are.  Then q = prim2con(prim, cell-averaged B) at every padded cell, and
+ * prim (8 padded arrays, ghosts included: they are the FIXED boundary values) is
+ * kept as the Newton starting point. */
+grmhd_status grmhd_init_from_prims(grmhd_ctx* ctx, const double* const* prim, const double* const* A_edge,
+                                   grmhd_stream_t stream);
+
+/* Delta t = cfl / max_cells sum_d alpha sqrt(gamma^dd) / dx_d (Sec. 2.5, speed of
+ * light).  Synchronises the stream. */
+grmhd_status grmhd_compute_dt(grmhd_ctx* ctx, double* dt, grmhd_stream_t stream);
+
+/* One IMEX stage i (0-based) of Sec. 2.3: the implicit E + velocity solve of
+ * Sec. 2.4 for the stage state, then the explicit operator (MC + HLL fluxes,
+ * sources, UCT edge EMF and CT face update, Secs. 2.1, 3.2) folded into the later
+ * stages' bases and the final combination; the last stage writes q^{n+1} into the
+ * bound state.  Stages of one step must run in order 0..s-1 with the same dt. */
+grmhd_status grmhd_stage(grmhd_ctx* ctx, int i, double dt, grmhd_stream_t stream);
+
+/* All stages of one step: q^n -> q^{n+1}. */
+grmhd_status grmhd_step(grmhd_ctx* ctx, double dt, grmhd_stream_t stream);
+
+/* Primitives of the bound state with E held fixed (Sec. 2.6) into prim_out
+ * (8 padded arrays; interior written, ghosts copied from the context). */
+grmhd_status grmhd_get_prims(grmhd_ctx* ctx, double* const* prim_out, grmhd_stream_t stream);
+
+/* Implicit solve (Sec. 2.4) on caller buffers over the interior: q (8, in/out: q_E
+ * replaced by the solution), bface (3), prim (8, in: Newton start, out: solution),
+ * R (3, out: (q_E - q_E,in)/a_dt).  a_dt = a_ii dt; a_dt <= 0 holds E fixed. */
+grmhd_status grmhd_implicit(grmhd_ctx* ctx, double a_dt, double* const* q, const double* const* bface,
+                            double* const* prim, double* const* R, grmhd_stream_t stream);
+
+/* Explicit operator on caller buffers: prim (8 padded, ghosts = FIXED values) and
+ * bface (3) -> L (11 padded: 8 cell-centred rates on the interior, 3 face rates on
+ * the faces that the step updates). */
+grmhd_status grmhd_explicit_L(grmhd_ctx* ctx, const double* const* prim, const double* const* bface,
+                              double* const* L, grmhd_stream_t stream);
+
+/* Diagnostics of the bound state: divb = {mean |div q_B|, rms, max} over interior
+ * cells (Sec. 3.2), totals = volume sums of the 8 cell-centred q, nfail = Newton
+ * failures since create.  Synchronises the stream. */
+grmhd_status grmhd_diagnostics(grmhd_ctx* ctx, double* divb, double* totals, long long* nfail,
+                               grmhd_stream_t stream);
+
+/* Kernels launched by this context since create (host-side count). */
+long long grmhd_launch_count(const grmhd_ctx* ctx);
+
+/* Optional per-kernel timing (not part of the paper's method: measurement only).
+ * When enabled, CUDA events are recorded on the launching stream around every
+ * stage kernel (at most 64 launches between two grmhd_kernel_times calls; later
+ * ones go untimed).  grmhd_kernel_times waits for the recorded events and returns
+ * the cumulative milliseconds and launch counts per kind: [0] implicit solve,
+ * [1] face fluxes, [2] edge EMFs, [3] update. */
+grmhd_status grmhd_set_timing(grmhd_ctx* ctx, int enable);
+grmhd_status grmhd_kernel_times(grmhd_ctx* ctx, double* ms, long long* launches);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* grmhd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRMHD_H */

@@ -90,9 +90,10 @@ def _dpp(arrs):
 class Grid:
     """Uniform Cartesian grid: ``ndim`` active directions, ``n`` interior cells,
     cell widths ``dx``, boundary kinds ``bc`` (periodic / outflow / fixed), ideal-gas
-    ``gamma``.  Inactive directions have one cell and no ghosts."""
+    ``gamma``, atmosphere floor ``rho_atm``/``p_atm`` (0: none).  Inactive directions
+    have one cell and no ghosts."""
 
-    def __init__(self, ndim, n, dx, bc, gamma):
+    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0):
         n = list(n) + [1] * (3 - len(n))
         dx = list(dx) + [1.0] * (3 - len(dx))
         bc = list(bc) + ["periodic"] * (3 - len(bc))
@@ -104,7 +105,8 @@ class Grid:
         self.ng = [2 if d < ndim else 0 for d in range(3)]
         self.N = [self.n[d] + 2 * self.ng[d] for d in range(3)]
         self._gi = (C.c_int * 7)(ndim, *self.n, *self.bc)
-        self._gd = (C.c_double * 4)(*self.dx, self.gamma)
+        self.rho_atm, self.p_atm = float(rho_atm), float(p_atm)
+        self._gd = (C.c_double * 6)(*self.dx, self.gamma, self.rho_atm, self.p_atm)
 
     @property
     def shape(self):
@@ -285,7 +287,7 @@ class State:
 def from_problem(prob):
     """Oracle state from a ``paper_2110_03732_gb300.problems.Problem``: face q_B from
     the edge potential (oracle curl) or taken as given."""
-    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma)
+    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm)
     if prob.A_edge is not None:
         bf = curl_A(grid, [np.ascontiguousarray(a, dtype=np.float64) for a in prob.A_edge])
     else:

@@ -44,7 +44,11 @@
  *     (left as given).
  *   - Newton: analytic Jacobian, backtracking line search on 0.5|f|^2 with the Armijo
  *     condition and a bounded step (Press et al., "globally convergent Newton");
- *     initial guess = the previous stage's velocity, from rest as the fallback.
+ *     initial guess = the previous stage's velocity, from rest as the fallback;
+ *     converged when |f| is at round-off against the momentum terms it balances.
+ *   - atmosphere (not described in the paper): with rho_atm > 0, a cell whose
+ *     D < 10 rho_atm, or whose solve fails, is set to rest at (rho_atm, p_atm) with E
+ *     kept and no stiff update.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -62,6 +66,8 @@ typedef struct {
     int n[3], ng[3], N[3], act[3], bc[3];
     double dx[3];
     double Gam;        /* ideal-gas adiabatic index Gamma */
+    double rho_atm;    /* atmosphere density (0: no atmosphere treatment) */
+    double p_atm;      /* atmosphere pressure */
     long ncell;        /* padded cells */
 } OGrid;
 
@@ -77,6 +83,8 @@ static void grid_setup(OGrid* g, const int* gi, const double* gd)
         g->dx[d] = gd[d];
     }
     g->Gam = gd[3];
+    g->rho_atm = gd[4];
+    g->p_atm = gd[5];
     g->ncell = (long)g->N[0] * g->N[1] * g->N[2];
 }
 
@@ -392,19 +400,27 @@ static int newton_cell(const OCell* c, double* u, double* E, double* rho, double
             if (lq > 0.5 * lam) lq = 0.5 * lam;
             lam = lq;
         }
-        double dn = 0, un2 = 0;
+        double dn = 0;
         for (int i = 0; i < 3; i++) {
             double s = lam * dx[i];
-            dn += s * s; un2 += u[i] * u[i];
+            dn += s * s;
             u[i] = un[i];
         }
-        if (sqrt(dn) <= tol * (1.0 + sqrt(un2))) {
-            /* a small step is convergence only where the residual is small too */
-            residual(c, u, f, NULL, E, &W, &wt);
-            double fs = 0;
-            for (int i = 0; i < 3; i++) fs += fabs(c->S[i]);
-            if (sqrt(2.0 * half_norm2(f)) <= 1e-9 * (fs + c->tau + c->D)) break;
+        /* f_i has momentum units: it is converged when it is at round-off against the
+         * momentum terms it balances (|S_i|, |eps_ilm E^l B^m|, |w_t u_i|); a step that
+         * no longer moves u also ends the iteration */
+        residual(c, u, f, NULL, E, &W, &wt);
+        double M = 0, fm = 0, um = 0;
+        for (int i = 0; i < 3; i++) {
+            double exb = 0;
+            for (int l = 0; l < 3; l++)
+                for (int m = 0; m < 3; m++) exb += c->sg * levi(i, l, m) * E[l] * c->B[m];
+            M = fmax(M, fmax(fabs(c->S[i]), fmax(fabs(exb), fabs(wt * c->g * u[i]))));
+            fm = fmax(fm, fabs(f[i]));
+            um = fmax(um, fabs(u[i]));
         }
+        if (fm <= tol * M) break;
+        if (sqrt(dn) <= 1e-15 * um) break;
     }
     if (it > kmax) return -1;
     residual(c, u, f, NULL, E, &W, &wt);
@@ -724,7 +740,8 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
 /* exported API                                                         */
 /* ------------------------------------------------------------------ */
 
-/* gi: ndim, n0, n1, n2, bc0, bc1, bc2 ; gd: dx0, dx1, dx2, Gamma.  All arrays padded. */
+/* gi: ndim, n0, n1, n2, bc0, bc1, bc2 ; gd: dx0, dx1, dx2, Gamma, rho_atm, p_atm.
+ * All arrays padded. */
 
 /* staggered q_B from an edge vector potential (Sec. 4, q_B^i = eta^{ijk} d_j A_k with
  * sqrt(gamma_hat) = 1).  A[c] lives on edges along c (lower corner index). Faces whose
@@ -833,15 +850,32 @@ int orc_implicit(const int* gi, const double* gd, double a_dt, double** q, doubl
         /* initial guess: the velocity of the previous stage held in prim (the paper
          * does not fix one); from rest if that is not finite or does not converge */
         double u[3], E[3], rho, p;
-        int fin = 1;
-        for (int i = 0; i < 3; i++) { u[i] = prim[1 + i][c]; if (!(fabs(u[i]) < 1e30)) fin = 0; }
-        if (!fin) for (int i = 0; i < 3; i++) u[i] = 0.0;
-        int it = newton_cell(&cl, u, E, &rho, &p, 100, 1e-14);
-        if (it < 0 && fin) {
-            for (int i = 0; i < 3; i++) u[i] = 0.0;
+        int it = 0, atmo = 0;
+        if (G.rho_atm > 0 && cl.D < 10.0 * G.rho_atm) {
+            atmo = 1;
+        } else {
+            int fin = 1;
+            for (int i = 0; i < 3; i++) { u[i] = prim[1 + i][c]; if (!(fabs(u[i]) < 1e30)) fin = 0; }
+            if (!fin) for (int i = 0; i < 3; i++) u[i] = 0.0;
             it = newton_cell(&cl, u, E, &rho, &p, 100, 1e-14);
+            if (it < 0 && fin) {
+                for (int i = 0; i < 3; i++) u[i] = 0.0;
+                it = newton_cell(&cl, u, E, &rho, &p, 100, 1e-14);
+            }
+            if (it < 0) {
+                fails++;
+                if (!(G.rho_atm > 0)) continue;
+                atmo = 1;
+            }
         }
-        if (it < 0) { fails++; continue; }
+        if (atmo) {
+            /* atmosphere: rest state at the floor density and pressure, E kept (no stiff
+             * update) */
+            rho = G.rho_atm;
+            p = G.p_atm;
+            for (int i = 0; i < 3; i++) { u[i] = 0.0; E[i] = cl.Es[i]; }
+            it = 0;
+        }
         if (it > maxit) maxit = it;
         prim[0][c] = rho;
         for (int i = 0; i < 3; i++) prim[1 + i][c] = u[i];

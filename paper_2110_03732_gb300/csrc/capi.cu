@@ -1,0 +1,583 @@
+// C-ABI of the GB300 resistive-MHD IMEX stage: context, scratch carving, launch
+// sequencing.  See include/grmhd.h for the contract of every call.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/grmhd.h"
+#include "kernels.h"
+
+using namespace grmhd;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+grmhd_status fail(grmhd_status s, const char* fmt, const char* a = "")
+{
+    snprintf(g_err, sizeof g_err, fmt, a);
+    return s;
+}
+
+grmhd_status cuda_fail(cudaError_t e, const char* where)
+{
+    snprintf(g_err, sizeof g_err, "%s: %s", where, cudaGetErrorString(e));
+    return GRMHD_ERR_CUDA;
+}
+
+constexpr int kRedBlocks = 1024;   // partial rows of the reductions
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+struct grmhd_ctx_s {
+    Dims g;
+    grmhd_grid grid;
+    grmhd_params par;
+    grmhd_tableau tab;
+    double dV;
+    int nsm;
+    bool bound, any_fixed;
+    double* q[8];
+    double* bf[3];
+    double* prim[8];
+    double* R[3];
+    double* base[4][11];
+    double* acc[11];
+    double* F[3][8];
+    double* Eh[3];
+    double* red_part;
+    double* red_out;
+    unsigned long long* nfail;
+    const double* psi;
+    const double* alp;
+    const double* eta;
+    double eta_u;
+    long long launches;
+    // optional per-kernel timing: events around each launch, folded on request
+    bool timing;
+    int npend;
+    cudaEvent_t ev[64][2];
+    int ev_kind[64];
+    double t_ms[4];
+    long long t_n[4];
+};
+
+namespace {
+
+grmhd_status check_grid(const grmhd_grid* g)
+{
+    if (!g) return fail(GRMHD_ERR_ARG, "grid is NULL");
+    if (g->ndim < 1 || g->ndim > 3) return fail(GRMHD_ERR_ARG, "ndim must be 1, 2 or 3");
+    for (int d = 0; d < g->ndim; d++) {
+        if (g->n[d] < 1) return fail(GRMHD_ERR_ARG, "n[d] must be >= 1 in every active direction");
+        if (!(g->hi[d] > g->lo[d])) return fail(GRMHD_ERR_ARG, "hi must exceed lo in every active direction");
+        if (g->bc[d] < 0 || g->bc[d] > 2) return fail(GRMHD_ERR_ARG, "bc must be PERIODIC, OUTFLOW or FIXED");
+        if (g->bc[d] == GRMHD_BC_PERIODIC && g->n[d] < 2)
+            return fail(GRMHD_ERR_ARG, "a periodic direction needs at least 2 cells");
+    }
+    return GRMHD_OK;
+}
+
+grmhd_status check_tab(const grmhd_tableau* t)
+{
+    if (!t) return fail(GRMHD_ERR_ARG, "tableau is NULL");
+    if (t->s < 1 || t->s > 4) return fail(GRMHD_ERR_ARG, "tableau must have 1..4 stages");
+    for (int i = 0; i < t->s; i++) {
+        if (!(t->A[i * t->s + i] > 0.0)) return fail(GRMHD_ERR_ARG, "implicit tableau needs a_ii > 0");
+        for (int j = i; j < t->s; j++)
+            if (t->At[i * t->s + j] != 0.0) return fail(GRMHD_ERR_ARG, "explicit tableau must be strictly lower");
+        for (int j = i + 1; j < t->s; j++)
+            if (t->A[i * t->s + j] != 0.0) return fail(GRMHD_ERR_ARG, "implicit tableau must be lower triangular");
+    }
+    return GRMHD_OK;
+}
+
+Dims make_dims(const grmhd_grid* gr, double gam)
+{
+    Dims g;
+    g.ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        g.act[d] = d < gr->ndim;
+        g.n[d] = g.act[d] ? gr->n[d] : 1;
+        g.ng[d] = g.act[d] ? 2 : 0;
+        g.N[d] = g.n[d] + 2 * g.ng[d];
+        g.bc[d] = g.act[d] ? gr->bc[d] : GRMHD_BC_PERIODIC;
+        g.idx[d] = g.act[d] ? g.n[d] / (gr->hi[d] - gr->lo[d]) : 0.0;
+        g.ncell *= g.N[d];
+    }
+    g.st[0] = 1;
+    g.st[1] = g.N[0];
+    g.st[2] = (long long)g.N[0] * g.N[1];
+    g.gh = gam / (gam - 1.0);
+    g.igh = (gam - 1.0) / gam;
+    return g;
+}
+
+// scratch carve: returns the byte count; with base != NULL assigns the pointers
+size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base)
+{
+    const size_t arr = round_up(sizeof(double) * (size_t)g.ncell);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += round_up(bytes);
+        return p;
+    };
+    for (int v = 0; v < 8; v++) { char* p = take(arr); if (c) c->prim[v] = (double*)p; }
+    for (int v = 0; v < 3; v++) { char* p = take(arr); if (c) c->R[v] = (double*)p; }
+    for (int k = 1; k < s; k++)
+        for (int v = 0; v < 11; v++) { char* p = take(arr); if (c) c->base[k][v] = (double*)p; }
+    for (int v = 0; v < 11; v++) { char* p = take(arr); if (c) c->acc[v] = (double*)p; }
+    for (int d = 0; d < ndim; d++)
+        for (int v = 0; v < 8; v++) { char* p = take(arr); if (c) c->F[d][v] = (double*)p; }
+    for (int v = 0; v < 3; v++) { char* p = take(arr); if (c) c->Eh[v] = (double*)p; }
+    { char* p = take(sizeof(double) * kRedBlocks * 11); if (c) c->red_part = (double*)p; }
+    { char* p = take(sizeof(double) * 16); if (c) c->red_out = (double*)p; }
+    { char* p = take(sizeof(unsigned long long)); if (c) c->nfail = (unsigned long long*)p; }
+    return off;
+}
+
+CP8 cp8(double* const* p)
+{
+    CP8 r;
+    for (int v = 0; v < 8; v++) r.p[v] = p[v];
+    return r;
+}
+CP8 cp8c(const double* const* p)
+{
+    CP8 r;
+    for (int v = 0; v < 8; v++) r.p[v] = p[v];
+    return r;
+}
+CP3 cp3(double* const* p)
+{
+    CP3 r;
+    for (int v = 0; v < 3; v++) r.p[v] = p[v];
+    return r;
+}
+CP3 cp3c(const double* const* p)
+{
+    CP3 r;
+    for (int v = 0; v < 3; v++) r.p[v] = p[v];
+    return r;
+}
+P8 p8(double* const* p)
+{
+    P8 r;
+    for (int v = 0; v < 8; v++) r.p[v] = p[v];
+    return r;
+}
+P3 p3(double* const* p)
+{
+    P3 r;
+    for (int v = 0; v < 3; v++) r.p[v] = p ? p[v] : nullptr;
+    return r;
+}
+
+bool emf_needed(const Dims& g, int c) { return g.act[(c + 1) % 3] || g.act[(c + 2) % 3]; }
+
+// kernel kinds for the timing hooks
+enum { KIND_IMPLICIT = 0, KIND_FLUX = 1, KIND_EMF = 2, KIND_UPDATE = 3 };
+
+int tbegin(grmhd_ctx* c, int kind, cudaStream_t st)
+{
+    if (!c->timing || c->npend >= 64) return -1;
+    const int i = c->npend++;
+    c->ev_kind[i] = kind;
+    cudaEventRecord(c->ev[i][0], st);
+    return i;
+}
+
+void tend(grmhd_ctx* c, int i, cudaStream_t st)
+{
+    if (i >= 0) cudaEventRecord(c->ev[i][1], st);
+}
+
+// fluxes, EMFs and the update for the given stage primitives / faces
+grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaStream_t st)
+{
+    const Dims& g = c->g;
+    cudaError_t e;
+    for (int d = 0; d < 3; d++) {
+        if (!g.act[d]) continue;
+        const int tk = tbegin(c, KIND_FLUX, st);
+        e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st);
+        tend(c, tk, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "flux kernel");
+    }
+    for (int k = 0; k < 3; k++) {
+        if (!emf_needed(g, k)) continue;
+        const int tk = tbegin(c, KIND_EMF, st);
+        e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st);
+        tend(c, tk, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "emf kernel");
+    }
+    for (int d = 0; d < 3; d++)
+        for (int v = 0; v < 8; v++) a.F[d][v] = g.act[d] ? c->F[d][v] : nullptr;
+    for (int k = 0; k < 3; k++) a.Eh[k] = c->Eh[k];
+    for (int v = 0; v < 8; v++) a.prim[v] = prim.p[v];
+    for (int k = 0; k < 3; k++) a.bf[k] = bfs.p[k];
+    a.psi = c->psi;
+    a.alp = c->alp;
+    const int tk = tbegin(c, KIND_UPDATE, st);
+    e = launch_update(g, a, c->nsm, st);
+    tend(c, tk, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "update kernel");
+    return GRMHD_OK;
+}
+
+grmhd_status need_bound(const grmhd_ctx* c)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    if (!c->bound) return fail(GRMHD_ERR_STATE, "call grmhd_bind first");
+    return GRMHD_OK;
+}
+
+
+}  // namespace
+
+extern "C" {
+
+grmhd_status grmhd_tableau_ssp2(grmhd_tableau* t)
+{
+    if (!t) return fail(GRMHD_ERR_ARG, "tableau is NULL");
+    memset(t, 0, sizeof *t);
+    const double gm = 1.0 - 1.0 / std::sqrt(2.0);
+    t->s = 2;
+    t->At[2] = 1.0;  // At[1][0]
+    t->A[0] = gm;
+    t->A[2] = 1.0 - 2.0 * gm;
+    t->A[3] = gm;
+    t->wt[0] = t->wt[1] = 0.5;
+    t->w[0] = t->w[1] = 0.5;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_scratch_bytes(const grmhd_grid* grid, const grmhd_tableau* tab, size_t* bytes)
+{
+    grmhd_status s = check_grid(grid);
+    if (s != GRMHD_OK) return s;
+    if ((s = check_tab(tab)) != GRMHD_OK) return s;
+    if (!bytes) return fail(GRMHD_ERR_ARG, "bytes is NULL");
+    Dims g = make_dims(grid, 2.0);
+    *bytes = carve(nullptr, g, tab->s, grid->ndim, nullptr);
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const grmhd_tableau* tab,
+                          grmhd_ctx** out)
+{
+    grmhd_status s = check_grid(grid);
+    if (s != GRMHD_OK) return s;
+    if ((s = check_tab(tab)) != GRMHD_OK) return s;
+    if (!par || !out) return fail(GRMHD_ERR_ARG, "params/out is NULL");
+    if (!(par->gamma_eos > 1.0)) return fail(GRMHD_ERR_ARG, "gamma_eos must exceed 1");
+    if (par->rho_atm < 0.0 || par->p_atm < 0.0) return fail(GRMHD_ERR_ARG, "atmosphere floor must be >= 0");
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    grmhd_ctx* c = new (std::nothrow) grmhd_ctx_s();
+    if (!c) return fail(GRMHD_ERR_ARG, "out of host memory");
+    c->g = make_dims(grid, par->gamma_eos);
+    c->grid = *grid;
+    c->par = *par;
+    if (c->par.newton_tol <= 0.0) c->par.newton_tol = 1e-13;
+    if (c->par.newton_kmax <= 0) c->par.newton_kmax = 50;
+    c->tab = *tab;
+    c->dV = 1.0;
+    c->any_fixed = false;
+    for (int d = 0; d < grid->ndim; d++) {
+        c->dV *= (grid->hi[d] - grid->lo[d]) / grid->n[d];
+        if (grid->bc[d] == GRMHD_BC_FIXED) c->any_fixed = true;
+    }
+    c->nsm = nsm;
+    *out = c;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_destroy(grmhd_ctx* ctx)
+{
+    if (ctx && ctx->timing)
+        for (int i = 0; i < 64; i++) {
+            cudaEventDestroy(ctx->ev[i][0]);
+            cudaEventDestroy(ctx->ev[i][1]);
+        }
+    delete ctx;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_set_timing(grmhd_ctx* c, int enable)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    if (enable && !c->timing) {
+        for (int i = 0; i < 64; i++)
+            for (int k = 0; k < 2; k++) {
+                cudaError_t e = cudaEventCreate(&c->ev[i][k]);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+            }
+        c->timing = true;
+        c->npend = 0;
+        for (int k = 0; k < 4; k++) { c->t_ms[k] = 0.0; c->t_n[k] = 0; }
+    }
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_kernel_times(grmhd_ctx* c, double* ms, long long* launches)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    if (!c->timing) return fail(GRMHD_ERR_STATE, "timing is off: call grmhd_set_timing first");
+    for (int i = 0; i < c->npend; i++) {
+        cudaError_t e = cudaEventSynchronize(c->ev[i][1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, c->ev[i][0], c->ev[i][1]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        c->t_ms[c->ev_kind[i]] += t;
+        c->t_n[c->ev_kind[i]] += 1;
+    }
+    c->npend = 0;
+    for (int k = 0; k < 4; k++) {
+        if (ms) ms[k] = c->t_ms[k];
+        if (launches) launches[k] = c->t_n[k];
+    }
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_bind(grmhd_ctx* c, double* const* q, double* const* bface, void* scratch, size_t scratch_bytes)
+{
+    if (!c || !q || !bface || !scratch) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_bind");
+    for (int v = 0; v < 8; v++)
+        if (!q[v]) return fail(GRMHD_ERR_ARG, "q[v] is NULL");
+    for (int v = 0; v < 3; v++)
+        if (!bface[v]) return fail(GRMHD_ERR_ARG, "bface[v] is NULL");
+    if ((uintptr_t)scratch % kAlign) return fail(GRMHD_ERR_SCRATCH, "scratch must be 256-byte aligned");
+    const size_t need = carve(nullptr, c->g, c->tab.s, c->grid.ndim, nullptr);
+    if (scratch_bytes < need) return fail(GRMHD_ERR_SCRATCH, "scratch smaller than grmhd_scratch_bytes");
+    carve(c, c->g, c->tab.s, c->grid.ndim, (char*)scratch);
+    for (int v = 0; v < 8; v++) c->q[v] = q[v];
+    for (int v = 0; v < 3; v++) c->bf[v] = bface[v];
+    c->bound = true;
+    cudaError_t e = cudaMemsetAsync(c->nfail, 0, sizeof(unsigned long long), 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_set_metric(grmhd_ctx* c, const double* alpha, const double* psi)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    if ((alpha || psi) && c->tab.s == 1)
+        return fail(GRMHD_ERR_ARG, "a curved metric needs a tableau with at least two stages");
+    c->alp = alpha;
+    c->psi = psi;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_set_eta(grmhd_ctx* c, const double* eta_cc, double eta_uniform)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    if (!eta_cc && !(eta_uniform > 0.0)) return fail(GRMHD_ERR_ARG, "uniform eta must be positive");
+    c->eta = eta_cc;
+    c->eta_u = eta_uniform;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, const double* const* A_edge,
+                                   grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!prim) return fail(GRMHD_ERR_ARG, "prim is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const Dims& g = c->g;
+    const size_t bytes = sizeof(double) * (size_t)g.ncell;
+    cudaError_t e;
+    if (A_edge) {
+        for (int v = 0; v < 3; v++) {
+            e = cudaMemsetAsync(c->bf[v], 0, bytes, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+        }
+        e = launch_curlA(g, cp3c(A_edge), p3(c->bf), c->nsm, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "curl kernel");
+    }
+    for (int v = 0; v < 8; v++) {
+        e = cudaMemcpyAsync(c->prim[v], prim[v], bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    e = launch_prim2con(g, cp8c(prim), cp3(c->bf), c->psi, p8(c->q), c->nsm, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "prim2con kernel");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_compute_dt(grmhd_ctx* c, double* dt, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!dt) return fail(GRMHD_ERR_ARG, "dt is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_dt(c->g, c->psi, c->alp, c->red_part, kRedBlocks, c->red_out, st);
+    c->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(e, "dt kernel");
+    double mx = 0.0;
+    e = cudaMemcpyAsync(&mx, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "dt readback");
+    if (!(mx > 0.0)) return fail(GRMHD_ERR_ARG, "characteristic speeds vanish");
+    *dt = c->par.cfl / mx;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (i < 0 || i >= c->tab.s) return fail(GRMHD_ERR_ARG, "stage index out of range");
+    if (!(dt > 0.0)) return fail(GRMHD_ERR_ARG, "dt must be positive");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = c->tab.s;
+    cudaError_t e;
+    if (i == 0 && c->any_fixed) {
+        // FIXED boundaries: the later stages' face arrays carry the boundary values too
+        for (int k = 1; k < S; k++)
+            for (int v = 0; v < 3; v++) {
+                e = cudaMemcpyAsync(c->base[k][8 + v], c->bf[v], sizeof(double) * (size_t)c->g.ncell,
+                                    cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+            }
+    }
+    double* const* qb = i == 0 ? c->q : c->base[i];
+    double* const* fb = i == 0 ? c->bf : c->base[i] + 8;
+    const double a_dt = c->tab.A[i * S + i] * dt;
+    P3 none = p3(nullptr);
+    const int tk = tbegin(c, KIND_IMPLICIT, st);
+    e = launch_implicit(c->g, cp8(qb), cp3(fb), c->psi, c->alp, c->eta, c->eta_u, a_dt, p8(c->prim), p3(c->R), none,
+                        c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, c->nfail, c->nsm, st);
+    tend(c, tk, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
+    UpdateArgs a;
+    memset(&a, 0, sizeof a);
+    a.mode = UPD_STAGE;
+    a.stage = i;
+    a.s = S;
+    a.dt = dt;
+    for (int r = 0; r < S; r++) {
+        for (int k = 0; k < S; k++) {
+            a.At[r][k] = c->tab.At[r * S + k];
+            a.A[r][k] = c->tab.A[r * S + k];
+        }
+        a.wt[r] = c->tab.wt[r];
+        a.w[r] = c->tab.w[r];
+    }
+    for (int v = 0; v < 3; v++) a.R[v] = c->R[v];
+    for (int v = 0; v < 8; v++) a.qn[v] = c->q[v];
+    for (int v = 0; v < 3; v++) a.qn[8 + v] = c->bf[v];
+    for (int k = 1; k < S; k++)
+        for (int v = 0; v < 11; v++) a.base[k][v] = c->base[k][v];
+    for (int v = 0; v < 11; v++) a.acc[v] = c->acc[v];
+    CP8 pr;
+    for (int v = 0; v < 8; v++) pr.p[v] = c->prim[v];
+    return explicit_part(c, pr, cp3(fb), a, st);
+}
+
+grmhd_status grmhd_step(grmhd_ctx* c, double dt, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    for (int i = 0; i < c->tab.s; i++) {
+        s = grmhd_stage(c, i, dt, stream);
+        if (s != GRMHD_OK) return s;
+    }
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_get_prims(grmhd_ctx* c, double* const* prim_out, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!prim_out) return fail(GRMHD_ERR_ARG, "prim_out is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    for (int v = 0; v < 8; v++) {
+        e = cudaMemcpyAsync(prim_out[v], c->prim[v], sizeof(double) * (size_t)c->g.ncell, cudaMemcpyDeviceToDevice,
+                            st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    }
+    e = launch_implicit(c->g, cp8(c->q), cp3(c->bf), c->psi, c->alp, c->eta, c->eta_u, 0.0, p8(prim_out),
+                        p3(nullptr), p3(nullptr), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, c->nfail, c->nsm, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "con2prim kernel");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_implicit(grmhd_ctx* c, double a_dt, double* const* q, const double* const* bface,
+                            double* const* prim, double* const* R, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!q || !bface || !prim || !R) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_implicit");
+    cudaError_t e = launch_implicit(c->g, cp8(q), cp3c(bface), c->psi, c->alp, c->eta, c->eta_u, a_dt, p8(prim),
+                                    p3(R), p3(q + 5), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, c->nfail, c->nsm,
+                                    (cudaStream_t)stream);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_explicit_L(grmhd_ctx* c, const double* const* prim, const double* const* bface, double* const* L,
+                              grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!prim || !bface || !L) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_explicit_L");
+    UpdateArgs a;
+    memset(&a, 0, sizeof a);
+    a.mode = UPD_WRITE_L;
+    for (int v = 0; v < 11; v++) a.L[v] = L[v];
+    return explicit_part(c, cp8c(prim), cp3c(bface), a, (cudaStream_t)stream);
+}
+
+grmhd_status grmhd_diagnostics(grmhd_ctx* c, double* divb, double* totals, long long* nfail, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_diag(c->g, cp3(c->bf), cp8(c->q), c->dV, c->red_part, kRedBlocks, c->red_out, st);
+    c->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics kernel");
+    double out[11];
+    unsigned long long nf = 0;
+    e = cudaMemcpyAsync(out, c->red_out, sizeof out, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nf, c->nfail, sizeof nf, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics readback");
+    const double ncell = (double)c->g.n[0] * c->g.n[1] * c->g.n[2];
+    if (divb) {
+        divb[0] = out[0] / ncell;
+        divb[1] = std::sqrt(out[1] / ncell);
+        divb[2] = out[2];
+    }
+    if (totals)
+        for (int v = 0; v < 8; v++) totals[v] = out[3 + v];
+    if (nfail) *nfail = (long long)nf;
+    return nf ? GRMHD_WARN_C2P_FAILED : GRMHD_OK;
+}
+
+long long grmhd_launch_count(const grmhd_ctx* c) { return c ? c->launches : 0; }
+
+const char* grmhd_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,661 @@
+// CUDA kernels of one IMEX-RK stage of resistive (GR)MHD with staggered
+// constrained transport (arXiv 2110.03732), sm_103a, FP64.
+//
+//   k_implicit   Sec. 2.4: per-cell Newton on u coupled to the implicit E update;
+//                writes stage primitives and the stiff rate R = (q_E - q_E,base)/(a_ii dt)
+//   k_flux<D>    Sec. 2.1 + Sec. 5 defaults: MC reconstruction to the D-faces, HLL flux
+//                with the maximal-diffusivity speeds of Sec. 2.5
+//   k_emf<C>     Sec. 3.2 steps (i)-(vii): upwind (UCT-HLL) edge EMF hat{E}_C
+//   k_update<M>  flux divergence + non-stiff sources (Sec. 2.1) and the CT face update
+//                (Sec. 3.2); writes L, or folds it straight into the IMEX stage bases and
+//                the final combination (Sec. 2.3)
+//   k_prim2con, k_curlA (Sec. 4), k_dt (Sec. 2.5), k_divb, k_totals: set-up and
+//   diagnostics
+#include "grmhd_device.cuh"
+#include "kernels.h"
+
+namespace grmhd {
+
+// ---------------------------------------------------------------------------
+// implicit step
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(128) k_implicit(Dims g, CP8 qb, CP3 bf, const double* __restrict__ psi,
+                                                  const double* __restrict__ alp, const double* __restrict__ eta,
+                                                  double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax,
+                                                  double tol, double rho_atm, double p_atm,
+                                                  unsigned long long* __restrict__ nfail)
+{
+    const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = g.ng[0] + (int)(t % g.n[0]);
+        c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
+        c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long id = lin(g, c[0], c[1], c[2]);
+        const double ps = psi ? psi[id] : 1.0;
+        const double al = alp ? alp[id] : 1.0;
+        const double p2 = ps * ps, p4 = p2 * p2, ip2 = 1.0 / p2, ip4 = ip2 * ip2, ip6 = ip4 * ip2;
+        CellIn ci;
+        ci.gh = g.gh;
+        ci.igh = g.igh;
+        ci.D = qb.p[0][id] * ip6;
+        ci.S[0] = qb.p[1][id] * ip6 * ip2;
+        ci.S[1] = qb.p[2][id] * ip6 * ip2;
+        ci.S[2] = qb.p[3][id] * ip6 * ip2;
+        ci.tau = qb.p[4][id] * ip6;
+        double qEs[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            qEs[i] = qb.p[5 + i][id];
+            ci.Es[i] = qEs[i] * ip4;
+            ci.B[i] = cell_qB(g, bf.p[i], i, c) * ip4;
+        }
+        const double et = eta ? eta[id] : eta_u;
+        ci.etat = a_dt > 0.0 ? et / (al * a_dt) : -1.0;
+        double u[3];
+        Eval e;
+        bool atmo = false;
+        if (rho_atm > 0.0 && ci.D < 10.0 * rho_atm) {
+            atmo = true;
+        } else {
+            bool fin = true;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                u[i] = p2 * prim.p[1 + i][id];
+                if (!(fabs(u[i]) < 1e30)) fin = false;
+            }
+            if (!fin) u[0] = u[1] = u[2] = 0.0;
+            int it = newton_solve(ci, u, e, kmax, tol);
+            if (it < 0 && fin) {
+                u[0] = u[1] = u[2] = 0.0;
+                it = newton_solve(ci, u, e, kmax, tol);
+            }
+            if (it < 0) {
+                atomicAdd(nfail, 1ull);
+                if (!(rho_atm > 0.0)) {
+                    // no atmosphere: leave the cell's primitives as they were, no stiff update
+                    if (R.p[0])
+#pragma unroll
+                        for (int i = 0; i < 3; i++) R.p[i][id] = 0.0;
+                    continue;
+                }
+                atmo = true;
+            }
+        }
+        double rho, pres;
+        if (atmo) {
+            // atmosphere: rest state at the floor density and pressure, E kept
+            rho = rho_atm;
+            pres = p_atm;
+            u[0] = u[1] = u[2] = 0.0;
+            e.E[0] = ci.Es[0];
+            e.E[1] = ci.Es[1];
+            e.E[2] = ci.Es[2];
+        } else {
+            const double iW = 1.0 / e.W;
+            rho = ci.D * iW;
+            pres = (e.wt * iW - rho) * g.igh;
+        }
+        prim.p[0][id] = rho;
+        prim.p[4][id] = pres;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            prim.p[1 + i][id] = u[i] * ip2;
+            prim.p[5 + i][id] = e.E[i] * ip2;
+            const double qEn = p4 * e.E[i];
+            if (R.p[0]) R.p[i][id] = a_dt > 0.0 ? (qEn - qEs[i]) / a_dt : 0.0;
+            if (qE_out.p[0]) qE_out.p[i][id] = qEn;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// face fluxes
+// ---------------------------------------------------------------------------
+
+template <int D>
+__global__ void __launch_bounds__(128) k_flux(Dims g, CP8 prim, CP3 bf, const double* __restrict__ psi,
+                                              const double* __restrict__ alp, P8 F)
+{
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1), e2 = g.n[2] + (D == 2);
+    const long long tot = (long long)e0 * e1 * e2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = g.ng[0] + (int)(t % e0);
+        c[1] = g.ng[1] + (int)((t / e0) % e1);
+        c[2] = g.ng[2] + (int)(t / ((long long)e0 * e1));
+        long long mi[4], ri[4];
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            cs[D] += s - 2;
+            mi[s] = cell_at(g, cs);
+            ri[s] = lin(g, cs[0], cs[1], cs[2]);
+        }
+        double prL[8], prR[8], BL[3], BR[3];
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+            const double* a = prim.p[v];
+            mc_face(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3]], prL[v], prR[v]);
+        }
+        // transverse cell-centred B (primitive = q_B / psi^6 at the cell)
+#pragma unroll
+        for (int tt = 0; tt < 2; tt++) {
+            const int e = tt == 0 ? T1 : T2;
+            double b[4];
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                int cs[3] = {c[0], c[1], c[2]};
+                cs[D] += s - 2;
+                const double ps = psi ? psi[ri[s]] : 1.0;
+                const double p2 = ps * ps;
+                b[s] = cell_qB(g, bf.p[e], e, cs) / (p2 * p2 * p2);
+            }
+            mc_face(b[0], b[1], b[2], b[3], BL[e], BR[e]);
+        }
+        const double psf = psi ? 0.5 * (psi[ri[1]] + psi[ri[2]]) : 1.0;
+        const double alf = alp ? 0.5 * (alp[ri[1]] + alp[ri[2]]) : 1.0;
+        const double pf2 = psf * psf;
+        const double bn = bf.p[D][face_at(g, D, c)] / (pf2 * pf2 * pf2);
+        BL[D] = bn;
+        BR[D] = bn;
+        FaceState sL, sR;
+        face_state(prL, BL, D, psf, alf, g.gh, sL);
+        face_state(prR, BR, D, psf, alf, g.gh, sR);
+        // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity)
+        const double cs = alf / pf2;
+        const long long o = lin(g, c[0], c[1], c[2]);
+#pragma unroll
+        for (int v = 0; v < 8; v++)
+            F.p[v][o] = (cs * sL.f[v] + cs * sR.f[v] - cs * cs * (sR.q[v] - sL.q[v])) / (cs + cs);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// upwind constrained transport: hat{E}_C on the edges along C, stored at the corner
+// index that is lower in a = C+1 and b = C+2
+// ---------------------------------------------------------------------------
+
+template <int C>
+__global__ void __launch_bounds__(128) k_emf(Dims g, CP8 prim, CP3 bf, const double* __restrict__ psi,
+                                             const double* __restrict__ alp, double* __restrict__ Eh)
+{
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    const bool aa = g.act[A], ba = g.act[B];
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) e[d] = (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    const long long tot = (long long)e[0] * e[1] * e[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = g.ng[0] + (int)(t % e[0]);
+        c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
+        c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+        // steps (ii)-(iii): covariant E_C = psi^4 E^C, to A-faces then along B
+        double s[2][4];   // [X = A-side L/R][B offset -2..+1]
+        const int nb = ba ? 4 : 1;
+        for (int ob = 0; ob < nb; ob++) {
+            int cb[3] = {c[0], c[1], c[2]};
+            if (ba) cb[B] += ob - 2;
+            if (aa) {
+                double v[4];
+#pragma unroll
+                for (int sa = 0; sa < 4; sa++) {
+                    int cs[3] = {cb[0], cb[1], cb[2]};
+                    cs[A] += sa - 2;
+                    const double ps = psi ? psi[lin(g, cs[0], cs[1], cs[2])] : 1.0;
+                    const double p2 = ps * ps;
+                    v[sa] = p2 * p2 * prim.p[5 + C][cell_at(g, cs)];
+                }
+                mc_face(v[0], v[1], v[2], v[3], s[0][ob], s[1][ob]);
+            } else {
+                const double ps = psi ? psi[lin(g, cb[0], cb[1], cb[2])] : 1.0;
+                const double p2 = ps * ps;
+                s[0][ob] = s[1][ob] = p2 * p2 * prim.p[5 + C][cell_at(g, cb)];
+            }
+        }
+        double EXY[2][2];
+#pragma unroll
+        for (int X = 0; X < 2; X++) {
+            if (ba) mc_face(s[X][0], s[X][1], s[X][2], s[X][3], EXY[X][0], EXY[X][1]);
+            else EXY[X][0] = EXY[X][1] = s[X][0];
+        }
+        // step (iv): q_B^B (B-faces) along A, q_B^A (A-faces) along B
+        double qBbL, qBbR, qBaL, qBaR;
+        if (aa) {
+            double v[4];
+#pragma unroll
+            for (int sa = 0; sa < 4; sa++) {
+                int cs[3] = {c[0], c[1], c[2]};
+                cs[A] += sa - 2;
+                v[sa] = bf.p[B][face_at(g, B, cs)];
+            }
+            mc_face(v[0], v[1], v[2], v[3], qBbL, qBbR);
+        } else {
+            qBbL = qBbR = bf.p[B][face_at(g, B, c)];
+        }
+        if (ba) {
+            double v[4];
+#pragma unroll
+            for (int sb = 0; sb < 4; sb++) {
+                int cs[3] = {c[0], c[1], c[2]};
+                cs[B] += sb - 2;
+                v[sb] = bf.p[A][face_at(g, A, cs)];
+            }
+            mc_face(v[0], v[1], v[2], v[3], qBaL, qBaR);
+        } else {
+            qBaL = qBaR = bf.p[A][face_at(g, A, c)];
+        }
+        // lapse at the edge (mean of the adjacent cells) and the face speeds
+        const long long i0 = lin(g, c[0], c[1], c[2]);
+        const long long sA = aa ? g.st[A] : 0, sB = ba ? g.st[B] : 0;
+        double ale = 1.0, ca = 1.0, cb = 1.0;
+        if (alp || psi) {
+            int nce = 1;
+            double sum = alp ? alp[i0] : 1.0;
+            if (aa) { sum += alp ? alp[i0 - sA] : 1.0; nce++; }
+            if (ba) {
+                sum += alp ? alp[i0 - sB] : 1.0; nce++;
+                if (aa) { sum += alp ? alp[i0 - sA - sB] : 1.0; nce++; }
+            }
+            ale = sum / nce;
+            if (aa) {
+                ca = 0.0;
+                for (int tt = 0; tt < (ba ? 2 : 1); tt++) {
+                    const long long cf = i0 - tt * sB, cfm = cf - sA;
+                    const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+                    const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+                    ca = fmax(ca, alf / (psf * psf));
+                }
+            }
+            if (ba) {
+                cb = 0.0;
+                for (int tt = 0; tt < (aa ? 2 : 1); tt++) {
+                    const long long cf = i0 - tt * sA, cfm = cf - sB;
+                    const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+                    const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+                    cb = fmax(cb, alf / (psf * psf));
+                }
+            }
+        }
+        // steps (v)-(vii): hat{E}^{XY} = alpha E_C^{XY}; Londrillo & Del Zanna (2004)
+        const double hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
+        Eh[i0] = (ca * cb * hLL + ca * cb * hLR + ca * cb * hRL + ca * cb * hRR) / ((ca + ca) * (cb + cb)) +
+                 ca * ca / (ca + ca) * (qBbR - qBbL) - cb * cb / (cb + cb) * (qBaR - qBaL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// update: cell-centred L (flux divergence + non-stiff sources) and face L_B (CT)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void out_value(const UpdateArgs& a, int v, long long o, double L, bool has_r)
+{
+    if (a.mode == UPD_WRITE_L) {
+        a.L[v][o] = L;
+        return;
+    }
+    const double r = has_r ? a.R[v - 5][o] : 0.0;
+    const double qn = a.qn[v][o];
+    for (int k = a.stage + 1; k < a.s; k++) {
+        const double prev = a.stage == 0 ? qn : a.base[k][v][o];
+        a.base[k][v][o] = prev + a.dt * (a.At[k][a.stage] * L + a.A[k][a.stage] * r);
+    }
+    const double prev = a.stage == 0 ? qn : a.acc[v][o];
+    const double nv = prev + a.dt * (a.wt[a.stage] * L + a.w[a.stage] * r);
+    if (a.stage == a.s - 1) a.qn[v][o] = nv;
+    else a.acc[v][o] = nv;
+}
+
+__global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
+{
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) e[d] = g.act[d] ? g.n[d] + 1 : 1;
+    const long long tot = (long long)e[0] * e[1] * e[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = g.ng[0] + (int)(t % e[0]);
+        c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
+        c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+        bool interior = true;
+#pragma unroll
+        for (int d = 0; d < 3; d++)
+            if (c[d] >= g.ng[d] + g.n[d]) interior = false;
+        const long long o = lin(g, c[0], c[1], c[2]);
+        if (interior) {
+            double Lc[8];
+#pragma unroll
+            for (int v = 0; v < 8; v++) Lc[v] = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (!g.act[d]) continue;
+                const long long o1 = o + g.st[d];
+#pragma unroll
+                for (int v = 0; v < 8; v++) Lc[v] -= (a.F[d][v][o1] - a.F[d][v][o]) * g.idx[d];
+            }
+            const double ps = a.psi ? a.psi[o] : 1.0;
+            const double al = a.alp ? a.alp[o] : 1.0;
+            const double p2 = ps * ps, p4 = p2 * p2, p6 = p4 * p2;
+            double u[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) u[i] = a.prim[1 + i][o];
+            const double W = sqrt(1.0 + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+            const double iW = 1.0 / W;
+            // Gauss law: sqrt(gamma) rho_e = div q_E by central differences
+            double divqE = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (!g.act[d]) continue;
+                int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+                cp[d] += 1;
+                cm[d] -= 1;
+                double sp = a.psi ? a.psi[o + g.st[d]] : 1.0, sm = a.psi ? a.psi[o - g.st[d]] : 1.0;
+                sp = sp * sp;
+                sm = sm * sm;
+                const double qp = sp * sp * sp * a.prim[5 + d][cell_at(g, cp)];
+                const double qm = sm * sm * sm * a.prim[5 + d][cell_at(g, cm)];
+                divqE += (qp - qm) * (0.5 * g.idx[d]);
+            }
+            // s_E (non-stiff part) = -alpha sqrt(gamma) rho_e v^i
+#pragma unroll
+            for (int i = 0; i < 3; i++) Lc[5 + i] -= al * divqE * (u[i] * iW);
+            if (a.psi || a.alp) {
+                // s_S and s_tau for beta = 0, K_ij = 0 (Sec. 2.1) in the orthonormal frame:
+                //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
+                //   s_tau = -psi^4 S_hat_i d_i alpha
+                const double rho = a.prim[0][o], p = a.prim[4][o];
+                double uh[3], Eh[3], Bh[3];
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    uh[i] = p2 * u[i];
+                    Eh[i] = p2 * a.prim[5 + i][o];
+                    Bh[i] = p2 * cell_qB(g, a.bf[i], i, c) / p6;
+                }
+                const double rhoh = rho + g.gh * p;
+                const double U = 0.5 * (Eh[0] * Eh[0] + Eh[1] * Eh[1] + Eh[2] * Eh[2] + Bh[0] * Bh[0] +
+                                        Bh[1] * Bh[1] + Bh[2] * Bh[2]);
+                const double D = rho * W;
+                const double tauD = rhoh * W * W - p + U;  // tau + D
+                double S[3];
+                S[0] = rhoh * W * uh[0] + (Eh[1] * Bh[2] - Eh[2] * Bh[1]);
+                S[1] = rhoh * W * uh[1] + (Eh[2] * Bh[0] - Eh[0] * Bh[2]);
+                S[2] = rhoh * W * uh[2] + (Eh[0] * Bh[1] - Eh[1] * Bh[0]);
+                const double tr = rhoh * (uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2]) + 3.0 * p + U;
+                (void)D;
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    if (!g.act[i]) continue;
+                    const double ap = a.alp ? a.alp[o + g.st[i]] : 1.0, am = a.alp ? a.alp[o - g.st[i]] : 1.0;
+                    const double pp = a.psi ? a.psi[o + g.st[i]] : 1.0, pm = a.psi ? a.psi[o - g.st[i]] : 1.0;
+                    const double dal = (ap - am) * (0.5 * g.idx[i]);
+                    const double dps = (pp - pm) * (0.5 * g.idx[i]);
+                    Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps / ps) * tr);
+                    Lc[4] -= p4 * S[i] * dal;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 8; v++) out_value(a, v, o, Lc[v], v >= 5);
+        }
+        // CT: d q_B^fa / dt = -d_fb hat{E}_fc + d_fc hat{E}_fb  (fa, fb, fc cyclic)
+#pragma unroll
+        for (int fa = 0; fa < 3; fa++) {
+            const int fb = (fa + 1) % 3, fc = (fa + 2) % 3;
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                int hi = g.ng[d] + g.n[d] - 1;
+                if (d == fa && g.act[d] && g.bc[d] != BC_PERIODIC) hi += 1;
+                if (c[d] > hi) ok = false;
+            }
+            if (!ok) continue;
+            double r = 0.0;
+            if (g.act[fb]) r -= (a.Eh[fc][o + g.st[fb]] - a.Eh[fc][o]) * g.idx[fb];
+            if (g.act[fc]) r += (a.Eh[fb][o + g.st[fc]] - a.Eh[fb][o]) * g.idx[fc];
+            out_value(a, 8 + fa, o, r, false);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// set-up: face q_B = curl of the edge potential (Sec. 4), prim -> cons (Sec. 2.1)
+// ---------------------------------------------------------------------------
+
+__global__ void k_curlA(Dims g, CP3 A, P3 bf)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = (int)(t % g.N[0]);
+        c[1] = (int)((t / g.N[0]) % g.N[1]);
+        c[2] = (int)(t / ((long long)g.N[0] * g.N[1]));
+#pragma unroll
+        for (int fa = 0; fa < 3; fa++) {
+            const int fb = (fa + 1) % 3, fc = (fa + 2) % 3;
+            if ((g.act[fb] && c[fb] + 1 >= g.N[fb]) || (g.act[fc] && c[fc] + 1 >= g.N[fc])) continue;
+            double r = 0.0;
+            if (g.act[fb]) r += (A.p[fc][t + g.st[fb]] - A.p[fc][t]) * g.idx[fb];
+            if (g.act[fc]) r -= (A.p[fb][t + g.st[fc]] - A.p[fb][t]) * g.idx[fc];
+            bf.p[fa][t] = r;
+        }
+    }
+}
+
+__global__ void k_prim2con(Dims g, CP8 prim, CP3 bf, const double* __restrict__ psi, P8 q)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = (int)(t % g.N[0]);
+        c[1] = (int)((t / g.N[0]) % g.N[1]);
+        c[2] = (int)(t / ((long long)g.N[0] * g.N[1]));
+        const double ps = psi ? psi[t] : 1.0;
+        const double p2 = ps * ps, p6 = p2 * p2 * p2;
+        double pr[8], B[3];
+#pragma unroll
+        for (int v = 0; v < 8; v++) pr[v] = prim.p[v][t];
+#pragma unroll
+        for (int e = 0; e < 3; e++) B[e] = cell_qB(g, bf.p[e], e, c) / p6;
+        FaceState s;
+        face_state(pr, B, 0, ps, 1.0, g.gh, s);
+#pragma unroll
+        for (int v = 0; v < 8; v++) q.p[v][t] = s.q[v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reductions (fixed-order block trees: deterministic for a given launch shape)
+// ---------------------------------------------------------------------------
+
+template <typename Op>
+__device__ __forceinline__ double block_reduce(double v, Op op, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (w == 0) {
+        v = l < nw ? sh[l] : 0.0;   // identity of sum, and of max over non-negative values
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+struct OpSum { __device__ double operator()(double a, double b) const { return a + b; } };
+struct OpMax { __device__ double operator()(double a, double b) const { return fmax(a, b); } };
+
+// per block: [max over cells of sum_d alpha sqrt(gamma^dd)/dx_d]
+__global__ void __launch_bounds__(256) k_dt(Dims g, const double* __restrict__ psi, const double* __restrict__ alp,
+                                            double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
+    double m = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = g.ng[0] + (int)(t % g.n[0]);
+        const int j = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
+        const int k = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long o = lin(g, i, j, k);
+        const double ps = psi ? psi[o] : 1.0;
+        const double sp = (alp ? alp[o] : 1.0) / (ps * ps);
+        m = fmax(m, sp * (g.idx[0] + g.idx[1] + g.idx[2]));
+    }
+    m = block_reduce(m, OpMax(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+// per block: [sum |div q_B|, sum div^2, max |div|, sum q_0..q_7 (times dV)]
+__global__ void __launch_bounds__(256) k_diag(Dims g, CP3 bf, CP8 q, double dV, double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
+    double s1 = 0.0, s2 = 0.0, mx = 0.0, tq[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) tq[v] = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = g.ng[0] + (int)(t % g.n[0]);
+        c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
+        c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long o = lin(g, c[0], c[1], c[2]);
+        double dv = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!g.act[d]) continue;
+            int cu[3] = {c[0], c[1], c[2]};
+            cu[d] += 1;
+            dv += (bf.p[d][face_at(g, d, cu)] - bf.p[d][o]) * g.idx[d];
+        }
+        s1 += fabs(dv);
+        s2 += dv * dv;
+        mx = fmax(mx, fabs(dv));
+#pragma unroll
+        for (int v = 0; v < 8; v++) tq[v] += q.p[v][o] * dV;
+    }
+    double r = block_reduce(s1, OpSum(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 11 + 0] = r;
+    r = block_reduce(s2, OpSum(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 11 + 1] = r;
+    r = block_reduce(mx, OpMax(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 11 + 2] = r;
+#pragma unroll
+    for (int v = 0; v < 8; v++) {
+        r = block_reduce(tq[v], OpSum(), sh);
+        if (threadIdx.x == 0) part[blockIdx.x * 11 + 3 + v] = r;
+    }
+}
+
+// second pass: one block folds `nb` partial rows of width `w`; column kinds: 0 sum, 1 max
+__global__ void __launch_bounds__(256) k_fold(const double* __restrict__ part, int nb, int w,
+                                              const int* __restrict__ kinds_unused, unsigned kinds_mask,
+                                              double* __restrict__ out)
+{
+    __shared__ double sh[32];
+    (void)kinds_unused;
+    for (int col = 0; col < w; col++) {
+        const bool is_max = (kinds_mask >> col) & 1u;
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+            const double x = part[(long long)b * w + col];
+            v = is_max ? fmax(v, x) : v + x;
+        }
+        v = is_max ? block_reduce(v, OpMax(), sh) : block_reduce(v, OpSum(), sh);
+        if (threadIdx.x == 0) out[col] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static int grid_for(long long work, int threads, int nsm)
+{
+    long long b = (work + threads - 1) / threads;
+    const long long cap = (long long)nsm * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cudaError_t launch_implicit(const Dims& g, CP8 qb, CP3 bf, const double* psi, const double* alp, const double* eta,
+                            double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax, double tol,
+                            double rho_atm, double p_atm, unsigned long long* nfail, int nsm, cudaStream_t st)
+{
+    const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
+    k_implicit<<<grid_for(work, 128, nsm), 128, 0, st>>>(g, qb, bf, psi, alp, eta, eta_u, a_dt, prim, R, qE_out,
+                                                         kmax, tol, rho_atm, p_atm, nfail);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
+                        cudaStream_t st)
+{
+    const long long work = (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
+    const int b = grid_for(work, 128, nsm);
+    if (d == 0) k_flux<0><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+    else if (d == 1) k_flux<1><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+    else k_flux<2><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
+                       int nsm, cudaStream_t st)
+{
+    long long work = 1;
+    for (int d = 0; d < 3; d++) work *= (d == c) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    const int b = grid_for(work, 128, nsm);
+    if (c == 0) k_emf<0><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+    else if (c == 1) k_emf<1><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+    else k_emf<2><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStream_t st)
+{
+    long long work = 1;
+    for (int d = 0; d < 3; d++) work *= g.act[d] ? g.n[d] + 1 : 1;
+    k_update<<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_curlA(const Dims& g, CP3 A, P3 bf, int nsm, cudaStream_t st)
+{
+    k_curlA<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, A, bf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prim2con(const Dims& g, CP8 prim, CP3 bf, const double* psi, P8 q, int nsm, cudaStream_t st)
+{
+    k_prim2con<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, prim, bf, psi, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const Dims& g, const double* psi, const double* alp, double* part, int nblk, double* out,
+                      cudaStream_t st)
+{
+    k_dt<<<nblk, 256, 0, st>>>(g, psi, alp, part);
+    k_fold<<<1, 256, 0, st>>>(part, nblk, 1, nullptr, 1u, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const Dims& g, CP3 bf, CP8 q, double dV, double* part, int nblk, double* out,
+                        cudaStream_t st)
+{
+    k_diag<<<nblk, 256, 0, st>>>(g, bf, q, dV, part);
+    k_fold<<<1, 256, 0, st>>>(part, nblk, 11, nullptr, 1u << 2, out);
+    return cudaGetLastError();
+}
+
+}  // namespace grmhd

@@ -1,0 +1,47 @@
+// Launch interface between the C-ABI layer (capi.cu) and the kernels (kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "grmhd_device.cuh"
+
+namespace grmhd {
+
+enum { UPD_WRITE_L = 0, UPD_STAGE = 1 };
+
+// Arguments of the update kernel.  Variables 0..7 are cell-centred (D, S_1..3, tau,
+// E^1..3), 8..10 are the face fields.
+struct UpdateArgs {
+    int mode;               // UPD_WRITE_L: L -> L[]; UPD_STAGE: fold into base/acc/qn
+    int stage, s;
+    double dt;
+    double At[4][4], A[4][4], wt[4], w[4];
+    const double* F[3][8];  // face fluxes per active direction
+    const double* Eh[3];    // edge EMFs
+    const double* prim[8];  // stage primitives (padded)
+    const double* bf[3];    // stage face fields
+    const double* psi;
+    const double* alp;
+    const double* R[3];     // stiff rates of this stage (E components)
+    double* L[11];
+    double* qn[11];         // bound state: read at stage 0, written by the last stage
+    double* base[4][11];    // bases of later stages (index k >= 1)
+    double* acc[11];        // running final combination
+};
+
+cudaError_t launch_implicit(const Dims& g, CP8 qb, CP3 bf, const double* psi, const double* alp, const double* eta,
+                            double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax, double tol,
+                            double rho_atm, double p_atm, unsigned long long* nfail, int nsm, cudaStream_t st);
+cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
+                        cudaStream_t st);
+cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
+                       int nsm, cudaStream_t st);
+cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStream_t st);
+cudaError_t launch_curlA(const Dims& g, CP3 A, P3 bf, int nsm, cudaStream_t st);
+cudaError_t launch_prim2con(const Dims& g, CP8 prim, CP3 bf, const double* psi, P8 q, int nsm, cudaStream_t st);
+cudaError_t launch_dt(const Dims& g, const double* psi, const double* alp, double* part, int nblk, double* out,
+                      cudaStream_t st);
+cudaError_t launch_diag(const Dims& g, CP3 bf, CP8 q, double dV, double* part, int nblk, double* out,
+                        cudaStream_t st);
+
+}  // namespace grmhd

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of ``libgrmhd.so`` (the C ABI in ``include/grmhd.h``).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  Importing this module fails
+loudly when the library has not been built (``paper_2110_03732_gb300.build``); there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+GRMHD_OK = 0
+GRMHD_WARN_C2P_FAILED = 1
+BC = {"periodic": 0, "outflow": 1, "fixed": 2}
+
+
+class GrmhdError(RuntimeError):
+    pass
+
+
+class Grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("bc", C.c_int * 3)]
+
+
+class Tableau(C.Structure):
+    _fields_ = [("s", C.c_int), ("At", C.c_double * 16), ("A", C.c_double * 16), ("wt", C.c_double * 4),
+                ("w", C.c_double * 4)]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma_eos", C.c_double), ("cfl", C.c_double), ("newton_tol", C.c_double),
+                ("newton_kmax", C.c_int), ("reserved", C.c_int), ("rho_atm", C.c_double), ("p_atm", C.c_double)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load ``libgrmhd.so``; raises if it is missing (build it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise GrmhdError(f"{path} is missing: run paper_2110_03732_gb300.build.build() (nvcc, sm_103a)")
+    L = C.CDLL(path)
+    vp = C.c_void_p
+    dpp = C.POINTER(C.c_void_p)
+    L.grmhd_tableau_ssp2.argtypes = [C.POINTER(Tableau)]
+    L.grmhd_scratch_bytes.argtypes = [C.POINTER(Grid), C.POINTER(Tableau), C.POINTER(C.c_size_t)]
+    L.grmhd_create.argtypes = [C.POINTER(Grid), C.POINTER(Params), C.POINTER(Tableau), C.POINTER(vp)]
+    L.grmhd_destroy.argtypes = [vp]
+    L.grmhd_bind.argtypes = [vp, dpp, dpp, vp, C.c_size_t]
+    L.grmhd_set_metric.argtypes = [vp, vp, vp]
+    L.grmhd_set_eta.argtypes = [vp, vp, C.c_double]
+    L.grmhd_init_from_prims.argtypes = [vp, dpp, dpp, vp]
+    L.grmhd_compute_dt.argtypes = [vp, C.POINTER(C.c_double), vp]
+    L.grmhd_stage.argtypes = [vp, C.c_int, C.c_double, vp]
+    L.grmhd_step.argtypes = [vp, C.c_double, vp]
+    L.grmhd_get_prims.argtypes = [vp, dpp, vp]
+    L.grmhd_implicit.argtypes = [vp, C.c_double, dpp, dpp, dpp, dpp, vp]
+    L.grmhd_explicit_L.argtypes = [vp, dpp, dpp, dpp, vp]
+    L.grmhd_diagnostics.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp]
+    L.grmhd_set_timing.argtypes = [vp, C.c_int]
+    L.grmhd_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.grmhd_launch_count.argtypes = [vp]
+    L.grmhd_launch_count.restype = C.c_longlong
+    L.grmhd_last_error.restype = C.c_char_p
+    for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
+                 "grmhd_set_metric", "grmhd_set_eta", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
+                 "grmhd_step", "grmhd_get_prims", "grmhd_implicit", "grmhd_explicit_L", "grmhd_diagnostics",
+                 "grmhd_set_timing", "grmhd_kernel_times"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def check(status, what=""):
+    if status < 0:
+        msg = lib().grmhd_last_error().decode()
+        raise GrmhdError(f"{what}: status {status}: {msg}")
+    return status
+
+
+def _ptrs(tensors):
+    arr = (C.c_void_p * len(tensors))(*[None if t is None else t.data_ptr() for t in tensors])
+    return C.cast(arr, C.POINTER(C.c_void_p)), arr
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_grid(ndim, n, lo, hi, bc):
+    g = Grid()
+    g.ndim = ndim
+    for d in range(3):
+        g.n[d] = int(n[d]) if d < ndim else 1
+        g.lo[d] = float(lo[d])
+        g.hi[d] = float(hi[d])
+        b = bc[d]
+        g.bc[d] = BC[b] if isinstance(b, str) else int(b)
+    return g
+
+
+def ssp2():
+    t = Tableau()
+    check(lib().grmhd_tableau_ssp2(C.byref(t)), "tableau")
+    return t
+
+
+def scratch_bytes(grid, tab):
+    n = C.c_size_t(0)
+    check(lib().grmhd_scratch_bytes(C.byref(grid), C.byref(tab), C.byref(n)), "scratch_bytes")
+    return n.value
+
+
+class Solver:
+    """One resistive-MHD problem resident on the GPU: state, scratch and context.
+
+    ``q`` (8 tensors) and ``bf`` (3 tensors) are the padded, densitised conserved
+    cell and face fields; the library updates them in place."""
+
+    def __init__(self, ndim, n, lo, hi, bc, gamma, cfl=0.4, tableau=None, device="cuda", newton_tol=0.0,
+                 newton_kmax=0, rho_atm=0.0, p_atm=0.0):
+        self.L = lib()
+        self.grid = make_grid(ndim, n, lo, hi, bc)
+        self.tab = ssp2() if tableau is None else tableau
+        self.par = Params(float(gamma), float(cfl), float(newton_tol), int(newton_kmax), 0, float(rho_atm),
+                          float(p_atm))
+        self.device = torch.device(device)
+        ng = [2 if d < ndim else 0 for d in range(3)]
+        self.N = [self.grid.n[d] + 2 * ng[d] for d in range(3)]
+        self.shape = (self.N[2], self.N[1], self.N[0])
+        self.ndim = ndim
+        self.ng = ng
+        self.cells = self.grid.n[0] * self.grid.n[1] * self.grid.n[2]
+        opts = dict(dtype=torch.float64, device=self.device)
+        self.q = [torch.zeros(self.shape, **opts) for _ in range(8)]
+        self.bf = [torch.zeros(self.shape, **opts) for _ in range(3)]
+        nbytes = scratch_bytes(self.grid, self.tab)
+        # torch's caching allocator returns 512-byte aligned blocks
+        self.scratch = torch.zeros(nbytes, dtype=torch.uint8, device=self.device)
+        ctx = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.L.grmhd_create(C.byref(self.grid), C.byref(self.par), C.byref(self.tab), C.byref(ctx)),
+                  "create")
+        self.ctx = ctx
+        pq, self._kq = _ptrs(self.q)
+        pb, self._kb = _ptrs(self.bf)
+        check(self.L.grmhd_bind(ctx, pq, pb, C.c_void_p(self.scratch.data_ptr()), nbytes), "bind")
+        self.alpha = self.psi = self.eta = None
+        self.eta_u = 0.0
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.L.grmhd_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    # -- configuration -------------------------------------------------------
+    def set_metric(self, alpha=None, psi=None):
+        self.alpha = None if alpha is None else self._dev(alpha)
+        self.psi = None if psi is None else self._dev(psi)
+        check(self.L.grmhd_set_metric(self.ctx, self._vp(self.alpha), self._vp(self.psi)), "set_metric")
+
+    def set_eta(self, eta=None, eta_u=0.0):
+        self.eta = None if eta is None else self._dev(eta)
+        self.eta_u = float(eta_u)
+        check(self.L.grmhd_set_eta(self.ctx, self._vp(self.eta), self.eta_u), "set_eta")
+
+    def init_from_prims(self, prim, A_edge=None, bface=None, stream=None):
+        prim = [self._dev(p) for p in prim]
+        if bface is not None:
+            for d in range(3):
+                self.bf[d].copy_(self._dev(bface[d]))
+        A = None if A_edge is None else [self._dev(a) for a in A_edge]
+        pp, k1 = _ptrs(prim)
+        pa, k2 = _ptrs(A) if A is not None else (None, None)
+        check(self.L.grmhd_init_from_prims(self.ctx, pp, pa, _stream(stream)), "init_from_prims")
+        self._keep = (prim, A)
+
+    @classmethod
+    def from_problem(cls, prob, device="cuda", **kw):
+        kw.setdefault("rho_atm", prob.rho_atm)
+        kw.setdefault("p_atm", prob.p_atm)
+        s = cls(prob.ndim, prob.n, prob.lo, prob.hi, prob.bc, prob.gamma, prob.cfl, device=device, **kw)
+        s.set_metric(prob.alpha, prob.psi)
+        s.set_eta(prob.eta, prob.eta_u if prob.eta is None else (prob.eta_u or 1.0))
+        s.init_from_prims(prob.prim, A_edge=prob.A_edge, bface=None if prob.A_edge is not None else prob.bface)
+        return s
+
+    # -- stepping ------------------------------------------------------------
+    def compute_dt(self, stream=None):
+        dt = C.c_double(0.0)
+        check(self.L.grmhd_compute_dt(self.ctx, C.byref(dt), _stream(stream)), "compute_dt")
+        return dt.value
+
+    def stage(self, i, dt, stream=None):
+        return check(self.L.grmhd_stage(self.ctx, int(i), float(dt), _stream(stream)), "stage")
+
+    def step(self, dt, stream=None):
+        return check(self.L.grmhd_step(self.ctx, float(dt), _stream(stream)), "step")
+
+    def get_prims(self, stream=None):
+        out = [torch.zeros(self.shape, dtype=torch.float64, device=self.device) for _ in range(8)]
+        po, k = _ptrs(out)
+        check(self.L.grmhd_get_prims(self.ctx, po, _stream(stream)), "get_prims")
+        return out
+
+    def implicit(self, a_dt, q, bface, prim, stream=None):
+        """Implicit solve on caller tensors (q is modified; prim in/out). Returns R."""
+        R = [torch.zeros(self.shape, dtype=torch.float64, device=self.device) for _ in range(3)]
+        pq, k1 = _ptrs(q)
+        pb, k2 = _ptrs(bface)
+        pp, k3 = _ptrs(prim)
+        pr, k4 = _ptrs(R)
+        check(self.L.grmhd_implicit(self.ctx, float(a_dt), pq, pb, pp, pr, _stream(stream)), "implicit")
+        return R
+
+    def explicit_L(self, prim, bface, stream=None):
+        Lt = [torch.zeros(self.shape, dtype=torch.float64, device=self.device) for _ in range(11)]
+        pp, k1 = _ptrs(prim)
+        pb, k2 = _ptrs(bface)
+        pl, k3 = _ptrs(Lt)
+        check(self.L.grmhd_explicit_L(self.ctx, pp, pb, pl, _stream(stream)), "explicit_L")
+        return Lt
+
+    def diagnostics(self, stream=None):
+        divb = (C.c_double * 3)()
+        tot = (C.c_double * 8)()
+        nf = C.c_longlong(0)
+        check(self.L.grmhd_diagnostics(self.ctx, divb, tot, C.byref(nf), _stream(stream)), "diagnostics")
+        return list(divb), list(tot), nf.value
+
+    def launch_count(self):
+        return int(self.L.grmhd_launch_count(self.ctx))
+
+    KERNEL_KINDS = ("implicit", "flux", "emf", "update")
+
+    def set_timing(self, on=True):
+        check(self.L.grmhd_set_timing(self.ctx, int(on)), "set_timing")
+
+    def kernel_times(self):
+        """Cumulative (ms, launches) per kernel kind since timing was enabled."""
+        ms = (C.c_double * 4)()
+        n = (C.c_longlong * 4)()
+        check(self.L.grmhd_kernel_times(self.ctx, ms, n), "kernel_times")
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
+
+    # -- helpers -------------------------------------------------------------
+    def _dev(self, a):
+        if isinstance(a, torch.Tensor):
+            t = a.to(device=self.device, dtype=torch.float64)
+        else:
+            t = torch.as_tensor(a, dtype=torch.float64).to(self.device)
+        return t.contiguous()
+
+    @staticmethod
+    def _vp(t):
+        return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(None)
+
+    def interior(self):
+        return tuple(slice(self.ng[d], self.ng[d] + self.grid.n[d]) for d in (2, 1, 0))

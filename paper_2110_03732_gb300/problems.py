@@ -57,6 +57,8 @@ class Problem:
     eta: np.ndarray = None   # per-cell resistivity, or None (then eta_u)
     eta_u: float = 0.0
     cfl: float = 0.4
+    rho_atm: float = 0.0     # atmosphere floor density (0: no atmosphere treatment)
+    p_atm: float = 0.0
     t_end: float = 0.0
     steps: int = 0
     info: dict = field(default_factory=dict)
@@ -201,7 +203,7 @@ def star(n=256, L=20.0, K=100.0, gamma=2.0, rho_c=1.28e-3, M=1.4, atm_frac=1e-10
     A = [Ax, Ay, z.copy()]
     eta = np.where(r < R, eta_in, eta_out)
     return Problem("star_3d", ndim, nn, lo, hi, ["outflow"] * 3, gamma, prim, A_edge=A, alpha=alpha,
-                   psi=psi, eta=eta, eta_u=eta_in, cfl=0.4, steps=500,
+                   psi=psi, eta=eta, eta_u=eta_in, cfl=0.4, steps=500, rho_atm=rho_atm, p_atm=K * rho_atm ** gamma,
                    info={"R": R, "rho_atm": rho_atm, "p_c": p_c})
 
 

@@ -1,0 +1,129 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a,
+exports every function that include/grmhd.h declares, and rejects invalid grids,
+tableaux and parameters before touching the device."""
+import ctypes as C
+import math
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "grmhd.h")
+
+pytestmark = pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                                reason="nvcc not available")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2110_03732_gb300 import build
+    path = build.build()
+    return C.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(grmhd_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_no_device_allocation_symbols_in_sources():
+    """The library allocates no device memory: the caller passes all buffers."""
+    csrc = os.path.join(ROOT, "paper_2110_03732_gb300", "csrc")
+    for f in os.listdir(csrc):
+        s = open(os.path.join(csrc, f)).read()
+        assert "cudaMalloc" not in s and "cudaFree" not in s, f
+
+
+def _grid(ndim=2, n=(8, 8, 1), bc=(0, 0, 0), lo=(0, 0, 0), hi=(1, 1, 1)):
+    from paper_2110_03732_gb300.grmhd import Grid
+    g = Grid()
+    g.ndim = ndim
+    for d in range(3):
+        g.n[d] = n[d]
+        g.lo[d] = lo[d]
+        g.hi[d] = hi[d]
+        g.bc[d] = bc[d]
+    return g
+
+
+def test_ssp2_tableau_values(lib):
+    from paper_2110_03732_gb300.grmhd import Tableau
+    t = Tableau()
+    assert lib.grmhd_tableau_ssp2(C.byref(t)) == 0
+    g = 1 - 1 / math.sqrt(2)
+    assert t.s == 2
+    assert list(t.At[:4]) == [0, 0, 1, 0]
+    assert abs(t.A[0] - g) < 1e-16 and abs(t.A[2] - (1 - 2 * g)) < 1e-16 and abs(t.A[3] - g) < 1e-16
+    assert list(t.wt[:2]) == [0.5, 0.5] and list(t.w[:2]) == [0.5, 0.5]
+
+
+def test_scratch_bytes_formula(lib):
+    from paper_2110_03732_gb300.grmhd import Tableau
+    t = Tableau()
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    for ndim, n in ((1, (400, 1, 1)), (2, (512, 512, 1)), (3, (20, 12, 9))):
+        g = _grid(ndim, n)
+        b = C.c_size_t()
+        assert lib.grmhd_scratch_bytes(C.byref(g), C.byref(t), C.byref(b)) == 0
+        ncell = 1
+        for d in range(3):
+            ncell *= n[d] + 4 if d < ndim else 1
+        arr = -(-8 * ncell // 256) * 256
+        narr = 8 + 3 + 11 * (t.s - 1) + 11 + 8 * ndim + 3
+        small = -(-8 * 1024 * 11 // 256) * 256 + 256 + 256
+        assert b.value == narr * arr + small
+
+
+@pytest.mark.parametrize("field,value", [("ndim", 0), ("ndim", 4), ("n", 0), ("hi", -1.0), ("bc", 7),
+                                         ("periodic1", 1)])
+def test_invalid_grid_rejected(lib, field, value):
+    from paper_2110_03732_gb300.grmhd import Tableau
+    t = Tableau()
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    g = _grid()
+    if field == "ndim":
+        g.ndim = value
+    elif field == "n":
+        g.n[1] = value
+    elif field == "hi":
+        g.hi[0] = value
+    elif field == "bc":
+        g.bc[0] = value
+    elif field == "periodic1":
+        g.n[0] = 1
+    b = C.c_size_t()
+    assert lib.grmhd_scratch_bytes(C.byref(g), C.byref(t), C.byref(b)) == -1
+    lib.grmhd_last_error.restype = C.c_char_p
+    assert len(lib.grmhd_last_error()) > 0
+
+
+def test_invalid_tableau_and_params_rejected(lib):
+    from paper_2110_03732_gb300.grmhd import Params, Tableau
+    g = _grid()
+    b = C.c_size_t()
+    t = Tableau()
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    t.A[3] = 0.0  # a_22 = 0: not diagonally implicit
+    assert lib.grmhd_scratch_bytes(C.byref(g), C.byref(t), C.byref(b)) == -1
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    t.At[1] = 0.3  # explicit part not strictly lower
+    assert lib.grmhd_scratch_bytes(C.byref(g), C.byref(t), C.byref(b)) == -1
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    t.s = 5
+    assert lib.grmhd_scratch_bytes(C.byref(g), C.byref(t), C.byref(b)) == -1
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    p = Params(1.0, 0.4, 0.0, 0, 0, 0.0, 0.0)   # Gamma must exceed 1
+    ctx = C.c_void_p()
+    assert lib.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
+    assert not ctx.value
