@@ -295,10 +295,13 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
-# FP64 flops per zone-stage executed by each kernel kind, counted by ncu on the
-# 512^2 workload (2 * DFMA + DADD + DMUL instructions per launch / cells); see
-# profiles/.  None until counted.
-FP64_FLOPS_PER_CELL = {"implicit": None, "flux": None, "emf": None, "update": None}
+# FP64 flops per cell per launch of each kernel kind (2 * DFMA + DADD + DMUL thread
+# instructions / cells), counted by ncu on the 512^2 workload for the kernels as they
+# stand (profiles/ot512_fp64_kernels.md).  The flux and EMF figures are per launch
+# (one direction / one component; the EMF value is the mean of its three launches).
+# TRAFFIC: dram read + write bytes per launch from the same capture.
+FP64_FLOPS_PER_CELL = {"implicit": 1289.2, "flux": 703.4, "emf": 164.5, "update": 179.0}
+TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 23.4e6, "emf": 6.4e6, "update": 109.8e6}
 
 
 def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):
@@ -309,8 +312,8 @@ def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):
                 "note": "FP64 flop count per cell not yet measured"}
     ach = fl * cells / (k_avg_ms / 1e3) / 1e12
     return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "avg_launch_ms": k_avg_ms,
-            "peak_source": "nominal FP64 (profiling recipe)"}
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(kname), "avg_launch_ms": k_avg_ms,
+            "flops_per_cell": fl, "peak_source": "nominal FP64 of the profiling recipe (probe: 1.19-1.20)"}
 
 
 def main():
