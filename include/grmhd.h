@@ -175,6 +175,29 @@ grmhd_status grmhd_kernel_times(grmhd_ctx* ctx, double* ms, long long* launches)
 /* Message of the last error on the calling thread ("" if none). */
 const char* grmhd_last_error(void);
 
+/* div B norms of caller-owned face fields without allocating anything.  The paper
+ * has no counterpart to this call: it exists for callers that cannot allocate
+ * device memory where they want the check (for example a host whose device memory
+ * is all owned by its own pool or arena, or a loop that must not allocate after
+ * start-up) and so cannot provide the scratch that grmhd_bind needs.
+ *
+ * grid: as for grmhd_create; bface: 3 padded face arrays (device, q_B^x, q_B^y,
+ * q_B^z, read-only); out: 3 device doubles written with {mean |div q_B|, rms,
+ * max |div q_B|} over interior cells, the same quantities as grmhd_diagnostics.
+ * Runs on `stream`; does not synchronise.
+ *
+ * Scratch: a fixed array inside the library (8192 rows x 3 doubles = 192 KiB) that
+ * every GPU loading the library holds until the process exits; grids with more than
+ * 8192 * 256 = 2,097,152 interior cells are rejected with GRMHD_ERR_ARG.  Each call
+ * rewrites every row it reads, so nothing needs clearing between calls, but all
+ * calls share the array: calls that overlap on the GPU (on different streams, or
+ * from different threads) race and must be ordered by the caller.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  It calls no
+ * allocation routine. */
+grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double* const* bface, double* out,
+                                grmhd_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,6 +34,11 @@ size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 }  // namespace
 
+namespace grmhd {
+// lets other translation units of the library report through grmhd_last_error
+void set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace grmhd
+
 struct grmhd_ctx_s {
     Dims g;
     grmhd_grid grid;
