@@ -257,6 +257,28 @@ def run_native(args):
     e2e_value = ws * cells * STAGES / (float(np.mean(e2e_ms)) / 1e3)
 
     divb, tot, nfail = S.diagnostics()
+
+    # mixed precision (FP32 reconstruction, HLL and edge EMF; FP64 implicit solve,
+    # sources and CT): same workload, same timing rules
+    Sm = grmhd.Solver.from_problem(pr, device=dev, precision="mixed")
+    for _ in range(max(args.warmup, 3)):
+        Sm.step(dt)
+    torch.cuda.synchronize()
+    mixed_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        Sm.step(dt)
+        e1.record(stream)
+        e1.synchronize()
+        mixed_ms.append(e0.elapsed_time(e1))
+    mixed_total = sum(mixed_ms) / 1e3
+    if ws > 1:
+        t = torch.tensor([mixed_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        mixed_total = float(t.item())
+    mixed_value = ws * cells * STAGES * args.steps / mixed_total
+    del Sm
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -285,6 +307,10 @@ def run_native(args):
         "gpu_launches": launches,
         "clocks": clk,
         "divb_max": divb[2], "newton_failures": nfail,
+        "mixed": {"value": mixed_value, "unit": UNIT, "ms_per_step": 1e3 * mixed_total / args.steps,
+                  "p50_ms_per_step": float(np.percentile(mixed_ms, 50)),
+                  "p99_ms_per_step": float(np.percentile(mixed_ms, 99)),
+                  "dtype": "f32 reconstruction/HLL/edge EMF, f64 implicit solve/sources/CT/stage combination"},
     }
     if not args.no_cpu_baseline:
         rate, el = cpu_oracle_rate(256, 2)
@@ -300,8 +326,8 @@ def run_native(args):
 # stand (profiles/ot512_fp64_kernels.md).  The flux and EMF figures are per launch
 # (one direction / one component; the EMF value is the mean of its three launches).
 # TRAFFIC: dram read + write bytes per launch from the same capture.
-FP64_FLOPS_PER_CELL = {"implicit": 1289.2, "flux": 703.4, "emf": 164.5, "update": 179.0}
-TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 23.4e6, "emf": 6.4e6, "update": 109.8e6}
+FP64_FLOPS_PER_CELL = {"implicit": 755.8, "flux": 355.7, "emf": 70.9, "update": 158.0}
+TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 23.3e6, "emf": 6.4e6, "update": 109.3e6}
 
 
 def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):

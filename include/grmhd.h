@@ -55,6 +55,7 @@ typedef enum {
 } grmhd_status;
 
 enum { GRMHD_BC_PERIODIC = 0, GRMHD_BC_OUTFLOW = 1, GRMHD_BC_FIXED = 2 };
+enum { GRMHD_PREC_FP64 = 0, GRMHD_PREC_MIXED = 1 };
 
 /* Uniform Cartesian grid (Sec. 5 test set-ups).  bc: per direction; FIXED keeps the
  * ghost values that init wrote (Sec. 5, "values at the outer boundaries are kept
@@ -83,7 +84,11 @@ typedef struct {
     double newton_tol; /* Newton residual tolerance, relative to the momentum terms of
                           f_i (Sec. 2.4); 0 -> 1e-13 */
     int newton_kmax;   /* Newton iteration cap; 0 -> 50 */
-    int reserved;
+    int precision;     /* GRMHD_PREC_FP64: every step in FP64.  GRMHD_PREC_MIXED: MC
+                          reconstruction, HLL fluxes and the edge EMF in FP32; the
+                          implicit solve / con2prim, sources, CT face update and stage
+                          combination stay FP64 (div B stays at FP64 round-off because
+                          each FP32 edge EMF is shared by the faces around it) */
     double rho_atm;    /* atmosphere (not in the paper): a cell with D < 10 rho_atm, or
                           whose solve fails, is set to rest at (rho_atm, p_atm) with E
                           kept; 0 disables it (failures then keep their primitives) */

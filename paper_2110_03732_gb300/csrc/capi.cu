@@ -55,6 +55,10 @@ struct grmhd_ctx_s {
     double* acc[11];
     double* F[3][8];
     double* Eh[3];
+    float* p32[11];      // mixed precision: FP32 stage primitives + cell-centred q_B
+    float* F32[3][8];    // mixed precision: FP32 face fluxes
+    float* Eh32[3];      // mixed precision: FP32 edge EMFs
+    bool mixed;
     double* red_part;
     double* red_out;
     unsigned long long* nfail;
@@ -141,6 +145,11 @@ size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base)
     for (int d = 0; d < ndim; d++)
         for (int v = 0; v < 8; v++) { char* p = take(arr); if (c) c->F[d][v] = (double*)p; }
     for (int v = 0; v < 3; v++) { char* p = take(arr); if (c) c->Eh[v] = (double*)p; }
+    const size_t arr32 = round_up(sizeof(float) * (size_t)g.ncell);
+    for (int v = 0; v < 11; v++) { char* p = take(arr32); if (c) c->p32[v] = (float*)p; }
+    for (int d = 0; d < ndim; d++)
+        for (int v = 0; v < 8; v++) { char* p = take(arr32); if (c) c->F32[d][v] = (float*)p; }
+    for (int v = 0; v < 3; v++) { char* p = take(arr32); if (c) c->Eh32[v] = (float*)p; }
     { char* p = take(sizeof(double) * kRedBlocks * 11); if (c) c->red_part = (double*)p; }
     { char* p = take(sizeof(double) * 16); if (c) c->red_out = (double*)p; }
     { char* p = take(sizeof(unsigned long long)); if (c) c->nfail = (unsigned long long*)p; }
@@ -186,6 +195,13 @@ P3 p3(double* const* p)
 
 bool emf_needed(const Dims& g, int c) { return g.act[(c + 1) % 3] || g.act[(c + 2) % 3]; }
 
+F11 f11(grmhd_ctx* c)
+{
+    F11 r;
+    for (int v = 0; v < 11; v++) r.p[v] = c->mixed ? c->p32[v] : nullptr;
+    return r;
+}
+
 // kernel kinds for the timing hooks
 enum { KIND_IMPLICIT = 0, KIND_FLUX = 1, KIND_EMF = 2, KIND_UPDATE = 3 };
 
@@ -208,10 +224,20 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
 {
     const Dims& g = c->g;
     cudaError_t e;
+    // mixed precision: reconstruction, HLL and the edge EMF in FP32 from the stage's
+    // FP32 primitives; the update (sources, CT, stage folds) stays FP64
+    PrimIn<float> p32;
+    for (int v = 0; v < 11; v++) p32.p[v] = c->p32[v];
     for (int d = 0; d < 3; d++) {
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
-        e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st);
+        if (c->mixed) {
+            FluxOut<float> fo;
+            for (int v = 0; v < 8; v++) fo.p[v] = c->F32[d][v];
+            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st);
+        } else {
+            e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st);
+        }
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "flux kernel");
@@ -219,14 +245,17 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     for (int k = 0; k < 3; k++) {
         if (!emf_needed(g, k)) continue;
         const int tk = tbegin(c, KIND_EMF, st);
-        e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st);
+        if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh32[k], c->nsm, st);
+        else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st);
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "emf kernel");
     }
+    a.f32 = c->mixed ? 1 : 0;
     for (int d = 0; d < 3; d++)
-        for (int v = 0; v < 8; v++) a.F[d][v] = g.act[d] ? c->F[d][v] : nullptr;
-    for (int k = 0; k < 3; k++) a.Eh[k] = c->Eh[k];
+        for (int v = 0; v < 8; v++)
+            a.F[d][v] = !g.act[d] ? nullptr : c->mixed ? (const void*)c->F32[d][v] : (const void*)c->F[d][v];
+    for (int k = 0; k < 3; k++) a.Eh[k] = c->mixed ? (const void*)c->Eh32[k] : (const void*)c->Eh[k];
     for (int v = 0; v < 8; v++) a.prim[v] = prim.p[v];
     for (int k = 0; k < 3; k++) a.bf[k] = bfs.p[k];
     a.psi = c->psi;
@@ -286,6 +315,8 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
     if (!par || !out) return fail(GRMHD_ERR_ARG, "params/out is NULL");
     if (!(par->gamma_eos > 1.0)) return fail(GRMHD_ERR_ARG, "gamma_eos must exceed 1");
     if (par->rho_atm < 0.0 || par->p_atm < 0.0) return fail(GRMHD_ERR_ARG, "atmosphere floor must be >= 0");
+    if (par->precision != GRMHD_PREC_FP64 && par->precision != GRMHD_PREC_MIXED)
+        return fail(GRMHD_ERR_ARG, "precision must be GRMHD_PREC_FP64 or GRMHD_PREC_MIXED");
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -306,6 +337,7 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
         if (grid->bc[d] == GRMHD_BC_FIXED) c->any_fixed = true;
     }
     c->nsm = nsm;
+    c->mixed = par->precision == GRMHD_PREC_MIXED;
     *out = c;
     return GRMHD_OK;
 }
@@ -424,6 +456,11 @@ grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, cons
     e = launch_prim2con(g, cp8c(prim), cp3(c->bf), c->psi, p8(c->q), c->nsm, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "prim2con kernel");
+    if (c->mixed) {
+        e = launch_prim_to32(g, cp8c(prim), cp3(c->bf), f11(c), c->nsm, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "prim_to32 kernel");
+    }
     return GRMHD_OK;
 }
 
@@ -469,7 +506,8 @@ grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
     P3 none = p3(nullptr);
     const int tk = tbegin(c, KIND_IMPLICIT, st);
     e = launch_implicit(c->g, cp8(qb), cp3(fb), c->psi, c->alp, c->eta, c->eta_u, a_dt, p8(c->prim), p3(c->R), none,
-                        c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, c->nfail, c->nsm, st);
+                        c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, f11(c), c->nfail, c->nsm,
+                        st);
     tend(c, tk, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
@@ -522,7 +560,8 @@ grmhd_status grmhd_get_prims(grmhd_ctx* c, double* const* prim_out, grmhd_stream
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     }
     e = launch_implicit(c->g, cp8(c->q), cp3(c->bf), c->psi, c->alp, c->eta, c->eta_u, 0.0, p8(prim_out),
-                        p3(nullptr), p3(nullptr), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, c->nfail, c->nsm, st);
+                        p3(nullptr), p3(nullptr), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, F11{},
+                        c->nfail, c->nsm, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "con2prim kernel");
     return GRMHD_OK;
@@ -535,8 +574,8 @@ grmhd_status grmhd_implicit(grmhd_ctx* c, double a_dt, double* const* q, const d
     if (s != GRMHD_OK) return s;
     if (!q || !bface || !prim || !R) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_implicit");
     cudaError_t e = launch_implicit(c->g, cp8(q), cp3c(bface), c->psi, c->alp, c->eta, c->eta_u, a_dt, p8(prim),
-                                    p3(R), p3(q + 5), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, c->nfail, c->nsm,
-                                    (cudaStream_t)stream);
+                                    p3(R), p3(q + 5), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm,
+                                    c->par.p_atm, F11{}, c->nfail, c->nsm, (cudaStream_t)stream);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
     return GRMHD_OK;
@@ -548,6 +587,11 @@ grmhd_status grmhd_explicit_L(grmhd_ctx* c, const double* const* prim, const dou
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     if (!prim || !bface || !L) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_explicit_L");
+    if (c->mixed) {
+        cudaError_t e = launch_prim_to32(c->g, cp8c(prim), cp3c(bface), f11(c), c->nsm, (cudaStream_t)stream);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "prim_to32 kernel");
+    }
     UpdateArgs a;
     memset(&a, 0, sizeof a);
     a.mode = UPD_WRITE_L;

@@ -100,56 +100,83 @@ __device__ __forceinline__ double cell_qB(const Dims& g, const double* __restric
 
 // ---------------------------------------------------------------------------
 // MC limiter (monotonised central, van Leer 1974)
+//
+// The half slope used for a face state is 1/2 minmod(2 d-, (d- + d+)/2, 2 d+)
+// = minmod(d-, (u+ - u-)/4, d+) exactly (the factors are powers of two).  minmod is
+// evaluated on the IEEE bit patterns with integer instructions: the three arguments
+// agree in sign when their sign bits agree, and among same-signed doubles the one
+// of least magnitude has the least 63-bit magnitude field.  GB300's FP64 pipe is the
+// bottleneck of this path, so keeping compares and selects off it matters.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double minmod3(double a, double b, double c)
-{
-    if (a > 0.0 && b > 0.0 && c > 0.0) return fmin(a, fmin(b, c));
-    if (a < 0.0 && b < 0.0 && c < 0.0) return fmax(a, fmax(b, c));
-    return 0.0;
-}
+template <typename T> struct Bits;
+template <> struct Bits<double> {
+    using I = long long;
+    static __device__ __forceinline__ I to(double x) { return __double_as_longlong(x); }
+    static __device__ __forceinline__ double from(I i) { return __longlong_as_double(i); }
+    static constexpr I MAG = 0x7fffffffffffffffLL;
+};
+template <> struct Bits<float> {
+    using I = int;
+    static __device__ __forceinline__ I to(float x) { return __float_as_int(x); }
+    static __device__ __forceinline__ float from(I i) { return __int_as_float(i); }
+    static constexpr I MAG = 0x7fffffff;
+};
 
-__device__ __forceinline__ double mc_slope(double um, double u0, double up)
+template <typename T>
+__device__ __forceinline__ T minmod3(T a, T b, T c)
 {
-    return minmod3(2.0 * (u0 - um), 0.5 * (up - um), 2.0 * (up - u0));
+    using I = typename Bits<T>::I;
+    const I ia = Bits<T>::to(a), ib = Bits<T>::to(b), ic = Bits<T>::to(c);
+    const I ma = ia & Bits<T>::MAG, mb = ib & Bits<T>::MAG, mc = ic & Bits<T>::MAG;
+    I r = ma <= mb ? ia : ib;
+    const I mr = ma <= mb ? ma : mb;
+    r = mr <= mc ? r : ic;
+    // sign bits differ somewhere -> 0 (signed zeros of agreeing sign give that zero)
+    return ((ia ^ ib) | (ia ^ ic)) < 0 ? T(0) : Bits<T>::from(r);
 }
 
 // left/right states at the face between a1 and a2 from the four cells a0 a1 a2 a3
-__device__ __forceinline__ void mc_face(double a0, double a1, double a2, double a3, double& L, double& R)
+template <typename T>
+__device__ __forceinline__ void mc_face(T a0, T a1, T a2, T a3, T& L, T& R)
 {
-    L = a1 + 0.5 * mc_slope(a0, a1, a2);
-    R = a2 - 0.5 * mc_slope(a1, a2, a3);
+    const T dm = a1 - a0, d0 = a2 - a1, dp = a3 - a2;
+    L = a1 + minmod3<T>(dm, T(0.25) * (a2 - a0), d0);
+    R = a2 - minmod3<T>(d0, T(0.25) * (a3 - a1), dp);
 }
 
 // ---------------------------------------------------------------------------
 // physical state at a face in the orthonormal frame (Sec. 2.1)
 // ---------------------------------------------------------------------------
 
-struct FaceState {
-    double q[8];    // densitised conserved: D, S_1..3, tau, E^1..3
-    double f[8];    // flux of the same along the face normal
+template <typename T>
+struct FaceStateT {
+    T q[8];    // densitised conserved: D, S_1..3, tau, E^1..3
+    T f[8];    // flux of the same along the face normal
 };
+using FaceState = FaceStateT<double>;
 
 // prim: rho, u^1..3, p, E^1..3 (coordinate components) and B^1..3 (coordinate);
-// psi, alpha at the face; d = normal direction
-__device__ __forceinline__ void face_state(const double* pr, const double* B, int d, double psi, double alp,
-                                           double gh, FaceState& s)
+// psi, alpha at the face; d = normal direction.  T = double on the FP64 path, float
+// for the reconstruction and fluxes of the mixed-precision path.
+template <typename T>
+__device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi, T alp, T gh, FaceStateT<T>& s)
 {
-    const double p2 = psi * psi, p4 = p2 * p2, p6 = p4 * p2;
-    const double rho = pr[0], p = pr[4];
-    double u[3], E[3], Bh[3];
+    const T p2 = psi * psi, p4 = p2 * p2, p6 = p4 * p2;
+    const T rho = pr[0], p = pr[4];
+    T u[3], E[3], Bh[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) { u[i] = p2 * pr[1 + i]; E[i] = p2 * pr[5 + i]; Bh[i] = p2 * B[i]; }
-    const double W = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const double iW = 1.0 / W;
-    const double rhoh = rho + gh * p;
-    const double D = rho * W;
-    const double U = 0.5 * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + Bh[0] * Bh[0] + Bh[1] * Bh[1] + Bh[2] * Bh[2]);
-    double S[3];
+    const T W = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const T iW = T(1) / W;
+    const T rhoh = rho + gh * p;
+    const T D = rho * W;
+    const T U = T(0.5) * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + Bh[0] * Bh[0] + Bh[1] * Bh[1] + Bh[2] * Bh[2]);
+    T S[3];
     S[0] = rhoh * W * u[0] + (E[1] * Bh[2] - E[2] * Bh[1]);
     S[1] = rhoh * W * u[1] + (E[2] * Bh[0] - E[0] * Bh[2]);
     S[2] = rhoh * W * u[2] + (E[0] * Bh[1] - E[1] * Bh[0]);
-    const double tau = rhoh * W * W - p + U - D;
+    const T tau = rhoh * W * W - p + U - D;
     s.q[0] = p6 * D;
 #pragma unroll
     for (int j = 0; j < 3; j++) s.q[1 + j] = p6 * p2 * S[j];
@@ -157,17 +184,17 @@ __device__ __forceinline__ void face_state(const double* pr, const double* B, in
 #pragma unroll
     for (int j = 0; j < 3; j++) s.q[5 + j] = p4 * E[j];
     // fluxes along d (beta = 0)
-    const double vd = u[d] * iW;
-    const double rhw2 = rhoh * W * W;
+    const T vd = u[d] * iW;
+    const T rhw2 = rhoh * W * W;
     s.f[0] = p4 * alp * D * vd;
 #pragma unroll
     for (int j = 0; j < 3; j++)
-        s.f[1 + j] = p6 * alp * ((j == d ? p + U : 0.0) + rhw2 * vd * (u[j] * iW) - E[d] * E[j] - Bh[d] * Bh[j]);
+        s.f[1 + j] = p6 * alp * ((j == d ? p + U : T(0)) + rhw2 * vd * (u[j] * iW) - E[d] * E[j] - Bh[d] * Bh[j]);
     s.f[4] = p4 * alp * (S[d] - vd * D);
     // (f_E^j)^d = alpha psi^2 eta^{djk} B_hat_k
-    const double ap2 = alp * p2;
+    const T ap2 = alp * p2;
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
-    s.f[5 + d] = 0.0;
+    s.f[5 + d] = T(0);
     s.f[5 + d1] = ap2 * Bh[d2];
     s.f[5 + d2] = -ap2 * Bh[d1];
 }
@@ -286,6 +313,86 @@ __device__ __forceinline__ bool newton_dir(const double J[3][3], const double* f
     return true;
 }
 
+// Newton direction x = -J^{-1} f with J formed and inverted in FP32 (62x the FP64
+// rate on GB300).  The root is fixed by the FP64 residual f, so a direction accurate
+// to ~1e-6 only turns quadratic convergence into fast linear convergence.  J is
+// normalised by its diagonal and f by the momentum scale M before the conversion,
+// keeping every float O(1).  Returns false when the FP32 system is singular or the
+// direction is not finite (the caller then uses the FP64 Jacobian).
+__device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const double* u, const Eval& e, double* x)
+{
+    const double iW = 1.0 / e.W;
+    float uf[3], Ef[3], Esf[3], Bf[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        uf[i] = (float)u[i];
+        Ef[i] = (float)e.E[i];
+        Esf[i] = (float)c.Es[i];
+        Bf[i] = (float)c.B[i];
+    }
+    float dE[3][3];
+    if (c.etat >= 0.0) {
+        const float A1 = (float)e.A1, Esu = (float)e.Esu, s = (float)e.iWe, iWf = (float)iW;
+        const float a2 = A1 * A1 * Esu * iWf;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++)
+                dE[i][j] = (-Ef[i] * uf[j] * iWf + A1 * uf[i] * Esf[j] - a2 * uf[i] * uf[j] +
+                            (i == j ? A1 * Esu : 0.0f)) * s;
+        dE[0][1] -= Bf[2] * s; dE[0][2] += Bf[1] * s;
+        dE[1][2] -= Bf[0] * s; dE[1][0] += Bf[2] * s;
+        dE[2][0] -= Bf[1] * s; dE[2][1] += Bf[0] * s;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) dE[i][j] = 0.0f;
+    }
+    // normalise J by 1/w_t (J = w_t I + ...) and f by 1/M:
+    //   J_ij / w_t = delta_ij + u_i (dw_t/du_j)/w_t + (dE/du_j x B)_i / w_t
+    //   (dw_t/du_j)/w_t = ((tau + D - U)/w_t u_j/W - W dU_j/w_t - 2 u_j) / (W^2 - 1/Gamma_hat)
+    const double sc = 1.0 / e.wt;
+    const float scf = (float)sc, idenf = (float)e.iden, Wf = (float)e.W, iWf = (float)iW;
+    const float basef = (float)((c.tau + c.D - e.U) * sc);
+    float J[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const float dU = Ef[0] * dE[0][j] + Ef[1] * dE[1][j] + Ef[2] * dE[2][j];
+        const float dw = (basef * uf[j] * iWf - Wf * dU * scf - 2.0f * uf[j]) * idenf;
+        const float cx = (dE[1][j] * Bf[2] - dE[2][j] * Bf[1]) * scf;
+        const float cy = (dE[2][j] * Bf[0] - dE[0][j] * Bf[2]) * scf;
+        const float cz = (dE[0][j] * Bf[1] - dE[1][j] * Bf[0]) * scf;
+        J[0][j] = uf[0] * dw + cx;
+        J[1][j] = uf[1] * dw + cy;
+        J[2][j] = uf[2] * dw + cz;
+    }
+    J[0][0] += 1.0f; J[1][1] += 1.0f; J[2][2] += 1.0f;
+    const double iM = e.M > 0.0 ? 1.0 / e.M : 0.0;
+    const float f0 = (float)(e.f[0] * iM), f1 = (float)(e.f[1] * iM), f2 = (float)(e.f[2] * iM);
+    const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const float det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(fabsf(det) > 1e-30f)) return false;
+    const float id = 1.0f / det;
+    const float c10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    const float c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    const float c12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    const float c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    const float c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    const float c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const float y0 = (c00 * f0 + c10 * f1 + c20 * f2) * id;
+    const float y1 = (c01 * f0 + c11 * f1 + c21 * f2) * id;
+    const float y2 = (c02 * f0 + c12 * f1 + c22 * f2) * id;
+    // (sc J) x = -sc f = -sc M f'  ->  x = -(sc M) y
+    const double k = -sc * e.M;
+    x[0] = k * (double)y0;
+    x[1] = k * (double)y1;
+    x[2] = k * (double)y2;
+    return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+}
+
 // Globally convergent Newton (backtracking on |f|^2 with the Armijo condition and a
 // bounded step).  u: in = initial guess, out = solution.  Converged when |f| is at
 // `tol` against its own momentum scale M, or when the step no longer moves u.
@@ -294,9 +401,14 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
 {
     evaluate(c, u, e);
     for (int it = 1; it <= kmax; it++) {
-        double J[3][3], dx[3];
-        jacobian(c, u, e, J);
-        if (!newton_dir(J, e.f, dx)) return -1;
+        double dx[3];
+        // FP32 directions first; the FP64 Jacobian takes over if they have not
+        // converged within 10 iterations or fail
+        if (it > 10 || !newton_dir_f32(c, u, e, dx)) {
+            double J[3][3];
+            jacobian(c, u, e, J);
+            if (!newton_dir(J, e.f, dx)) return -1;
+        }
         const double nu = fmax(1.0, sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
         const double nx = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
         if (nx > 100.0 * nu) {

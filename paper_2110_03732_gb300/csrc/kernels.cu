@@ -20,12 +20,18 @@ namespace grmhd {
 // implicit step
 // ---------------------------------------------------------------------------
 
+template <bool M>
 __global__ void __launch_bounds__(128) k_implicit(Dims g, CP8 qb, CP3 bf, const double* __restrict__ psi,
                                                   const double* __restrict__ alp, const double* __restrict__ eta,
                                                   double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax,
-                                                  double tol, double rho_atm, double p_atm,
+                                                  double tol, double rho_atm, double p_atm, F11 p32,
                                                   unsigned long long* __restrict__ nfail)
 {
+    if constexpr (!M) {
+        // flat metric: alpha = psi = 1 known at compile time
+        psi = nullptr;
+        alp = nullptr;
+    }
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x) {
@@ -100,6 +106,18 @@ __global__ void __launch_bounds__(128) k_implicit(Dims g, CP8 qb, CP3 bf, const 
         }
         prim.p[0][id] = rho;
         prim.p[4][id] = pres;
+        if (p32.p[0]) {
+            // FP32 copy for the mixed-precision explicit kernels, with the densitised
+            // cell-centred q_B of the stage
+            p32.p[0][id] = (float)rho;
+            p32.p[4][id] = (float)pres;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                p32.p[1 + i][id] = (float)(u[i] * ip2);
+                p32.p[5 + i][id] = (float)(e.E[i] * ip2);
+                p32.p[8 + i][id] = (float)(ci.B[i] * p4);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             prim.p[1 + i][id] = u[i] * ip2;
@@ -115,10 +133,27 @@ __global__ void __launch_bounds__(128) k_implicit(Dims g, CP8 qb, CP3 bf, const 
 // face fluxes
 // ---------------------------------------------------------------------------
 
-template <int D>
-__global__ void __launch_bounds__(128) k_flux(Dims g, CP8 prim, CP3 bf, const double* __restrict__ psi,
-                                              const double* __restrict__ alp, P8 F)
+// cell-centred densitised q_B^e of the (mapped) cell: from the staggered faces on
+// the FP64 path, from the stage's FP32 copy on the mixed path
+__device__ __forceinline__ double cell_qB_in(const Dims& g, const PrimIn<double>&, const CP3& bf, int e, const int* cs,
+                                             long long)
 {
+    return cell_qB(g, bf.p[e], e, cs);
+}
+__device__ __forceinline__ float cell_qB_in(const Dims&, const PrimIn<float>& pa, const CP3&, int e, const int*,
+                                            long long mi)
+{
+    return pa.p[8 + e][mi];
+}
+
+template <int D, bool M, typename T>
+__global__ void __launch_bounds__(128) k_flux(Dims g, PrimIn<T> prim, CP3 bf, const double* __restrict__ psi,
+                                              const double* __restrict__ alp, FluxOut<T> F)
+{
+    if constexpr (!M) {
+        psi = nullptr;
+        alp = nullptr;
+    }
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1), e2 = g.n[2] + (D == 2);
     const long long tot = (long long)e0 * e1 * e2;
@@ -136,38 +171,38 @@ __global__ void __launch_bounds__(128) k_flux(Dims g, CP8 prim, CP3 bf, const do
             mi[s] = cell_at(g, cs);
             ri[s] = lin(g, cs[0], cs[1], cs[2]);
         }
-        double prL[8], prR[8], BL[3], BR[3];
+        T prL[8], prR[8], BL[3], BR[3];
 #pragma unroll
         for (int v = 0; v < 8; v++) {
-            const double* a = prim.p[v];
-            mc_face(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3]], prL[v], prR[v]);
+            const T* a = prim.p[v];
+            mc_face<T>(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3]], prL[v], prR[v]);
         }
         // transverse cell-centred B (primitive = q_B / psi^6 at the cell)
 #pragma unroll
         for (int tt = 0; tt < 2; tt++) {
             const int e = tt == 0 ? T1 : T2;
-            double b[4];
+            T b[4];
 #pragma unroll
             for (int s = 0; s < 4; s++) {
                 int cs[3] = {c[0], c[1], c[2]};
                 cs[D] += s - 2;
-                const double ps = psi ? psi[ri[s]] : 1.0;
-                const double p2 = ps * ps;
-                b[s] = cell_qB(g, bf.p[e], e, cs) / (p2 * p2 * p2);
+                const T ps = psi ? (T)psi[ri[s]] : T(1);
+                const T p2 = ps * ps;
+                b[s] = (T)cell_qB_in(g, prim, bf, e, cs, mi[s]) / (p2 * p2 * p2);
             }
-            mc_face(b[0], b[1], b[2], b[3], BL[e], BR[e]);
+            mc_face<T>(b[0], b[1], b[2], b[3], BL[e], BR[e]);
         }
-        const double psf = psi ? 0.5 * (psi[ri[1]] + psi[ri[2]]) : 1.0;
-        const double alf = alp ? 0.5 * (alp[ri[1]] + alp[ri[2]]) : 1.0;
-        const double pf2 = psf * psf;
-        const double bn = bf.p[D][face_at(g, D, c)] / (pf2 * pf2 * pf2);
+        const T psf = psi ? (T)(0.5 * (psi[ri[1]] + psi[ri[2]])) : T(1);
+        const T alf = alp ? (T)(0.5 * (alp[ri[1]] + alp[ri[2]])) : T(1);
+        const T pf2 = psf * psf;
+        const T bn = (T)bf.p[D][face_at(g, D, c)] / (pf2 * pf2 * pf2);
         BL[D] = bn;
         BR[D] = bn;
-        FaceState sL, sR;
-        face_state(prL, BL, D, psf, alf, g.gh, sL);
-        face_state(prR, BR, D, psf, alf, g.gh, sR);
+        FaceStateT<T> sL, sR;
+        face_state<T>(prL, BL, D, psf, alf, (T)g.gh, sL);
+        face_state<T>(prR, BR, D, psf, alf, (T)g.gh, sR);
         // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity)
-        const double cs = alf / pf2;
+        const T cs = alf / pf2;
         const long long o = lin(g, c[0], c[1], c[2]);
 #pragma unroll
         for (int v = 0; v < 8; v++)
@@ -180,16 +215,21 @@ __global__ void __launch_bounds__(128) k_flux(Dims g, CP8 prim, CP3 bf, const do
 // index that is lower in a = C+1 and b = C+2
 // ---------------------------------------------------------------------------
 
-template <int C>
-__global__ void __launch_bounds__(128) k_emf(Dims g, CP8 prim, CP3 bf, const double* __restrict__ psi,
-                                             const double* __restrict__ alp, double* __restrict__ Eh)
+template <int C, bool M, typename T>
+__global__ void __launch_bounds__(128) k_emf(Dims g, PrimIn<T> prim, CP3 bf, const double* __restrict__ psi,
+                                             const double* __restrict__ alp, T* __restrict__ Eh)
 {
+    if constexpr (!M) {
+        psi = nullptr;
+        alp = nullptr;
+    }
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     const bool aa = g.act[A], ba = g.act[B];
     int e[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) e[d] = (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
     const long long tot = (long long)e[0] * e[1] * e[2];
+    const T* __restrict__ Ec = prim.p[5 + C];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x) {
         int c[3];
@@ -197,64 +237,64 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, CP8 prim, CP3 bf, const dou
         c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
         c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
         // steps (ii)-(iii): covariant E_C = psi^4 E^C, to A-faces then along B
-        double s[2][4];   // [X = A-side L/R][B offset -2..+1]
+        T s[2][4];   // [X = A-side L/R][B offset -2..+1]
         const int nb = ba ? 4 : 1;
         for (int ob = 0; ob < nb; ob++) {
             int cb[3] = {c[0], c[1], c[2]};
             if (ba) cb[B] += ob - 2;
             if (aa) {
-                double v[4];
+                T v[4];
 #pragma unroll
                 for (int sa = 0; sa < 4; sa++) {
                     int cs[3] = {cb[0], cb[1], cb[2]};
                     cs[A] += sa - 2;
-                    const double ps = psi ? psi[lin(g, cs[0], cs[1], cs[2])] : 1.0;
-                    const double p2 = ps * ps;
-                    v[sa] = p2 * p2 * prim.p[5 + C][cell_at(g, cs)];
+                    const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
+                    const T p2 = ps * ps;
+                    v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
                 }
-                mc_face(v[0], v[1], v[2], v[3], s[0][ob], s[1][ob]);
+                mc_face<T>(v[0], v[1], v[2], v[3], s[0][ob], s[1][ob]);
             } else {
-                const double ps = psi ? psi[lin(g, cb[0], cb[1], cb[2])] : 1.0;
-                const double p2 = ps * ps;
-                s[0][ob] = s[1][ob] = p2 * p2 * prim.p[5 + C][cell_at(g, cb)];
+                const T ps = psi ? (T)psi[lin(g, cb[0], cb[1], cb[2])] : T(1);
+                const T p2 = ps * ps;
+                s[0][ob] = s[1][ob] = p2 * p2 * Ec[cell_at(g, cb)];
             }
         }
-        double EXY[2][2];
+        T EXY[2][2];
 #pragma unroll
         for (int X = 0; X < 2; X++) {
-            if (ba) mc_face(s[X][0], s[X][1], s[X][2], s[X][3], EXY[X][0], EXY[X][1]);
+            if (ba) mc_face<T>(s[X][0], s[X][1], s[X][2], s[X][3], EXY[X][0], EXY[X][1]);
             else EXY[X][0] = EXY[X][1] = s[X][0];
         }
         // step (iv): q_B^B (B-faces) along A, q_B^A (A-faces) along B
-        double qBbL, qBbR, qBaL, qBaR;
+        T qBbL, qBbR, qBaL, qBaR;
         if (aa) {
-            double v[4];
+            T v[4];
 #pragma unroll
             for (int sa = 0; sa < 4; sa++) {
                 int cs[3] = {c[0], c[1], c[2]};
                 cs[A] += sa - 2;
-                v[sa] = bf.p[B][face_at(g, B, cs)];
+                v[sa] = (T)bf.p[B][face_at(g, B, cs)];
             }
-            mc_face(v[0], v[1], v[2], v[3], qBbL, qBbR);
+            mc_face<T>(v[0], v[1], v[2], v[3], qBbL, qBbR);
         } else {
-            qBbL = qBbR = bf.p[B][face_at(g, B, c)];
+            qBbL = qBbR = (T)bf.p[B][face_at(g, B, c)];
         }
         if (ba) {
-            double v[4];
+            T v[4];
 #pragma unroll
             for (int sb = 0; sb < 4; sb++) {
                 int cs[3] = {c[0], c[1], c[2]};
                 cs[B] += sb - 2;
-                v[sb] = bf.p[A][face_at(g, A, cs)];
+                v[sb] = (T)bf.p[A][face_at(g, A, cs)];
             }
-            mc_face(v[0], v[1], v[2], v[3], qBaL, qBaR);
+            mc_face<T>(v[0], v[1], v[2], v[3], qBaL, qBaR);
         } else {
-            qBaL = qBaR = bf.p[A][face_at(g, A, c)];
+            qBaL = qBaR = (T)bf.p[A][face_at(g, A, c)];
         }
         // lapse at the edge (mean of the adjacent cells) and the face speeds
         const long long i0 = lin(g, c[0], c[1], c[2]);
         const long long sA = aa ? g.st[A] : 0, sB = ba ? g.st[B] : 0;
-        double ale = 1.0, ca = 1.0, cb = 1.0;
+        T ale = T(1), ca = T(1), cb = T(1);
         if (alp || psi) {
             int nce = 1;
             double sum = alp ? alp[i0] : 1.0;
@@ -263,28 +303,30 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, CP8 prim, CP3 bf, const dou
                 sum += alp ? alp[i0 - sB] : 1.0; nce++;
                 if (aa) { sum += alp ? alp[i0 - sA - sB] : 1.0; nce++; }
             }
-            ale = sum / nce;
+            ale = (T)(sum / nce);
             if (aa) {
-                ca = 0.0;
+                double cmax = 0.0;
                 for (int tt = 0; tt < (ba ? 2 : 1); tt++) {
                     const long long cf = i0 - tt * sB, cfm = cf - sA;
                     const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
                     const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-                    ca = fmax(ca, alf / (psf * psf));
+                    cmax = fmax(cmax, alf / (psf * psf));
                 }
+                ca = (T)cmax;
             }
             if (ba) {
-                cb = 0.0;
+                double cmax = 0.0;
                 for (int tt = 0; tt < (aa ? 2 : 1); tt++) {
                     const long long cf = i0 - tt * sA, cfm = cf - sB;
                     const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
                     const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-                    cb = fmax(cb, alf / (psf * psf));
+                    cmax = fmax(cmax, alf / (psf * psf));
                 }
+                cb = (T)cmax;
             }
         }
         // steps (v)-(vii): hat{E}^{XY} = alpha E_C^{XY}; Londrillo & Del Zanna (2004)
-        const double hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
+        const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
         Eh[i0] = (ca * cb * hLL + ca * cb * hLR + ca * cb * hRL + ca * cb * hRR) / ((ca + ca) * (cb + cb)) +
                  ca * ca / (ca + ca) * (qBbR - qBbL) - cb * cb / (cb + cb) * (qBaR - qBaL);
     }
@@ -312,8 +354,13 @@ __device__ __forceinline__ void out_value(const UpdateArgs& a, int v, long long 
     else a.acc[v][o] = nv;
 }
 
+template <bool M, typename T>
 __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
 {
+    // flat metric: alpha = psi = 1 known at compile time (locals, so that the
+    // parameter block itself stays unmodified and in constant memory)
+    const double* __restrict__ psi = M ? a.psi : nullptr;
+    const double* __restrict__ alp = M ? a.alp : nullptr;
     int e[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) e[d] = g.act[d] ? g.n[d] + 1 : 1;
@@ -338,10 +385,13 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
                 if (!g.act[d]) continue;
                 const long long o1 = o + g.st[d];
 #pragma unroll
-                for (int v = 0; v < 8; v++) Lc[v] -= (a.F[d][v][o1] - a.F[d][v][o]) * g.idx[d];
+                for (int v = 0; v < 8; v++) {
+                    const T* __restrict__ Fv = (const T*)a.F[d][v];
+                    Lc[v] -= ((double)Fv[o1] - (double)Fv[o]) * g.idx[d];
+                }
             }
-            const double ps = a.psi ? a.psi[o] : 1.0;
-            const double al = a.alp ? a.alp[o] : 1.0;
+            const double ps = psi ? psi[o] : 1.0;
+            const double al = alp ? alp[o] : 1.0;
             const double p2 = ps * ps, p4 = p2 * p2, p6 = p4 * p2;
             double u[3];
 #pragma unroll
@@ -356,7 +406,7 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
                 int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
                 cp[d] += 1;
                 cm[d] -= 1;
-                double sp = a.psi ? a.psi[o + g.st[d]] : 1.0, sm = a.psi ? a.psi[o - g.st[d]] : 1.0;
+                double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
                 sp = sp * sp;
                 sm = sm * sm;
                 const double qp = sp * sp * sp * a.prim[5 + d][cell_at(g, cp)];
@@ -366,7 +416,7 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
             // s_E (non-stiff part) = -alpha sqrt(gamma) rho_e v^i
 #pragma unroll
             for (int i = 0; i < 3; i++) Lc[5 + i] -= al * divqE * (u[i] * iW);
-            if (a.psi || a.alp) {
+            if (psi || alp) {
                 // s_S and s_tau for beta = 0, K_ij = 0 (Sec. 2.1) in the orthonormal frame:
                 //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
                 //   s_tau = -psi^4 S_hat_i d_i alpha
@@ -392,8 +442,8 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
 #pragma unroll
                 for (int i = 0; i < 3; i++) {
                     if (!g.act[i]) continue;
-                    const double ap = a.alp ? a.alp[o + g.st[i]] : 1.0, am = a.alp ? a.alp[o - g.st[i]] : 1.0;
-                    const double pp = a.psi ? a.psi[o + g.st[i]] : 1.0, pm = a.psi ? a.psi[o - g.st[i]] : 1.0;
+                    const double ap = alp ? alp[o + g.st[i]] : 1.0, am = alp ? alp[o - g.st[i]] : 1.0;
+                    const double pp = psi ? psi[o + g.st[i]] : 1.0, pm = psi ? psi[o - g.st[i]] : 1.0;
                     const double dal = (ap - am) * (0.5 * g.idx[i]);
                     const double dps = (pp - pm) * (0.5 * g.idx[i]);
                     Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps / ps) * tr);
@@ -416,8 +466,10 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
             }
             if (!ok) continue;
             double r = 0.0;
-            if (g.act[fb]) r -= (a.Eh[fc][o + g.st[fb]] - a.Eh[fc][o]) * g.idx[fb];
-            if (g.act[fc]) r += (a.Eh[fb][o + g.st[fc]] - a.Eh[fb][o]) * g.idx[fc];
+            const T* __restrict__ Ec = (const T*)a.Eh[fc];
+            const T* __restrict__ Eb = (const T*)a.Eh[fb];
+            if (g.act[fb]) r -= ((double)Ec[o + g.st[fb]] - (double)Ec[o]) * g.idx[fb];
+            if (g.act[fc]) r += ((double)Eb[o + g.st[fc]] - (double)Eb[o]) * g.idx[fc];
             out_value(a, 8 + fa, o, r, false);
         }
     }
@@ -466,6 +518,23 @@ __global__ void k_prim2con(Dims g, CP8 prim, CP3 bf, const double* __restrict__ 
         face_state(pr, B, 0, ps, 1.0, g.gh, s);
 #pragma unroll
         for (int v = 0; v < 8; v++) q.p[v][t] = s.q[v];
+    }
+}
+
+// FP32 copy of caller primitives at every padded cell (fixed-boundary ghosts
+// included) with the densitised cell-centred q_B, for the mixed-precision path
+__global__ void k_prim_to32(Dims g, CP8 prim, CP3 bf, F11 p32)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = (int)(t % g.N[0]);
+        c[1] = (int)((t / g.N[0]) % g.N[1]);
+        c[2] = (int)(t / ((long long)g.N[0] * g.N[1]));
+#pragma unroll
+        for (int v = 0; v < 8; v++) p32.p[v][t] = (float)prim.p[v][t];
+#pragma unroll
+        for (int e = 0; e < 3; e++) p32.p[8 + e][t] = (float)cell_qB(g, bf.p[e], e, c);
     }
 }
 
@@ -591,34 +660,88 @@ static int grid_for(long long work, int threads, int nsm)
 
 cudaError_t launch_implicit(const Dims& g, CP8 qb, CP3 bf, const double* psi, const double* alp, const double* eta,
                             double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax, double tol,
-                            double rho_atm, double p_atm, unsigned long long* nfail, int nsm, cudaStream_t st)
+                            double rho_atm, double p_atm, F11 p32, unsigned long long* nfail, int nsm,
+                            cudaStream_t st)
 {
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
-    k_implicit<<<grid_for(work, 128, nsm), 128, 0, st>>>(g, qb, bf, psi, alp, eta, eta_u, a_dt, prim, R, qE_out,
-                                                         kmax, tol, rho_atm, p_atm, nfail);
+    if (psi || alp)
+        k_implicit<true><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, qb, bf, psi, alp, eta, eta_u, a_dt, prim, R,
+                                                                   qE_out, kmax, tol, rho_atm, p_atm, p32, nfail);
+    else
+        k_implicit<false><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, qb, bf, psi, alp, eta, eta_u, a_dt, prim, R,
+                                                                    qE_out, kmax, tol, rho_atm, p_atm, p32, nfail);
     return cudaGetLastError();
+}
+
+template <typename T>
+static void flux_dispatch(const Dims& g, int d, bool m, int b, cudaStream_t st, const PrimIn<T>& prim, CP3 bf,
+                          const double* psi, const double* alp, FluxOut<T> F)
+{
+    if (d == 0) m ? k_flux<0, true, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F)
+                  : k_flux<0, false, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+    else if (d == 1) m ? k_flux<1, true, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F)
+                       : k_flux<1, false, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+    else m ? k_flux<2, true, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F)
+           : k_flux<2, false, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+}
+
+template <typename T>
+static void emf_dispatch(const Dims& g, int c, bool m, int b, cudaStream_t st, const PrimIn<T>& prim, CP3 bf,
+                         const double* psi, const double* alp, T* Eh)
+{
+    if (c == 0) m ? k_emf<0, true, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh)
+                  : k_emf<0, false, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+    else if (c == 1) m ? k_emf<1, true, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh)
+                       : k_emf<1, false, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+    else m ? k_emf<2, true, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh)
+           : k_emf<2, false, T><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+}
+
+static long long flux_work(const Dims& g, int d)
+{
+    return (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
+}
+
+static long long emf_work(const Dims& g, int c)
+{
+    long long work = 1;
+    for (int d = 0; d < 3; d++) work *= (d == c) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    return work;
 }
 
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
                         cudaStream_t st)
 {
-    const long long work = (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
-    const int b = grid_for(work, 128, nsm);
-    if (d == 0) k_flux<0><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
-    else if (d == 1) k_flux<1><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
-    else k_flux<2><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, F);
+    PrimIn<double> pa;
+    FluxOut<double> fo;
+    for (int v = 0; v < 8; v++) {
+        pa.p[v] = prim.p[v];
+        fo.p[v] = F.p[v];
+    }
+    flux_dispatch<double>(g, d, psi || alp, grid_for(flux_work(g, d), 128, nsm), st, pa, bf, psi, alp, fo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st)
+{
+    flux_dispatch<float>(g, d, psi || alp, grid_for(flux_work(g, d), 128, nsm), st, prim, bf, psi, alp, F);
     return cudaGetLastError();
 }
 
 cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
                        int nsm, cudaStream_t st)
 {
-    long long work = 1;
-    for (int d = 0; d < 3; d++) work *= (d == c) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
-    const int b = grid_for(work, 128, nsm);
-    if (c == 0) k_emf<0><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
-    else if (c == 1) k_emf<1><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
-    else k_emf<2><<<b, 128, 0, st>>>(g, prim, bf, psi, alp, Eh);
+    PrimIn<double> pa;
+    for (int v = 0; v < 8; v++) pa.p[v] = prim.p[v];
+    emf_dispatch<double>(g, c, psi || alp, grid_for(emf_work(g, c), 128, nsm), st, pa, bf, psi, alp, Eh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
+                         const double* alp, float* Eh, int nsm, cudaStream_t st)
+{
+    emf_dispatch<float>(g, c, psi || alp, grid_for(emf_work(g, c), 128, nsm), st, prim, bf, psi, alp, Eh);
     return cudaGetLastError();
 }
 
@@ -626,7 +749,14 @@ cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStrea
 {
     long long work = 1;
     for (int d = 0; d < 3; d++) work *= g.act[d] ? g.n[d] + 1 : 1;
-    k_update<<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+    const int b = grid_for(work, 128, nsm);
+    if (a.f32) {
+        if (a.psi || a.alp) k_update<true, float><<<b, 128, 0, st>>>(g, a);
+        else k_update<false, float><<<b, 128, 0, st>>>(g, a);
+    } else {
+        if (a.psi || a.alp) k_update<true, double><<<b, 128, 0, st>>>(g, a);
+        else k_update<false, double><<<b, 128, 0, st>>>(g, a);
+    }
     return cudaGetLastError();
 }
 
@@ -639,6 +769,12 @@ cudaError_t launch_curlA(const Dims& g, CP3 A, P3 bf, int nsm, cudaStream_t st)
 cudaError_t launch_prim2con(const Dims& g, CP8 prim, CP3 bf, const double* psi, P8 q, int nsm, cudaStream_t st)
 {
     k_prim2con<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, prim, bf, psi, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st)
+{
+    k_prim_to32<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, prim, bf, p32);
     return cudaGetLastError();
 }
 

@@ -9,15 +9,24 @@ namespace grmhd {
 
 enum { UPD_WRITE_L = 0, UPD_STAGE = 1 };
 
+// stage primitives as the explicit kernels read them: FP64 (rho, u^1..3, p, E^1..3),
+// or FP32 on the mixed-precision path with the densitised cell-centred q_B^1..3 added
+template <typename T> struct PrimIn;
+template <> struct PrimIn<double> { const double* p[8]; };
+template <> struct PrimIn<float> { const float* p[11]; };
+template <typename T> struct FluxOut { T* p[8]; };
+struct F11 { float* p[11]; };
+
 // Arguments of the update kernel.  Variables 0..7 are cell-centred (D, S_1..3, tau,
 // E^1..3), 8..10 are the face fields.
 struct UpdateArgs {
     int mode;               // UPD_WRITE_L: L -> L[]; UPD_STAGE: fold into base/acc/qn
     int stage, s;
+    int f32;                // fluxes and EMFs are FP32 (mixed precision) instead of FP64
     double dt;
     double At[4][4], A[4][4], wt[4], w[4];
-    const double* F[3][8];  // face fluxes per active direction
-    const double* Eh[3];    // edge EMFs
+    const void* F[3][8];    // face fluxes per active direction (double or float)
+    const void* Eh[3];      // edge EMFs (double or float)
     const double* prim[8];  // stage primitives (padded)
     const double* bf[3];    // stage face fields
     const double* psi;
@@ -31,7 +40,13 @@ struct UpdateArgs {
 
 cudaError_t launch_implicit(const Dims& g, CP8 qb, CP3 bf, const double* psi, const double* alp, const double* eta,
                             double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax, double tol,
-                            double rho_atm, double p_atm, unsigned long long* nfail, int nsm, cudaStream_t st);
+                            double rho_atm, double p_atm, F11 p32, unsigned long long* nfail, int nsm,
+                            cudaStream_t st);
+cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st);
+cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
+                         const double* alp, float* Eh, int nsm, cudaStream_t st);
+cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
                         cudaStream_t st);
 cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,

@@ -37,7 +37,7 @@ class Tableau(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("gamma_eos", C.c_double), ("cfl", C.c_double), ("newton_tol", C.c_double),
-                ("newton_kmax", C.c_int), ("reserved", C.c_int), ("rho_atm", C.c_double), ("p_atm", C.c_double)]
+                ("newton_kmax", C.c_int), ("precision", C.c_int), ("rho_atm", C.c_double), ("p_atm", C.c_double)]
 
 
 def library_path():
@@ -133,11 +133,13 @@ class Solver:
     cell and face fields; the library updates them in place."""
 
     def __init__(self, ndim, n, lo, hi, bc, gamma, cfl=0.4, tableau=None, device="cuda", newton_tol=0.0,
-                 newton_kmax=0, rho_atm=0.0, p_atm=0.0):
+                 newton_kmax=0, rho_atm=0.0, p_atm=0.0, precision="fp64"):
         self.L = lib()
         self.grid = make_grid(ndim, n, lo, hi, bc)
         self.tab = ssp2() if tableau is None else tableau
-        self.par = Params(float(gamma), float(cfl), float(newton_tol), int(newton_kmax), 0, float(rho_atm),
+        prec = {"fp64": 0, "mixed": 1}[precision] if isinstance(precision, str) else int(precision)
+        self.precision = prec
+        self.par = Params(float(gamma), float(cfl), float(newton_tol), int(newton_kmax), prec, float(rho_atm),
                           float(p_atm))
         self.device = torch.device(device)
         ng = [2 if d < ndim else 0 for d in range(3)]

@@ -81,8 +81,10 @@ def test_scratch_bytes_formula(lib):
             ncell *= n[d] + 4 if d < ndim else 1
         arr = -(-8 * ncell // 256) * 256
         narr = 8 + 3 + 11 * (t.s - 1) + 11 + 8 * ndim + 3
+        arr32 = -(-4 * ncell // 256) * 256
+        narr32 = 11 + 8 * ndim + 3
         small = -(-8 * 1024 * 11 // 256) * 256 + 256 + 256
-        assert b.value == narr * arr + small
+        assert b.value == narr * arr + narr32 * arr32 + small
 
 
 @pytest.mark.parametrize("field,value", [("ndim", 0), ("ndim", 4), ("n", 0), ("hi", -1.0), ("bc", 7),
