@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--n", type=int, default=N_OT, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -58,6 +60,17 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x, device):
+    """Largest value of x over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -228,11 +241,7 @@ def run_native(args):
     ktimes = S.kernel_times()
     launches = S.launch_count() - launches0
 
-    total_s = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dev)
     ms_per_step = 1e3 * total_s / args.steps
     value = ws * cells * STAGES * args.steps / total_s
 
@@ -272,11 +281,7 @@ def run_native(args):
         e1.record(stream)
         e1.synchronize()
         mixed_ms.append(e0.elapsed_time(e1))
-    mixed_total = sum(mixed_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([mixed_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        mixed_total = float(t.item())
+    mixed_total = max_over_ranks(sum(mixed_ms) / 1e3, dev)
     mixed_value = ws * cells * STAGES * args.steps / mixed_total
     del Sm
     if rank != 0:
@@ -312,6 +317,9 @@ def run_native(args):
                   "p99_ms_per_step": float(np.percentile(mixed_ms, 99)),
                   "dtype": "f32 reconstruction/HLL/edge EMF, f64 implicit solve/sources/CT/stage combination"},
     }
+    if not args.no_batched:
+        line["batched"] = bench_batched(grmhd, P, dev, args)
+        line["serving"] = bench_serving(dev, args)
     if not args.no_cpu_baseline:
         rate, el = cpu_oracle_rate(256, 2)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -319,6 +327,65 @@ def run_native(args):
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_batched(grmhd, P, dev, args):
+    """256 independent Orszag-Tang boxes (sides drawn from 64..512, eta log-uniform in
+    [1e-6, 1], seeded phases) advanced by one batched, autotuned, graph-captured step
+    (mixed precision).  Inputs (~20 GB) exceed L2, so no flush is needed."""
+    import torch
+    probs = P.ot_batch(0, 256)
+    solvers = [grmhd.Solver.from_problem(pr, device=dev, precision="mixed") for pr in probs]
+    cells = sum(s.cells for s in solvers)
+    B = grmhd.Batch(solvers)
+    B.set_dt([s.compute_dt() for s in solvers])
+    cfg = B.autotune(reps=2)
+    for _ in range(3):
+        B.step()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            B.step(stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(5, min(args.steps, 20))
+    times = []
+    for _ in range(k):
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    nfail = sum(s.diagnostics()[2] for s in solvers[:8])
+    out = {"workload": "256 Orszag-Tang boxes, sides U{64,128,256,512}, eta 10^U[-6,0], seed 0",
+           "boxes": len(probs), "cells": cells, "precision": "mixed", "value": cells * STAGES / (ms / 1e3),
+           "unit": UNIT, "ms_per_step": ms, "steps": k, "graph_captured": True,
+           "launch_config": {kk: list(vv) for kk, vv in cfg.items()}, "newton_failures_first8": nfail}
+    del graph, B, solvers
+    torch.cuda.synchronize()
+    return out
+
+
+def bench_serving(dev, args):
+    """Seeded Poisson stream (200 requests/s) of 1-D shock tubes (400-4096 cells, to
+    t = 0.4), 2-D Orszag-Tang vortices (128^2-512^2, 100 steps) and 3-D stars
+    (64^3-128^3, 100 steps), eta log-uniform in [1e-6, 1], served by continuous
+    batching under a 150 GB device-memory budget (mixed precision)."""
+    from paper_2110_03732_gb300 import problems as P
+    from paper_2110_03732_gb300.serve import Request, Server
+    reqs = []
+    for i, (t, pr, steps) in enumerate(P.request_stream(0, args.serve_requests, rate=200.0)):
+        reqs.append(Request(i, t, pr, steps, t_end=pr.t_end if pr.ndim == 1 else None))
+    srv = Server(budget_bytes=150e9, precision="mixed", device=dev)
+    results, stats = srv.run(reqs, realtime=True)
+    stats["unit"] = UNIT
+    stats["workload"] = f"{len(reqs)} requests, Poisson 200/s, seed 0"
+    return stats
 
 
 # FP64 flops per cell per launch of each kernel kind (2 * DFMA + DADD + DMUL thread

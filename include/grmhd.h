@@ -180,6 +180,41 @@ grmhd_status grmhd_kernel_times(grmhd_ctx* ctx, double* ms, long long* launches)
 /* Message of the last error on the calling thread ("" if none). */
 const char* grmhd_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Batched execution (not in the paper: throughput for many independent problems).
+ * A batch advances n bound contexts together -- uneven grid sizes, 1-D/2-D/3-D,
+ * flat or fixed-metric, any resistivity -- issuing one launch per kernel kind and
+ * stage for all of them.  Each problem runs exactly the per-cell arithmetic it runs
+ * alone (same kernels' item bodies, no cross-problem reduction), so its results are
+ * bitwise those of grmhd_step on that context.  All contexts must share the tableau
+ * and the precision.  The batch reads the contexts' state, scratch, metric and eta
+ * at the time of grmhd_batch_create; re-create it after re-binding a context.
+ * ------------------------------------------------------------------------ */
+typedef struct grmhd_batch_s grmhd_batch;
+
+/* Device scratch (256-byte aligned) for a batch of these contexts: the per-problem,
+ * per-stage descriptor table and the work lists. */
+grmhd_status grmhd_batch_scratch_bytes(grmhd_ctx* const* ctxs, int n, size_t* bytes);
+/* Build the batch (uploads its work lists; synchronises the legacy default stream). */
+grmhd_status grmhd_batch_create(grmhd_ctx* const* ctxs, int n, void* scratch, size_t scratch_bytes,
+                                grmhd_batch** out);
+/* Per-problem time steps (host array of n); uploads the descriptors of problems
+ * whose dt changed (synchronises the stream when it does). */
+grmhd_status grmhd_batch_set_dt(grmhd_batch* b, const double* dt, grmhd_stream_t stream);
+/* One IMEX step of every problem with its current dt (launches only: can be
+ * captured in a CUDA graph once the dts are set). */
+grmhd_status grmhd_batch_step(grmhd_batch* b, grmhd_stream_t stream);
+/* Autotuner: times stage-0 kernels (which write only scratch) for each candidate
+ * (threads per block, items per work chunk) per kernel kind and keeps the fastest.
+ * The Newton starting points it overwrites are saved to host memory and restored,
+ * so later results are unchanged.  reps: timed repetitions per candidate.
+ * Synchronises the stream. */
+grmhd_status grmhd_batch_autotune(grmhd_batch* b, int reps, grmhd_stream_t stream);
+/* Chosen launch shape per kernel kind (8 entries: implicit, flux x/y/z, emf x/y/z,
+ * update). */
+grmhd_status grmhd_batch_config(const grmhd_batch* b, int* threads, int* items);
+grmhd_status grmhd_batch_destroy(grmhd_batch* b);
+
 /* div B norms of caller-owned face fields without allocating anything.  The paper
  * has no counterpart to this call: it exists for callers that cannot allocate
  * device memory where they want the check (for example a host whose device memory

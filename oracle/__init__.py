@@ -93,7 +93,7 @@ class Grid:
     ``gamma``, atmosphere floor ``rho_atm``/``p_atm`` (0: none).  Inactive directions
     have one cell and no ghosts."""
 
-    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0):
+    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0, xi=0.0):
         n = list(n) + [1] * (3 - len(n))
         dx = list(dx) + [1.0] * (3 - len(dx))
         bc = list(bc) + ["periodic"] * (3 - len(bc))
@@ -105,8 +105,8 @@ class Grid:
         self.ng = [2 if d < ndim else 0 for d in range(3)]
         self.N = [self.n[d] + 2 * self.ng[d] for d in range(3)]
         self._gi = (C.c_int * 7)(ndim, *self.n, *self.bc)
-        self.rho_atm, self.p_atm = float(rho_atm), float(p_atm)
-        self._gd = (C.c_double * 6)(*self.dx, self.gamma, self.rho_atm, self.p_atm)
+        self.rho_atm, self.p_atm, self.xi = float(rho_atm), float(p_atm), float(xi)
+        self._gd = (C.c_double * 7)(*self.dx, self.gamma, self.rho_atm, self.p_atm, self.xi)
 
     @property
     def shape(self):
@@ -150,10 +150,11 @@ def prim2con(grid, prim, bf, psi=None):
     return q
 
 
-def solve_cell(D, S, tau, Es, B, psi, etat, gamma, guess=None):
+def solve_cell(D, S, tau, Es, B, psi, etat, gamma, guess=None, xi=0.0):
     """One-cell implicit solve (Sec. 2.4).  ``etat < 0`` holds E fixed; ``guess`` is
-    the initial velocity (default: rest).  Returns (iterations, u[3], E[3], rho, p)."""
-    inp = np.array([D, *S, tau, *Es, *B], dtype=np.float64)
+    the initial velocity (default: rest); ``xi`` the dynamo parameter.  Returns
+    (iterations, u[3], E[3], rho, p)."""
+    inp = np.array([D, *S, tau, *Es, *B, xi], dtype=np.float64)
     g = None if guess is None else np.ascontiguousarray(guess, dtype=np.float64)
     u = np.zeros(3)
     E = np.zeros(3)
@@ -162,9 +163,9 @@ def solve_cell(D, S, tau, Es, B, psi, etat, gamma, guess=None):
     return it, u, E, rp[0], rp[1]
 
 
-def residual_cell(D, S, tau, Es, B, psi, etat, gamma, u):
+def residual_cell(D, S, tau, Es, B, psi, etat, gamma, u, xi=0.0):
     """Residual f_i, analytic Jacobian J_ij and E^i(u) at velocity ``u``."""
-    inp = np.array([D, *S, tau, *Es, *B], dtype=np.float64)
+    inp = np.array([D, *S, tau, *Es, *B, xi], dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
     f = np.zeros(3)
     J = np.zeros(9)
@@ -287,7 +288,7 @@ class State:
 def from_problem(prob):
     """Oracle state from a ``paper_2110_03732_gb300.problems.Problem``: face q_B from
     the edge potential (oracle curl) or taken as given."""
-    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm)
+    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0))
     if prob.A_edge is not None:
         bf = curl_A(grid, [np.ascontiguousarray(a, dtype=np.float64) for a in prob.A_edge])
     else:

@@ -16,7 +16,7 @@
  *
  * Paper passages followed (section / equation):
  *   conserved variables, fluxes, sources          Sec. 2.1 (q, f^i, s; Gauss law for rho_e)
- *   Ohm's law (xi = 0 only)                       Sec. 2.2
+ *   Ohm's law with the mean-field dynamo xi       Sec. 2.2
  *   IMEX-RK stages, SSP2(2,2,2) tableau           Sec. 2.3 (Table "IMEX-SSP2(2,2,2)")
  *   implicit E + velocity Newton, A_k, Jacobian   Sec. 2.4 (eq. im_E, f_i, J_ij)
  *   characteristic speeds (maximal diffusivity)   Sec. 2.5
@@ -68,6 +68,7 @@ typedef struct {
     double Gam;        /* ideal-gas adiabatic index Gamma */
     double rho_atm;    /* atmosphere density (0: no atmosphere treatment) */
     double p_atm;      /* atmosphere pressure */
+    double xi;         /* mean-field dynamo parameter (uniform) */
     long ncell;        /* padded cells */
 } OGrid;
 
@@ -85,6 +86,7 @@ static void grid_setup(OGrid* g, const int* gi, const double* gd)
     g->Gam = gd[3];
     g->rho_atm = gd[4];
     g->p_atm = gd[5];
+    g->xi = gd[6];
     g->ncell = (long)g->N[0] * g->N[1] * g->N[2];
 }
 
@@ -247,12 +249,15 @@ typedef struct {
     double g;                          /* psi^4 */
     double sg;                         /* psi^6 */
     double etat;                       /* eta_tilde; < 0 means E held fixed (E = E*) */
+    double xi;                         /* mean-field dynamo parameter (Sec. 2.2) */
     double Gh;                         /* Gamma_hat_1 = Gamma/(Gamma-1) */
 } OCell;
 
-/* E(u) from eq. im_E with xi = 0 (A_2 = A_3 = A_4 = 0, A_5 = -1):
- *   A_0 E^i = eta_t E*^i + A_1 (E*_k u^k) u^i + A_5 eps^{ijk} u_j B_k
- * and its derivative dE^i/du^j from the Sec. 2.4 expression.  Returns W. */
+/* E(u) from eq. im_E:
+ *   A_0 E^i = eta_t E*^i + A_1 (E*_k u^k) u^i + A_2 eps^{ijk} u_j E*_k + A_3 B^i
+ *             + A_4 (B_k u^k) u^i + A_5 eps^{ijk} u_j B_k
+ * with the A_k(W) of Sec. 2.4, and its derivative dE^i/du^j from the Sec. 2.4
+ * expression (with the A_k' printed there).  Returns W. */
 static double efield(const OCell* c, const double* u, double* E, double dE[3][3])
 {
     double g = c->g, sg = c->sg;
@@ -268,33 +273,52 @@ static double efield(const OCell* c, const double* u, double* E, double dE[3][3]
         }
         return W;
     }
-    double et = c->etat;
-    double A0 = W + et;
-    double A1 = et / (1.0 + et * W);
-    double A5 = -1.0;
-    double A0d = 1.0;
-    double A1d = -et * et / ((1.0 + W * et) * (1.0 + W * et));
-    double Esu = 0, eps_uB[3];
-    for (int k = 0; k < 3; k++) Esu += Es_lo[k] * u[k];
+    double et = c->etat, xi = c->xi, x2 = xi * xi;
+    double p = W + et, q = 1.0 + et * W;
+    double A0 = W + et + x2 * (W * W - 1.0) / p;
+    double A1 = et / q + x2 * et * W / (p * q);
+    double A2 = -xi * et / p;
+    double A3 = xi * q / p;
+    double A4 = xi * (1.0 - et * et + x2) / (p * q);
+    double A5 = -1.0 - x2 * W / p;
+    double A0d = 1.0 + x2 * (1.0 + W * W + 2.0 * W * et) / (p * p);
+    double A1d = -et * et / (q * q) - x2 * et * et * (W * W - 1.0) / (q * q * p * p);
+    double A2d = xi * et / (p * p);
+    double A3d = xi * (et * et - 1.0) / (p * p);
+    double A4d = -xi * (1.0 - et * et + x2) * (1.0 + et * et + 2.0 * W * et) / (q * q * p * p);
+    double A5d = -x2 * et / (p * p);
+    double Esu = 0, Bu = 0, eps_uEs[3], eps_uB[3];
+    for (int k = 0; k < 3; k++) { Esu += Es_lo[k] * u[k]; Bu += B_lo[k] * u[k]; }
     for (int i = 0; i < 3; i++) {
-        double s = 0;
+        double s1 = 0, s2 = 0;
         for (int j = 0; j < 3; j++)
-            for (int k = 0; k < 3; k++) s += levi(i, j, k) / sg * u_lo[j] * B_lo[k];
-        eps_uB[i] = s;
+            for (int k = 0; k < 3; k++) {
+                s1 += levi(i, j, k) / sg * u_lo[j] * Es_lo[k];
+                s2 += levi(i, j, k) / sg * u_lo[j] * B_lo[k];
+            }
+        eps_uEs[i] = s1;
+        eps_uB[i] = s2;
     }
     for (int i = 0; i < 3; i++)
-        E[i] = (et * c->Es[i] + A1 * Esu * u[i] + A5 * eps_uB[i]) / A0;
+        E[i] = (et * c->Es[i] + A1 * Esu * u[i] + A2 * eps_uEs[i] + A3 * c->B[i] + A4 * Bu * u[i] + A5 * eps_uB[i]) / A0;
     if (dE) {
-        /* A_0 W dE^i/du^j = -A0' E^i u_j + A_1 W u^i E*_j + (A_1 W delta^i_j + A1' u^i u_j)(E*_k u^k)
-         *                   + eps^{ilm} (A_5 W gamma_lj + A5' u_l u_j) B_m,   A5' = 0 */
+        /* A_0 W dE^i/du^j = -A0' E^i u_j + A_1 W u^i E*_j + A3' B^i u_j + A_4 W u^i B_j
+         *   + (A_1 W delta^i_j + A1' u^i u_j)(E*_k u^k) + eps^{ilm}(A_2 W gamma_lj + A2' u_l u_j) E*_m
+         *   + (A_4 W delta^i_j + A4' u^i u_j)(B_k u^k) + eps^{ilm}(A_5 W gamma_lj + A5' u_l u_j) B_m */
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) {
-                double t = -A0d * E[i] * u_lo[j] + A1 * W * u[i] * Es_lo[j]
-                           + (A1 * W * (i == j ? 1.0 : 0.0) + A1d * u[i] * u_lo[j]) * Esu;
+                double dl = (i == j ? 1.0 : 0.0);
+                double t = -A0d * E[i] * u_lo[j] + A1 * W * u[i] * Es_lo[j] + A3d * c->B[i] * u_lo[j]
+                           + A4 * W * u[i] * B_lo[j]
+                           + (A1 * W * dl + A1d * u[i] * u_lo[j]) * Esu
+                           + (A4 * W * dl + A4d * u[i] * u_lo[j]) * Bu;
                 double s = 0;
                 for (int l = 0; l < 3; l++)
-                    for (int m = 0; m < 3; m++)
-                        s += levi(i, l, m) / sg * (A5 * W * (l == j ? g : 0.0)) * B_lo[m];
+                    for (int m = 0; m < 3; m++) {
+                        double glj = (l == j ? g : 0.0);
+                        s += levi(i, l, m) / sg * ((A2 * W * glj + A2d * u_lo[l] * u_lo[j]) * Es_lo[m]
+                                                   + (A5 * W * glj + A5d * u_lo[l] * u_lo[j]) * B_lo[m]);
+                    }
                 dE[i][j] = (t + s) / (A0 * W);
             }
     }
@@ -740,7 +764,7 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
 /* exported API                                                         */
 /* ------------------------------------------------------------------ */
 
-/* gi: ndim, n0, n1, n2, bc0, bc1, bc2 ; gd: dx0, dx1, dx2, Gamma, rho_atm, p_atm.
+/* gi: ndim, n0, n1, n2, bc0, bc1, bc2 ; gd: dx0, dx1, dx2, Gamma, rho_atm, p_atm, xi.
  * All arrays padded. */
 
 /* staggered q_B from an edge vector potential (Sec. 4, q_B^i = eta^{ijk} d_j A_k with
@@ -788,7 +812,7 @@ void orc_prim2con(const int* gi, const double* gd, double* const* prim, double* 
 }
 
 /* single-cell implicit solve, exposed for the pins.  in: D, S_i, tau, E*^i, B^i
- * (undensitised), psi, eta_tilde (< 0: E fixed), Gamma, initial guess (NULL: rest).
+ * (undensitised), xi; psi, eta_tilde (< 0: E fixed), Gamma, initial guess (NULL: rest).
  * out: u^i, E^i, rho, p.  returns Newton iterations or -1 */
 int orc_solve_cell(const double* in, double psi, double etat, double Gam, const double* guess, double* u, double* E,
                    double* rho_p)
@@ -799,6 +823,7 @@ int orc_solve_cell(const double* in, double psi, double etat, double Gam, const 
     c.tau = in[4];
     c.g = pow(psi, 4); c.sg = pow(psi, 6);
     c.etat = etat; c.Gh = Gam / (Gam - 1.0);
+    c.xi = in[11];
     for (int i = 0; i < 3; i++) u[i] = guess ? guess[i] : 0.0;
     return newton_cell(&c, u, E, &rho_p[0], &rho_p[1], 100, 1e-14);
 }
@@ -812,6 +837,7 @@ void orc_residual_cell(const double* in, double psi, double etat, double Gam, co
     c.tau = in[4];
     c.g = pow(psi, 4); c.sg = pow(psi, 6);
     c.etat = etat; c.Gh = Gam / (Gam - 1.0);
+    c.xi = in[11];
     double J[3][3];
     residual(&c, u, f, J, E, NULL, NULL);
     for (int i = 0; i < 3; i++) for (int j = 0; j < 3; j++) J9[3 * i + j] = J[i][j];
@@ -843,6 +869,7 @@ int orc_implicit(const int* gi, const double* gd, double a_dt, double** q, doubl
         double ps = psi_at(psi, c), sg = pow(ps, 6);
         OCell cl;
         cl.g = pow(ps, 4); cl.sg = sg; cl.Gh = G.Gam / (G.Gam - 1.0);
+        cl.xi = G.xi;
         cl.D = q[0][c] / sg; cl.tau = q[4][c] / sg;
         for (int i = 0; i < 3; i++) { cl.S[i] = q[1 + i][c] / sg; cl.Es[i] = q[5 + i][c] / sg; cl.B[i] = qBc[i][c] / sg; }
         double et = eta ? eta[c] : eta_u;

@@ -7,6 +7,7 @@
 #include <new>
 
 #include "../../include/grmhd.h"
+#include "capi_internal.h"
 #include "kernels.h"
 
 using namespace grmhd;
@@ -194,6 +195,28 @@ P3 p3(double* const* p)
 }
 
 bool emf_needed(const Dims& g, int c) { return g.act[(c + 1) % 3] || g.act[(c + 2) % 3]; }
+
+ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE_out, F11 p32)
+{
+    ImpArgs a;
+    a.qb = qb;
+    a.bf = bf;
+    a.psi = c->psi;
+    a.alp = c->alp;
+    a.eta = c->eta;
+    a.eta_u = c->eta_u;
+    a.a_dt = a_dt;
+    a.prim = prim;
+    a.R = R;
+    a.qE_out = qE_out;
+    a.kmax = c->par.newton_kmax;
+    a.tol = c->par.newton_tol;
+    a.rho_atm = c->par.rho_atm;
+    a.p_atm = c->par.p_atm;
+    a.p32 = p32;
+    a.nfail = c->nfail;
+    return a;
+}
 
 F11 f11(grmhd_ctx* c)
 {
@@ -489,51 +512,22 @@ grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
     if (i < 0 || i >= c->tab.s) return fail(GRMHD_ERR_ARG, "stage index out of range");
     if (!(dt > 0.0)) return fail(GRMHD_ERR_ARG, "dt must be positive");
     cudaStream_t st = (cudaStream_t)stream;
-    const int S = c->tab.s;
     cudaError_t e;
     if (i == 0 && c->any_fixed) {
-        // FIXED boundaries: the later stages' face arrays carry the boundary values too
-        for (int k = 1; k < S; k++)
-            for (int v = 0; v < 3; v++) {
-                e = cudaMemcpyAsync(c->base[k][8 + v], c->bf[v], sizeof(double) * (size_t)c->g.ncell,
-                                    cudaMemcpyDeviceToDevice, st);
-                if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
-            }
+        e = ctx_copy_fixed_faces(c, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     }
-    double* const* qb = i == 0 ? c->q : c->base[i];
-    double* const* fb = i == 0 ? c->bf : c->base[i] + 8;
-    const double a_dt = c->tab.A[i * S + i] * dt;
-    P3 none = p3(nullptr);
+    ImpArgs ia;
+    UpdateArgs a;
+    ctx_stage_args(c, i, dt, &ia, &a);
     const int tk = tbegin(c, KIND_IMPLICIT, st);
-    e = launch_implicit(c->g, cp8(qb), cp3(fb), c->psi, c->alp, c->eta, c->eta_u, a_dt, p8(c->prim), p3(c->R), none,
-                        c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, f11(c), c->nfail, c->nsm,
-                        st);
+    e = launch_implicit(c->g, ia, c->nsm, st);
     tend(c, tk, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
-    UpdateArgs a;
-    memset(&a, 0, sizeof a);
-    a.mode = UPD_STAGE;
-    a.stage = i;
-    a.s = S;
-    a.dt = dt;
-    for (int r = 0; r < S; r++) {
-        for (int k = 0; k < S; k++) {
-            a.At[r][k] = c->tab.At[r * S + k];
-            a.A[r][k] = c->tab.A[r * S + k];
-        }
-        a.wt[r] = c->tab.wt[r];
-        a.w[r] = c->tab.w[r];
-    }
-    for (int v = 0; v < 3; v++) a.R[v] = c->R[v];
-    for (int v = 0; v < 8; v++) a.qn[v] = c->q[v];
-    for (int v = 0; v < 3; v++) a.qn[8 + v] = c->bf[v];
-    for (int k = 1; k < S; k++)
-        for (int v = 0; v < 11; v++) a.base[k][v] = c->base[k][v];
-    for (int v = 0; v < 11; v++) a.acc[v] = c->acc[v];
     CP8 pr;
     for (int v = 0; v < 8; v++) pr.p[v] = c->prim[v];
-    return explicit_part(c, pr, cp3(fb), a, st);
+    return explicit_part(c, pr, ia.bf, a, st);
 }
 
 grmhd_status grmhd_step(grmhd_ctx* c, double dt, grmhd_stream_t stream)
@@ -559,9 +553,8 @@ grmhd_status grmhd_get_prims(grmhd_ctx* c, double* const* prim_out, grmhd_stream
                             st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     }
-    e = launch_implicit(c->g, cp8(c->q), cp3(c->bf), c->psi, c->alp, c->eta, c->eta_u, 0.0, p8(prim_out),
-                        p3(nullptr), p3(nullptr), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm, c->par.p_atm, F11{},
-                        c->nfail, c->nsm, st);
+    e = launch_implicit(c->g, imp_args(c, cp8(c->q), cp3(c->bf), 0.0, p8(prim_out), p3(nullptr), p3(nullptr), F11{}),
+                        c->nsm, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "con2prim kernel");
     return GRMHD_OK;
@@ -573,9 +566,8 @@ grmhd_status grmhd_implicit(grmhd_ctx* c, double a_dt, double* const* q, const d
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     if (!q || !bface || !prim || !R) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_implicit");
-    cudaError_t e = launch_implicit(c->g, cp8(q), cp3c(bface), c->psi, c->alp, c->eta, c->eta_u, a_dt, p8(prim),
-                                    p3(R), p3(q + 5), c->par.newton_kmax, c->par.newton_tol, c->par.rho_atm,
-                                    c->par.p_atm, F11{}, c->nfail, c->nsm, (cudaStream_t)stream);
+    cudaError_t e = launch_implicit(c->g, imp_args(c, cp8(q), cp3c(bface), a_dt, p8(prim), p3(R), p3(q + 5), F11{}),
+                                    c->nsm, (cudaStream_t)stream);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
     return GRMHD_OK;
@@ -630,3 +622,102 @@ long long grmhd_launch_count(const grmhd_ctx* c) { return c ? c->launches : 0; }
 const char* grmhd_last_error(void) { return g_err; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// accessors for the batched executor (capi_internal.h)
+// ---------------------------------------------------------------------------
+
+const Dims& ctx_dims(const grmhd_ctx* c) { return c->g; }
+bool ctx_metric(const grmhd_ctx* c) { return c->psi || c->alp; }
+bool ctx_bound(const grmhd_ctx* c) { return c->bound; }
+bool ctx_mixed(const grmhd_ctx* c) { return c->mixed; }
+bool ctx_any_fixed(const grmhd_ctx* c) { return c->any_fixed; }
+int ctx_stages(const grmhd_ctx* c) { return c->tab.s; }
+int ctx_nsm(const grmhd_ctx* c) { return c->nsm; }
+
+bool ctx_same_scheme(const grmhd_ctx* a, const grmhd_ctx* b)
+{
+    if (a->mixed != b->mixed || a->tab.s != b->tab.s) return false;
+    const int n = a->tab.s * a->tab.s;
+    for (int k = 0; k < n; k++)
+        if (a->tab.At[k] != b->tab.At[k] || a->tab.A[k] != b->tab.A[k]) return false;
+    for (int k = 0; k < a->tab.s; k++)
+        if (a->tab.wt[k] != b->tab.wt[k] || a->tab.w[k] != b->tab.w[k]) return false;
+    return true;
+}
+
+void ctx_stage_args(grmhd_ctx* c, int i, double dt, ImpArgs* ia, UpdateArgs* a)
+{
+    const int S = c->tab.s;
+    double* const* qb = i == 0 ? c->q : c->base[i];
+    double* const* fb = i == 0 ? c->bf : c->base[i] + 8;
+    const double a_dt = c->tab.A[i * S + i] * dt;
+    *ia = imp_args(c, cp8(qb), cp3(fb), a_dt, p8(c->prim), p3(c->R), p3(nullptr), f11(c));
+    memset(a, 0, sizeof *a);
+    a->mode = UPD_STAGE;
+    a->stage = i;
+    a->s = S;
+    a->dt = dt;
+    for (int r = 0; r < S; r++) {
+        for (int k = 0; k < S; k++) {
+            a->At[r][k] = c->tab.At[r * S + k];
+            a->A[r][k] = c->tab.A[r * S + k];
+        }
+        a->wt[r] = c->tab.wt[r];
+        a->w[r] = c->tab.w[r];
+    }
+    for (int v = 0; v < 3; v++) a->R[v] = c->R[v];
+    for (int v = 0; v < 8; v++) a->qn[v] = c->q[v];
+    for (int v = 0; v < 3; v++) a->qn[8 + v] = c->bf[v];
+    for (int k = 1; k < S; k++)
+        for (int v = 0; v < 11; v++) a->base[k][v] = c->base[k][v];
+    for (int v = 0; v < 11; v++) a->acc[v] = c->acc[v];
+}
+
+float* ctx_p32(grmhd_ctx* c, int v) { return c->p32[v]; }
+double* ctx_flux64(grmhd_ctx* c, int d, int v) { return d < c->grid.ndim ? c->F[d][v] : nullptr; }
+float* ctx_flux32(grmhd_ctx* c, int d, int v) { return d < c->grid.ndim ? c->F32[d][v] : nullptr; }
+double* ctx_emf64(grmhd_ctx* c, int k) { return c->Eh[k]; }
+float* ctx_emf32(grmhd_ctx* c, int k) { return c->Eh32[k]; }
+
+cudaError_t ctx_copy_fixed_faces(grmhd_ctx* c, cudaStream_t st)
+{
+    for (int k = 1; k < c->tab.s; k++)
+        for (int v = 0; v < 3; v++) {
+            cudaError_t e = cudaMemcpyAsync(c->base[k][8 + v], c->bf[v], sizeof(double) * (size_t)c->g.ncell,
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+grmhd_status batch_fail(grmhd_status s, const char* msg)
+{
+    grmhd::set_last_error(msg);
+    return s;
+}
+
+cudaError_t ctx_save_guess(grmhd_ctx* c, std::vector<double>& host, cudaStream_t st)
+{
+    const size_t n = (size_t)c->g.ncell;
+    host.resize(8 * n + 1);
+    for (int v = 0; v < 8; v++) {
+        cudaError_t e = cudaMemcpyAsync(host.data() + v * n, c->prim[v], n * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(host.data() + 8 * n, c->nfail, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t ctx_restore_guess(grmhd_ctx* c, const std::vector<double>& host, cudaStream_t st)
+{
+    const size_t n = (size_t)c->g.ncell;
+    for (int v = 0; v < 8; v++) {
+        cudaError_t e = cudaMemcpyAsync(c->prim[v], host.data() + v * n, n * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->nfail, host.data() + 8 * n, sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}

@@ -1,0 +1,453 @@
+// Per-item bodies of the stage kernels (one cell, face or edge each), shared by
+// the single-problem kernels (kernels.cu) and the batched multi-problem kernels
+// (batch.cu), so that a problem advanced alone or inside a batch runs exactly the
+// same arithmetic.  See kernels.cu for the paper passages each body follows.
+#pragma once
+
+#include "grmhd_device.cuh"
+#include "kernels.h"
+
+namespace grmhd {
+
+// ---------------------------------------------------------------------------
+// implicit step (Sec. 2.4): item t = interior cell t (x fastest)
+// ---------------------------------------------------------------------------
+
+template <bool M>
+__device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, long long t)
+{
+    // flat metric: alpha = psi = 1 known at compile time
+    const double* __restrict__ psi = M ? a.psi : nullptr;
+    const double* __restrict__ alp = M ? a.alp : nullptr;
+    const CP8& qb = a.qb;
+    const CP3& bf = a.bf;
+    const double* __restrict__ eta = a.eta;
+    const double eta_u = a.eta_u, a_dt = a.a_dt, tol = a.tol, rho_atm = a.rho_atm, p_atm = a.p_atm;
+    const int kmax = a.kmax;
+    const P8& prim = a.prim;
+    const P3& R = a.R;
+    const P3& qE_out = a.qE_out;
+    const F11& p32 = a.p32;
+    unsigned long long* nfail = a.nfail;
+    int c[3];
+    c[0] = g.ng[0] + (int)(t % g.n[0]);
+    c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
+    c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+    const long long id = lin(g, c[0], c[1], c[2]);
+    const double ps = psi ? psi[id] : 1.0;
+    const double al = alp ? alp[id] : 1.0;
+    const double p2 = ps * ps, p4 = p2 * p2, ip2 = 1.0 / p2, ip4 = ip2 * ip2, ip6 = ip4 * ip2;
+    CellIn ci;
+    ci.gh = g.gh;
+    ci.igh = g.igh;
+    ci.D = qb.p[0][id] * ip6;
+    ci.S[0] = qb.p[1][id] * ip6 * ip2;
+    ci.S[1] = qb.p[2][id] * ip6 * ip2;
+    ci.S[2] = qb.p[3][id] * ip6 * ip2;
+    ci.tau = qb.p[4][id] * ip6;
+    double qEs[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        qEs[i] = qb.p[5 + i][id];
+        ci.Es[i] = qEs[i] * ip4;
+        ci.B[i] = cell_qB(g, bf.p[i], i, c) * ip4;
+    }
+    const double et = eta ? eta[id] : eta_u;
+    ci.etat = a_dt > 0.0 ? et / (al * a_dt) : -1.0;
+    double u[3];
+    Eval e;
+    bool atmo = false;
+    if (rho_atm > 0.0 && ci.D < 10.0 * rho_atm) {
+        atmo = true;
+    } else {
+        bool fin = true;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            u[i] = p2 * prim.p[1 + i][id];
+            if (!(fabs(u[i]) < 1e30)) fin = false;
+        }
+        if (!fin) u[0] = u[1] = u[2] = 0.0;
+        int it = newton_solve(ci, u, e, kmax, tol);
+        if (it < 0 && fin) {
+            u[0] = u[1] = u[2] = 0.0;
+            it = newton_solve(ci, u, e, kmax, tol);
+        }
+        if (it < 0) {
+            atomicAdd(nfail, 1ull);
+            if (!(rho_atm > 0.0)) {
+                // no atmosphere: leave the cell's primitives as they were, no stiff update
+                if (R.p[0])
+#pragma unroll
+                    for (int i = 0; i < 3; i++) R.p[i][id] = 0.0;
+                return;
+            }
+            atmo = true;
+        }
+    }
+    double rho, pres;
+    if (atmo) {
+        // atmosphere: rest state at the floor density and pressure, E kept
+        rho = rho_atm;
+        pres = p_atm;
+        u[0] = u[1] = u[2] = 0.0;
+        e.E[0] = ci.Es[0];
+        e.E[1] = ci.Es[1];
+        e.E[2] = ci.Es[2];
+    } else {
+        const double iW = 1.0 / e.W;
+        rho = ci.D * iW;
+        pres = (e.wt * iW - rho) * g.igh;
+    }
+    prim.p[0][id] = rho;
+    prim.p[4][id] = pres;
+    if (p32.p[0]) {
+        // FP32 copy for the mixed-precision explicit kernels, with the densitised
+        // cell-centred q_B of the stage
+        p32.p[0][id] = (float)rho;
+        p32.p[4][id] = (float)pres;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            p32.p[1 + i][id] = (float)(u[i] * ip2);
+            p32.p[5 + i][id] = (float)(e.E[i] * ip2);
+            p32.p[8 + i][id] = (float)(ci.B[i] * p4);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        prim.p[1 + i][id] = u[i] * ip2;
+        prim.p[5 + i][id] = e.E[i] * ip2;
+        const double qEn = p4 * e.E[i];
+        if (R.p[0]) R.p[i][id] = a_dt > 0.0 ? (qEn - qEs[i]) / a_dt : 0.0;
+        if (qE_out.p[0]) qE_out.p[i][id] = qEn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// face fluxes (Sec. 2.1, Sec. 2.5, Sec. 5 defaults): item t = D-face t
+// ---------------------------------------------------------------------------
+
+// cell-centred densitised q_B^e of the (mapped) cell: from the staggered faces on
+// the FP64 path, from the stage's FP32 copy on the mixed path
+__device__ __forceinline__ double cell_qB_in(const Dims& g, const PrimIn<double>&, const CP3& bf, int e, const int* cs,
+                                             long long)
+{
+    return cell_qB(g, bf.p[e], e, cs);
+}
+__device__ __forceinline__ float cell_qB_in(const Dims&, const PrimIn<float>& pa, const CP3&, int e, const int*,
+                                            long long mi)
+{
+    return pa.p[8 + e][mi];
+}
+
+template <int D, bool M, typename T>
+__device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
+                                          const double* alp_in, const FluxOut<T>& F, long long t)
+{
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    const double* __restrict__ alp = M ? alp_in : nullptr;
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1);
+    int c[3];
+    c[0] = g.ng[0] + (int)(t % e0);
+    c[1] = g.ng[1] + (int)((t / e0) % e1);
+    c[2] = g.ng[2] + (int)(t / ((long long)e0 * e1));
+    long long mi[4], ri[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        int cs[3] = {c[0], c[1], c[2]};
+        cs[D] += s - 2;
+        mi[s] = cell_at(g, cs);
+        ri[s] = lin(g, cs[0], cs[1], cs[2]);
+    }
+    T prL[8], prR[8], BL[3], BR[3];
+#pragma unroll
+    for (int v = 0; v < 8; v++) {
+        const T* a = prim.p[v];
+        mc_face<T>(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3]], prL[v], prR[v]);
+    }
+    // transverse cell-centred B (primitive = q_B / psi^6 at the cell)
+#pragma unroll
+    for (int tt = 0; tt < 2; tt++) {
+        const int e = tt == 0 ? T1 : T2;
+        T b[4];
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            cs[D] += s - 2;
+            const T ps = psi ? (T)psi[ri[s]] : T(1);
+            const T p2 = ps * ps;
+            b[s] = (T)cell_qB_in(g, prim, bf, e, cs, mi[s]) / (p2 * p2 * p2);
+        }
+        mc_face<T>(b[0], b[1], b[2], b[3], BL[e], BR[e]);
+    }
+    const T psf = psi ? (T)(0.5 * (psi[ri[1]] + psi[ri[2]])) : T(1);
+    const T alf = alp ? (T)(0.5 * (alp[ri[1]] + alp[ri[2]])) : T(1);
+    const T pf2 = psf * psf;
+    const T bn = (T)bf.p[D][face_at(g, D, c)] / (pf2 * pf2 * pf2);
+    BL[D] = bn;
+    BR[D] = bn;
+    FaceStateT<T> sL, sR;
+    face_state<T>(prL, BL, D, psf, alf, (T)g.gh, sL);
+    face_state<T>(prR, BR, D, psf, alf, (T)g.gh, sR);
+    // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity)
+    const T cs = alf / pf2;
+    const long long o = lin(g, c[0], c[1], c[2]);
+#pragma unroll
+    for (int v = 0; v < 8; v++)
+        F.p[v][o] = (cs * sL.f[v] + cs * sR.f[v] - cs * cs * (sR.q[v] - sL.q[v])) / (cs + cs);
+}
+
+// ---------------------------------------------------------------------------
+// upwind constrained transport (Sec. 3.2): item t = C-edge t
+// ---------------------------------------------------------------------------
+
+template <int C, bool M, typename T>
+__device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
+                                         const double* alp_in, T* __restrict__ Eh, long long t)
+{
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    const double* __restrict__ alp = M ? alp_in : nullptr;
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    const bool aa = g.act[A], ba = g.act[B];
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) e[d] = (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    const T* __restrict__ Ec = prim.p[5 + C];
+    int c[3];
+    c[0] = g.ng[0] + (int)(t % e[0]);
+    c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
+    c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+    // steps (ii)-(iii): covariant E_C = psi^4 E^C, to A-faces then along B
+    T s[2][4];   // [X = A-side L/R][B offset -2..+1]
+    const int nb = ba ? 4 : 1;
+    for (int ob = 0; ob < nb; ob++) {
+        int cb[3] = {c[0], c[1], c[2]};
+        if (ba) cb[B] += ob - 2;
+        if (aa) {
+            T v[4];
+#pragma unroll
+            for (int sa = 0; sa < 4; sa++) {
+                int cs[3] = {cb[0], cb[1], cb[2]};
+                cs[A] += sa - 2;
+                const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
+                const T p2 = ps * ps;
+                v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
+            }
+            mc_face<T>(v[0], v[1], v[2], v[3], s[0][ob], s[1][ob]);
+        } else {
+            const T ps = psi ? (T)psi[lin(g, cb[0], cb[1], cb[2])] : T(1);
+            const T p2 = ps * ps;
+            s[0][ob] = s[1][ob] = p2 * p2 * Ec[cell_at(g, cb)];
+        }
+    }
+    T EXY[2][2];
+#pragma unroll
+    for (int X = 0; X < 2; X++) {
+        if (ba) mc_face<T>(s[X][0], s[X][1], s[X][2], s[X][3], EXY[X][0], EXY[X][1]);
+        else EXY[X][0] = EXY[X][1] = s[X][0];
+    }
+    // step (iv): q_B^B (B-faces) along A, q_B^A (A-faces) along B
+    T qBbL, qBbR, qBaL, qBaR;
+    if (aa) {
+        T v[4];
+#pragma unroll
+        for (int sa = 0; sa < 4; sa++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            cs[A] += sa - 2;
+            v[sa] = (T)bf.p[B][face_at(g, B, cs)];
+        }
+        mc_face<T>(v[0], v[1], v[2], v[3], qBbL, qBbR);
+    } else {
+        qBbL = qBbR = (T)bf.p[B][face_at(g, B, c)];
+    }
+    if (ba) {
+        T v[4];
+#pragma unroll
+        for (int sb = 0; sb < 4; sb++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            cs[B] += sb - 2;
+            v[sb] = (T)bf.p[A][face_at(g, A, cs)];
+        }
+        mc_face<T>(v[0], v[1], v[2], v[3], qBaL, qBaR);
+    } else {
+        qBaL = qBaR = (T)bf.p[A][face_at(g, A, c)];
+    }
+    // lapse at the edge (mean of the adjacent cells) and the face speeds
+    const long long i0 = lin(g, c[0], c[1], c[2]);
+    const long long sA = aa ? g.st[A] : 0, sB = ba ? g.st[B] : 0;
+    T ale = T(1), ca = T(1), cb = T(1);
+    if (alp || psi) {
+        int nce = 1;
+        double sum = alp ? alp[i0] : 1.0;
+        if (aa) { sum += alp ? alp[i0 - sA] : 1.0; nce++; }
+        if (ba) {
+            sum += alp ? alp[i0 - sB] : 1.0; nce++;
+            if (aa) { sum += alp ? alp[i0 - sA - sB] : 1.0; nce++; }
+        }
+        ale = (T)(sum / nce);
+        if (aa) {
+            double cmax = 0.0;
+            for (int tt = 0; tt < (ba ? 2 : 1); tt++) {
+                const long long cf = i0 - tt * sB, cfm = cf - sA;
+                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+                cmax = fmax(cmax, alf / (psf * psf));
+            }
+            ca = (T)cmax;
+        }
+        if (ba) {
+            double cmax = 0.0;
+            for (int tt = 0; tt < (aa ? 2 : 1); tt++) {
+                const long long cf = i0 - tt * sA, cfm = cf - sB;
+                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+                cmax = fmax(cmax, alf / (psf * psf));
+            }
+            cb = (T)cmax;
+        }
+    }
+    // steps (v)-(vii): hat{E}^{XY} = alpha E_C^{XY}; Londrillo & Del Zanna (2004)
+    const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
+    Eh[i0] = (ca * cb * hLL + ca * cb * hLR + ca * cb * hRL + ca * cb * hRR) / ((ca + ca) * (cb + cb)) +
+             ca * ca / (ca + ca) * (qBbR - qBbL) - cb * cb / (cb + cb) * (qBaR - qBaL);
+}
+
+// ---------------------------------------------------------------------------
+// update (Sec. 2.1 sources, Sec. 3.2 CT, Sec. 2.3 stage folds): item t = cell/face t
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void out_value(const UpdateArgs& a, int v, long long o, double L, bool has_r)
+{
+    if (a.mode == UPD_WRITE_L) {
+        a.L[v][o] = L;
+        return;
+    }
+    const double r = has_r ? a.R[v - 5][o] : 0.0;
+    const double qn = a.qn[v][o];
+    for (int k = a.stage + 1; k < a.s; k++) {
+        const double prev = a.stage == 0 ? qn : a.base[k][v][o];
+        a.base[k][v][o] = prev + a.dt * (a.At[k][a.stage] * L + a.A[k][a.stage] * r);
+    }
+    const double prev = a.stage == 0 ? qn : a.acc[v][o];
+    const double nv = prev + a.dt * (a.wt[a.stage] * L + a.w[a.stage] * r);
+    if (a.stage == a.s - 1) a.qn[v][o] = nv;
+    else a.acc[v][o] = nv;
+}
+
+template <bool M, typename T>
+__device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, long long t)
+{
+    // flat metric: alpha = psi = 1 known at compile time
+    const double* __restrict__ psi = M ? a.psi : nullptr;
+    const double* __restrict__ alp = M ? a.alp : nullptr;
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) e[d] = g.act[d] ? g.n[d] + 1 : 1;
+    int c[3];
+    c[0] = g.ng[0] + (int)(t % e[0]);
+    c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
+    c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+    bool interior = true;
+#pragma unroll
+    for (int d = 0; d < 3; d++)
+        if (c[d] >= g.ng[d] + g.n[d]) interior = false;
+    const long long o = lin(g, c[0], c[1], c[2]);
+    if (interior) {
+        double Lc[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) Lc[v] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!g.act[d]) continue;
+            const long long o1 = o + g.st[d];
+#pragma unroll
+            for (int v = 0; v < 8; v++) {
+                const T* __restrict__ Fv = (const T*)a.F[d][v];
+                Lc[v] -= ((double)Fv[o1] - (double)Fv[o]) * g.idx[d];
+            }
+        }
+        const double ps = psi ? psi[o] : 1.0;
+        const double al = alp ? alp[o] : 1.0;
+        const double p2 = ps * ps, p4 = p2 * p2, p6 = p4 * p2;
+        double u[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) u[i] = a.prim[1 + i][o];
+        const double W = sqrt(1.0 + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+        const double iW = 1.0 / W;
+        // Gauss law: sqrt(gamma) rho_e = div q_E by central differences
+        double divqE = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!g.act[d]) continue;
+            int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+            cp[d] += 1;
+            cm[d] -= 1;
+            double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
+            sp = sp * sp;
+            sm = sm * sm;
+            const double qp = sp * sp * sp * a.prim[5 + d][cell_at(g, cp)];
+            const double qm = sm * sm * sm * a.prim[5 + d][cell_at(g, cm)];
+            divqE += (qp - qm) * (0.5 * g.idx[d]);
+        }
+        // s_E (non-stiff part) = -alpha sqrt(gamma) rho_e v^i
+#pragma unroll
+        for (int i = 0; i < 3; i++) Lc[5 + i] -= al * divqE * (u[i] * iW);
+        if (psi || alp) {
+            // s_S and s_tau for beta = 0, K_ij = 0 (Sec. 2.1) in the orthonormal frame:
+            //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
+            //   s_tau = -psi^4 S_hat_i d_i alpha
+            const double rho = a.prim[0][o], p = a.prim[4][o];
+            double uh[3], Eh[3], Bh[3];
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                uh[i] = p2 * u[i];
+                Eh[i] = p2 * a.prim[5 + i][o];
+                Bh[i] = p2 * cell_qB(g, a.bf[i], i, c) / p6;
+            }
+            const double rhoh = rho + g.gh * p;
+            const double U = 0.5 * (Eh[0] * Eh[0] + Eh[1] * Eh[1] + Eh[2] * Eh[2] + Bh[0] * Bh[0] +
+                                    Bh[1] * Bh[1] + Bh[2] * Bh[2]);
+            const double D = rho * W;
+            const double tauD = rhoh * W * W - p + U;  // tau + D
+            double S[3];
+            S[0] = rhoh * W * uh[0] + (Eh[1] * Bh[2] - Eh[2] * Bh[1]);
+            S[1] = rhoh * W * uh[1] + (Eh[2] * Bh[0] - Eh[0] * Bh[2]);
+            S[2] = rhoh * W * uh[2] + (Eh[0] * Bh[1] - Eh[1] * Bh[0]);
+            const double tr = rhoh * (uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2]) + 3.0 * p + U;
+            (void)D;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                if (!g.act[i]) continue;
+                const double ap = alp ? alp[o + g.st[i]] : 1.0, am = alp ? alp[o - g.st[i]] : 1.0;
+                const double pp = psi ? psi[o + g.st[i]] : 1.0, pm = psi ? psi[o - g.st[i]] : 1.0;
+                const double dal = (ap - am) * (0.5 * g.idx[i]);
+                const double dps = (pp - pm) * (0.5 * g.idx[i]);
+                Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps / ps) * tr);
+                Lc[4] -= p4 * S[i] * dal;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 8; v++) out_value(a, v, o, Lc[v], v >= 5);
+    }
+    // CT: d q_B^fa / dt = -d_fb hat{E}_fc + d_fc hat{E}_fb  (fa, fb, fc cyclic)
+#pragma unroll
+    for (int fa = 0; fa < 3; fa++) {
+        const int fb = (fa + 1) % 3, fc = (fa + 2) % 3;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            int hi = g.ng[d] + g.n[d] - 1;
+            if (d == fa && g.act[d] && g.bc[d] != BC_PERIODIC) hi += 1;
+            if (c[d] > hi) ok = false;
+        }
+        if (!ok) continue;
+        double r = 0.0;
+        const T* __restrict__ Ec = (const T*)a.Eh[fc];
+        const T* __restrict__ Eb = (const T*)a.Eh[fb];
+        if (g.act[fb]) r -= ((double)Ec[o + g.st[fb]] - (double)Ec[o]) * g.idx[fb];
+        if (g.act[fc]) r += ((double)Eb[o + g.st[fc]] - (double)Eb[o]) * g.idx[fc];
+        out_value(a, 8 + fa, o, r, false);
+    }
+}
+
+}  // namespace grmhd

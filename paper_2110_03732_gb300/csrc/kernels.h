@@ -17,6 +17,42 @@ template <> struct PrimIn<float> { const float* p[11]; };
 template <typename T> struct FluxOut { T* p[8]; };
 struct F11 { float* p[11]; };
 
+// arguments of the implicit solve of one problem and stage
+struct ImpArgs {
+    CP8 qb;                 // stage base q (8)
+    CP3 bf;                 // stage face fields
+    const double* psi;
+    const double* alp;
+    const double* eta;      // per-cell resistivity or NULL
+    double eta_u;
+    double a_dt;            // a_ii dt (<= 0: E held fixed)
+    P8 prim;                // in: Newton start; out: stage primitives
+    P3 R;                   // stiff rates (or NULL)
+    P3 qE_out;              // solved q_E (or NULL)
+    int kmax;
+    double tol, rho_atm, p_atm;
+    F11 p32;                // FP32 copy for the mixed path (or NULL)
+    unsigned long long* nfail;
+};
+
+template <typename T>
+struct FluxArgs {
+    PrimIn<T> prim;
+    CP3 bf;
+    const double* psi;
+    const double* alp;
+    FluxOut<T> F;
+};
+
+template <typename T>
+struct EmfArgs {
+    PrimIn<T> prim;
+    CP3 bf;
+    const double* psi;
+    const double* alp;
+    T* Eh;
+};
+
 // Arguments of the update kernel.  Variables 0..7 are cell-centred (D, S_1..3, tau,
 // E^1..3), 8..10 are the face fields.
 struct UpdateArgs {
@@ -38,10 +74,7 @@ struct UpdateArgs {
     double* acc[11];        // running final combination
 };
 
-cudaError_t launch_implicit(const Dims& g, CP8 qb, CP3 bf, const double* psi, const double* alp, const double* eta,
-                            double eta_u, double a_dt, P8 prim, P3 R, P3 qE_out, int kmax, double tol,
-                            double rho_atm, double p_atm, F11 p32, unsigned long long* nfail, int nsm,
-                            cudaStream_t st);
+cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
                           const double* alp, FluxOut<float> F, int nsm, cudaStream_t st);
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,

@@ -72,13 +72,22 @@ def lib():
     L.grmhd_diagnostics.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp]
     L.grmhd_set_timing.argtypes = [vp, C.c_int]
     L.grmhd_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.grmhd_batch_scratch_bytes.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]
+    L.grmhd_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_size_t, C.POINTER(vp)]
+    L.grmhd_batch_set_dt.argtypes = [vp, C.POINTER(C.c_double), vp]
+    L.grmhd_batch_step.argtypes = [vp, vp]
+    L.grmhd_batch_autotune.argtypes = [vp, C.c_int, vp]
+    L.grmhd_batch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.grmhd_batch_destroy.argtypes = [vp]
     L.grmhd_launch_count.argtypes = [vp]
     L.grmhd_launch_count.restype = C.c_longlong
     L.grmhd_last_error.restype = C.c_char_p
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
                  "grmhd_set_metric", "grmhd_set_eta", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
                  "grmhd_step", "grmhd_get_prims", "grmhd_implicit", "grmhd_explicit_L", "grmhd_diagnostics",
-                 "grmhd_set_timing", "grmhd_kernel_times"):
+                 "grmhd_set_timing", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
+                 "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
+                 "grmhd_batch_destroy"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -277,3 +286,52 @@ class Solver:
 
     def interior(self):
         return tuple(slice(self.ng[d], self.ng[d] + self.grid.n[d]) for d in (2, 1, 0))
+
+
+class Batch:
+    """Many Solver problems advanced together (grmhd_batch_*): one launch per kernel
+    kind and stage covers all of them.  Each problem's results are bitwise those of
+    stepping it alone.  The solvers must share the tableau and the precision."""
+
+    KINDS = ("implicit", "flux_x", "flux_y", "flux_z", "emf_x", "emf_y", "emf_z", "update")
+
+    def __init__(self, solvers):
+        self.L = lib()
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        arr = (C.c_void_p * n)(*[s.ctx.value for s in self.solvers])
+        self._arr = arr
+        nb = C.c_size_t(0)
+        check(self.L.grmhd_batch_scratch_bytes(arr, n, C.byref(nb)), "batch_scratch_bytes")
+        dev = self.solvers[0].device
+        self.scratch = torch.zeros(max(nb.value, 1), dtype=torch.uint8, device=dev)
+        b = C.c_void_p()
+        check(self.L.grmhd_batch_create(arr, n, C.c_void_p(self.scratch.data_ptr()), nb.value, C.byref(b)),
+              "batch_create")
+        self.b = b
+        self.n = n
+
+    def __del__(self):
+        try:
+            if getattr(self, "b", None):
+                self.L.grmhd_batch_destroy(self.b)
+                self.b = None
+        except Exception:
+            pass
+
+    def set_dt(self, dts, stream=None):
+        arr = (C.c_double * self.n)(*[float(x) for x in dts])
+        check(self.L.grmhd_batch_set_dt(self.b, arr, _stream(stream)), "batch_set_dt")
+
+    def step(self, stream=None):
+        return check(self.L.grmhd_batch_step(self.b, _stream(stream)), "batch_step")
+
+    def autotune(self, reps=3, stream=None):
+        check(self.L.grmhd_batch_autotune(self.b, int(reps), _stream(stream)), "batch_autotune")
+        return self.config()
+
+    def config(self):
+        th = (C.c_int * 8)()
+        it = (C.c_int * 8)()
+        check(self.L.grmhd_batch_config(self.b, th, it), "batch_config")
+        return {k: (th[i], it[i]) for i, k in enumerate(self.KINDS)}

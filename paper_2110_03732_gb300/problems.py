@@ -361,3 +361,49 @@ def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2,
     eta_arr = 10.0 ** rng.uniform(math.log10(eta) - 1, math.log10(eta) + 1, shp)
     return Problem(f"random_box_{ndim}d", ndim, nn, lo, hi, [bc] * 3, gamma, prim, bface=bface, A_edge=A,
                    alpha=alpha, psi=psi, eta=eta_arr, eta_u=eta, cfl=0.4)
+
+
+# --------------------------------------------------------------------------
+# batched and served workloads
+# --------------------------------------------------------------------------
+
+def ot_batch(seed=0, n_boxes=256, sizes=(64, 128, 256, 512), eta_range=(-6.0, 0.0)):
+    """Independent 2-D Orszag-Tang boxes: side drawn uniformly from `sizes`, eta
+    log-uniform in 10^eta_range, phase shifts uniform in [0, 2 pi)^2 (seeded)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_boxes):
+        n = int(rng.choice(sizes))
+        eta = 10.0 ** rng.uniform(*eta_range)
+        ph = tuple(rng.uniform(0, 2 * math.pi, 2))
+        out.append(orszag_tang(n, eta=eta, phase=ph))
+    return out
+
+
+def request_stream(seed=0, n_requests=64, rate=200.0, tube_cells=(400, 4096), vortex_side=(128, 512),
+                   star_side=(64, 128), eta_range=(-6.0, 0.0), steps_2d3d=100):
+    """Seeded Poisson stream of runs: (arrival time [s], Problem, number of steps).
+    Kinds drawn uniformly: 1-D shock tube (cells in `tube_cells`, run to t = 0.4),
+    2-D Orszag-Tang (side in `vortex_side`, `steps_2d3d` steps), 3-D star (side in
+    `star_side`, `steps_2d3d` steps); eta log-uniform in 10^eta_range for every run."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n_requests):
+        t += rng.exponential(1.0 / rate)
+        kind = int(rng.integers(0, 3))
+        eta = 10.0 ** rng.uniform(*eta_range)
+        if kind == 0:
+            n = int(rng.integers(tube_cells[0], tube_cells[1] + 1))
+            pr = shock_tube(n, eta=eta)
+            steps = int(math.ceil(pr.t_end / (pr.cfl * (pr.hi[0] - pr.lo[0]) / n) - 1e-9))
+        elif kind == 1:
+            n = int(rng.integers(vortex_side[0], vortex_side[1] + 1))
+            pr = orszag_tang(n, eta=eta, phase=tuple(rng.uniform(0, 2 * math.pi, 2)))
+            steps = steps_2d3d
+        else:
+            n = int(rng.integers(star_side[0], star_side[1] + 1))
+            pr = star(n=n, eta_in=eta)
+            steps = steps_2d3d
+        out.append((t, pr, steps))
+    return out

@@ -203,3 +203,68 @@ def test_ssp2_tableau_order_conditions():
     # L-stability: stability function of the implicit part vanishes at infinity
     # R(z) = 1 + z w^T (I - z A)^{-1} 1 -> 1 - w^T A^{-1} 1
     assert abs(1 - w @ np.linalg.solve(A, np.ones(2))) < 1e-14
+
+
+def stiff_rhs_xi(u, E, B, psi, xi):
+    """-W{[E + v x B - (E.v)v] - xi [B - v x E - (B.v)v]} (Ohm's law with the
+    mean-field dynamo, Sec. 2.2; eta = 1), orthonormal components -> contravariant."""
+    g = psi ** 4
+    W = math.sqrt(1.0 + g * (u @ u))
+    vh, Eh, Bh = psi * psi * u / W, psi * psi * E, psi * psi * B
+    J = W * ((Eh + np.cross(vh, Bh) - (Eh @ vh) * vh) - xi * (Bh - np.cross(vh, Eh) - (Bh @ vh) * vh))
+    return -J / (psi * psi)
+
+
+@pytest.mark.parametrize("xi", [0.1, 0.5, 2.0])
+@pytest.mark.parametrize("psi", [1.0, 1.2])
+def test_dynamo_constructed_root(xi, psi):
+    """Sec. 2.4 with xi != 0: the printed A_k(W) must give back a constructed root of
+    E = E* - (W/eta_t){[E + v x B - (E.v)v] - xi[B - v x E - (B.v)v]}.  A strong dynamo
+    (xi = 2) can have a second physical root; a solve that lands there must still
+    satisfy every stage equation, and that may happen only rarely."""
+    rng = np.random.default_rng(21)
+    gam = 4.0 / 3.0
+    other = 0
+    for k in range(40):
+        rho, u, p, _, B = random_state(rng, psi)
+        etat = 10 ** rng.uniform(-3, 3)
+        W = math.sqrt(1 + psi ** 4 * (u @ u))
+        E = -np.cross(psi * psi * u / W, psi * psi * B) / (psi * psi) + min(0.5, etat) * rng.normal(0, 1, 3)
+        D, S, tau = p2c(rho, u, p, E, B, psi, gam)
+        Es = E - (1.0 / etat) * stiff_rhs_xi(u, E, B, psi, xi)
+        guess = u + rng.normal(0, 0.05, 3)
+        it, uu, EE, r, pp = oracle.solve_cell(D, S, tau, Es, B, psi, etat, gam, guess, xi=xi)
+        assert it > 0, k
+        if np.abs(uu - u).max() > 1e-8 and xi > 1.0:
+            other += 1
+            D2, S2, tau2 = p2c(r, uu, pp, EE, B, psi, gam)
+            assert abs(D2 - D) <= 1e-12 * D and abs(tau2 - tau) <= 1e-11 * (tau + D)
+            res = EE - Es - (1.0 / etat) * stiff_rhs_xi(uu, EE, B, psi, xi)
+            assert np.abs(res).max() <= 1e-10 * (1 + np.abs(Es).max()) and r > 0 and pp > 0
+            continue
+        np.testing.assert_allclose(uu, u, rtol=1e-10, atol=1e-11)
+        np.testing.assert_allclose(EE, E, rtol=1e-10, atol=1e-10 * (1 + np.abs(B).max()))
+    assert other <= 2
+
+
+@pytest.mark.parametrize("xi", [0.3, 1.5])
+def test_dynamo_jacobian_finite_difference(xi):
+    rng = np.random.default_rng(8)
+    gam, psi = 5.0 / 3.0, 1.15
+    for _ in range(15):
+        rho, u, p, E, B = random_state(rng, psi)
+        D, S, tau = p2c(rho, u, p, E, B, psi, gam)
+        Es = E + rng.normal(0, 0.3, 3)
+        etat = 10 ** rng.uniform(-2, 2)
+        ut = u + rng.normal(0, 0.2, 3)
+        f, J, _ = oracle.residual_cell(D, S, tau, Es, B, psi, etat, gam, ut, xi=xi)
+        Jfd = np.zeros((3, 3))
+        for j in range(3):
+            h = 1e-6 * (1 + abs(ut[j]))
+            up, um = ut.copy(), ut.copy()
+            up[j] += h
+            um[j] -= h
+            fp, _, _ = oracle.residual_cell(D, S, tau, Es, B, psi, etat, gam, up, xi=xi)
+            fm, _, _ = oracle.residual_cell(D, S, tau, Es, B, psi, etat, gam, um, xi=xi)
+            Jfd[:, j] = (fp - fm) / (2 * h)
+        np.testing.assert_allclose(J, Jfd, rtol=1e-6, atol=1e-6 * np.abs(J).max())
