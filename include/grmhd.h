@@ -120,6 +120,12 @@ grmhd_status grmhd_set_metric(grmhd_ctx* ctx, const double* alpha, const double*
 /* Resistivity (Sec. 2.2): eta_cc a padded cell array, or NULL for the uniform eta. */
 grmhd_status grmhd_set_eta(grmhd_ctx* ctx, const double* eta_cc, double eta_uniform);
 
+/* Mean-field dynamo (Sec. 2.2, Ohm's law e = xi b + eta j): uniform xi, 0 by
+ * default.  The implicit solve then uses the full A_k(W) of Sec. 2.4.  A strong
+ * dynamo can give the implicit system more than one physical root; the solve starts
+ * from the previous stage's velocity and so follows the root continuous in time. */
+grmhd_status grmhd_set_dynamo(grmhd_ctx* ctx, double xi);
+
 /* Initial state (Sec. 4 + Sec. 2.1): if A_edge is not NULL the face fields become
  * the discrete curl q_B^i = eta^{ijk} d_j A_k of the three padded edge arrays (faces
  * whose stencil leaves the array are zero); otherwise the bound face arrays are used

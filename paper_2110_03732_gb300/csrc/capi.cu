@@ -67,6 +67,7 @@ struct grmhd_ctx_s {
     const double* alp;
     const double* eta;
     double eta_u;
+    double xi;           // mean-field dynamo parameter (0: none)
     long long launches;
     // optional per-kernel timing: events around each launch, folded on request
     bool timing;
@@ -213,6 +214,7 @@ ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE
     a.tol = c->par.newton_tol;
     a.rho_atm = c->par.rho_atm;
     a.p_atm = c->par.p_atm;
+    a.xi = c->xi;
     a.p32 = p32;
     a.nfail = c->nfail;
     return a;
@@ -450,6 +452,14 @@ grmhd_status grmhd_set_eta(grmhd_ctx* c, const double* eta_cc, double eta_unifor
     if (!eta_cc && !(eta_uniform > 0.0)) return fail(GRMHD_ERR_ARG, "uniform eta must be positive");
     c->eta = eta_cc;
     c->eta_u = eta_uniform;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_set_dynamo(grmhd_ctx* c, double xi)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    if (!(xi == xi)) return fail(GRMHD_ERR_ARG, "xi must be a number");
+    c->xi = xi;
     return GRMHD_OK;
 }
 

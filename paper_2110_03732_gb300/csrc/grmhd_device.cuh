@@ -206,8 +206,67 @@ __device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi
 struct CellIn {
     double D, S[3], tau, Es[3], B[3];   // undensitised orthonormal components
     double etat;                        // eta / (alpha a_ii dt); < 0: E held fixed
+    double xi;                          // mean-field dynamo parameter (Sec. 2.2)
     double gh, igh;
 };
+
+// A_k(W) of Sec. 2.4 for the dynamo parameter xi, and their W-derivatives:
+//   A_0 = W + eta_t + xi^2 (W^2 - 1)/p,  A_1 = eta_t/q + xi^2 eta_t W/(p q),
+//   A_2 = -xi eta_t/p,  A_3 = xi q/p,  A_4 = xi (1 - eta_t^2 + xi^2)/(p q),
+//   A_5 = -1 - xi^2 W/p,  with p = W + eta_t, q = 1 + eta_t W
+struct Dyn {
+    double A[6], Ad[6];
+};
+
+__device__ __forceinline__ void dyn_coeffs(double W, double et, double xi, Dyn& d, bool derivs)
+{
+    const double x2 = xi * xi, p = W + et, q = 1.0 + et * W;
+    const double ip = 1.0 / p, iq = 1.0 / q, ipq = ip * iq;
+    d.A[0] = W + et + x2 * (W * W - 1.0) * ip;
+    d.A[1] = et * iq + x2 * et * W * ipq;
+    d.A[2] = -xi * et * ip;
+    d.A[3] = xi * q * ip;
+    d.A[4] = xi * (1.0 - et * et + x2) * ipq;
+    d.A[5] = -1.0 - x2 * W * ip;
+    if (derivs) {
+        const double ip2 = ip * ip, iq2 = iq * iq;
+        d.Ad[0] = 1.0 + x2 * (1.0 + W * W + 2.0 * W * et) * ip2;
+        d.Ad[1] = -et * et * iq2 - x2 * et * et * (W * W - 1.0) * iq2 * ip2;
+        d.Ad[2] = xi * et * ip2;
+        d.Ad[3] = xi * (et * et - 1.0) * ip2;
+        d.Ad[4] = -xi * (1.0 - et * et + x2) * (1.0 + et * et + 2.0 * W * et) * iq2 * ip2;
+        d.Ad[5] = -x2 * et * ip2;
+    }
+}
+
+// dE_i/du_j with the dynamo (Sec. 2.4, orthonormal frame):
+//   W A_0 dE_i/du_j = -A0' E_i u_j + A_1 W u_i E*_j + A3' B_i u_j + A_4 W u_i B_j
+//     + (A_1 W delta_ij + A1' u_i u_j)(E*.u) + A_2 W eps_ijm E*_m + A2' (u x E*)_i u_j
+//     + (A_4 W delta_ij + A4' u_i u_j)(B.u) + A_5 W eps_ijm B_m + A5' (u x B)_i u_j
+template <typename T>
+__device__ __forceinline__ void dE_dynamo(const T* A, const T* Ad, T W, const T* u, const T* E, const T* Es,
+                                          const T* B, T dE[3][3])
+{
+    const T Esu = Es[0] * u[0] + Es[1] * u[1] + Es[2] * u[2];
+    const T Bu = B[0] * u[0] + B[1] * u[1] + B[2] * u[2];
+    const T uxEs[3] = {u[1] * Es[2] - u[2] * Es[1], u[2] * Es[0] - u[0] * Es[2], u[0] * Es[1] - u[1] * Es[0]};
+    const T uxB[3] = {u[1] * B[2] - u[2] * B[1], u[2] * B[0] - u[0] * B[2], u[0] * B[1] - u[1] * B[0]};
+    const T s = T(1) / (A[0] * W);
+    const T dg = A[1] * W * Esu + A[4] * W * Bu;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            dE[i][j] = (-Ad[0] * E[i] * u[j] + A[1] * W * u[i] * Es[j] + Ad[3] * B[i] * u[j] + A[4] * W * u[i] * B[j] +
+                        (Ad[1] * Esu + Ad[4] * Bu) * u[i] * u[j] + (Ad[2] * uxEs[i] + Ad[5] * uxB[i]) * u[j] +
+                        (i == j ? dg : T(0))) * s;
+    // A_2 W eps_ijm E*_m + A_5 W eps_ijm B_m
+    const T X[3] = {(A[2] * Es[0] + A[5] * B[0]) * W * s, (A[2] * Es[1] + A[5] * B[1]) * W * s,
+                    (A[2] * Es[2] + A[5] * B[2]) * W * s};
+    dE[0][1] += X[2]; dE[0][2] -= X[1];
+    dE[1][2] += X[0]; dE[1][0] -= X[2];
+    dE[2][0] += X[1]; dE[2][1] -= X[0];
+}
 
 struct Eval {
     double W, E[3], wt, U, A1, iWe, iden, Esu, f[3], g;
@@ -221,7 +280,24 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
 {
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     e.W = sqrt(1.0 + uu);
-    if (c.etat >= 0.0) {
+    if (c.etat >= 0.0 && c.xi != 0.0) {
+        // A_0 E = eta_t E* + A_1 (E*.u) u + A_2 u x E* + A_3 B + A_4 (B.u) u + A_5 u x B
+        Dyn dy;
+        dyn_coeffs(e.W, c.etat, c.xi, dy, false);
+        e.iWe = 1.0 / dy.A[0];
+        e.A1 = dy.A[1];
+        e.Esu = c.Es[0] * u[0] + c.Es[1] * u[1] + c.Es[2] * u[2];
+        const double Bu = c.B[0] * u[0] + c.B[1] * u[1] + c.B[2] * u[2];
+        const double a = dy.A[1] * e.Esu, b = dy.A[4] * Bu;
+        const double uxEs[3] = {u[1] * c.Es[2] - u[2] * c.Es[1], u[2] * c.Es[0] - u[0] * c.Es[2],
+                                u[0] * c.Es[1] - u[1] * c.Es[0]};
+        const double uxB[3] = {u[1] * c.B[2] - u[2] * c.B[1], u[2] * c.B[0] - u[0] * c.B[2],
+                               u[0] * c.B[1] - u[1] * c.B[0]};
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            e.E[i] = (c.etat * c.Es[i] + (a + b) * u[i] + dy.A[2] * uxEs[i] + dy.A[3] * c.B[i] + dy.A[5] * uxB[i]) *
+                     e.iWe;
+    } else if (c.etat >= 0.0) {
         e.iWe = 1.0 / (e.W + c.etat);
         e.A1 = c.etat / (1.0 + c.etat * e.W);
         e.Esu = c.Es[0] * u[0] + c.Es[1] * u[1] + c.Es[2] * u[2];
@@ -255,7 +331,11 @@ __device__ __forceinline__ void jacobian(const CellIn& c, const double* u, const
 {
     const double iW = 1.0 / e.W;
     double dE[3][3];   // dE_i / du_j
-    if (c.etat >= 0.0) {
+    if (c.etat >= 0.0 && c.xi != 0.0) {
+        Dyn dy;
+        dyn_coeffs(e.W, c.etat, c.xi, dy, true);
+        dE_dynamo<double>(dy.A, dy.Ad, e.W, u, e.E, c.Es, c.B, dE);
+    } else if (c.etat >= 0.0) {
         // W (W + eta_t) dE_i/du_j = -E_i u_j + A_1 W u_i E*_j + (A_1 W delta_ij - A_1^2 u_i u_j)(E*.u)
         //                          - W eps_ijl B_l
         const double A1 = e.A1, a2 = A1 * A1 * e.Esu * iW;
@@ -331,7 +411,17 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const double* u,
         Bf[i] = (float)c.B[i];
     }
     float dE[3][3];
-    if (c.etat >= 0.0) {
+    if (c.etat >= 0.0 && c.xi != 0.0) {
+        Dyn dy;
+        dyn_coeffs(e.W, c.etat, c.xi, dy, true);
+        float A[6], Ad[6];
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            A[k] = (float)dy.A[k];
+            Ad[k] = (float)dy.Ad[k];
+        }
+        dE_dynamo<float>(A, Ad, (float)e.W, uf, Ef, Esf, Bf, dE);
+    } else if (c.etat >= 0.0) {
         const float A1 = (float)e.A1, Esu = (float)e.Esu, s = (float)e.iWe, iWf = (float)iW;
         const float a2 = A1 * A1 * Esu * iWf;
 #pragma unroll

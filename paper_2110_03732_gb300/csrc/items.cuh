@@ -40,6 +40,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     CellIn ci;
     ci.gh = g.gh;
     ci.igh = g.igh;
+    ci.xi = a.xi;
     ci.D = qb.p[0][id] * ip6;
     ci.S[0] = qb.p[1][id] * ip6 * ip2;
     ci.S[1] = qb.p[2][id] * ip6 * ip2;

@@ -31,6 +31,7 @@ struct ImpArgs {
     P3 qE_out;              // solved q_E (or NULL)
     int kmax;
     double tol, rho_atm, p_atm;
+    double xi;              // mean-field dynamo parameter
     F11 p32;                // FP32 copy for the mixed path (or NULL)
     unsigned long long* nfail;
 };

@@ -62,6 +62,7 @@ def lib():
     L.grmhd_bind.argtypes = [vp, dpp, dpp, vp, C.c_size_t]
     L.grmhd_set_metric.argtypes = [vp, vp, vp]
     L.grmhd_set_eta.argtypes = [vp, vp, C.c_double]
+    L.grmhd_set_dynamo.argtypes = [vp, C.c_double]
     L.grmhd_init_from_prims.argtypes = [vp, dpp, dpp, vp]
     L.grmhd_compute_dt.argtypes = [vp, C.POINTER(C.c_double), vp]
     L.grmhd_stage.argtypes = [vp, C.c_int, C.c_double, vp]
@@ -83,7 +84,7 @@ def lib():
     L.grmhd_launch_count.restype = C.c_longlong
     L.grmhd_last_error.restype = C.c_char_p
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
-                 "grmhd_set_metric", "grmhd_set_eta", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
+                 "grmhd_set_metric", "grmhd_set_eta", "grmhd_set_dynamo", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
                  "grmhd_step", "grmhd_get_prims", "grmhd_implicit", "grmhd_explicit_L", "grmhd_diagnostics",
                  "grmhd_set_timing", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
@@ -193,6 +194,9 @@ class Solver:
         self.eta_u = float(eta_u)
         check(self.L.grmhd_set_eta(self.ctx, self._vp(self.eta), self.eta_u), "set_eta")
 
+    def set_dynamo(self, xi):
+        check(self.L.grmhd_set_dynamo(self.ctx, float(xi)), "set_dynamo")
+
     def init_from_prims(self, prim, A_edge=None, bface=None, stream=None):
         prim = [self._dev(p) for p in prim]
         if bface is not None:
@@ -211,6 +215,8 @@ class Solver:
         s = cls(prob.ndim, prob.n, prob.lo, prob.hi, prob.bc, prob.gamma, prob.cfl, device=device, **kw)
         s.set_metric(prob.alpha, prob.psi)
         s.set_eta(prob.eta, prob.eta_u if prob.eta is None else (prob.eta_u or 1.0))
+        if getattr(prob, "xi", 0.0):
+            s.set_dynamo(prob.xi)
         s.init_from_prims(prob.prim, A_edge=prob.A_edge, bface=None if prob.A_edge is not None else prob.bface)
         return s
 

@@ -57,6 +57,7 @@ class Problem:
     eta: np.ndarray = None   # per-cell resistivity, or None (then eta_u)
     eta_u: float = 0.0
     cfl: float = 0.4
+    xi: float = 0.0          # mean-field dynamo parameter
     rho_atm: float = 0.0     # atmosphere floor density (0: no atmosphere treatment)
     p_atm: float = 0.0
     t_end: float = 0.0
@@ -309,7 +310,7 @@ def random_prims(seed, shape, u_scale=0.5, e_scale=0.5, b_scale=1.0):
     return [rho, *u, p, *E], B
 
 
-def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2, metric=False):
+def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2, metric=False, xi=0.0):
     """A small seeded box of smooth-plus-noise states for stencil parity tests: every
     field is a constant plus a few random Fourier modes plus noise of relative size
     ``amp``; face B from a random edge potential.  ``metric=True`` adds a smooth lapse
@@ -360,7 +361,7 @@ def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2,
         psi = smooth(1.1, 0.05)
     eta_arr = 10.0 ** rng.uniform(math.log10(eta) - 1, math.log10(eta) + 1, shp)
     return Problem(f"random_box_{ndim}d", ndim, nn, lo, hi, [bc] * 3, gamma, prim, bface=bface, A_edge=A,
-                   alpha=alpha, psi=psi, eta=eta_arr, eta_u=eta, cfl=0.4)
+                   alpha=alpha, psi=psi, eta=eta_arr, eta_u=eta, cfl=0.4, xi=xi)
 
 
 # --------------------------------------------------------------------------
@@ -407,3 +408,23 @@ def request_stream(seed=0, n_requests=64, rate=200.0, tube_cells=(400, 4096), vo
             steps = steps_2d3d
         out.append((t, pr, steps))
     return out
+
+
+def dynamo_1d(k=1, n=64, eta=0.1, xi=0.5, rho=1e12, p=1.0, gamma=4.0 / 3.0):
+    """One-dimensional steady dynamo (Sec. 5): B = 0.1 (0, sin kx, -cos kx), E = 0, v = 0
+    on periodic [-pi, pi], uniform eta and dynamo parameter xi.  The paper freezes the
+    matter; a density of 1e12 keeps it at rest here.  Frozen-matter growth rate of
+    the helical mode: the positive root of lambda^2 + lambda/eta + k^2 - k xi/eta = 0."""
+    ndim, nn, lo, hi = 1, [n, 1, 1], [-math.pi, 0.0, 0.0], [math.pi, 1.0, 1.0]
+    c, f = _axes(ndim, nn, lo, hi)
+    X, _, _ = _mesh(c[0], c[1], c[2])
+    z = np.zeros_like(X)
+    prim = [np.full_like(X, rho), z.copy(), z.copy(), z.copy(), np.full_like(X, p), z.copy(), z.copy(), z.copy()]
+    bface = [z.copy(), 0.1 * np.sin(k * X), -0.1 * np.cos(k * X)]
+    return Problem("dynamo_1d", ndim, nn, lo, hi, ["periodic"] * 3, gamma, prim, bface=bface, eta_u=eta, xi=xi,
+                   cfl=0.4, t_end=6.0)
+
+
+def dynamo_growth_rate(k, eta, xi):
+    """Positive root of lambda^2 + lambda/eta + k^2 - k xi/eta = 0."""
+    return 0.5 * (-1.0 / eta + math.sqrt(1.0 / eta ** 2 + 4.0 * (k * xi / eta - k * k)))

@@ -277,3 +277,36 @@ def test_minimal_grids(G):
     for pr in (P.random_box(3, 2, [2, 5], bc="periodic"), P.random_box(3, 2, [1, 6], bc="outflow"),
                P.random_box(3, 3, [2, 3, 2], bc="periodic")):
         _steps(G, pr, 2, dt=0.01)
+
+
+def test_step_dynamo(G):
+    """Mean-field dynamo (xi != 0): the 1-D helical test and a 3-D box with a metric.
+    The helical test freezes the matter with rho = 1e12, which makes tau = rho h W^2 - p - D
+    round-off of a 1e12 quantity on both sides (as in the telegraph case); the parity run
+    takes rho = 10, where every variable is well conditioned and the dynamo terms
+    still dominate the field evolution."""
+    _steps(G, P.dynamo_1d(k=1, n=48, rho=10.0), 4)
+    _steps(G, P.random_box(13, 3, [9, 8, 7], bc="periodic", metric=True, xi=0.4), 3)
+
+
+def test_implicit_parity_dynamo(G):
+    pr = P.random_box(33, 2, [17, 15], bc="periodic", xi=0.7)
+    st = oracle.from_problem(pr)
+    rng = np.random.default_rng(9)
+    q = [a.copy() for a in st.q]
+    for k in range(3):
+        q[5 + k] = q[5 + k] + 0.05 * rng.normal(size=q[5 + k].shape)
+    for a_dt in (1e-3, 3e-2):
+        qo = [a.copy() for a in q]
+        po = [a.copy() for a in st.prim]
+        po, Ro, fails, _ = oracle.implicit(st.grid, a_dt, qo, st.bf, pr.alpha, pr.psi, pr.eta, pr.eta_u, po)
+        assert fails == 0
+        S = gpu_solver(G, pr)
+        qg = [torch.as_tensor(a, device="cuda").contiguous() for a in q]
+        pg = [torch.as_tensor(a, device="cuda").contiguous() for a in st.prim]
+        bg = [torch.as_tensor(a, device="cuda").contiguous() for a in st.bf]
+        S.implicit(a_dt, qg, bg, pg)
+        torch.cuda.synchronize()
+        I = st.grid.interior()
+        for v in range(8):
+            assert rel_l1(cpu(pg[v])[I], po[v][I]) <= TOL, (a_dt, v)

@@ -458,3 +458,37 @@ def test_killing_energy_in_static_metric():
         drift.append(abs(ek1 - ek0))
     assert drift[0] < 1e-3
     assert math.log2(drift[0] / drift[1]) > 1.5
+
+
+def test_dynamo_growth_rates():
+    """Sec. 5 steady dynamo: the k = 1 helical field grows at the printed 0.385, the
+    k = 5 one stays put (dynamo and resistivity cancel); the frozen-matter dispersion
+    relation gives exactly those numbers and the printed fastest rate 0.59 (eta = 0.1;
+    see tests/golden/dynamo_growth.txt for the reading of the printed eta)."""
+    rows = golden("dynamo_growth.txt")
+    assert abs(P.dynamo_growth_rate(1, 0.1, 0.5) - rows[1]) < 5e-4
+    assert abs(P.dynamo_growth_rate(5, 0.1, 0.5) - rows[5]) < 1e-12
+    assert abs(P.dynamo_growth_rate(2.5, 0.1, 0.5) - 0.59) < 1e-3
+    amps = {}
+    for k, n in ((1, 64), (5, 64), (5, 128)):
+        pr = P.dynamo_1d(k=k, n=n)
+        st = oracle.from_problem(pr)
+        dt = oracle.cfl_dt(st.grid, pr.cfl)
+        hist = []
+        t = 0.0
+        while t < pr.t_end - 1e-12:
+            st.step(dt)
+            t += dt
+            hist.append((t, np.abs(interior(st, st.bf[1])).max()))
+        assert st.fails == 0
+        amps[(k, n)] = hist
+    h = amps[(1, 64)]
+    a2 = next(a for t, a in h if t >= 2.0)
+    t2 = next(t for t, a in h if t >= 2.0)
+    rate = math.log(h[-1][1] / a2) / (h[-1][0] - t2)
+    assert abs(rate / rows[1] - 1) < 0.03, rate
+    # k = 5: no physical growth; the numerical decay of the balanced mode falls at
+    # about second order with resolution
+    r64 = math.log(amps[(5, 64)][-1][1] / 0.1) / amps[(5, 64)][-1][0]
+    r128 = math.log(amps[(5, 128)][-1][1] / 0.1) / amps[(5, 128)][-1][0]
+    assert abs(r128) < 0.03 and abs(r128) < 0.3 * abs(r64), (r64, r128)
