@@ -67,6 +67,15 @@ def lib():
             L.orc_dt.restype = C.c_double
             L.orc_divb.argtypes = [ip, dp, dpp, dp]
             L.orc_totals.argtypes = [ip, dp, dpp, dp]
+            L.orc_curl_A_cc.argtypes = [ip, dp, dpp, dpp]
+            L.orc_prim2con_cc.argtypes = [ip, dp, dpp, dpp, dp, dpp]
+            L.orc_implicit_cc.argtypes = [ip, dp, C.c_double, dpp, dpp, dp, dp, dp, C.c_double, dpp, dpp, ip]
+            L.orc_implicit_cc.restype = C.c_int
+            L.orc_explicit_L_glm.argtypes = [ip, dp, C.c_double, dpp, dpp, dp, dp, dp, dpp]
+            L.orc_step_glm.argtypes = [ip, dp, C.c_int, dp, dp, dp, dp, C.c_double, C.c_double, dpp, dpp, dp,
+                                       dp, dp, dp, C.c_double, dpp, ip]
+            L.orc_step_glm.restype = C.c_int
+            L.orc_divb_cc.argtypes = [ip, dp, dpp, dp]
             _lib = L
     return _lib
 
@@ -294,3 +303,118 @@ def from_problem(prob):
     else:
         bf = [np.ascontiguousarray(b, dtype=np.float64).copy() for b in prob.bface]
     return State(grid, prob.prim, bf, prob.alpha, prob.psi, prob.eta, prob.eta_u)
+
+
+# --------------------------------------------------------------------------
+# GLM hyperbolic cleaning variant (Sec. 3.1): cell-centred q_B (3) and q_Phi
+# --------------------------------------------------------------------------
+
+def curl_A_cc(grid, A):
+    """Cell-centred q_B from a cell-centred potential (central differences)."""
+    qB = grid.zeros(3)
+    pa, k1 = _dpp(A)
+    pb, k2 = _dpp(qB)
+    lib().orc_curl_A_cc(grid.gi, grid.gd, pa, pb)
+    return qB
+
+
+def prim2con_cc(grid, prim, qB, psi=None):
+    q = grid.zeros(8)
+    pp, k1 = _dpp(prim)
+    pb, k2 = _dpp(qB)
+    pq, k3 = _dpp(q)
+    lib().orc_prim2con_cc(grid.gi, grid.gd, pp, pb, _dp(psi), pq)
+    return q
+
+
+def implicit_cc(grid, a_dt, q, qB, alpha=None, psi=None, eta=None, eta_u=0.0, prim=None):
+    """The implicit solve with cell-centred q_B given directly."""
+    prim = grid.zeros(8) if prim is None else prim
+    R = grid.zeros(3)
+    st = (C.c_int * 2)(0, 0)
+    pq, k1 = _dpp(q)
+    pb, k2 = _dpp(qB)
+    pp, k3 = _dpp(prim)
+    pr, k4 = _dpp(R)
+    f = lib().orc_implicit_cc(grid.gi, grid.gd, a_dt, pq, pb, _dp(alpha), _dp(psi), _dp(eta), eta_u, pp, pr,
+                              C.cast(st, C.POINTER(C.c_int)))
+    return prim, R, f, st[1]
+
+
+def explicit_L_glm(grid, kappa, prim, qB, qphi, alpha=None, psi=None):
+    """GLM explicit operator: 12 cell-centred arrays (8 + q_B^1..3 + q_Phi)."""
+    L = grid.zeros(12)
+    pp, k1 = _dpp(prim)
+    pb, k2 = _dpp(qB)
+    pl, k3 = _dpp(L)
+    lib().orc_explicit_L_glm(grid.gi, grid.gd, float(kappa), pp, pb, _dp(qphi), _dp(alpha), _dp(psi), pl)
+    return L
+
+
+def step_glm(grid, dt, kappa, q, qB, qphi, prim, alpha=None, psi=None, eta=None, eta_u=0.0, tableau=None):
+    """One IMEX step of the GLM variant in place on q (8), qB (3), qphi."""
+    At, A, wt, w = ssp2_tableau() if tableau is None else tableau
+    s = len(wt)
+    At = np.ascontiguousarray(At, dtype=np.float64).ravel()
+    A = np.ascontiguousarray(A, dtype=np.float64).ravel()
+    wt = np.ascontiguousarray(wt, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    st = (C.c_int * 2)(0, 0)
+    pq, k1 = _dpp(q)
+    pb, k2 = _dpp(qB)
+    pp, k3 = _dpp(prim)
+    rc = lib().orc_step_glm(grid.gi, grid.gd, s, _dp(At), _dp(A), _dp(wt), _dp(w), dt, float(kappa), pq, pb,
+                            _dp(qphi), _dp(alpha), _dp(psi), _dp(eta), eta_u, pp, C.cast(st, C.POINTER(C.c_int)))
+    if rc != 0:
+        raise ValueError("oracle: tableau must be diagonally implicit with a_ii > 0")
+    return st[0], st[1]
+
+
+def divb_cc(grid, qB):
+    """(mean |div q_B|, rms, max) of cell-centred fields by central differences."""
+    out = np.zeros(3)
+    pb, k = _dpp(qB)
+    lib().orc_divb_cc(grid.gi, grid.gd, pb, _dp(out))
+    return out
+
+
+class GLMState:
+    """An oracle run of the GLM variant: q (8), cell-centred qB (3), qphi."""
+
+    def __init__(self, grid, prim, qB, qphi, kappa, alpha=None, psi=None, eta=None, eta_u=0.0):
+        self.grid = grid
+        self.kappa = float(kappa)
+        self.qB = [np.ascontiguousarray(b, dtype=np.float64).copy() for b in qB]
+        self.qphi = np.ascontiguousarray(qphi, dtype=np.float64).copy()
+        self.prim = [np.ascontiguousarray(p, dtype=np.float64).copy() for p in prim]
+        self.alpha = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
+        self.psi = None if psi is None else np.ascontiguousarray(psi, dtype=np.float64)
+        self.eta = None if eta is None else np.ascontiguousarray(eta, dtype=np.float64)
+        self.eta_u = float(eta_u)
+        self.q = prim2con_cc(grid, self.prim, self.qB, self.psi)
+        self.t = 0.0
+        self.fails = 0
+        self.max_iters = 0
+
+    def step(self, dt, tableau=None):
+        f, it = step_glm(self.grid, dt, self.kappa, self.q, self.qB, self.qphi, self.prim, self.alpha, self.psi,
+                         self.eta, self.eta_u, tableau)
+        self.fails += f
+        self.max_iters = max(self.max_iters, it)
+        self.t += dt
+
+
+def from_problem_glm(prob, kappa=None):
+    """GLM oracle state from a Problem: cell-centred q_B from ``prob.A_cell`` (oracle
+    central curl) or ``prob.bcell``; q_Phi = psi^6 ``prob.phi`` (0 if None)."""
+    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0))
+    if prob.A_cell is not None:
+        qB = curl_A_cc(grid, [np.ascontiguousarray(a, dtype=np.float64) for a in prob.A_cell])
+    else:
+        qB = [np.ascontiguousarray(b, dtype=np.float64).copy() for b in prob.bcell]
+    qphi = grid.zeros()
+    if prob.phi is not None:
+        sg = 1.0 if prob.psi is None else prob.psi ** 6
+        qphi = np.ascontiguousarray(sg * prob.phi, dtype=np.float64)
+    k = prob.kappa if kappa is None else kappa
+    return GLMState(grid, prob.prim, qB, qphi, k, prob.alpha, prob.psi, prob.eta, prob.eta_u)

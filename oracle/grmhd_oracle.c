@@ -4,7 +4,8 @@
  * A plain, slow, double-precision CPU statement of one IMEX Runge-Kutta step of
  * resistive (general-relativistic) MHD on a uniform Cartesian grid with a fixed,
  * conformally flat background metric (gamma_ij = psi^4 delta_ij, beta^i = 0),
- * staggered face magnetic fields and upwind constrained transport, following
+ * staggered face magnetic fields and upwind constrained transport (or, as a
+ * variant, cell-centred magnetic fields with GLM hyperbolic cleaning), following
  * arXiv 2110.03732 (Cheong et al., "Gmunu: ... resistive GRMHD").
  *
  * Only tests, __graft_entry__.smoke() and bench.py's cpu_baseline leg may use this
@@ -21,6 +22,7 @@
  *   implicit E + velocity Newton, A_k, Jacobian   Sec. 2.4 (eq. im_E, f_i, J_ij)
  *   characteristic speeds (maximal diffusivity)   Sec. 2.5
  *   constrained transport, UCT-HLL edge EMF       Sec. 3.2 (steps i-vii)
+ *   GLM hyperbolic cleaning (cell-centred B, Phi) Sec. 3.1 (q_Phi, f_Phi, s_Phi, s_B)
  *   B from an edge vector potential               Sec. 4
  *   MC limiter + HLL defaults                     Sec. 5 (opening paragraph)
  *
@@ -515,6 +517,66 @@ typedef struct {
     const double* psi;
 } OCtx;
 
+/* non-stiff sources of the 8 cell-centred variables at interior cell c (Sec. 2.1,
+ * beta = 0, K_ij = 0), added to Lc: the Gauss-law charge term of s_E and, with a
+ * metric, s_S and s_tau.  Bc: cell-centred contravariant B^i (ghosts filled). */
+static void cell_sources(const OCtx* X, double* const* prim, double* const* Bc, long c, double* Lc)
+{
+    const OGrid* g = X->g;
+    double ps = psi_at(X->psi, c), al = alp_at(X->alp, c);
+    double gg = ps * ps * ps * ps, sg = gg * ps * ps;
+    double uu = 0;
+    for (int i = 0; i < 3; i++) uu += gg * prim[1 + i][c] * prim[1 + i][c];
+    double W = sqrt(1.0 + uu);
+    double v_up[3];
+    for (int i = 0; i < 3; i++) v_up[i] = prim[1 + i][c] / W;
+    /* Gauss law: sqrt(gamma) rho_e = div q_E (central difference) */
+    double divqE = 0;
+    for (int d = 0; d < 3; d++) {
+        if (!g->act[d]) continue;
+        long cp1 = shift(g, c, d, 1), cm1 = shift(g, c, d, -1);
+        double qEp = pow(psi_at(X->psi, cp1), 6) * prim[5 + d][cp1];
+        double qEm = pow(psi_at(X->psi, cm1), 6) * prim[5 + d][cm1];
+        divqE += (qEp - qEm) / (2.0 * g->dx[d]);
+    }
+    double rhoe = divqE / sg;
+    /* s_E non-stiff part: sqrt(gamma) (rho_e beta^i - alpha rho_e v^i), beta = 0 */
+    for (int i = 0; i < 3; i++) Lc[5 + i] += -sg * al * rhoe * v_up[i];
+    if (X->alp || X->psi) {
+        /* s_S_i and s_tau with beta = 0, K_ij = 0 (Sec. 2.1):
+         *   s_S_i = alpha sqrt(gamma) { -T^00 alpha d_i alpha + 1/2 T^jk d_i gamma_jk }
+         *   s_tau = alpha sqrt(gamma) { -T^0j d_j alpha }
+         * T^00 = (tau + D)/alpha^2, alpha T^0j = S^j, T^jk = stress (spatial) */
+        double rho = prim[0][c], p = prim[4][c], h = 1.0 + g->Gam / (g->Gam - 1.0) * p / rho;
+        double E2 = 0, B2 = 0;
+        for (int i = 0; i < 3; i++) { E2 += gg * prim[5 + i][c] * prim[5 + i][c]; B2 += gg * Bc[i][c] * Bc[i][c]; }
+        double pr8[NPR], q8[NQ], Bp[3];
+        for (int v = 0; v < NPR; v++) pr8[v] = prim[v][c];
+        for (int k = 0; k < 3; k++) Bp[k] = Bc[k][c];
+        prim2con_point(pr8, Bp, ps, g->Gam, q8);
+        double D = q8[0] / sg, tau = q8[4] / sg, S_lo[3];
+        for (int j = 0; j < 3; j++) S_lo[j] = q8[1 + j] / sg;
+        double T00 = (tau + D) / (al * al);
+        double Tjk[3][3];
+        for (int j = 0; j < 3; j++)
+            for (int k = 0; k < 3; k++)
+                Tjk[j][k] = rho * h * W * W * v_up[j] * v_up[k] + p * (j == k ? 1.0 / gg : 0.0)
+                            + 0.5 * (E2 + B2) * (j == k ? 1.0 / gg : 0.0)
+                            - prim[5 + j][c] * prim[5 + k][c] - Bc[j][c] * Bc[k][c];
+        for (int i = 0; i < 3; i++) {
+            if (!g->act[i]) continue;
+            long cp1 = shift(g, c, i, 1), cm1 = shift(g, c, i, -1);
+            double dal = (alp_at(X->alp, cp1) - alp_at(X->alp, cm1)) / (2.0 * g->dx[i]);
+            double dps = (psi_at(X->psi, cp1) - psi_at(X->psi, cm1)) / (2.0 * g->dx[i]);
+            double dgam = 4.0 * ps * ps * ps * dps;     /* d_i gamma_jj (j = k) */
+            double tr = 0;
+            for (int j = 0; j < 3; j++) tr += Tjk[j][j] * dgam;
+            Lc[1 + i] += al * sg * (-T00 * al * dal + 0.5 * tr);
+            Lc[4] += al * sg * (-(S_lo[i] / gg) / al * dal);
+        }
+    }
+}
+
 /* prim: 8 padded arrays with ghosts filled; qBc: cell-centred q_B (3, filled);
  * bf: face q_B (3, ghosts filled); out L: 8 cell-centred + 3 face (interior) */
 static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, double* const* bf, double** L)
@@ -580,58 +642,7 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
             long cp1 = shift(g, c, d, 1);
             for (int v = 0; v < NQ; v++) Lc[v] -= (F[d][v][cp1] - F[d][v][c]) / g->dx[d];
         }
-        double ps = psi_at(X->psi, c), al = alp_at(X->alp, c);
-        double gg = ps * ps * ps * ps, sg = gg * ps * ps;
-        double uu = 0;
-        for (int i = 0; i < 3; i++) uu += gg * prim[1 + i][c] * prim[1 + i][c];
-        double W = sqrt(1.0 + uu);
-        double v_up[3];
-        for (int i = 0; i < 3; i++) v_up[i] = prim[1 + i][c] / W;
-        /* Gauss law: sqrt(gamma) rho_e = div q_E (central difference) */
-        double divqE = 0;
-        for (int d = 0; d < 3; d++) {
-            if (!g->act[d]) continue;
-            long cp1 = shift(g, c, d, 1), cm1 = shift(g, c, d, -1);
-            double qEp = pow(psi_at(X->psi, cp1), 6) * prim[5 + d][cp1];
-            double qEm = pow(psi_at(X->psi, cm1), 6) * prim[5 + d][cm1];
-            divqE += (qEp - qEm) / (2.0 * g->dx[d]);
-        }
-        double rhoe = divqE / sg;
-        /* s_E non-stiff part: sqrt(gamma) (rho_e beta^i - alpha rho_e v^i), beta = 0 */
-        for (int i = 0; i < 3; i++) Lc[5 + i] += -sg * al * rhoe * v_up[i];
-        if (X->alp || X->psi) {
-            /* s_S_i and s_tau with beta = 0, K_ij = 0 (Sec. 2.1):
-             *   s_S_i = alpha sqrt(gamma) { -T^00 alpha d_i alpha + 1/2 T^jk d_i gamma_jk }
-             *   s_tau = alpha sqrt(gamma) { -T^0j d_j alpha }
-             * T^00 = (tau + D)/alpha^2, alpha T^0j = S^j, T^jk = stress (spatial) */
-            double rho = prim[0][c], p = prim[4][c], h = 1.0 + g->Gam / (g->Gam - 1.0) * p / rho;
-            double E2 = 0, B2 = 0;
-            for (int i = 0; i < 3; i++) { E2 += gg * prim[5 + i][c] * prim[5 + i][c]; B2 += gg * Bc[i][c] * Bc[i][c]; }
-            double pr8[NPR], q8[NQ], Bp[3];
-            for (int v = 0; v < NPR; v++) pr8[v] = prim[v][c];
-            for (int k = 0; k < 3; k++) Bp[k] = Bc[k][c];
-            prim2con_point(pr8, Bp, ps, g->Gam, q8);
-            double D = q8[0] / sg, tau = q8[4] / sg, S_lo[3];
-            for (int j = 0; j < 3; j++) S_lo[j] = q8[1 + j] / sg;
-            double T00 = (tau + D) / (al * al);
-            double Tjk[3][3];
-            for (int j = 0; j < 3; j++)
-                for (int k = 0; k < 3; k++)
-                    Tjk[j][k] = rho * h * W * W * v_up[j] * v_up[k] + p * (j == k ? 1.0 / gg : 0.0)
-                                + 0.5 * (E2 + B2) * (j == k ? 1.0 / gg : 0.0)
-                                - prim[5 + j][c] * prim[5 + k][c] - Bc[j][c] * Bc[k][c];
-            for (int i = 0; i < 3; i++) {
-                if (!g->act[i]) continue;
-                long cp1 = shift(g, c, i, 1), cm1 = shift(g, c, i, -1);
-                double dal = (alp_at(X->alp, cp1) - alp_at(X->alp, cm1)) / (2.0 * g->dx[i]);
-                double dps = (psi_at(X->psi, cp1) - psi_at(X->psi, cm1)) / (2.0 * g->dx[i]);
-                double dgam = 4.0 * ps * ps * ps * dps;     /* d_i gamma_jj (j = k) */
-                double tr = 0;
-                for (int j = 0; j < 3; j++) tr += Tjk[j][j] * dgam;
-                Lc[1 + i] += al * sg * (-T00 * al * dal + 0.5 * tr);
-                Lc[4] += al * sg * (-(S_lo[i] / gg) / al * dal);
-            }
-        }
+        cell_sources(X, prim, Bc, c, Lc);
         for (int v = 0; v < NQ; v++) L[v][c] = Lc[v];
     }
     /* upwind constrained transport: edge EMF hat{E}_c for c = 0,1,2 with the pair
@@ -848,20 +859,11 @@ void orc_residual_cell(const double* in, double psi, double etat, double Gam, co
  * R = (q_E - q_E,base)/(a_ii dt) (3, interior).  eta: per-cell or NULL -> eta_u.
  * a_dt = a_ii * dt; a_dt <= 0 means E held fixed (plain con2prim).
  * stats[0] += failures, stats[1] = max iterations.  Returns failures. */
-int orc_implicit(const int* gi, const double* gd, double a_dt, double** q, double* const* bf,
-                 const double* alp, const double* psi, const double* eta, double eta_u,
-                 double** prim, double** R, int* stats)
+static int implicit_cells(const OGrid* Gp, double a_dt, double** q, double* const* qBc,
+                          const double* alp, const double* psi, const double* eta, double eta_u,
+                          double** prim, double** R, int* stats)
 {
-    OGrid G; grid_setup(&G, gi, gd);
-    double* qBc[3];
-    double* bfc[3];
-    for (int d = 0; d < 3; d++) {
-        qBc[d] = dalloc(G.ncell);
-        bfc[d] = dalloc(G.ncell);
-        memcpy(bfc[d], bf[d], sizeof(double) * G.ncell);
-        fill_face_ghosts(&G, bfc[d], d);
-    }
-    cell_qB(&G, bfc, qBc);
+    const OGrid G = *Gp;
     int fails = 0, maxit = 0, ijk[3];
     for (long c = 0; c < G.ncell; c++) {
         coords(&G, c, ijk);
@@ -914,8 +916,26 @@ int orc_implicit(const int* gi, const double* gd, double a_dt, double** q, doubl
             q[5 + i][c] = qEn;
         }
     }
-    for (int d = 0; d < 3; d++) { free(qBc[d]); free(bfc[d]); }
     if (stats) { stats[0] += fails; if (maxit > stats[1]) stats[1] = maxit; }
+    return fails;
+}
+
+int orc_implicit(const int* gi, const double* gd, double a_dt, double** q, double* const* bf,
+                 const double* alp, const double* psi, const double* eta, double eta_u,
+                 double** prim, double** R, int* stats)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    double* qBc[3];
+    double* bfc[3];
+    for (int d = 0; d < 3; d++) {
+        qBc[d] = dalloc(G.ncell);
+        bfc[d] = dalloc(G.ncell);
+        memcpy(bfc[d], bf[d], sizeof(double) * G.ncell);
+        fill_face_ghosts(&G, bfc[d], d);
+    }
+    cell_qB(&G, bfc, qBc);
+    int fails = implicit_cells(&G, a_dt, q, qBc, alp, psi, eta, eta_u, prim, R, stats);
+    for (int d = 0; d < 3; d++) { free(qBc[d]); free(bfc[d]); }
     return fails;
 }
 
@@ -1068,4 +1088,286 @@ void orc_totals(const int* gi, const double* gd, double* const* q, double* out)
         if (!is_interior(&G, ijk)) continue;
         for (int v = 0; v < NQ; v++) out[v] += q[v][c] * dV;
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* GLM hyperbolic divergence cleaning with cell-centred B (Sec. 3.1)     */
+/* ------------------------------------------------------------------ */
+/*
+ * The variant evolves 12 cell-centred variables: the 8 above, q_B^1..3 at cell
+ * centres, and q_Phi = sqrt(gamma) Phi.  All 12 are reconstructed (as primitives:
+ * rho, u, p, E, B = q_B/sqrt(gamma), Phi = q_Phi/sqrt(gamma)) and advanced by HLL
+ * fluxes in the conservative form of Sec. 2.1, with beta = 0:
+ *     (f_B^j)^i = -(1/sqrt(gamma)) sqrt(gamma) eta^{ijk} alpha E_k = eta^{jik} alpha E_k
+ *     (f_Phi)^i = alpha q_B^i
+ * and the sources of Sec. 3.1 with K_ij = 0:
+ *     s_B^i  = -sqrt(gamma) alpha gamma^{ij} d_j Phi
+ *     s_Phi  =  sqrt(gamma) [ -alpha kappa_B Phi + B^i d_i alpha ]
+ * Readings: the flux and source of Phi are taken from their reference-metric
+ * definitions (Sec. 3.1) in the conservative form d_t q + d_i f^i = s of Sec. 2.1
+ * (the projected Phi equation printed before them has the opposite sign on the
+ * divergence, which would make the (B, Phi) system anti-diffusive); d_j Phi and
+ * d_i alpha are central differences of the cell values; the charge field Psi is
+ * not evolved (charge conservation is not handled by default, Sec. 5), so rho_e
+ * still comes from Gauss's law.  The kappa_B damping belongs to the explicit part.
+ */
+#define NGLM 12   /* 8 + q_B^1..3 + q_Phi */
+
+/* face state and flux of the 12 GLM variables; pr: 8 primitives, B: B^1..3, Phi */
+static void face_flux_glm(const double* pr, const double* B, double Phi, int d, double psi, double alp, double Gam,
+                          double* q, double* F)
+{
+    double g = psi * psi * psi * psi, sg = g * psi * psi;
+    face_flux(pr, B, d, psi, alp, Gam, q, F);
+    for (int j = 0; j < 3; j++) {
+        q[NQ + j] = sg * B[j];
+        double s = 0;
+        for (int k = 0; k < 3; k++) s += levi(j, d, k) * alp * g * pr[5 + k];   /* eta^{jdk} alpha E_k */
+        F[NQ + j] = s;
+    }
+    q[NQ + 3] = sg * Phi;
+    F[NQ + 3] = alp * sg * B[d];
+}
+
+/* prim (8), qB (3) and qPhi with ghosts filled; L out: 12 cell-centred arrays (interior) */
+static void explicit_L_glm(const OCtx* X, double kappa, double* const* prim, double* const* qB, const double* qPhi,
+                           double** L)
+{
+    const OGrid* g = X->g;
+    long nc = g->ncell;
+    int ijk[3];
+    double* rec[NGLM];           /* reconstructed: 8 primitives, B^1..3, Phi */
+    double* Bc[3];
+    for (int v = 0; v < NPR; v++) rec[v] = prim[v];
+    for (int v = NPR; v < NGLM; v++) rec[v] = dalloc(nc);
+    for (long c = 0; c < nc; c++) {
+        double sg = pow(psi_at(X->psi, c), 6);
+        for (int d = 0; d < 3; d++) rec[NPR + d][c] = qB[d][c] / sg;
+        rec[NPR + 3][c] = qPhi[c] / sg;
+    }
+    for (int d = 0; d < 3; d++) Bc[d] = rec[NPR + d];
+    double* F[3][NGLM];
+    for (int d = 0; d < 3; d++) for (int v = 0; v < NGLM; v++) F[d][v] = NULL;
+    for (int d = 0; d < 3; d++) {
+        if (!g->act[d]) continue;
+        for (int v = 0; v < NGLM; v++) F[d][v] = dalloc(nc);
+        for (long c = 0; c < nc; c++) {
+            coords(g, c, ijk);
+            int f = ijk[d];
+            if (f < 2 || f > g->N[d] - 2) continue;
+            long cm2 = shift(g, c, d, -2), cm1 = shift(g, c, d, -1), cp1 = shift(g, c, d, 1);
+            double rL[NGLM], rR[NGLM];
+            for (int v = 0; v < NGLM; v++) {
+                const double* a = rec[v];
+                rL[v] = a[cm1] + 0.5 * mc_slope(a[cm2], a[cm1], a[c]);
+                rR[v] = a[c] - 0.5 * mc_slope(a[cm1], a[c], a[cp1]);
+            }
+            double psf = 0.5 * (psi_at(X->psi, cm1) + psi_at(X->psi, c));
+            double alf = 0.5 * (alp_at(X->alp, cm1) + alp_at(X->alp, c));
+            double gf = psf * psf * psf * psf;
+            double qL[NGLM], qR[NGLM], FL[NGLM], FR[NGLM];
+            face_flux_glm(rL, rL + NPR, rL[NPR + 3], d, psf, alf, g->Gam, qL, FL);
+            face_flux_glm(rR, rR + NPR, rR[NPR + 3], d, psf, alf, g->Gam, qR, FR);
+            double lp = alf * sqrt(1.0 / gf), lm = -alf * sqrt(1.0 / gf);
+            double cp = fmax(0.0, lp), cm = fmax(0.0, -lm);
+            for (int v = 0; v < NGLM; v++)
+                F[d][v][c] = (cp * FL[v] + cm * FR[v] - cp * cm * (qR[v] - qL[v])) / (cp + cm);
+        }
+    }
+    for (long c = 0; c < nc; c++) {
+        coords(g, c, ijk);
+        if (!is_interior(g, ijk)) continue;
+        double Lc[NGLM];
+        for (int v = 0; v < NGLM; v++) Lc[v] = 0.0;
+        for (int d = 0; d < 3; d++) {
+            if (!g->act[d]) continue;
+            long cp1 = shift(g, c, d, 1);
+            for (int v = 0; v < NGLM; v++) Lc[v] -= (F[d][v][cp1] - F[d][v][c]) / g->dx[d];
+        }
+        cell_sources(X, prim, Bc, c, Lc);
+        double ps = psi_at(X->psi, c), al = alp_at(X->alp, c);
+        double gg = ps * ps * ps * ps, sg = gg * ps * ps;
+        /* s_B^i = -sqrt(gamma) alpha gamma^{ij} d_j Phi ; s_Phi = -alpha kappa q_Phi + q_B^i d_i alpha */
+        Lc[NQ + 3] += -al * kappa * qPhi[c];
+        for (int i = 0; i < 3; i++) {
+            if (!g->act[i]) continue;
+            long cp1 = shift(g, c, i, 1), cm1 = shift(g, c, i, -1);
+            double dPhi = (rec[NPR + 3][cp1] - rec[NPR + 3][cm1]) / (2.0 * g->dx[i]);
+            double dal = (alp_at(X->alp, cp1) - alp_at(X->alp, cm1)) / (2.0 * g->dx[i]);
+            Lc[NQ + i] += -sg * al * (1.0 / gg) * dPhi;
+            Lc[NQ + 3] += qB[i][c] * dal;
+        }
+        for (int v = 0; v < NGLM; v++) L[v][c] = Lc[v];
+    }
+    for (int v = NPR; v < NGLM; v++) free(rec[v]);
+    for (int d = 0; d < 3; d++)
+        for (int v = 0; v < NGLM; v++) free(F[d][v]);
+}
+
+/* cell-centred q_B^i = eta^{ijk} d_j A_k from a cell-centred potential by central
+ * differences (Sec. 4, the cell-centred case), on interior cells; the potential is
+ * used as given on the whole padded grid (as for the edge potential); ghosts of q_B
+ * untouched */
+void orc_curl_A_cc(const int* gi, const double* gd, double* const* A, double** qB)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    int ijk[3];
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        for (int i = 0; i < 3; i++) {
+            double r = 0;
+            for (int j = 0; j < 3; j++) {
+                if (!G.act[j]) continue;
+                for (int k = 0; k < 3; k++) {
+                    double e = levi(i, j, k);
+                    if (e == 0.0) continue;
+                    r += e * (A[k][shift(&G, c, j, 1)] - A[k][shift(&G, c, j, -1)]) / (2.0 * G.dx[j]);
+                }
+            }
+            qB[i][c] = r;
+        }
+    }
+}
+
+/* prim (8) + cell-centred q_B (3) -> q (8), all cells (q_B ghosts filled first) */
+void orc_prim2con_cc(const int* gi, const double* gd, double* const* prim, double* const* qB_in, const double* psi,
+                     double** q)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    double* qB[3];
+    for (int d = 0; d < 3; d++) {
+        qB[d] = dalloc(G.ncell);
+        memcpy(qB[d], qB_in[d], sizeof(double) * G.ncell);
+        fill_cell_ghosts(&G, qB[d]);
+    }
+    for (long c = 0; c < G.ncell; c++) {
+        double pr[NPR], B[3], qq[NQ];
+        double ps = psi_at(psi, c), sg = pow(ps, 6);
+        for (int v = 0; v < NPR; v++) pr[v] = prim[v][c];
+        for (int d = 0; d < 3; d++) B[d] = qB[d][c] / sg;
+        prim2con_point(pr, B, ps, G.Gam, qq);
+        for (int v = 0; v < NQ; v++) q[v][c] = qq[v];
+    }
+    for (int d = 0; d < 3; d++) free(qB[d]);
+}
+
+/* the implicit solve with the cell-centred q_B given directly (interior read) */
+int orc_implicit_cc(const int* gi, const double* gd, double a_dt, double** q, double* const* qB,
+                    const double* alp, const double* psi, const double* eta, double eta_u,
+                    double** prim, double** R, int* stats)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    return implicit_cells(&G, a_dt, q, qB, alp, psi, eta, eta_u, prim, R, stats);
+}
+
+/* GLM explicit operator: prim (8), qB (3), qPhi; L out: 12 arrays */
+void orc_explicit_L_glm(const int* gi, const double* gd, double kappa, double* const* prim_in, double* const* qB_in,
+                        const double* qPhi_in, const double* alp, const double* psi, double** L)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    OCtx X = {&G, alp, psi};
+    double* prim[NPR];
+    double* qB[3];
+    double* qPhi = dalloc(G.ncell);
+    for (int v = 0; v < NPR; v++) {
+        prim[v] = dalloc(G.ncell);
+        memcpy(prim[v], prim_in[v], sizeof(double) * G.ncell);
+        fill_cell_ghosts(&G, prim[v]);
+    }
+    for (int d = 0; d < 3; d++) {
+        qB[d] = dalloc(G.ncell);
+        memcpy(qB[d], qB_in[d], sizeof(double) * G.ncell);
+        fill_cell_ghosts(&G, qB[d]);
+    }
+    memcpy(qPhi, qPhi_in, sizeof(double) * G.ncell);
+    fill_cell_ghosts(&G, qPhi);
+    explicit_L_glm(&X, kappa, prim, qB, qPhi, L);
+    for (int v = 0; v < NPR; v++) free(prim[v]);
+    for (int d = 0; d < 3; d++) free(qB[d]);
+    free(qPhi);
+}
+
+/* one IMEX step of the GLM variant: q (8), qB (3 cell-centred), qPhi updated in place
+ * (interior); otherwise as orc_step */
+int orc_step_glm(const int* gi, const double* gd, int s, const double* At, const double* A,
+                 const double* wt, const double* w, double dt, double kappa, double** q, double** qB, double* qPhi,
+                 const double* alp, const double* psi, const double* eta, double eta_u,
+                 double** prim, int* stats)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    if (s < 1 || s > MAXS) return -1;
+    for (int i = 0; i < s; i++) if (!(A[i * s + i] > 0)) return -1;
+    long nc = G.ncell;
+    double* Ls[MAXS][NGLM];
+    double* Rs[MAXS][3];
+    double* qs[NGLM];
+    double* qn[NGLM];
+    for (int v = 0; v < NQ; v++) qn[v] = q[v];
+    for (int d = 0; d < 3; d++) qn[NQ + d] = qB[d];
+    qn[NQ + 3] = qPhi;
+    for (int i = 0; i < s; i++) {
+        for (int v = 0; v < NGLM; v++) Ls[i][v] = dalloc(nc);
+        for (int v = 0; v < 3; v++) Rs[i][v] = dalloc(nc);
+    }
+    for (int v = 0; v < NGLM; v++) qs[v] = dalloc(nc);
+    int ijk[3];
+    for (int i = 0; i < s; i++) {
+        for (int v = 0; v < NGLM; v++) memcpy(qs[v], qn[v], sizeof(double) * nc);
+        for (int j = 0; j < i; j++) {
+            double at_ = At[i * s + j], a_ = A[i * s + j];
+            for (long c = 0; c < nc; c++) {
+                coords(&G, c, ijk);
+                if (!is_interior(&G, ijk)) continue;
+                for (int v = 0; v < NGLM; v++) {
+                    qs[v][c] += dt * at_ * Ls[j][v][c];
+                    if (v >= 5 && v < NQ) qs[v][c] += dt * a_ * Rs[j][v - 5][c];
+                }
+            }
+        }
+        orc_implicit_cc(gi, gd, A[i * s + i] * dt, qs, qs + NQ, alp, psi, eta, eta_u, prim, Rs[i], stats);
+        orc_explicit_L_glm(gi, gd, kappa, prim, qs + NQ, qs[NQ + 3], alp, psi, Ls[i]);
+    }
+    for (long c = 0; c < nc; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        for (int i = 0; i < s; i++)
+            for (int v = 0; v < NGLM; v++) {
+                qn[v][c] += dt * wt[i] * Ls[i][v][c];
+                if (v >= 5 && v < NQ) qn[v][c] += dt * w[i] * Rs[i][v - 5][c];
+            }
+    }
+    for (int i = 0; i < s; i++) {
+        for (int v = 0; v < NGLM; v++) free(Ls[i][v]);
+        for (int v = 0; v < 3; v++) free(Rs[i][v]);
+    }
+    for (int v = 0; v < NGLM; v++) free(qs[v]);
+    return 0;
+}
+
+/* div q_B of cell-centred fields by central differences over interior cells
+ * (Eq. divb_0 with sqrt(gamma_hat) = 1): mean |div|, rms, max */
+void orc_divb_cc(const int* gi, const double* gd, double* const* qB_in, double* out)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    double* qB[3];
+    for (int d = 0; d < 3; d++) {
+        qB[d] = dalloc(G.ncell);
+        memcpy(qB[d], qB_in[d], sizeof(double) * G.ncell);
+        fill_cell_ghosts(&G, qB[d]);
+    }
+    int ijk[3];
+    double s1 = 0, s2 = 0, mx = 0;
+    long n = 0;
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (!is_interior(&G, ijk)) continue;
+        double dv = 0;
+        for (int d = 0; d < 3; d++)
+            if (G.act[d]) dv += (qB[d][shift(&G, c, d, 1)] - qB[d][shift(&G, c, d, -1)]) / (2.0 * G.dx[d]);
+        s1 += fabs(dv); s2 += dv * dv; if (fabs(dv) > mx) mx = fabs(dv);
+        n++;
+    }
+    out[0] = s1 / n; out[1] = sqrt(s2 / n); out[2] = mx;
+    for (int d = 0; d < 3; d++) free(qB[d]);
 }

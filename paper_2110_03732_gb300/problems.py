@@ -58,6 +58,12 @@ class Problem:
     eta_u: float = 0.0
     cfl: float = 0.4
     xi: float = 0.0          # mean-field dynamo parameter
+    # GLM variant (cell-centred B): potential at cell centres or q_B at cell centres,
+    # initial Phi (None: 0) and the damping kappa_B
+    A_cell: list = None
+    bcell: list = None
+    phi: np.ndarray = None
+    kappa: float = 0.0
     rho_atm: float = 0.0     # atmosphere floor density (0: no atmosphere treatment)
     p_atm: float = 0.0
     t_end: float = 0.0
@@ -137,10 +143,12 @@ def shock_tube(n=400, eta=1e-3, with_B=True):
                    eta_u=eta, cfl=0.4, t_end=0.4)
 
 
-def orszag_tang(n=512, eta=1e-4, phase=(0.0, 0.0), gamma=4.0 / 3.0, eta_field=False):
+def orszag_tang(n=512, eta=1e-4, phase=(0.0, 0.0), gamma=4.0 / 3.0, eta_field=False, kappa=1.0):
     """2-D resistive relativistic Orszag-Tang vortex on periodic [0, 2 pi]^2:
     rho = 1, p = 1, v = (-0.5 sin y, 0.5 sin x), B = (-sin y, sin 2x) from the edge
-    potential A_z = cos y + cos(2x)/2, E = -v x B.  ``phase`` shifts x and y."""
+    potential A_z = cos y + cos(2x)/2, E = -v x B.  ``phase`` shifts x and y.  The
+    potential is also given at cell centres, with ``kappa`` the damping of the GLM
+    variant."""
     ndim, nn = 2, [n, n, 1]
     lo, hi = [0.0, 0.0, 0.0], [2 * math.pi, 2 * math.pi, 1.0]
     c, f = _axes(ndim, nn, lo, hi)
@@ -155,9 +163,11 @@ def orszag_tang(n=512, eta=1e-4, phase=(0.0, 0.0), gamma=4.0 / 3.0, eta_field=Fa
     FX, FY, _ = _mesh(f[0] + px, f[1] + py, c[2])
     Az = np.cos(FY) + 0.5 * np.cos(2 * FX)
     A = [z.copy(), z.copy(), Az]
+    # the same potential at cell centres, for the cell-centred (GLM) variant
+    A_cell = [z.copy(), z.copy(), np.cos(Y) + 0.5 * np.cos(2 * X)]
     eta_arr = np.full_like(X, eta) if eta_field else None
     return Problem("orszag_tang_2d", ndim, nn, lo, hi, ["periodic"] * 3, gamma, prim, A_edge=A,
-                   eta=eta_arr, eta_u=eta, cfl=0.4, steps=1000)
+                   eta=eta_arr, eta_u=eta, cfl=0.4, steps=1000, A_cell=A_cell, kappa=kappa)
 
 
 def star(n=256, L=20.0, K=100.0, gamma=2.0, rho_c=1.28e-3, M=1.4, atm_frac=1e-10, b_frac=1e-3,
@@ -310,11 +320,14 @@ def random_prims(seed, shape, u_scale=0.5, e_scale=0.5, b_scale=1.0):
     return [rho, *u, p, *E], B
 
 
-def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2, metric=False, xi=0.0):
+def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2, metric=False, xi=0.0,
+               glm=False, kappa=2.0):
     """A small seeded box of smooth-plus-noise states for stencil parity tests: every
     field is a constant plus a few random Fourier modes plus noise of relative size
     ``amp``; face B from a random edge potential.  ``metric=True`` adds a smooth lapse
-    and conformal factor."""
+    and conformal factor.  ``glm=True`` adds cell-centred q_B (not divergence-free)
+    and a Phi field for the GLM variant (drawn after everything else, so the other
+    fields do not change)."""
     rng = np.random.default_rng(seed)
     nn = [n[d] if d < ndim else 1 for d in range(3)]
     lo, hi = [0.0] * 3, [1.0] * 3
@@ -360,8 +373,14 @@ def random_box(seed, ndim, n, bc="periodic", gamma=5.0 / 3.0, amp=0.2, eta=1e-2,
         alpha = smooth(0.8, 0.05)
         psi = smooth(1.1, 0.05)
     eta_arr = 10.0 ** rng.uniform(math.log10(eta) - 1, math.log10(eta) + 1, shp)
+    bcell = phi = None
+    if glm:
+        # cell-centred fields for the GLM variant (with a divergence), and a Phi
+        bcell = [smooth(0.3 * (d - 1), 0.5) + 0.05 * rng.normal(size=shp) for d in range(3)]
+        phi = smooth(0.0, 0.1) + 0.01 * rng.normal(size=shp)
     return Problem(f"random_box_{ndim}d", ndim, nn, lo, hi, [bc] * 3, gamma, prim, bface=bface, A_edge=A,
-                   alpha=alpha, psi=psi, eta=eta_arr, eta_u=eta, cfl=0.4, xi=xi)
+                   alpha=alpha, psi=psi, eta=eta_arr, eta_u=eta, cfl=0.4, xi=xi, bcell=bcell, phi=phi,
+                   kappa=kappa)
 
 
 # --------------------------------------------------------------------------
@@ -428,3 +447,46 @@ def dynamo_1d(k=1, n=64, eta=0.1, xi=0.5, rho=1e12, p=1.0, gamma=4.0 / 3.0):
 def dynamo_growth_rate(k, eta, xi):
     """Positive root of lambda^2 + lambda/eta + k^2 - k xi/eta = 0."""
     return 0.5 * (-1.0 / eta + math.sqrt(1.0 / eta ** 2 + 4.0 * (k * xi / eta - k * k)))
+
+
+# --------------------------------------------------------------------------
+# GLM hyperbolic cleaning workloads (Sec. 3.1, Sec. 5)
+# --------------------------------------------------------------------------
+
+def glm_wave(n=64, k=1, b=1e-3, kappa=1.0, rho=1.0, p=1.0, gamma=4.0 / 3.0, eta=1.0):
+    """1-D (B^x, Phi) mode on periodic [0, 2 pi]: cell-centred B^x = b cos(kx), Phi = 0,
+    matter at rest, E = 0.  For small b the GLM subsystem is the damped wave
+    f'' + kappa f' + k^2 f = 0 for the amplitude f(t) of B^x (see glm_wave_amplitude)."""
+    ndim, nn, lo, hi = 1, [n, 1, 1], [0.0, 0.0, 0.0], [2 * math.pi, 1.0, 1.0]
+    c, f = _axes(ndim, nn, lo, hi)
+    X, _, _ = _mesh(c[0], c[1], c[2])
+    z = np.zeros_like(X)
+    prim = [np.full_like(X, rho), z.copy(), z.copy(), z.copy(), np.full_like(X, p), z.copy(), z.copy(), z.copy()]
+    bcell = [b * np.cos(k * X), z.copy(), z.copy()]
+    return Problem("glm_wave_1d", ndim, nn, lo, hi, ["periodic"] * 3, gamma, prim, bcell=bcell, phi=z.copy(),
+                   kappa=kappa, eta_u=eta, cfl=0.4, info={"k": k, "b": b})
+
+
+def glm_wave_amplitude(t, k, kappa):
+    """Amplitude of B^x for f'' + kappa f' + k^2 f = 0, f(0) = 1, f'(0) = 0 (k > kappa/2)."""
+    w = math.sqrt(k * k - 0.25 * kappa * kappa)
+    return math.exp(-0.5 * kappa * t) * (math.cos(w * t) + 0.5 * kappa / w * math.sin(w * t))
+
+
+def monopole(n=64, ndim=3, kappa=1.0, R=0.2, L=2.0, rho=1.0, eps=0.1, gamma=5.0 / 3.0, eta=1e-16):
+    """Magnetic monopole test for hyperbolic cleaning (Sec. 5): cell-centred
+    B^x = exp(-r^2/R^2) - exp(-1) for r < R, else 0 (a Gaussian monopole), rho = 1,
+    eps = 0.1 (p = (Gamma - 1) rho eps), Gamma = 5/3, v = E = 0, eta = 1e-16, on
+    [-L, L]^ndim with outflow boundaries (the paper's run is 3-D, 64^3)."""
+    nn = [n if d < ndim else 1 for d in range(3)]
+    lo = [-L if d < ndim else 0.0 for d in range(3)]
+    hi = [L if d < ndim else 1.0 for d in range(3)]
+    c, f = _axes(ndim, nn, lo, hi)
+    X, Y, Z = _mesh(c[0], c[1], c[2])
+    r2 = X * X + (Y * Y if ndim > 1 else 0.0) + (Z * Z if ndim > 2 else 0.0)
+    bx = np.where(r2 < R * R, np.exp(-r2 / (R * R)) - math.exp(-1.0), 0.0)
+    z = np.zeros_like(X)
+    prim = [np.full_like(X, rho), z.copy(), z.copy(), z.copy(), np.full_like(X, (gamma - 1.0) * rho * eps),
+            z.copy(), z.copy(), z.copy()]
+    return Problem(f"monopole_{ndim}d", ndim, nn, lo, hi, ["outflow"] * 3, gamma, prim, bcell=[bx, z.copy(), z.copy()],
+                   phi=z.copy(), kappa=kappa, eta_u=eta, cfl=0.4)

@@ -1,0 +1,263 @@
+"""Pins of the oracle's GLM hyperbolic-cleaning variant (Sec. 3.1): cell-centred q_B^i
+and q_Phi advanced with the other cell-centred variables.  Each check is fixed by
+the mathematics, not by the oracle itself:
+
+* a small (B^x, Phi) mode is the damped wave f'' + kappa f' + k^2 f = 0 (closed form);
+* on a periodic flat grid the totals of D, S, tau and q_B are conserved exactly, and
+  the total of q_Phi follows the explicit SSP2 stability polynomial of -kappa dt;
+* the monopole test of Sec. 5: the L1 norm of div B falls faster for larger kappa;
+* in 1-D with uniform B^x the GLM and CT operators are the same scheme, so a GLM
+  step equals the (separately pinned) CT step;
+* mirror x <-> y (B axial, Phi pseudoscalar) and a 1-D problem embedded along each
+  axis of a 3-D grid;
+* the central curl of a cell-centred potential: exact for a linear potential and
+  divergence-free (central differences commute);
+* a constant metric (alpha, psi) is a rescaling of flat space: the metric run on
+  dx / psi^2 with dt / alpha reproduces the flat run, variable by variable, with
+  the powers of psi that the densitisation gives (for the CT scheme as well);
+* the reflection x -> -x of a 1-D line with a metric.
+All 14 mistakes planted in a scratch copy of the GLM code (signs, metric factors,
+densitisation, indices, one-sided face states, stage folds) fail one of these."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_03732_gb300 import problems as P
+
+
+def _run_wave(n, T, kappa):
+    pr = P.glm_wave(n=n, k=1, kappa=kappa)
+    st = oracle.from_problem_glm(pr)
+    dt0 = oracle.cfl_dt(st.grid, pr.cfl)
+    nst = int(math.ceil(T / dt0))
+    for _ in range(nst):
+        st.step(T / nst)
+    assert st.fails == 0
+    X = (np.arange(n) + 0.5) * 2 * math.pi / n
+    bx = st.qB[0][st.grid.interior()].ravel()
+    return 2.0 * np.mean(bx * np.cos(X)) / pr.info["b"], st
+
+
+def test_glm_damped_wave_closed_form():
+    T, kappa = 3.0, 1.0
+    exact = P.glm_wave_amplitude(T, 1, kappa)
+    a64, _ = _run_wave(64, T, kappa)
+    a128, st = _run_wave(128, T, kappa)
+    e64, e128 = abs(a64 - exact), abs(a128 - exact)
+    assert e128 < 2e-4, (a128, exact)
+    assert e64 / e128 > 3.0, (e64, e128)          # second order
+    # Phi carries the other quadrature: Phi = b sin(kx) g(t), g = -f'/k
+    w = math.sqrt(1 - 0.25 * kappa ** 2)
+    fp = -math.exp(-0.5 * kappa * T) * (w + 0.25 * kappa ** 2 / w) * math.sin(w * T)
+    X = (np.arange(128) + 0.5) * 2 * math.pi / 128
+    g = 2.0 * np.mean(st.qphi[st.grid.interior()].ravel() * np.sin(X)) / 1e-3
+    assert abs(g - (-fp)) < 1e-3, (g, -fp)
+
+
+def test_glm_periodic_invariants():
+    pr = P.random_box(21, 2, [20, 18], bc="periodic", glm=True, kappa=3.0)
+    st = oracle.from_problem_glm(pr)
+    I = st.grid.interior()
+    dt = oracle.cfl_dt(st.grid, pr.cfl)
+    z = pr.kappa * dt
+
+    def tot():
+        return [st.q[v][I].sum() for v in range(5)] + [b[I].sum() for b in st.qB] + [st.qphi[I].sum()]
+
+    t0 = tot()
+    for _ in range(4):
+        before = tot()
+        st.step(dt)
+        after = tot()
+        r = after[8] / before[8]
+        assert abs(r - (1.0 - z + 0.5 * z * z)) < 1e-12, r
+    assert st.fails == 0
+    t1 = tot()
+    for v in range(8):
+        assert abs(t1[v] - t0[v]) <= 1e-13 * max(1.0, abs(t0[v])), (v, t0[v], t1[v])
+
+
+def test_glm_monopole_damping_increases_with_kappa():
+    """Sec. 5 monopole test, here in 2-D at 64^2 on [-2, 2]^2 (the paper's run is
+    64^3): at t = 0.5 the L1 norm of div B is strictly smaller for each larger kappa of
+    0, 1, 5, 10 (the paper's statement).  Much later the longest wavelengths of the
+    kappa = 10 run are over-damped and decay more slowly, so the check is at t = 0.5."""
+    res = []
+    for kappa in (0.0, 1.0, 5.0, 10.0):
+        pr = P.monopole(n=64, ndim=2, kappa=kappa)
+        st = oracle.from_problem_glm(pr)
+        dt = oracle.cfl_dt(st.grid, pr.cfl)
+        d0 = oracle.divb_cc(st.grid, st.qB)[0]
+        nst = int(round(0.5 / dt))
+        for _ in range(nst):
+            st.step(dt)
+        assert st.fails == 0
+        res.append(oracle.divb_cc(st.grid, st.qB)[0])
+    assert res[0] > d0                     # no damping: the monopole spreads
+    assert res[0] > res[1] > res[2] > res[3], res
+    assert res[3] < 0.35 * d0
+
+
+def test_glm_equals_ct_in_1d():
+    """1-D, uniform B^x, Phi = 0, flat: the GLM fluxes of the transverse B are the 1-D
+    reduction of the UCT edge EMF and B^x, Phi stay put, so both variants take the same
+    step."""
+    pr = P.shock_tube(200)
+    ct = oracle.from_problem(pr)
+    g = oracle.Grid(1, pr.n, pr.dx, pr.bc, pr.gamma)
+    glm = oracle.GLMState(g, pr.prim, [b.copy() for b in ct.bf], g.zeros(), kappa=2.0, eta_u=pr.eta_u)
+    dt = oracle.cfl_dt(g, pr.cfl)
+    for _ in range(3):
+        ct.step(dt)
+        glm.step(dt)
+    I = g.interior()
+    for v in range(8):
+        np.testing.assert_allclose(glm.q[v][I], ct.q[v][I], rtol=1e-12, atol=1e-13, err_msg=str(v))
+    for d in range(3):
+        np.testing.assert_allclose(glm.qB[d][I], ct.bf[d][I], rtol=1e-12, atol=1e-13, err_msg=str(d))
+    assert np.abs(glm.qphi[I]).max() < 1e-14
+
+
+def test_glm_transpose_symmetry():
+    """Mirror x <-> y: polar vectors swap components, B (axial) goes to minus its
+    swapped components and Phi (tied to div B, a pseudoscalar) changes sign."""
+    pr = P.random_box(8, 2, [12, 12], bc="periodic", glm=True, kappa=1.5)
+    st = oracle.from_problem_glm(pr)
+    sw = lambda a: np.ascontiguousarray(np.swapaxes(a, 1, 2))
+    prim_T = [sw(pr.prim[0]), sw(pr.prim[2]), sw(pr.prim[1]), sw(pr.prim[3]), sw(pr.prim[4]),
+              sw(pr.prim[6]), sw(pr.prim[5]), sw(pr.prim[7])]
+    qB_T = [-sw(st.qB[1]), -sw(st.qB[0]), -sw(st.qB[2])]
+    g_T = oracle.Grid(2, [12, 12], st.grid.dx[:2][::-1], ["periodic"] * 2, pr.gamma)
+    L = oracle.explicit_L_glm(st.grid, pr.kappa, st.prim, st.qB, st.qphi)
+    LT = oracle.explicit_L_glm(g_T, pr.kappa, prim_T, qB_T, -sw(st.qphi))
+    Lm = [L[0], L[2], L[1], L[3], L[4], L[6], L[5], L[7], -L[9], -L[8], -L[10], -L[11]]
+    I = st.grid.interior()
+    for k, (a, b) in enumerate(zip(Lm, LT)):
+        np.testing.assert_allclose(sw(a)[I], b[I], rtol=1e-12, atol=1e-11, err_msg=str(k))
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_glm_1d_problem_embedded_in_3d(axis):
+    n = 20
+    pr1 = P.random_box(23, 1, [n], bc="periodic", glm=True, kappa=2.0)
+    st1 = oracle.from_problem_glm(pr1)
+    shape3 = [4, 4, 4]
+    shape3[axis] = n
+    g3 = oracle.Grid(3, shape3, [pr1.dx[0]] * 3, ["periodic"] * 3, pr1.gamma)
+
+    def embed(a1):
+        out = np.empty(g3.shape)
+        np.moveaxis(out, 2 - axis, 2)[...] = a1[0, 0, :]
+        return out
+
+    perm = [(axis + k) % 3 for k in range(3)]
+    prim3 = [None] * 8
+    prim3[0] = embed(pr1.prim[0])
+    prim3[4] = embed(pr1.prim[4])
+    qB3 = [None] * 3
+    for k in range(3):
+        prim3[1 + perm[k]] = embed(pr1.prim[1 + k])
+        prim3[5 + perm[k]] = embed(pr1.prim[5 + k])
+        qB3[perm[k]] = embed(st1.qB[k])
+    st3 = oracle.GLMState(g3, prim3, qB3, embed(st1.qphi), pr1.kappa, eta=embed(pr1.eta), eta_u=pr1.eta_u)
+    dt = 0.2 * pr1.dx[0]
+    for _ in range(2):
+        st1.step(dt)
+        st3.step(dt)
+    sl3 = g3.interior()
+    line3 = lambda a: np.moveaxis(a[sl3], 2 - axis, 2)[0, 0, :]
+    l1 = lambda a: a[st1.grid.interior()][0, 0, :]
+    for v in (0, 4):
+        np.testing.assert_allclose(line3(st3.q[v]), l1(st1.q[v]), rtol=1e-12, atol=1e-13)
+    for k in range(3):
+        np.testing.assert_allclose(line3(st3.q[1 + perm[k]]), l1(st1.q[1 + k]), rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(line3(st3.q[5 + perm[k]]), l1(st1.q[5 + k]), rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(line3(st3.qB[perm[k]]), l1(st1.qB[k]), rtol=1e-11, atol=1e-12)
+    np.testing.assert_allclose(line3(st3.qphi), l1(st1.qphi), rtol=1e-11, atol=1e-12)
+
+
+def test_curl_of_cell_potential():
+    g = oracle.Grid(3, [6, 5, 7], [0.1, 0.2, 0.15], ["outflow"] * 3, 5.0 / 3.0)
+    Z, Y, X = np.meshgrid(*[(np.arange(g.N[d]) - 1.5) * g.dx[d] for d in (2, 1, 0)], indexing="ij")
+    # linear potential: B = curl A exactly
+    A = [0.3 * Y - 0.7 * Z, 1.1 * Z + 0.2 * X, -0.4 * X + 0.9 * Y]
+    qB = oracle.curl_A_cc(g, [np.ascontiguousarray(a) for a in A])
+    I = g.interior()
+    exact = [0.9 - 1.1, -0.7 - (-0.4), 0.2 - 0.3]   # (d_y A_z - d_z A_y, d_z A_x - d_x A_z, d_x A_y - d_y A_x)
+    for d in range(3):
+        np.testing.assert_allclose(qB[d][I], exact[d], rtol=0, atol=1e-13)
+    # a periodic random potential: the central divergence of the central curl vanishes
+    gp = oracle.Grid(3, [8, 6, 7], [0.1, 0.2, 0.15], ["periodic"] * 3, 5.0 / 3.0)
+    rng = np.random.default_rng(4)
+    Ap = []
+    for _ in range(3):
+        core = rng.normal(size=(7, 6, 8))
+        Ap.append(np.ascontiguousarray(np.pad(core, 2, mode="wrap")))
+    qBp = oracle.curl_A_cc(gp, Ap)
+    assert oracle.divb_cc(gp, qBp)[2] < 1e-12
+    assert np.abs(qBp[0][gp.interior()]).max() > 1.0
+
+
+def _scaled_pair(variant, al=0.8, ps=1.1):
+    """A flat problem and its image on a constant metric (alpha, psi): the metric run
+    on dx / psi^2 with dt / alpha is the flat run seen in coordinates, so its densitised
+    variables are the flat ones times psi^6 (D, tau, Phi), psi^8 (S_i), psi^4 (E^i, B^i)."""
+    p2, p4, p6 = ps ** 2, ps ** 4, ps ** 6
+    pr = P.random_box(31, 2, [14, 12], bc="periodic", glm=True, kappa=2.0)
+    gm = oracle.Grid(2, pr.n, [d / p2 for d in pr.dx], pr.bc, pr.gamma)
+    alpha, psi = np.full(pr.shape, al), np.full(pr.shape, ps)
+    prim_m = [pr.prim[0]] + [pr.prim[1 + i] / p2 for i in range(3)] + [pr.prim[4]] + \
+             [pr.prim[5 + i] / p2 for i in range(3)]
+    if variant == "glm":
+        sf = oracle.from_problem_glm(pr)
+        sm = oracle.GLMState(gm, prim_m, [p4 * b for b in sf.qB], p6 * sf.qphi, pr.kappa, alpha, psi, pr.eta,
+                             pr.eta_u)
+    else:
+        sf = oracle.from_problem(pr)
+        sm = oracle.State(gm, prim_m, [p4 * b for b in sf.bf], alpha, psi, pr.eta, pr.eta_u)
+    return pr, sf, sm, al, (p6, ps ** 8, p4)
+
+
+@pytest.mark.parametrize("variant", ["glm", "ct"])
+def test_constant_metric_is_a_rescaling(variant):
+    pr, sf, sm, al, (p6, p8, p4) = _scaled_pair(variant)
+    dtf = oracle.cfl_dt(sf.grid, pr.cfl)
+    dtm = oracle.cfl_dt(sm.grid, pr.cfl, sm.alpha, sm.psi)
+    assert abs(dtm * al / dtf - 1) < 1e-14
+    for _ in range(2):
+        sf.step(dtf)
+        sm.step(dtm)
+    assert sf.fails == 0 and sm.fails == 0
+    I = sf.grid.interior()
+    scale = [p6, p8, p8, p8, p6, p4, p4, p4]
+    for v in range(8):
+        np.testing.assert_allclose(sm.q[v][I], scale[v] * sf.q[v][I], rtol=1e-12, atol=1e-13 * np.abs(sm.q[v]).max(),
+                                   err_msg=str(v))
+    fm = sm.qB if variant == "glm" else sm.bf
+    ff = sf.qB if variant == "glm" else sf.bf
+    for d in range(3):
+        np.testing.assert_allclose(fm[d][I], p4 * ff[d][I], rtol=1e-12, atol=1e-13 * np.abs(fm[d]).max())
+    if variant == "glm":
+        np.testing.assert_allclose(sm.qphi[I], p6 * sf.qphi[I], rtol=1e-12, atol=1e-13 * np.abs(sm.qphi).max())
+
+
+def test_glm_reflection_1d():
+    """x -> -x on a periodic line (with a metric): u^x, E^x, S_x change sign, the
+    axial B keeps B^x and flips B^y, B^z, and Phi (pseudoscalar) flips.  A one-sided
+    choice anywhere in the face states breaks it."""
+    pr = P.random_box(29, 1, [22], bc="periodic", glm=True, kappa=1.0, metric=True)
+    st = oracle.from_problem_glm(pr)
+    rv = lambda a: np.ascontiguousarray(a[..., ::-1])
+    sgn_p = [1, -1, 1, 1, 1, -1, 1, 1]          # prim and q (rho/D, u/S, p/tau, E)
+    sgn_b = [1, -1, -1]
+    prim_R = [s * rv(a) for s, a in zip(sgn_p, st.prim)]
+    qB_R = [s * rv(a) for s, a in zip(sgn_b, st.qB)]
+    L = oracle.explicit_L_glm(st.grid, pr.kappa, st.prim, st.qB, st.qphi, pr.alpha, pr.psi)
+    LR = oracle.explicit_L_glm(st.grid, pr.kappa, prim_R, qB_R, -rv(st.qphi), rv(pr.alpha), rv(pr.psi))
+    I = st.grid.interior()
+    sg = sgn_p + sgn_b + [-1]
+    for v in range(12):
+        np.testing.assert_allclose(sg[v] * rv(L[v])[I], LR[v][I], rtol=1e-12, atol=1e-12 * np.abs(L[v]).max(),
+                                   err_msg=str(v))
