@@ -56,6 +56,10 @@ typedef enum {
 
 enum { GRMHD_BC_PERIODIC = 0, GRMHD_BC_OUTFLOW = 1, GRMHD_BC_FIXED = 2 };
 enum { GRMHD_PREC_FP64 = 0, GRMHD_PREC_MIXED = 1 };
+/* Divergence-free handling of B (Sec. 3): staggered face fields with upwind
+ * constrained transport (Sec. 3.2), or cell-centred fields with GLM hyperbolic
+ * cleaning (Sec. 3.1). */
+enum { GRMHD_DIVB_CT = 0, GRMHD_DIVB_GLM = 1 };
 
 /* Uniform Cartesian grid (Sec. 5 test set-ups).  bc: per direction; FIXED keeps the
  * ghost values that init wrote (Sec. 5, "values at the outer boundaries are kept
@@ -93,6 +97,14 @@ typedef struct {
                           whose solve fails, is set to rest at (rho_atm, p_atm) with E
                           kept; 0 disables it (failures then keep their primitives) */
     double p_atm;
+    int divb;          /* GRMHD_DIVB_CT (0, default) or GRMHD_DIVB_GLM.  GLM (Sec. 3.1):
+                          the three "bface" arrays of every call hold cell-centred
+                          q_B^i = psi^6 B^i instead of face values, and a fourth field
+                          q_Phi = psi^6 Phi (grmhd_bind_phi) is evolved with
+                          (f_Phi)^i = alpha q_B^i, s_Phi = -alpha kappa_b q_Phi
+                          + q_B^i d_i alpha and s_B^i = -psi^6 alpha gamma^{ij} d_j Phi.
+                          FP64 only; not accepted by the batched executor */
+    double kappa_b;    /* GLM damping kappa_B >= 0 (Sec. 3.1); unused by CT */
 } grmhd_params;
 
 /* IMEX-SSP2(2,2,2) of Sec. 2.3 (Pareschi & Russo), gamma = 1 - 1/sqrt(2). */
@@ -111,6 +123,12 @@ grmhd_status grmhd_destroy(grmhd_ctx* ctx);
  * E^1..3, densitised); bface: 3 padded face arrays (q_B^x, q_B^y, q_B^z); scratch:
  * at least grmhd_scratch_bytes bytes, 256-byte aligned. */
 grmhd_status grmhd_bind(grmhd_ctx* ctx, double* const* q, double* const* bface, void* scratch, size_t scratch_bytes);
+
+/* GLM only (Sec. 3.1): bind the caller's q_Phi = psi^6 Phi, one padded cell array
+ * (device), evolved in place with the bound state.  Required before
+ * grmhd_init_from_prims and grmhd_stage on a GLM context; GRMHD_ERR_STATE on a CT
+ * context. */
+grmhd_status grmhd_bind_phi(grmhd_ctx* ctx, double* q_phi);
 
 /* Fixed background metric (Sec. 2.1): alpha and psi as padded cell arrays read at
  * every padded cell (ghosts included, no boundary condition applied); NULL = flat
@@ -131,7 +149,11 @@ grmhd_status grmhd_set_dynamo(grmhd_ctx* ctx, double xi);
  * whose stencil leaves the array are zero); otherwise the bound face arrays are used
  * as they are.  Then q = prim2con(prim, cell-averaged B) at every padded cell, and
  * prim (8 padded arrays, ghosts included: they are the FIXED boundary values) is
- * kept as the Newton starting point. */
+ * kept as the Newton starting point.
+ * GLM context: A_edge, if given, is a potential at cell centres (read on the whole
+ * padded grid) and the interior cell fields become its central-difference curl
+ * (Sec. 4, cell-centred case; ghost values of q_B are left as bound); q uses the
+ * cell fields directly.  q_Phi is taken as bound (zero it for the usual start). */
 grmhd_status grmhd_init_from_prims(grmhd_ctx* ctx, const double* const* prim, const double* const* A_edge,
                                    grmhd_stream_t stream);
 
@@ -161,13 +183,20 @@ grmhd_status grmhd_implicit(grmhd_ctx* ctx, double a_dt, double* const* q, const
 
 /* Explicit operator on caller buffers: prim (8 padded, ghosts = FIXED values) and
  * bface (3) -> L (11 padded: 8 cell-centred rates on the interior, 3 face rates on
- * the faces that the step updates). */
+ * the faces that the step updates).  CT contexts only. */
 grmhd_status grmhd_explicit_L(grmhd_ctx* ctx, const double* const* prim, const double* const* bface,
                               double* const* L, grmhd_stream_t stream);
 
+/* GLM explicit operator (Sec. 3.1) on caller buffers: prim (8), cell-centred q_B (3)
+ * and q_Phi (padded, ghosts = FIXED values) -> L (12 padded arrays, interior: the 8
+ * cell-centred rates, then q_B^1..3 and q_Phi).  GLM contexts only. */
+grmhd_status grmhd_explicit_L_glm(grmhd_ctx* ctx, const double* const* prim, const double* const* qB,
+                                  const double* q_phi, double* const* L, grmhd_stream_t stream);
+
 /* Diagnostics of the bound state: divb = {mean |div q_B|, rms, max} over interior
- * cells (Sec. 3.2), totals = volume sums of the 8 cell-centred q, nfail = Newton
- * failures since create.  Synchronises the stream. */
+ * cells (Sec. 3.2; on a GLM context the central-difference divergence of the cell
+ * fields), totals = volume sums of the 8 cell-centred q, nfail = Newton failures
+ * since create.  Synchronises the stream. */
 grmhd_status grmhd_diagnostics(grmhd_ctx* ctx, double* divb, double* totals, long long* nfail,
                                grmhd_stream_t stream);
 
@@ -193,7 +222,7 @@ const char* grmhd_last_error(void);
  * stage for all of them.  Each problem runs exactly the per-cell arithmetic it runs
  * alone (same kernels' item bodies, no cross-problem reduction), so its results are
  * bitwise those of grmhd_step on that context.  All contexts must share the tableau
- * and the precision.  The batch reads the contexts' state, scratch, metric and eta
+ * and the precision, and use constrained transport (GRMHD_DIVB_CT).  The batch reads the contexts' state, scratch, metric and eta
  * at the time of grmhd_batch_create; re-create it after re-binding a context.
  * ------------------------------------------------------------------------ */
 typedef struct grmhd_batch_s grmhd_batch;

@@ -312,6 +312,8 @@ grmhd_status grmhd_batch_scratch_bytes(grmhd_ctx* const* ctxs, int n, size_t* by
     int s = 0;
     for (int p = 0; p < n; p++) {
         if (!ctxs[p] || !ctx_bound(ctxs[p])) return batch_fail(GRMHD_ERR_STATE, "every context must be bound");
+        if (ctx_glm(ctxs[p]))
+            return batch_fail(GRMHD_ERR_ARG, "batched execution supports constrained transport (GRMHD_DIVB_CT) only");
         s = ctx_stages(ctxs[p]);
     }
     *bytes = rup(sizeof(ProbStage) * (size_t)n * s) + rup(sizeof(Chunk) * chunk_capacity(ctxs, n));

@@ -1,5 +1,6 @@
 // C-ABI of the GB300 resistive-MHD IMEX stage: context, scratch carving, launch
 // sequencing.  See include/grmhd.h for the contract of every call.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -52,9 +53,9 @@ struct grmhd_ctx_s {
     double* bf[3];
     double* prim[8];
     double* R[3];
-    double* base[4][11];
-    double* acc[11];
-    double* F[3][8];
+    double* base[4][12];   // later stages' bases: 8 cell-centred + 3 B (+ q_Phi for GLM)
+    double* acc[12];
+    double* F[3][12];      // FP64 face fluxes (8; 12 for GLM)
     double* Eh[3];
     float* p32[11];      // mixed precision: FP32 stage primitives + cell-centred q_B
     float* F32[3][8];    // mixed precision: FP32 face fluxes
@@ -68,6 +69,9 @@ struct grmhd_ctx_s {
     const double* eta;
     double eta_u;
     double xi;           // mean-field dynamo parameter (0: none)
+    bool glm;            // GLM cleaning with cell-centred B (Sec. 3.1) instead of CT
+    double kappa;        // GLM damping kappa_B
+    double* qphi;        // GLM: bound q_Phi
     long long launches;
     // optional per-kernel timing: events around each launch, folded on request
     bool timing;
@@ -130,7 +134,7 @@ Dims make_dims(const grmhd_grid* gr, double gam)
 }
 
 // scratch carve: returns the byte count; with base != NULL assigns the pointers
-size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base)
+size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base, bool glm = false)
 {
     const size_t arr = round_up(sizeof(double) * (size_t)g.ncell);
     size_t off = 0;
@@ -139,6 +143,20 @@ size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base)
         off += round_up(bytes);
         return p;
     };
+    if (glm) {
+        // GLM: 12 cell-centred variables per stage base and flux direction, no EMFs
+        for (int v = 0; v < 8; v++) { char* p = take(arr); if (c) c->prim[v] = (double*)p; }
+        for (int v = 0; v < 3; v++) { char* p = take(arr); if (c) c->R[v] = (double*)p; }
+        for (int k = 1; k < s; k++)
+            for (int v = 0; v < 12; v++) { char* p = take(arr); if (c) c->base[k][v] = (double*)p; }
+        for (int v = 0; v < 12; v++) { char* p = take(arr); if (c) c->acc[v] = (double*)p; }
+        for (int d = 0; d < ndim; d++)
+            for (int v = 0; v < 12; v++) { char* p = take(arr); if (c) c->F[d][v] = (double*)p; }
+        { char* p = take(sizeof(double) * kRedBlocks * 11); if (c) c->red_part = (double*)p; }
+        { char* p = take(sizeof(double) * 16); if (c) c->red_out = (double*)p; }
+        { char* p = take(sizeof(unsigned long long)); if (c) c->nfail = (unsigned long long*)p; }
+        return off;
+    }
     for (int v = 0; v < 8; v++) { char* p = take(arr); if (c) c->prim[v] = (double*)p; }
     for (int v = 0; v < 3; v++) { char* p = take(arr); if (c) c->R[v] = (double*)p; }
     for (int k = 1; k < s; k++)
@@ -293,6 +311,70 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     return GRMHD_OK;
 }
 
+// GLM (Sec. 3.1): fluxes of the 12 cell-centred variables per direction, then the
+// update; qB / qphi are the stage's cell fields
+grmhd_status explicit_part_glm(grmhd_ctx* c, CP8 prim, CP3 qB, const double* qphi, GlmUpdateArgs& a,
+                               cudaStream_t st)
+{
+    const Dims& g = c->g;
+    cudaError_t e;
+    GlmFluxArgs fa;
+    for (int v = 0; v < 8; v++) fa.prim[v] = prim.p[v];
+    for (int v = 0; v < 3; v++) fa.qB[v] = qB.p[v];
+    fa.qphi = qphi;
+    fa.psi = c->psi;
+    fa.alp = c->alp;
+    for (int d = 0; d < 3; d++) {
+        if (!g.act[d]) continue;
+        for (int v = 0; v < 12; v++) fa.F[v] = c->F[d][v];
+        const int tk = tbegin(c, KIND_FLUX, st);
+        e = launch_glm_flux(g, d, fa, c->nsm, st);
+        tend(c, tk, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "GLM flux kernel");
+    }
+    for (int d = 0; d < 3; d++)
+        for (int v = 0; v < 12; v++) a.F[d][v] = g.act[d] ? c->F[d][v] : nullptr;
+    for (int v = 0; v < 8; v++) a.prim[v] = prim.p[v];
+    for (int v = 0; v < 3; v++) a.qB[v] = qB.p[v];
+    a.qphi = qphi;
+    a.psi = c->psi;
+    a.alp = c->alp;
+    a.kappa = c->kappa;
+    const int tk = tbegin(c, KIND_UPDATE, st);
+    e = launch_glm_update(g, a, c->nsm, st);
+    tend(c, tk, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "GLM update kernel");
+    return GRMHD_OK;
+}
+
+// GLM stage update arguments (the stage folds of UpdateArgs over 12 variables)
+void glm_stage_args(grmhd_ctx* c, int i, double dt, GlmUpdateArgs* a)
+{
+    const int S = c->tab.s;
+    memset(a, 0, sizeof *a);
+    a->mode = UPD_STAGE;
+    a->stage = i;
+    a->s = S;
+    a->dt = dt;
+    for (int r = 0; r < S; r++) {
+        for (int k = 0; k < S; k++) {
+            a->At[r][k] = c->tab.At[r * S + k];
+            a->A[r][k] = c->tab.A[r * S + k];
+        }
+        a->wt[r] = c->tab.wt[r];
+        a->w[r] = c->tab.w[r];
+    }
+    for (int v = 0; v < 3; v++) a->R[v] = c->R[v];
+    for (int v = 0; v < 8; v++) a->qn[v] = c->q[v];
+    for (int v = 0; v < 3; v++) a->qn[8 + v] = c->bf[v];
+    a->qn[11] = c->qphi;
+    for (int k = 1; k < S; k++)
+        for (int v = 0; v < 12; v++) a->base[k][v] = c->base[k][v];
+    for (int v = 0; v < 12; v++) a->acc[v] = c->acc[v];
+}
+
 grmhd_status need_bound(const grmhd_ctx* c)
 {
     if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
@@ -327,7 +409,9 @@ grmhd_status grmhd_scratch_bytes(const grmhd_grid* grid, const grmhd_tableau* ta
     if ((s = check_tab(tab)) != GRMHD_OK) return s;
     if (!bytes) return fail(GRMHD_ERR_ARG, "bytes is NULL");
     Dims g = make_dims(grid, 2.0);
-    *bytes = carve(nullptr, g, tab->s, grid->ndim, nullptr);
+    // enough for either divergence scheme
+    *bytes = std::max(carve(nullptr, g, tab->s, grid->ndim, nullptr, false),
+                      carve(nullptr, g, tab->s, grid->ndim, nullptr, true));
     return GRMHD_OK;
 }
 
@@ -342,6 +426,12 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
     if (par->rho_atm < 0.0 || par->p_atm < 0.0) return fail(GRMHD_ERR_ARG, "atmosphere floor must be >= 0");
     if (par->precision != GRMHD_PREC_FP64 && par->precision != GRMHD_PREC_MIXED)
         return fail(GRMHD_ERR_ARG, "precision must be GRMHD_PREC_FP64 or GRMHD_PREC_MIXED");
+    if (par->divb != GRMHD_DIVB_CT && par->divb != GRMHD_DIVB_GLM)
+        return fail(GRMHD_ERR_ARG, "divb must be GRMHD_DIVB_CT or GRMHD_DIVB_GLM");
+    if (par->divb == GRMHD_DIVB_GLM && par->precision != GRMHD_PREC_FP64)
+        return fail(GRMHD_ERR_ARG, "GLM cleaning runs in FP64 only");
+    if (par->divb == GRMHD_DIVB_GLM && !(par->kappa_b >= 0.0))
+        return fail(GRMHD_ERR_ARG, "kappa_b must be >= 0");
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -363,6 +453,8 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
     }
     c->nsm = nsm;
     c->mixed = par->precision == GRMHD_PREC_MIXED;
+    c->glm = par->divb == GRMHD_DIVB_GLM;
+    c->kappa = c->glm ? par->kappa_b : 0.0;
     *out = c;
     return GRMHD_OK;
 }
@@ -423,9 +515,9 @@ grmhd_status grmhd_bind(grmhd_ctx* c, double* const* q, double* const* bface, vo
     for (int v = 0; v < 3; v++)
         if (!bface[v]) return fail(GRMHD_ERR_ARG, "bface[v] is NULL");
     if ((uintptr_t)scratch % kAlign) return fail(GRMHD_ERR_SCRATCH, "scratch must be 256-byte aligned");
-    const size_t need = carve(nullptr, c->g, c->tab.s, c->grid.ndim, nullptr);
+    const size_t need = carve(nullptr, c->g, c->tab.s, c->grid.ndim, nullptr, c->glm);
     if (scratch_bytes < need) return fail(GRMHD_ERR_SCRATCH, "scratch smaller than grmhd_scratch_bytes");
-    carve(c, c->g, c->tab.s, c->grid.ndim, (char*)scratch);
+    carve(c, c->g, c->tab.s, c->grid.ndim, (char*)scratch, c->glm);
     for (int v = 0; v < 8; v++) c->q[v] = q[v];
     for (int v = 0; v < 3; v++) c->bf[v] = bface[v];
     c->bound = true;
@@ -433,6 +525,14 @@ grmhd_status grmhd_bind(grmhd_ctx* c, double* const* q, double* const* bface, vo
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_bind_phi(grmhd_ctx* c, double* q_phi)
+{
+    if (!c || !q_phi) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_bind_phi");
+    if (!c->glm) return fail(GRMHD_ERR_STATE, "grmhd_bind_phi needs a GLM context");
+    c->qphi = q_phi;
     return GRMHD_OK;
 }
 
@@ -473,6 +573,22 @@ grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, cons
     const Dims& g = c->g;
     const size_t bytes = sizeof(double) * (size_t)g.ncell;
     cudaError_t e;
+    if (c->glm) {
+        if (!c->qphi) return fail(GRMHD_ERR_STATE, "call grmhd_bind_phi first");
+        if (A_edge) {
+            e = launch_curlA_cc(g, cp3c(A_edge), p3(c->bf), c->nsm, st);
+            c->launches++;
+            if (e != cudaSuccess) return cuda_fail(e, "curl kernel");
+        }
+        for (int v = 0; v < 8; v++) {
+            e = cudaMemcpyAsync(c->prim[v], prim[v], bytes, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        e = launch_prim2con_cc(g, cp8c(prim), cp3(c->bf), c->psi, p8(c->q), c->nsm, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "prim2con kernel");
+        return GRMHD_OK;
+    }
     if (A_edge) {
         for (int v = 0; v < 3; v++) {
             e = cudaMemsetAsync(c->bf[v], 0, bytes, st);
@@ -523,6 +639,7 @@ grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
     if (!(dt > 0.0)) return fail(GRMHD_ERR_ARG, "dt must be positive");
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
+    if (c->glm && !c->qphi) return fail(GRMHD_ERR_STATE, "call grmhd_bind_phi first");
     if (i == 0 && c->any_fixed) {
         e = ctx_copy_fixed_faces(c, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
@@ -530,6 +647,20 @@ grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
     ImpArgs ia;
     UpdateArgs a;
     ctx_stage_args(c, i, dt, &ia, &a);
+    if (c->glm) {
+        // GLM: the stage's cell q_B (ia.bf) and q_Phi are the bound state at stage 0 and
+        // the stage base afterwards
+        const int tk = tbegin(c, KIND_IMPLICIT, st);
+        e = launch_implicit_cc(c->g, ia, c->nsm, st);
+        tend(c, tk, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
+        GlmUpdateArgs ga;
+        glm_stage_args(c, i, dt, &ga);
+        CP8 pr;
+        for (int v = 0; v < 8; v++) pr.p[v] = c->prim[v];
+        return explicit_part_glm(c, pr, ia.bf, i == 0 ? c->qphi : c->base[i][11], ga, st);
+    }
     const int tk = tbegin(c, KIND_IMPLICIT, st);
     e = launch_implicit(c->g, ia, c->nsm, st);
     tend(c, tk, st);
@@ -563,8 +694,8 @@ grmhd_status grmhd_get_prims(grmhd_ctx* c, double* const* prim_out, grmhd_stream
                             st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     }
-    e = launch_implicit(c->g, imp_args(c, cp8(c->q), cp3(c->bf), 0.0, p8(prim_out), p3(nullptr), p3(nullptr), F11{}),
-                        c->nsm, st);
+    const ImpArgs ia = imp_args(c, cp8(c->q), cp3(c->bf), 0.0, p8(prim_out), p3(nullptr), p3(nullptr), F11{});
+    e = c->glm ? launch_implicit_cc(c->g, ia, c->nsm, st) : launch_implicit(c->g, ia, c->nsm, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "con2prim kernel");
     return GRMHD_OK;
@@ -576,8 +707,9 @@ grmhd_status grmhd_implicit(grmhd_ctx* c, double a_dt, double* const* q, const d
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     if (!q || !bface || !prim || !R) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_implicit");
-    cudaError_t e = launch_implicit(c->g, imp_args(c, cp8(q), cp3c(bface), a_dt, p8(prim), p3(R), p3(q + 5), F11{}),
-                                    c->nsm, (cudaStream_t)stream);
+    const ImpArgs ia = imp_args(c, cp8(q), cp3c(bface), a_dt, p8(prim), p3(R), p3(q + 5), F11{});
+    cudaError_t e = c->glm ? launch_implicit_cc(c->g, ia, c->nsm, (cudaStream_t)stream)
+                           : launch_implicit(c->g, ia, c->nsm, (cudaStream_t)stream);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "implicit kernel");
     return GRMHD_OK;
@@ -589,6 +721,7 @@ grmhd_status grmhd_explicit_L(grmhd_ctx* c, const double* const* prim, const dou
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     if (!prim || !bface || !L) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_explicit_L");
+    if (c->glm) return fail(GRMHD_ERR_STATE, "GLM context: use grmhd_explicit_L_glm");
     if (c->mixed) {
         cudaError_t e = launch_prim_to32(c->g, cp8c(prim), cp3c(bface), f11(c), c->nsm, (cudaStream_t)stream);
         c->launches++;
@@ -601,12 +734,27 @@ grmhd_status grmhd_explicit_L(grmhd_ctx* c, const double* const* prim, const dou
     return explicit_part(c, cp8c(prim), cp3c(bface), a, (cudaStream_t)stream);
 }
 
+grmhd_status grmhd_explicit_L_glm(grmhd_ctx* c, const double* const* prim, const double* const* qB,
+                                  const double* q_phi, double* const* L, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!prim || !qB || !q_phi || !L) return fail(GRMHD_ERR_ARG, "NULL argument to grmhd_explicit_L_glm");
+    if (!c->glm) return fail(GRMHD_ERR_STATE, "grmhd_explicit_L_glm needs a GLM context");
+    GlmUpdateArgs a;
+    memset(&a, 0, sizeof a);
+    a.mode = UPD_WRITE_L;
+    for (int v = 0; v < 12; v++) a.L[v] = L[v];
+    return explicit_part_glm(c, cp8c(prim), cp3c(qB), q_phi, a, (cudaStream_t)stream);
+}
+
 grmhd_status grmhd_diagnostics(grmhd_ctx* c, double* divb, double* totals, long long* nfail, grmhd_stream_t stream)
 {
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_diag(c->g, cp3(c->bf), cp8(c->q), c->dV, c->red_part, kRedBlocks, c->red_out, st);
+    cudaError_t e = c->glm ? launch_diag_cc(c->g, cp3(c->bf), cp8(c->q), c->dV, c->red_part, kRedBlocks, c->red_out, st)
+                           : launch_diag(c->g, cp3(c->bf), cp8(c->q), c->dV, c->red_part, kRedBlocks, c->red_out, st);
     c->launches += 2;
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics kernel");
     double out[11];
@@ -642,6 +790,7 @@ bool ctx_metric(const grmhd_ctx* c) { return c->psi || c->alp; }
 bool ctx_bound(const grmhd_ctx* c) { return c->bound; }
 bool ctx_mixed(const grmhd_ctx* c) { return c->mixed; }
 bool ctx_any_fixed(const grmhd_ctx* c) { return c->any_fixed; }
+bool ctx_glm(const grmhd_ctx* c) { return c->glm; }
 int ctx_stages(const grmhd_ctx* c) { return c->tab.s; }
 int ctx_nsm(const grmhd_ctx* c) { return c->nsm; }
 
@@ -693,8 +842,9 @@ float* ctx_emf32(grmhd_ctx* c, int k) { return c->Eh32[k]; }
 cudaError_t ctx_copy_fixed_faces(grmhd_ctx* c, cudaStream_t st)
 {
     for (int k = 1; k < c->tab.s; k++)
-        for (int v = 0; v < 3; v++) {
-            cudaError_t e = cudaMemcpyAsync(c->base[k][8 + v], c->bf[v], sizeof(double) * (size_t)c->g.ncell,
+        for (int v = 0; v < (c->glm ? 4 : 3); v++) {
+            const double* src = v < 3 ? c->bf[v] : c->qphi;
+            cudaError_t e = cudaMemcpyAsync(c->base[k][8 + v], src, sizeof(double) * (size_t)c->g.ncell,
                                             cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) return e;
         }

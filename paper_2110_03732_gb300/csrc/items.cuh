@@ -13,7 +13,9 @@ namespace grmhd {
 // implicit step (Sec. 2.4): item t = interior cell t (x fastest)
 // ---------------------------------------------------------------------------
 
-template <bool M>
+// CC: the magnetic field is cell-centred (a.bf holds cell q_B, GLM variant) instead of
+// staggered on faces
+template <bool M, bool CC = false>
 __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, long long t)
 {
     // flat metric: alpha = psi = 1 known at compile time
@@ -51,7 +53,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     for (int i = 0; i < 3; i++) {
         qEs[i] = qb.p[5 + i][id];
         ci.Es[i] = qEs[i] * ip4;
-        ci.B[i] = cell_qB(g, bf.p[i], i, c) * ip4;
+        ci.B[i] = (CC ? bf.p[i][id] : cell_qB(g, bf.p[i], i, c)) * ip4;
     }
     const double et = eta ? eta[id] : eta_u;
     ci.etat = a_dt > 0.0 ? et / (al * a_dt) : -1.0;
@@ -335,6 +337,76 @@ __device__ __forceinline__ void out_value(const UpdateArgs& a, int v, long long 
     else a.acc[v][o] = nv;
 }
 
+// non-stiff sources of the 8 cell-centred variables at interior cell c (linear index
+// o), added to Lc (Sec. 2.1, beta = 0, K_ij = 0): the Gauss-law charge term of s_E
+// and, with a metric, s_S and s_tau.  bsrc: staggered face q_B, or cell q_B if CC.
+template <bool CC>
+__device__ __forceinline__ void cell_sources(const Dims& g, const double* const* prim, const double* const* bsrc,
+                                             const double* __restrict__ psi, const double* __restrict__ alp,
+                                             const int* c, long long o, double* Lc)
+{
+    const double ps = psi ? psi[o] : 1.0;
+    const double al = alp ? alp[o] : 1.0;
+    const double p2 = ps * ps, p4 = p2 * p2, p6 = p4 * p2;
+    double u[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) u[i] = prim[1 + i][o];
+    const double W = sqrt(1.0 + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    const double iW = 1.0 / W;
+    // Gauss law: sqrt(gamma) rho_e = div q_E by central differences
+    double divqE = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (!g.act[d]) continue;
+        int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+        cp[d] += 1;
+        cm[d] -= 1;
+        double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
+        sp = sp * sp;
+        sm = sm * sm;
+        const double qp = sp * sp * sp * prim[5 + d][cell_at(g, cp)];
+        const double qm = sm * sm * sm * prim[5 + d][cell_at(g, cm)];
+        divqE += (qp - qm) * (0.5 * g.idx[d]);
+    }
+    // s_E (non-stiff part) = -alpha sqrt(gamma) rho_e v^i
+#pragma unroll
+    for (int i = 0; i < 3; i++) Lc[5 + i] -= al * divqE * (u[i] * iW);
+    if (psi || alp) {
+        // s_S and s_tau for beta = 0, K_ij = 0 (Sec. 2.1) in the orthonormal frame:
+        //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
+        //   s_tau = -psi^4 S_hat_i d_i alpha
+        const double rho = prim[0][o], p = prim[4][o];
+        double uh[3], Eh[3], Bh[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            uh[i] = p2 * u[i];
+            Eh[i] = p2 * prim[5 + i][o];
+            Bh[i] = p2 * (CC ? bsrc[i][o] : cell_qB(g, bsrc[i], i, c)) / p6;
+        }
+        const double rhoh = rho + g.gh * p;
+        const double U = 0.5 * (Eh[0] * Eh[0] + Eh[1] * Eh[1] + Eh[2] * Eh[2] + Bh[0] * Bh[0] +
+                                Bh[1] * Bh[1] + Bh[2] * Bh[2]);
+        const double D = rho * W;
+        const double tauD = rhoh * W * W - p + U;  // tau + D
+        double S[3];
+        S[0] = rhoh * W * uh[0] + (Eh[1] * Bh[2] - Eh[2] * Bh[1]);
+        S[1] = rhoh * W * uh[1] + (Eh[2] * Bh[0] - Eh[0] * Bh[2]);
+        S[2] = rhoh * W * uh[2] + (Eh[0] * Bh[1] - Eh[1] * Bh[0]);
+        const double tr = rhoh * (uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2]) + 3.0 * p + U;
+        (void)D;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            if (!g.act[i]) continue;
+            const double ap = alp ? alp[o + g.st[i]] : 1.0, am = alp ? alp[o - g.st[i]] : 1.0;
+            const double pp = psi ? psi[o + g.st[i]] : 1.0, pm = psi ? psi[o - g.st[i]] : 1.0;
+            const double dal = (ap - am) * (0.5 * g.idx[i]);
+            const double dps = (pp - pm) * (0.5 * g.idx[i]);
+            Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps / ps) * tr);
+            Lc[4] -= p4 * S[i] * dal;
+        }
+    }
+}
+
 template <bool M, typename T>
 __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, long long t)
 {
@@ -367,66 +439,7 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
                 Lc[v] -= ((double)Fv[o1] - (double)Fv[o]) * g.idx[d];
             }
         }
-        const double ps = psi ? psi[o] : 1.0;
-        const double al = alp ? alp[o] : 1.0;
-        const double p2 = ps * ps, p4 = p2 * p2, p6 = p4 * p2;
-        double u[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) u[i] = a.prim[1 + i][o];
-        const double W = sqrt(1.0 + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-        const double iW = 1.0 / W;
-        // Gauss law: sqrt(gamma) rho_e = div q_E by central differences
-        double divqE = 0.0;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            if (!g.act[d]) continue;
-            int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
-            cp[d] += 1;
-            cm[d] -= 1;
-            double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
-            sp = sp * sp;
-            sm = sm * sm;
-            const double qp = sp * sp * sp * a.prim[5 + d][cell_at(g, cp)];
-            const double qm = sm * sm * sm * a.prim[5 + d][cell_at(g, cm)];
-            divqE += (qp - qm) * (0.5 * g.idx[d]);
-        }
-        // s_E (non-stiff part) = -alpha sqrt(gamma) rho_e v^i
-#pragma unroll
-        for (int i = 0; i < 3; i++) Lc[5 + i] -= al * divqE * (u[i] * iW);
-        if (psi || alp) {
-            // s_S and s_tau for beta = 0, K_ij = 0 (Sec. 2.1) in the orthonormal frame:
-            //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
-            //   s_tau = -psi^4 S_hat_i d_i alpha
-            const double rho = a.prim[0][o], p = a.prim[4][o];
-            double uh[3], Eh[3], Bh[3];
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                uh[i] = p2 * u[i];
-                Eh[i] = p2 * a.prim[5 + i][o];
-                Bh[i] = p2 * cell_qB(g, a.bf[i], i, c) / p6;
-            }
-            const double rhoh = rho + g.gh * p;
-            const double U = 0.5 * (Eh[0] * Eh[0] + Eh[1] * Eh[1] + Eh[2] * Eh[2] + Bh[0] * Bh[0] +
-                                    Bh[1] * Bh[1] + Bh[2] * Bh[2]);
-            const double D = rho * W;
-            const double tauD = rhoh * W * W - p + U;  // tau + D
-            double S[3];
-            S[0] = rhoh * W * uh[0] + (Eh[1] * Bh[2] - Eh[2] * Bh[1]);
-            S[1] = rhoh * W * uh[1] + (Eh[2] * Bh[0] - Eh[0] * Bh[2]);
-            S[2] = rhoh * W * uh[2] + (Eh[0] * Bh[1] - Eh[1] * Bh[0]);
-            const double tr = rhoh * (uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2]) + 3.0 * p + U;
-            (void)D;
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                if (!g.act[i]) continue;
-                const double ap = alp ? alp[o + g.st[i]] : 1.0, am = alp ? alp[o - g.st[i]] : 1.0;
-                const double pp = psi ? psi[o + g.st[i]] : 1.0, pm = psi ? psi[o - g.st[i]] : 1.0;
-                const double dal = (ap - am) * (0.5 * g.idx[i]);
-                const double dps = (pp - pm) * (0.5 * g.idx[i]);
-                Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps / ps) * tr);
-                Lc[4] -= p4 * S[i] * dal;
-            }
-        }
+        cell_sources<false>(g, a.prim, a.bf, psi, alp, c, o, Lc);
 #pragma unroll
         for (int v = 0; v < 8; v++) out_value(a, v, o, Lc[v], v >= 5);
     }

@@ -10,7 +10,8 @@
 //                (Sec. 3.2); writes L, or folds it straight into the IMEX stage bases and
 //                the final combination (Sec. 2.3)
 //   k_prim2con, k_curlA (Sec. 4), k_dt (Sec. 2.5), k_divb, k_totals: set-up and
-//   diagnostics
+//   diagnostics; k_implicit_cc, k_curlA_cc, k_prim2con_cc, k_diag_cc: the same for the
+//   cell-centred fields of the GLM variant (its flux and update kernels: glm.cu)
 #include "grmhd_device.cuh"
 #include "items.cuh"
 #include "kernels.h"
@@ -28,6 +29,16 @@ __global__ void __launch_bounds__(128) k_implicit(Dims g, ImpArgs a)
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
         implicit_item<M>(g, a, t);
+}
+
+// the same solve with cell-centred q_B (GLM variant, Sec. 3.1)
+template <bool M>
+__global__ void __launch_bounds__(128) k_implicit_cc(Dims g, ImpArgs a)
+{
+    const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x)
+        implicit_item<M, true>(g, a, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -113,6 +124,48 @@ __global__ void k_prim2con(Dims g, CP8 prim, CP3 bf, const double* __restrict__ 
         for (int v = 0; v < 8; v++) pr[v] = prim.p[v][t];
 #pragma unroll
         for (int e = 0; e < 3; e++) B[e] = cell_qB(g, bf.p[e], e, c) / p6;
+        FaceState s;
+        face_state(pr, B, 0, ps, 1.0, g.gh, s);
+#pragma unroll
+        for (int v = 0; v < 8; v++) q.p[v][t] = s.q[v];
+    }
+}
+
+// cell-centred q_B^i = eta^{ijk} d_j A_k from a cell-centred potential by central
+// differences (Sec. 4, cell-centred fields), interior cells; the potential is read
+// as given on the whole padded grid
+__global__ void k_curlA_cc(Dims g, CP3 A, P3 qB)
+{
+    const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = g.ng[0] + (int)(t % g.n[0]);
+        const int j = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
+        const int k = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long o = lin(g, i, j, k);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int b = (a + 1) % 3, c = (a + 2) % 3;
+            double r = 0.0;
+            if (g.act[b]) r += (A.p[c][o + g.st[b]] - A.p[c][o - g.st[b]]) * (0.5 * g.idx[b]);
+            if (g.act[c]) r -= (A.p[b][o + g.st[c]] - A.p[b][o - g.st[c]]) * (0.5 * g.idx[c]);
+            qB.p[a][o] = r;
+        }
+    }
+}
+
+// prim -> cons with cell-centred q_B, every padded cell
+__global__ void k_prim2con_cc(Dims g, CP8 prim, CP3 qB, const double* __restrict__ psi, P8 q)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.ncell;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double ps = psi ? psi[t] : 1.0;
+        const double p2 = ps * ps, p6 = p2 * p2 * p2;
+        double pr[8], B[3];
+#pragma unroll
+        for (int v = 0; v < 8; v++) pr[v] = prim.p[v][t];
+#pragma unroll
+        for (int e = 0; e < 3; e++) B[e] = qB.p[e][t] / p6;
         FaceState s;
         face_state(pr, B, 0, ps, 1.0, g.gh, s);
 #pragma unroll
@@ -225,6 +278,49 @@ __global__ void __launch_bounds__(256) k_diag(Dims g, CP3 bf, CP8 q, double dV, 
     }
 }
 
+// the same with cell-centred q_B: div by central differences (GLM variant)
+__global__ void __launch_bounds__(256) k_diag_cc(Dims g, CP3 qB, CP8 q, double dV, double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
+    double s1 = 0.0, s2 = 0.0, mx = 0.0, tq[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) tq[v] = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[0] = g.ng[0] + (int)(t % g.n[0]);
+        c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
+        c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+        const long long o = lin(g, c[0], c[1], c[2]);
+        double dv = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!g.act[d]) continue;
+            int cu[3] = {c[0], c[1], c[2]}, cl[3] = {c[0], c[1], c[2]};
+            cu[d] += 1;
+            cl[d] -= 1;
+            dv += (qB.p[d][cell_at(g, cu)] - qB.p[d][cell_at(g, cl)]) * (0.5 * g.idx[d]);
+        }
+        s1 += fabs(dv);
+        s2 += dv * dv;
+        mx = fmax(mx, fabs(dv));
+#pragma unroll
+        for (int v = 0; v < 8; v++) tq[v] += q.p[v][o] * dV;
+    }
+    double r = block_reduce(s1, OpSum(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 11 + 0] = r;
+    r = block_reduce(s2, OpSum(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 11 + 1] = r;
+    r = block_reduce(mx, OpMax(), sh);
+    if (threadIdx.x == 0) part[blockIdx.x * 11 + 2] = r;
+#pragma unroll
+    for (int v = 0; v < 8; v++) {
+        r = block_reduce(tq[v], OpSum(), sh);
+        if (threadIdx.x == 0) part[blockIdx.x * 11 + 3 + v] = r;
+    }
+}
+
 // second pass: one block folds `nb` partial rows of width `w`; column kinds: 0 sum, 1 max
 __global__ void __launch_bounds__(256) k_fold(const double* __restrict__ part, int nb, int w,
                                               const int* __restrict__ kinds_unused, unsigned kinds_mask,
@@ -262,6 +358,14 @@ cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
     if (a.psi || a.alp) k_implicit<true><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
     else k_implicit<false><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st)
+{
+    const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
+    if (a.psi || a.alp) k_implicit_cc<true><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+    else k_implicit_cc<false><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
     return cudaGetLastError();
 }
 
@@ -392,6 +496,26 @@ cudaError_t launch_diag(const Dims& g, CP3 bf, CP8 q, double dV, double* part, i
                         cudaStream_t st)
 {
     k_diag<<<nblk, 256, 0, st>>>(g, bf, q, dV, part);
+    k_fold<<<1, 256, 0, st>>>(part, nblk, 11, nullptr, 1u << 2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_curlA_cc(const Dims& g, CP3 A, P3 qB, int nsm, cudaStream_t st)
+{
+    k_curlA_cc<<<grid_for((long long)g.n[0] * g.n[1] * g.n[2], 256, nsm), 256, 0, st>>>(g, A, qB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, P8 q, int nsm, cudaStream_t st)
+{
+    k_prim2con_cc<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, prim, qB, psi, q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_cc(const Dims& g, CP3 qB, CP8 q, double dV, double* part, int nblk, double* out,
+                           cudaStream_t st)
+{
+    k_diag_cc<<<nblk, 256, 0, st>>>(g, qB, q, dV, part);
     k_fold<<<1, 256, 0, st>>>(part, nblk, 11, nullptr, 1u << 2, out);
     return cudaGetLastError();
 }

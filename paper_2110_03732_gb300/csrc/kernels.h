@@ -93,4 +93,46 @@ cudaError_t launch_dt(const Dims& g, const double* psi, const double* alp, doubl
 cudaError_t launch_diag(const Dims& g, CP3 bf, CP8 q, double dV, double* part, int nblk, double* out,
                         cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// GLM hyperbolic cleaning variant (Sec. 3.1): cell-centred q_B^1..3 and q_Phi are
+// evolved with the 8 cell-centred variables; variables 8..10 are q_B^1..3 and 11 is
+// q_Phi in the arrays below.  Kernels in glm.cu.
+// ---------------------------------------------------------------------------
+
+struct GlmFluxArgs {
+    const double* prim[8];  // stage primitives (padded)
+    const double* qB[3];    // stage cell-centred q_B
+    const double* qphi;     // stage q_Phi
+    const double* psi;
+    const double* alp;
+    double* F[12];          // face fluxes of the 12 variables along the launch direction
+};
+
+struct GlmUpdateArgs {
+    int mode;               // UPD_WRITE_L or UPD_STAGE (as UpdateArgs)
+    int stage, s;
+    double dt;
+    double kappa;           // kappa_B, the damping of Phi
+    double At[4][4], A[4][4], wt[4], w[4];
+    const double* F[3][12];
+    const double* prim[8];
+    const double* qB[3];
+    const double* qphi;
+    const double* psi;
+    const double* alp;
+    const double* R[3];
+    double* L[12];
+    double* qn[12];
+    double* base[4][12];
+    double* acc[12];
+};
+
+cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st);
+cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st);
+cudaError_t launch_glm_update(const Dims& g, const GlmUpdateArgs& a, int nsm, cudaStream_t st);
+cudaError_t launch_curlA_cc(const Dims& g, CP3 A, P3 qB, int nsm, cudaStream_t st);
+cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, P8 q, int nsm, cudaStream_t st);
+cudaError_t launch_diag_cc(const Dims& g, CP3 qB, CP8 q, double dV, double* part, int nblk, double* out,
+                           cudaStream_t st);
+
 }  // namespace grmhd

@@ -37,7 +37,10 @@ class Tableau(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("gamma_eos", C.c_double), ("cfl", C.c_double), ("newton_tol", C.c_double),
-                ("newton_kmax", C.c_int), ("precision", C.c_int), ("rho_atm", C.c_double), ("p_atm", C.c_double)]
+                ("newton_kmax", C.c_int), ("precision", C.c_int), ("rho_atm", C.c_double), ("p_atm", C.c_double),
+                ("divb", C.c_int), ("kappa_b", C.c_double)]
+
+DIVB = {"ct": 0, "glm": 1}
 
 
 def library_path():
@@ -70,6 +73,8 @@ def lib():
     L.grmhd_get_prims.argtypes = [vp, dpp, vp]
     L.grmhd_implicit.argtypes = [vp, C.c_double, dpp, dpp, dpp, dpp, vp]
     L.grmhd_explicit_L.argtypes = [vp, dpp, dpp, dpp, vp]
+    L.grmhd_explicit_L_glm.argtypes = [vp, dpp, dpp, vp, dpp, vp]
+    L.grmhd_bind_phi.argtypes = [vp, vp]
     L.grmhd_diagnostics.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp]
     L.grmhd_set_timing.argtypes = [vp, C.c_int]
     L.grmhd_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
@@ -88,7 +93,7 @@ def lib():
                  "grmhd_step", "grmhd_get_prims", "grmhd_implicit", "grmhd_explicit_L", "grmhd_diagnostics",
                  "grmhd_set_timing", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
-                 "grmhd_batch_destroy"):
+                 "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -140,17 +145,20 @@ class Solver:
     """One resistive-MHD problem resident on the GPU: state, scratch and context.
 
     ``q`` (8 tensors) and ``bf`` (3 tensors) are the padded, densitised conserved
-    cell and face fields; the library updates them in place."""
+    cell and face fields; the library updates them in place.  With ``divb="glm"``
+    (GLM cleaning, Sec. 3.1) ``bf`` holds cell-centred q_B and ``phi`` the evolved
+    q_Phi; ``kappa`` is the damping kappa_B."""
 
     def __init__(self, ndim, n, lo, hi, bc, gamma, cfl=0.4, tableau=None, device="cuda", newton_tol=0.0,
-                 newton_kmax=0, rho_atm=0.0, p_atm=0.0, precision="fp64"):
+                 newton_kmax=0, rho_atm=0.0, p_atm=0.0, precision="fp64", divb="ct", kappa=0.0):
         self.L = lib()
         self.grid = make_grid(ndim, n, lo, hi, bc)
         self.tab = ssp2() if tableau is None else tableau
         prec = {"fp64": 0, "mixed": 1}[precision] if isinstance(precision, str) else int(precision)
         self.precision = prec
+        self.glm = (DIVB[divb] if isinstance(divb, str) else int(divb)) == DIVB["glm"]
         self.par = Params(float(gamma), float(cfl), float(newton_tol), int(newton_kmax), prec, float(rho_atm),
-                          float(p_atm))
+                          float(p_atm), DIVB["glm"] if self.glm else DIVB["ct"], float(kappa))
         self.device = torch.device(device)
         ng = [2 if d < ndim else 0 for d in range(3)]
         self.N = [self.grid.n[d] + 2 * ng[d] for d in range(3)]
@@ -172,6 +180,10 @@ class Solver:
         pq, self._kq = _ptrs(self.q)
         pb, self._kb = _ptrs(self.bf)
         check(self.L.grmhd_bind(ctx, pq, pb, C.c_void_p(self.scratch.data_ptr()), nbytes), "bind")
+        self.phi = None
+        if self.glm:
+            self.phi = torch.zeros(self.shape, **opts)
+            check(self.L.grmhd_bind_phi(ctx, C.c_void_p(self.phi.data_ptr())), "bind_phi")
         self.alpha = self.psi = self.eta = None
         self.eta_u = 0.0
 
@@ -197,11 +209,19 @@ class Solver:
     def set_dynamo(self, xi):
         check(self.L.grmhd_set_dynamo(self.ctx, float(xi)), "set_dynamo")
 
-    def init_from_prims(self, prim, A_edge=None, bface=None, stream=None):
+    def init_from_prims(self, prim, A_edge=None, bface=None, stream=None, phi=None):
+        """Initial state.  CT: A_edge on edges (curl -> faces) or face q_B in bface.
+        GLM: A_edge is a cell-centred potential (central curl), or bface holds the
+        cell-centred q_B; phi is the initial q_Phi (zero if None)."""
         prim = [self._dev(p) for p in prim]
         if bface is not None:
             for d in range(3):
                 self.bf[d].copy_(self._dev(bface[d]))
+        if self.glm:
+            if phi is None:
+                self.phi.zero_()
+            else:
+                self.phi.copy_(self._dev(phi))
         A = None if A_edge is None else [self._dev(a) for a in A_edge]
         pp, k1 = _ptrs(prim)
         pa, k2 = _ptrs(A) if A is not None else (None, None)
@@ -212,12 +232,23 @@ class Solver:
     def from_problem(cls, prob, device="cuda", **kw):
         kw.setdefault("rho_atm", prob.rho_atm)
         kw.setdefault("p_atm", prob.p_atm)
+        if kw.get("divb") == "glm":
+            kw.setdefault("kappa", prob.kappa)
         s = cls(prob.ndim, prob.n, prob.lo, prob.hi, prob.bc, prob.gamma, prob.cfl, device=device, **kw)
         s.set_metric(prob.alpha, prob.psi)
         s.set_eta(prob.eta, prob.eta_u if prob.eta is None else (prob.eta_u or 1.0))
         if getattr(prob, "xi", 0.0):
             s.set_dynamo(prob.xi)
-        s.init_from_prims(prob.prim, A_edge=prob.A_edge, bface=None if prob.A_edge is not None else prob.bface)
+        if s.glm:
+            # cell-centred fields: the potential at cell centres, else q_B given at cells;
+            # q_Phi = psi^6 Phi
+            qphi = None
+            if prob.phi is not None:
+                qphi = prob.phi if prob.psi is None else prob.psi ** 6 * prob.phi
+            s.init_from_prims(prob.prim, A_edge=prob.A_cell, bface=None if prob.A_cell is not None else prob.bcell,
+                              phi=qphi)
+        else:
+            s.init_from_prims(prob.prim, A_edge=prob.A_edge, bface=None if prob.A_edge is not None else prob.bface)
         return s
 
     # -- stepping ------------------------------------------------------------
@@ -247,6 +278,15 @@ class Solver:
         pr, k4 = _ptrs(R)
         check(self.L.grmhd_implicit(self.ctx, float(a_dt), pq, pb, pp, pr, _stream(stream)), "implicit")
         return R
+
+    def explicit_L_glm(self, prim, qB, qphi, stream=None):
+        """GLM explicit operator: 12 arrays (8 cell-centred, q_B^1..3, q_Phi)."""
+        Lt = [torch.zeros(self.shape, dtype=torch.float64, device=self.device) for _ in range(12)]
+        pp, k1 = _ptrs(prim)
+        pb, k2 = _ptrs(qB)
+        pl, k3 = _ptrs(Lt)
+        check(self.L.grmhd_explicit_L_glm(self.ctx, pp, pb, self._vp(qphi), pl, _stream(stream)), "explicit_L_glm")
+        return Lt
 
     def explicit_L(self, prim, bface, stream=None):
         Lt = [torch.zeros(self.shape, dtype=torch.float64, device=self.device) for _ in range(11)]

@@ -84,7 +84,11 @@ def test_scratch_bytes_formula(lib):
         arr32 = -(-4 * ncell // 256) * 256
         narr32 = 11 + 8 * ndim + 3
         small = -(-8 * 1024 * 11 // 256) * 256 + 256 + 256
-        assert b.value == narr * arr + narr32 * arr32 + small
+        ct = narr * arr + narr32 * arr32 + small
+        # GLM layout: 12 cell-centred variables per stage base, running sum and flux
+        # direction, no edge EMFs and no FP32 arrays
+        glm = (8 + 3 + 12 * (t.s - 1) + 12 + 12 * ndim) * arr + small
+        assert b.value == max(ct, glm)
 
 
 @pytest.mark.parametrize("field,value", [("ndim", 0), ("ndim", 4), ("n", 0), ("hi", -1.0), ("bc", 7),
@@ -129,3 +133,23 @@ def test_invalid_tableau_and_params_rejected(lib):
     ctx = C.c_void_p()
     assert lib.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
     assert not ctx.value
+
+
+@pytest.mark.parametrize("case", ["bad_divb", "glm_mixed", "glm_negative_kappa"])
+def test_invalid_divergence_scheme_rejected(lib, case):
+    from paper_2110_03732_gb300.grmhd import Params, Tableau
+    g = _grid()
+    t = Tableau()
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    p = Params(5.0 / 3.0, 0.4, 0.0, 0, 0, 0.0, 0.0, 1, 1.0)
+    if case == "bad_divb":
+        p.divb = 3
+    elif case == "glm_mixed":
+        p.precision = 1
+    else:
+        p.kappa_b = -1.0
+    ctx = C.c_void_p()
+    assert lib.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
+    assert not ctx.value
+    lib.grmhd_last_error.restype = C.c_char_p
+    assert len(lib.grmhd_last_error()) > 0
