@@ -214,27 +214,30 @@ struct CellIn {
 //   A_0 = W + eta_t + xi^2 (W^2 - 1)/p,  A_1 = eta_t/q + xi^2 eta_t W/(p q),
 //   A_2 = -xi eta_t/p,  A_3 = xi q/p,  A_4 = xi (1 - eta_t^2 + xi^2)/(p q),
 //   A_5 = -1 - xi^2 W/p,  with p = W + eta_t, q = 1 + eta_t W
-struct Dyn {
-    double A[6], Ad[6];
+template <typename T>
+struct DynT {
+    T A[6], Ad[6];
 };
+using Dyn = DynT<double>;
 
-__device__ __forceinline__ void dyn_coeffs(double W, double et, double xi, Dyn& d, bool derivs)
+template <typename T>
+__device__ __forceinline__ void dyn_coeffs(T W, T et, T xi, DynT<T>& d, bool derivs)
 {
-    const double x2 = xi * xi, p = W + et, q = 1.0 + et * W;
-    const double ip = 1.0 / p, iq = 1.0 / q, ipq = ip * iq;
-    d.A[0] = W + et + x2 * (W * W - 1.0) * ip;
+    const T x2 = xi * xi, p = W + et, q = T(1) + et * W;
+    const T ip = T(1) / p, iq = T(1) / q, ipq = ip * iq;
+    d.A[0] = W + et + x2 * (W * W - T(1)) * ip;
     d.A[1] = et * iq + x2 * et * W * ipq;
     d.A[2] = -xi * et * ip;
     d.A[3] = xi * q * ip;
-    d.A[4] = xi * (1.0 - et * et + x2) * ipq;
-    d.A[5] = -1.0 - x2 * W * ip;
+    d.A[4] = xi * (T(1) - et * et + x2) * ipq;
+    d.A[5] = -T(1) - x2 * W * ip;
     if (derivs) {
-        const double ip2 = ip * ip, iq2 = iq * iq;
-        d.Ad[0] = 1.0 + x2 * (1.0 + W * W + 2.0 * W * et) * ip2;
-        d.Ad[1] = -et * et * iq2 - x2 * et * et * (W * W - 1.0) * iq2 * ip2;
+        const T ip2 = ip * ip, iq2 = iq * iq;
+        d.Ad[0] = T(1) + x2 * (T(1) + W * W + T(2) * W * et) * ip2;
+        d.Ad[1] = -et * et * iq2 - x2 * et * et * (W * W - T(1)) * iq2 * ip2;
         d.Ad[2] = xi * et * ip2;
-        d.Ad[3] = xi * (et * et - 1.0) * ip2;
-        d.Ad[4] = -xi * (1.0 - et * et + x2) * (1.0 + et * et + 2.0 * W * et) * iq2 * ip2;
+        d.Ad[3] = xi * (et * et - T(1)) * ip2;
+        d.Ad[4] = -xi * (T(1) - et * et + x2) * (T(1) + et * et + T(2) * W * et) * iq2 * ip2;
         d.Ad[5] = -x2 * et * ip2;
     }
 }
@@ -268,10 +271,16 @@ __device__ __forceinline__ void dE_dynamo(const T* A, const T* Ad, T W, const T*
     dE[2][0] += X[1]; dE[2][1] -= X[0];
 }
 
+// |x| as the high word of its IEEE pattern with the sign cleared.  It is monotone in
+// |x|, so integer maxima of these words give the largest magnitude to within 2^-20
+// (relative, from below) without using the FP64 pipe.
+__device__ __forceinline__ unsigned mag_hi(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+__device__ __forceinline__ double from_hi(unsigned h) { return __hiloint2double((int)h, 0); }
+
 struct Eval {
     double W, E[3], wt, U, A1, iWe, iden, Esu, f[3], g;
-    double fm;   // max |f_i|
-    double M;    // momentum scale of f: max(|S_i|, |(E x B)_i|, |w_t u_i|)
+    double fm;   // max |f_i| (high-word maximum: within 2^-20 below the exact one)
+    double M;    // momentum scale of f: max(|S_i|, |(E x B)_i|, |w_t u_i|), likewise
 };
 
 // E(u) from A_0 E = eta_t E* + A_1 (E*.u) u - u x B with A_0 = W + eta_t,
@@ -298,20 +307,26 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
             e.E[i] = (c.etat * c.Es[i] + (a + b) * u[i] + dy.A[2] * uxEs[i] + dy.A[3] * c.B[i] + dy.A[5] * uxB[i]) *
                      e.iWe;
     } else if (c.etat >= 0.0) {
-        e.iWe = 1.0 / (e.W + c.etat);
-        e.A1 = c.etat / (1.0 + c.etat * e.W);
+        // the three reciprocals 1/(W + eta_t), 1/(1 + eta_t W) and 1/(W^2 - 1/Gamma_hat)
+        // from one division: r = 1/(a b d), 1/a = r b d, ...  (a, b >= 1 and d > 0, so
+        // the product neither overflows nor cancels)
+        const double a = e.W + c.etat, b = 1.0 + c.etat * e.W, d = uu + 1.0 - c.igh;
+        const double ab = a * b, r = 1.0 / (ab * d);
+        e.iWe = r * (b * d);
+        e.A1 = c.etat * (r * (a * d));
+        e.iden = r * ab;
         e.Esu = c.Es[0] * u[0] + c.Es[1] * u[1] + c.Es[2] * u[2];
-        const double a = e.A1 * e.Esu;
-        e.E[0] = (c.etat * c.Es[0] + a * u[0] - (u[1] * c.B[2] - u[2] * c.B[1])) * e.iWe;
-        e.E[1] = (c.etat * c.Es[1] + a * u[1] - (u[2] * c.B[0] - u[0] * c.B[2])) * e.iWe;
-        e.E[2] = (c.etat * c.Es[2] + a * u[2] - (u[0] * c.B[1] - u[1] * c.B[0])) * e.iWe;
+        const double ae = e.A1 * e.Esu;
+        e.E[0] = (c.etat * c.Es[0] + ae * u[0] - (u[1] * c.B[2] - u[2] * c.B[1])) * e.iWe;
+        e.E[1] = (c.etat * c.Es[1] + ae * u[1] - (u[2] * c.B[0] - u[0] * c.B[2])) * e.iWe;
+        e.E[2] = (c.etat * c.Es[2] + ae * u[2] - (u[0] * c.B[1] - u[1] * c.B[0])) * e.iWe;
     } else {
         e.iWe = 0.0; e.A1 = 0.0; e.Esu = 0.0;
         e.E[0] = c.Es[0]; e.E[1] = c.Es[1]; e.E[2] = c.Es[2];
     }
     e.U = 0.5 * (e.E[0] * e.E[0] + e.E[1] * e.E[1] + e.E[2] * e.E[2] + c.B[0] * c.B[0] + c.B[1] * c.B[1] +
                  c.B[2] * c.B[2]);
-    e.iden = 1.0 / (uu + 1.0 - c.igh);
+    if (!(c.etat >= 0.0) || c.xi != 0.0) e.iden = 1.0 / (uu + 1.0 - c.igh);
     e.wt = (e.W * (c.tau + c.D - e.U) - c.D * c.igh) * e.iden;
     const double x0 = e.E[1] * c.B[2] - e.E[2] * c.B[1];
     const double x1 = e.E[2] * c.B[0] - e.E[0] * c.B[2];
@@ -321,9 +336,9 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
     e.f[1] = w1 - c.S[1] + x1;
     e.f[2] = w2 - c.S[2] + x2;
     e.g = e.f[0] * e.f[0] + e.f[1] * e.f[1] + e.f[2] * e.f[2];
-    e.fm = fmax(fabs(e.f[0]), fmax(fabs(e.f[1]), fabs(e.f[2])));
-    e.M = fmax(fmax(fmax(fabs(c.S[0]), fabs(c.S[1])), fmax(fabs(c.S[2]), fabs(x0))),
-               fmax(fmax(fabs(x1), fabs(x2)), fmax(fabs(w0), fmax(fabs(w1), fabs(w2)))));
+    e.fm = from_hi(max(mag_hi(e.f[0]), max(mag_hi(e.f[1]), mag_hi(e.f[2]))));
+    e.M = from_hi(max(max(max(mag_hi(c.S[0]), mag_hi(c.S[1])), max(mag_hi(c.S[2]), mag_hi(x0))),
+                      max(max(mag_hi(x1), mag_hi(x2)), max(mag_hi(w0), max(mag_hi(w1), mag_hi(w2))))));
 }
 
 // Jacobian J_ij = w_t delta_ij + u_i dw_t/du_j + (dE/du_j x B)_i
@@ -393,93 +408,124 @@ __device__ __forceinline__ bool newton_dir(const double J[3][3], const double* f
     return true;
 }
 
-// Newton direction x = -J^{-1} f with J formed and inverted in FP32 (62x the FP64
-// rate on GB300).  The root is fixed by the FP64 residual f, so a direction accurate
-// to ~1e-6 only turns quadratic convergence into fast linear convergence.  J is
-// normalised by its diagonal and f by the momentum scale M before the conversion,
-// keeping every float O(1).  Returns false when the FP32 system is singular or the
-// direction is not finite (the caller then uses the FP64 Jacobian).
-__device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const double* u, const Eval& e, double* x)
+// FP32 copies of the per-cell constants of the solve, converted once per cell
+struct CellF {
+    float Es[3], B[3], etat, xi, igh;
+};
+
+__device__ __forceinline__ CellF cell_f32(const CellIn& c)
 {
-    const double iW = 1.0 / e.W;
-    float uf[3], Ef[3], Esf[3], Bf[3];
+    CellF f;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        uf[i] = (float)u[i];
-        Ef[i] = (float)e.E[i];
-        Esf[i] = (float)c.Es[i];
-        Bf[i] = (float)c.B[i];
+        f.Es[i] = (float)c.Es[i];
+        f.B[i] = (float)c.B[i];
     }
-    float dE[3][3];
-    if (c.etat >= 0.0 && c.xi != 0.0) {
-        Dyn dy;
-        dyn_coeffs(e.W, c.etat, c.xi, dy, true);
-        float A[6], Ad[6];
+    f.etat = (float)c.etat;
+    f.xi = (float)c.xi;
+    f.igh = (float)c.igh;
+    return f;
+}
+
+// Newton direction x = -J^{-1} f with J formed and inverted in FP32 (62x the FP64
+// rate on GB300).  The root is fixed by the FP64 residual f, so a direction accurate
+// to ~1e-6 only turns quadratic convergence into fast linear convergence.  Everything
+// J needs is recomputed in FP32 from the FP32 velocity and the per-cell constants,
+// except the two FP64 quantities that can cancel (w_t and tau + D - U).  J is
+// normalised by w_t and f by the power of two nearest below its scale M (an exact
+// rescaling), keeping every float O(1).  Returns false when the FP32 system is
+// singular or the direction is not finite (the caller then uses the FP64 Jacobian).
+__device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf, const double* u, const Eval& e,
+                                               double* x)
+{
+    float uf[3];
 #pragma unroll
-        for (int k = 0; k < 6; k++) {
-            A[k] = (float)dy.A[k];
-            Ad[k] = (float)dy.Ad[k];
-        }
-        dE_dynamo<float>(A, Ad, (float)e.W, uf, Ef, Esf, Bf, dE);
+    for (int i = 0; i < 3; i++) uf[i] = (float)u[i];
+    const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+    const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
+    float Ef[3], dE[3][3];
+    if (c.etat >= 0.0 && c.xi != 0.0) {
+        DynT<float> dy;
+        dyn_coeffs<float>(Wf, cf.etat, cf.xi, dy, true);
+        const float s = 1.0f / dy.A[0];
+        const float Esu = cf.Es[0] * uf[0] + cf.Es[1] * uf[1] + cf.Es[2] * uf[2];
+        const float Bu = cf.B[0] * uf[0] + cf.B[1] * uf[1] + cf.B[2] * uf[2];
+        const float ab = dy.A[1] * Esu + dy.A[4] * Bu;
+        const float uxEs[3] = {uf[1] * cf.Es[2] - uf[2] * cf.Es[1], uf[2] * cf.Es[0] - uf[0] * cf.Es[2],
+                               uf[0] * cf.Es[1] - uf[1] * cf.Es[0]};
+        const float uxB[3] = {uf[1] * cf.B[2] - uf[2] * cf.B[1], uf[2] * cf.B[0] - uf[0] * cf.B[2],
+                              uf[0] * cf.B[1] - uf[1] * cf.B[0]};
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            Ef[i] = (cf.etat * cf.Es[i] + ab * uf[i] + dy.A[2] * uxEs[i] + dy.A[3] * cf.B[i] + dy.A[5] * uxB[i]) * s;
+        dE_dynamo<float>(dy.A, dy.Ad, Wf, uf, Ef, cf.Es, cf.B, dE);
     } else if (c.etat >= 0.0) {
-        const float A1 = (float)e.A1, Esu = (float)e.Esu, s = (float)e.iWe, iWf = (float)iW;
+        const float s = 1.0f / (Wf + cf.etat);
+        const float A1 = cf.etat / (1.0f + cf.etat * Wf);
+        const float Esu = cf.Es[0] * uf[0] + cf.Es[1] * uf[1] + cf.Es[2] * uf[2];
+        const float ae = A1 * Esu;
+        Ef[0] = (cf.etat * cf.Es[0] + ae * uf[0] - (uf[1] * cf.B[2] - uf[2] * cf.B[1])) * s;
+        Ef[1] = (cf.etat * cf.Es[1] + ae * uf[1] - (uf[2] * cf.B[0] - uf[0] * cf.B[2])) * s;
+        Ef[2] = (cf.etat * cf.Es[2] + ae * uf[2] - (uf[0] * cf.B[1] - uf[1] * cf.B[0])) * s;
         const float a2 = A1 * A1 * Esu * iWf;
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = 0; j < 3; j++)
-                dE[i][j] = (-Ef[i] * uf[j] * iWf + A1 * uf[i] * Esf[j] - a2 * uf[i] * uf[j] +
-                            (i == j ? A1 * Esu : 0.0f)) * s;
-        dE[0][1] -= Bf[2] * s; dE[0][2] += Bf[1] * s;
-        dE[1][2] -= Bf[0] * s; dE[1][0] += Bf[2] * s;
-        dE[2][0] -= Bf[1] * s; dE[2][1] += Bf[0] * s;
+                dE[i][j] = (-Ef[i] * uf[j] * iWf + A1 * uf[i] * cf.Es[j] - a2 * uf[i] * uf[j] +
+                            (i == j ? ae : 0.0f)) * s;
+        dE[0][1] -= cf.B[2] * s; dE[0][2] += cf.B[1] * s;
+        dE[1][2] -= cf.B[0] * s; dE[1][0] += cf.B[2] * s;
+        dE[2][0] -= cf.B[1] * s; dE[2][1] += cf.B[0] * s;
     } else {
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++) {
+            Ef[i] = cf.Es[i];
 #pragma unroll
             for (int j = 0; j < 3; j++) dE[i][j] = 0.0f;
+        }
     }
-    // normalise J by 1/w_t (J = w_t I + ...) and f by 1/M:
+    // normalise J by 1/w_t (J = w_t I + ...):
     //   J_ij / w_t = delta_ij + u_i (dw_t/du_j)/w_t + (dE/du_j x B)_i / w_t
     //   (dw_t/du_j)/w_t = ((tau + D - U)/w_t u_j/W - W dU_j/w_t - 2 u_j) / (W^2 - 1/Gamma_hat)
-    const double sc = 1.0 / e.wt;
-    const float scf = (float)sc, idenf = (float)e.iden, Wf = (float)e.W, iWf = (float)iW;
-    const float basef = (float)((c.tau + c.D - e.U) * sc);
+    const float scf = 1.0f / (float)e.wt;
+    const float basef = (float)(c.tau + c.D - e.U) * scf;
+    const float idenf = 1.0f / (uu + 1.0f - cf.igh);
     float J[3][3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         const float dU = Ef[0] * dE[0][j] + Ef[1] * dE[1][j] + Ef[2] * dE[2][j];
         const float dw = (basef * uf[j] * iWf - Wf * dU * scf - 2.0f * uf[j]) * idenf;
-        const float cx = (dE[1][j] * Bf[2] - dE[2][j] * Bf[1]) * scf;
-        const float cy = (dE[2][j] * Bf[0] - dE[0][j] * Bf[2]) * scf;
-        const float cz = (dE[0][j] * Bf[1] - dE[1][j] * Bf[0]) * scf;
+        const float cx = (dE[1][j] * cf.B[2] - dE[2][j] * cf.B[1]) * scf;
+        const float cy = (dE[2][j] * cf.B[0] - dE[0][j] * cf.B[2]) * scf;
+        const float cz = (dE[0][j] * cf.B[1] - dE[1][j] * cf.B[0]) * scf;
         J[0][j] = uf[0] * dw + cx;
         J[1][j] = uf[1] * dw + cy;
         J[2][j] = uf[2] * dw + cz;
     }
     J[0][0] += 1.0f; J[1][1] += 1.0f; J[2][2] += 1.0f;
-    const double iM = e.M > 0.0 ? 1.0 / e.M : 0.0;
-    const float f0 = (float)(e.f[0] * iM), f1 = (float)(e.f[1] * iM), f2 = (float)(e.f[2] * iM);
+    // f scaled by 2^-k with 2^k <= M < 2^(k+1): the exponent field of M, read as an integer
+    const int ek = (int)(mag_hi(e.M) >> 20);
+    const bool scale = ek >= 1 && ek <= 2045;
+    const double down = scale ? __hiloint2double((2046 - ek) << 20, 0) : 1.0;
+    const double up = scale ? __hiloint2double(ek << 20, 0) : 1.0;
+    const float f0 = (float)(e.f[0] * down), f1 = (float)(e.f[1] * down), f2 = (float)(e.f[2] * down);
     const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
     const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
     const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
     const float det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
     if (!(fabsf(det) > 1e-30f)) return false;
-    const float id = 1.0f / det;
+    const float id = -scf / det;
     const float c10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
     const float c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
     const float c12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
     const float c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
     const float c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
     const float c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    const float y0 = (c00 * f0 + c10 * f1 + c20 * f2) * id;
-    const float y1 = (c01 * f0 + c11 * f1 + c21 * f2) * id;
-    const float y2 = (c02 * f0 + c12 * f1 + c22 * f2) * id;
-    // (sc J) x = -sc f = -sc M f'  ->  x = -(sc M) y
-    const double k = -sc * e.M;
-    x[0] = k * (double)y0;
-    x[1] = k * (double)y1;
-    x[2] = k * (double)y2;
+    // (J / w_t) y = -(f 2^-k) / w_t  ->  x = 2^k y
+    x[0] = up * (double)((c00 * f0 + c10 * f1 + c20 * f2) * id);
+    x[1] = up * (double)((c01 * f0 + c11 * f1 + c21 * f2) * id);
+    x[2] = up * (double)((c02 * f0 + c12 * f1 + c22 * f2) * id);
     return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
 }
 
@@ -489,20 +535,22 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const double* u,
 // Returns iterations, or -1.
 __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol)
 {
+    const CellF cf = cell_f32(c);
     evaluate(c, u, e);
     for (int it = 1; it <= kmax; it++) {
         double dx[3];
         // FP32 directions first; the FP64 Jacobian takes over if they have not
         // converged within 10 iterations or fail
-        if (it > 10 || !newton_dir_f32(c, u, e, dx)) {
+        if (it > 10 || !newton_dir_f32(c, cf, u, e, dx)) {
             double J[3][3];
             jacobian(c, u, e, J);
             if (!newton_dir(J, e.f, dx)) return -1;
         }
-        const double nu = fmax(1.0, sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-        const double nx = sqrt(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
-        if (nx > 100.0 * nu) {
-            const double s = 100.0 * nu / nx;
+        // step bound |dx| <= 100 max(|u|, 1), compared in squares
+        const double nu2 = fmax(1.0, u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double nx2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        if (nx2 > 1e4 * nu2) {
+            const double s = sqrt(1e4 * nu2 / nx2);
             dx[0] *= s; dx[1] *= s; dx[2] *= s;
         }
         // slope of |f|^2 along the Newton direction is -2|f|^2
@@ -517,10 +565,10 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
             if (!(lq == lq)) lq = 0.5 * lam;
             lam = fmin(fmax(lq, 0.1 * lam), 0.5 * lam);
         }
-        const double step = lam * fmax(fabs(dx[0]), fmax(fabs(dx[1]), fabs(dx[2])));
+        const double step = lam * from_hi(max(mag_hi(dx[0]), max(mag_hi(dx[1]), mag_hi(dx[2]))));
         u[0] = ut[0]; u[1] = ut[1]; u[2] = ut[2];
         e = et;
-        const double umax = fmax(fabs(u[0]), fmax(fabs(u[1]), fabs(u[2])));
+        const double umax = from_hi(max(mag_hi(u[0]), max(mag_hi(u[1]), mag_hi(u[2]))));
         if (e.fm <= tol * e.M || step <= 1e-15 * umax) {
             if (!(e.wt > 0.0) || !(e.W < 1e10)) return -1;
             return it;
