@@ -200,6 +200,25 @@ grmhd_status grmhd_explicit_L_glm(grmhd_ctx* ctx, const double* const* prim, con
 grmhd_status grmhd_diagnostics(grmhd_ctx* ctx, double* divb, double* totals, long long* nfail,
                                grmhd_stream_t stream);
 
+/* Elliptic divergence cleaning (Sec. 3.3): solve lap(Phi) = div q_B and set
+ * q_B <- q_B - grad(Phi) on the bound field arrays, in place.  The paper applies it
+ * after every step and once after the initial data (Sec. 4); call it at those points.
+ * Operators (Cartesian reference metric): on a CT context the staggered div (face
+ * differences) and face gradient, whose composition is the compact Laplacian, so the
+ * cleaned field is divergence-free to the solver's accuracy; on a GLM context central
+ * differences with the same compact Laplacian (an approximate projection).  Periodic
+ * directions wrap; in the others Phi has zero normal gradient, so the boundary faces
+ * are kept and the mean divergence (their net flux) stays.
+ * Solver: `cycles` multigrid V(2,2) cycles (red-black Gauss-Seidel, cell-average
+ * restriction, linear interpolation, conjugate gradients on the coarsest level), each
+ * reducing the error about tenfold; launches only, deterministic, no synchronisation.
+ * scratch: caller-owned device memory of grmhd_clean_scratch_bytes bytes, 256-byte
+ * aligned.  Grids whose coarsest level (every active extent halved while all are even
+ * and >= 4) exceeds 4096 cells are rejected with GRMHD_ERR_ARG. */
+grmhd_status grmhd_clean_scratch_bytes(const grmhd_grid* grid, size_t* bytes);
+grmhd_status grmhd_clean_divb(grmhd_ctx* ctx, int cycles, void* scratch, size_t scratch_bytes,
+                              grmhd_stream_t stream);
+
 /* Kernels launched by this context since create (host-side count). */
 long long grmhd_launch_count(const grmhd_ctx* ctx);
 

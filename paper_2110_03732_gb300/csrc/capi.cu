@@ -9,6 +9,7 @@
 
 #include "../../include/grmhd.h"
 #include "capi_internal.h"
+#include "elliptic.h"
 #include "kernels.h"
 
 using namespace grmhd;
@@ -773,6 +774,39 @@ grmhd_status grmhd_diagnostics(grmhd_ctx* c, double* divb, double* totals, long 
         for (int v = 0; v < 8; v++) totals[v] = out[3 + v];
     if (nfail) *nfail = (long long)nf;
     return nf ? GRMHD_WARN_C2P_FAILED : GRMHD_OK;
+}
+
+grmhd_status grmhd_clean_scratch_bytes(const grmhd_grid* grid, size_t* bytes)
+{
+    grmhd_status s = check_grid(grid);
+    if (s != GRMHD_OK) return s;
+    if (!bytes) return fail(GRMHD_ERR_ARG, "bytes is NULL");
+    MgPlan plan;
+    const int r = mg_plan(make_dims(grid, 2.0), &plan);
+    if (r == -1) return fail(GRMHD_ERR_ARG, "multigrid: too many levels");
+    if (r == -2)
+        return fail(GRMHD_ERR_ARG,
+                    "multigrid: the coarsest level (every active extent halved while all are even and >= 4) "
+                    "has more than 4096 cells");
+    *bytes = round_up(mg_scratch_bytes(plan));
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_clean_divb(grmhd_ctx* c, int cycles, void* scratch, size_t scratch_bytes, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (cycles < 1 || cycles > 1000) return fail(GRMHD_ERR_ARG, "cycles must be in 1..1000");
+    if (!scratch) return fail(GRMHD_ERR_ARG, "scratch is NULL");
+    if ((uintptr_t)scratch % kAlign) return fail(GRMHD_ERR_SCRATCH, "scratch must be 256-byte aligned");
+    MgPlan plan;
+    if (mg_plan(c->g, &plan) != 0) return grmhd_clean_scratch_bytes(&c->grid, &scratch_bytes);
+    if (scratch_bytes < mg_scratch_bytes(plan))
+        return fail(GRMHD_ERR_SCRATCH, "scratch smaller than grmhd_clean_scratch_bytes");
+    cudaError_t e = mg_clean(c->g, plan, (double*)scratch, c->bf, c->glm, cycles, c->nsm, (cudaStream_t)stream,
+                             &c->launches);
+    if (e != cudaSuccess) return cuda_fail(e, "multigrid kernels");
+    return GRMHD_OK;
 }
 
 long long grmhd_launch_count(const grmhd_ctx* c) { return c ? c->launches : 0; }

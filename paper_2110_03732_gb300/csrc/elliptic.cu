@@ -1,0 +1,433 @@
+// Elliptic divergence cleaning (arXiv 2110.03732 Sec. 3.3) by geometric multigrid,
+// sm_103a, FP64: solve lap(Phi) = div q_B and set q_B <- q_B - grad(Phi).
+//
+// Operators (Cartesian reference metric, so flat):
+//   staggered fields (CT): div on cells from face differences, grad on faces from the
+//     two adjacent cells; lap = div(grad) is the compact (2 ndim + 1)-point stencil and
+//     the cleaned field is divergence-free to the solver's accuracy;
+//   cell-centred fields (GLM): div and grad by central differences with the same
+//     compact lap (an approximate projection).
+//   Periodic directions wrap; in the others Phi has zero normal gradient (no flux
+//   through the boundary face, which is not corrected).  The right-hand side is made
+//   mean-free (the constants are the null space).
+//
+// Multigrid: cell-centred levels, each halving every active extent while all of them
+// are even and at least 4.  V(2,2) cycles: red-black Gauss-Seidel smoothing (valid,
+// hence deterministic, because every level but the coarsest has even extents), the
+// residual of the 2^ndim children averaged to the coarse cell, tensor-product linear
+// interpolation (weights 3/4, 1/4) back.  The coarsest level (at most 4096 cells) is
+// solved by conjugate gradients in one thread block with fixed-order reductions and
+// a bounded iteration count.  Every launch is deterministic; the cycle count is fixed
+// by the caller, so a cleaning is launches only (no host synchronisation).
+#include <cuda_runtime.h>
+
+#include "elliptic.h"
+#include "grmhd_device.cuh"
+
+namespace grmhd {
+
+namespace {
+
+// cell (i, j, k) of a level, x fastest; returns the neighbour's index along d (side s =
+// +-1), or -1 past a non-periodic boundary
+__device__ __forceinline__ long long mg_nb(const MgLevel& L, const int* bc, int i, int j, int k, int d, int s)
+{
+    int c[3] = {i, j, k};
+    c[d] += s;
+    if (c[d] < 0 || c[d] >= L.n[d]) {
+        if (bc[d] != BC_PERIODIC) return -1;
+        c[d] = (c[d] + L.n[d]) % L.n[d];
+    }
+    return c[0] + (long long)L.n[0] * (c[1] + (long long)L.n[1] * c[2]);
+}
+
+struct MgArgs {
+    int bc[3];
+    int act[3];
+};
+
+__device__ __forceinline__ void mg_coords(const MgLevel& L, long long t, int& i, int& j, int& k)
+{
+    i = (int)(t % L.n[0]);
+    j = (int)((t / L.n[0]) % L.n[1]);
+    k = (int)(t / ((long long)L.n[0] * L.n[1]));
+}
+
+// (L Phi)_c split as sum_nb Phi_nb / h^2 - diag Phi_c; returns the neighbour sum and
+// the diagonal
+__device__ __forceinline__ void mg_stencil(const MgLevel& L, const MgArgs& m, const double* __restrict__ phi, int i,
+                                           int j, int k, double& nbsum, double& diag)
+{
+    nbsum = 0.0;
+    diag = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (!m.act[d]) continue;
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            const long long nb = mg_nb(L, m.bc, i, j, k, d, s);
+            if (nb < 0) continue;
+            nbsum += phi[nb] * L.ih2[d];
+            diag += L.ih2[d];
+        }
+    }
+}
+
+// red-black Gauss-Seidel half sweep of colour `color`
+__global__ void __launch_bounds__(256) k_mg_smooth(MgLevel L, MgArgs m, int color)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        mg_coords(L, t, i, j, k);
+        if (((i + j + k) & 1) != color) continue;
+        double nbsum, diag;
+        mg_stencil(L, m, L.phi, i, j, k, nbsum, diag);
+        if (diag > 0.0) L.phi[t] = (nbsum - L.rhs[t]) / diag;
+    }
+}
+
+// coarse rhs = mean of the children's residuals rhs - L Phi; coarse Phi = 0
+__global__ void __launch_bounds__(256) k_mg_restrict(MgLevel F, MgLevel C, MgArgs m)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < C.cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        int I, J, K;
+        mg_coords(C, t, I, J, K);
+        double sum = 0.0;
+        int cnt = 0;
+        for (int dk = 0; dk <= m.act[2]; dk++)
+            for (int dj = 0; dj <= m.act[1]; dj++)
+                for (int di = 0; di <= m.act[0]; di++) {
+                    const int i = 2 * I * m.act[0] + di, j = 2 * J * m.act[1] + dj, k = 2 * K * m.act[2] + dk;
+                    const long long f = i + (long long)F.n[0] * (j + (long long)F.n[1] * k);
+                    double nbsum, diag;
+                    mg_stencil(F, m, F.phi, i, j, k, nbsum, diag);
+                    sum += F.rhs[f] - (nbsum - diag * F.phi[f]);
+                    cnt++;
+                }
+        C.rhs[t] = sum / cnt;
+        C.phi[t] = 0.0;
+    }
+}
+
+// Phi_fine += linear interpolation of the coarse correction: along each active
+// direction the child takes 3/4 of its parent and 1/4 of the parent's neighbour on its
+// side (the parent itself past a non-periodic boundary)
+__global__ void __launch_bounds__(256) k_mg_prolong(MgLevel F, MgLevel C, MgArgs m)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < F.cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        mg_coords(F, t, c[0], c[1], c[2]);
+        int P[3], S[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            P[d] = m.act[d] ? c[d] >> 1 : c[d];
+            S[d] = m.act[d] ? ((c[d] & 1) ? 1 : -1) : 0;
+        }
+        double v = 0.0;
+        for (int ok = 0; ok <= m.act[2]; ok++)
+            for (int oj = 0; oj <= m.act[1]; oj++)
+                for (int oi = 0; oi <= m.act[0]; oi++) {
+                    const int off[3] = {oi, oj, ok};
+                    int q[3];
+                    double w = 1.0;
+                    for (int d = 0; d < 3; d++) {
+                        if (!m.act[d]) { q[d] = P[d]; continue; }
+                        q[d] = P[d] + off[d] * S[d];
+                        w *= off[d] ? 0.25 : 0.75;
+                        if (q[d] < 0 || q[d] >= C.n[d]) {
+                            if (m.bc[d] == BC_PERIODIC) q[d] = (q[d] + C.n[d]) % C.n[d];
+                            else q[d] = P[d];
+                        }
+                    }
+                    v += w * C.phi[q[0] + (long long)C.n[0] * (q[1] + (long long)C.n[1] * q[2])];
+                }
+        F.phi[t] += v;
+    }
+}
+
+// fixed-order block sum (blockDim.x a multiple of 32, at most 1024)
+__device__ __forceinline__ double mg_block_sum(double v, double* sh)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (l == 0) sh[32] = v;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// coarsest level: conjugate gradients on -lap (symmetric positive semi-definite) with
+// a mean-free right-hand side, in one block.  r, p and q are scratch vectors of the
+// level's size; iterations end at ||r|| <= 1e-15 ||b|| or after max_it.
+__global__ void __launch_bounds__(1024) k_mg_coarse_cg(MgLevel L, MgArgs m, double* __restrict__ res,
+                                                        double* __restrict__ p, double* __restrict__ q, int max_it)
+{
+    __shared__ double sh[33];
+    const long long n = L.cells;
+    // b = -(rhs - mean rhs); x = 0, r = b, p = r
+    double s = 0.0;
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) s += L.rhs[t];
+    const double mean = mg_block_sum(s, sh) / (double)n;
+    double rr = 0.0;
+    for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+        const double b = -(L.rhs[t] - mean);
+        res[t] = b;
+        p[t] = b;
+        L.phi[t] = 0.0;
+        rr += b * b;
+    }
+    rr = mg_block_sum(rr, sh);
+    const double stop = 1e-30 * rr;
+    for (int it = 0; it < max_it && rr > stop && rr > 0.0; it++) {
+        // q = -lap p
+        double pq = 0.0;
+        for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+            int i, j, k;
+            mg_coords(L, t, i, j, k);
+            double nbsum, diag;
+            mg_stencil(L, m, p, i, j, k, nbsum, diag);
+            const double v = diag * p[t] - nbsum;
+            q[t] = v;
+            pq += p[t] * v;
+        }
+        pq = mg_block_sum(pq, sh);
+        if (!(pq > 0.0)) break;
+        const double alpha = rr / pq;
+        double rn = 0.0;
+        for (long long t = threadIdx.x; t < n; t += blockDim.x) {
+            L.phi[t] += alpha * p[t];
+            const double r = res[t] - alpha * q[t];
+            res[t] = r;
+            rn += r * r;
+        }
+        rn = mg_block_sum(rn, sh);
+        const double beta = rn / rr;
+        rr = rn;
+        for (long long t = threadIdx.x; t < n; t += blockDim.x) p[t] = res[t] + beta * p[t];
+        __syncthreads();
+    }
+}
+
+// fine right-hand side: div q_B on the interior cells (faces or central), and block
+// partial sums for its mean
+__global__ void __launch_bounds__(256) k_mg_div(Dims g, CP3 bq, int cc, MgLevel L, MgArgs m, double* __restrict__ part)
+{
+    __shared__ double sh[33];
+    double s = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        mg_coords(L, t, c[0], c[1], c[2]);
+        int p[3] = {c[0] + g.ng[0], c[1] + g.ng[1], c[2] + g.ng[2]};
+        const long long o = lin(g, p[0], p[1], p[2]);
+        double dv = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!g.act[d]) continue;
+            if (cc) {
+                // central difference; past a non-periodic boundary the cell itself (zero
+                // gradient, whatever the boundary kind)
+                const long long hi = mg_nb(L, m.bc, c[0], c[1], c[2], d, 1);
+                const long long lo = mg_nb(L, m.bc, c[0], c[1], c[2], d, -1);
+                int ch[3] = {c[0], c[1], c[2]}, cl[3] = {c[0], c[1], c[2]};
+                if (hi >= 0) ch[d] = (c[d] + 1) % L.n[d];
+                if (lo >= 0) cl[d] = (c[d] - 1 + L.n[d]) % L.n[d];
+                const double vh = bq.p[d][lin(g, ch[0] + g.ng[0], ch[1] + g.ng[1], ch[2] + g.ng[2])];
+                const double vl = bq.p[d][lin(g, cl[0] + g.ng[0], cl[1] + g.ng[1], cl[2] + g.ng[2])];
+                dv += (vh - vl) * (0.5 * g.idx[d]);
+            } else {
+                int up[3] = {p[0], p[1], p[2]};
+                up[d] += 1;
+                dv += (bq.p[d][face_at(g, d, up)] - bq.p[d][o]) * g.idx[d];
+            }
+        }
+        L.rhs[t] = dv;
+        L.phi[t] = 0.0;
+        s += dv;
+    }
+    s = mg_block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// mean of the partial sums (one block), subtracted from the fine right-hand side
+__global__ void __launch_bounds__(256) k_mg_mean(const double* __restrict__ part, int nb, double* __restrict__ mean,
+                                                 long long cells)
+{
+    __shared__ double sh[33];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
+    s = mg_block_sum(s, sh);
+    if (threadIdx.x == 0) *mean = s / (double)cells;
+}
+
+__global__ void __launch_bounds__(256) k_mg_sub_mean(MgLevel L, const double* __restrict__ mean)
+{
+    const double mu = *mean;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.cells;
+         t += (long long)gridDim.x * blockDim.x)
+        L.rhs[t] -= mu;
+}
+
+// q_B -= grad Phi: staggered (lower face of each interior cell; the lower boundary face
+// of a non-periodic direction is kept) or central (cell-centred)
+__global__ void __launch_bounds__(256) k_mg_correct(Dims g, P3 bq, int cc, MgLevel L, MgArgs m)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        mg_coords(L, t, c[0], c[1], c[2]);
+        const long long o = lin(g, c[0] + g.ng[0], c[1] + g.ng[1], c[2] + g.ng[2]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (!g.act[d]) continue;
+            const long long lo = mg_nb(L, m.bc, c[0], c[1], c[2], d, -1);
+            if (cc) {
+                const long long hi = mg_nb(L, m.bc, c[0], c[1], c[2], d, 1);
+                const double pl = lo < 0 ? L.phi[t] : L.phi[lo];
+                const double ph = hi < 0 ? L.phi[t] : L.phi[hi];
+                bq.p[d][o] -= (ph - pl) * (0.5 * g.idx[d]);
+            } else if (lo >= 0) {
+                bq.p[d][o] -= (L.phi[t] - L.phi[lo]) * g.idx[d];
+            }
+        }
+    }
+}
+
+int mg_grid(long long work, int nsm)
+{
+    long long b = (work + 255) / 256;
+    const long long cap = (long long)nsm * 8;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+int mg_plan(const Dims& g, MgPlan* plan)
+{
+    MgPlan p;
+    p.nlev = 0;
+    int n[3] = {g.n[0], g.n[1], g.n[2]};
+    long long total = 0;
+    for (;;) {
+        if (p.nlev >= kMgMaxLevels) return -1;
+        MgLevel& L = p.lev[p.nlev];
+        long long cells = 1;
+        for (int d = 0; d < 3; d++) {
+            L.n[d] = n[d];
+            const double h = g.act[d] ? (1.0 / g.idx[d]) * (double)(g.n[d] / n[d]) : 1.0;
+            L.ih2[d] = g.act[d] ? 1.0 / (h * h) : 0.0;
+            cells *= n[d];
+        }
+        L.cells = cells;
+        L.offset = total;
+        total += cells;
+        p.nlev++;
+        bool can = true;
+        for (int d = 0; d < 3; d++)
+            if (g.act[d] && (n[d] % 2 != 0 || n[d] < 4)) can = false;
+        if (!can) break;
+        for (int d = 0; d < 3; d++)
+            if (g.act[d]) n[d] /= 2;
+    }
+    if (p.lev[p.nlev - 1].cells > kMgMaxCoarse) return -2;
+    p.total = total;
+    *plan = p;
+    return 0;
+}
+
+size_t mg_scratch_bytes(const MgPlan& p)
+{
+    // phi and rhs of every level; CG vectors r, p, q of the coarsest; partial sums; mean
+    const size_t coarse = (size_t)p.lev[p.nlev - 1].cells;
+    return sizeof(double) * (2 * (size_t)p.total + 3 * coarse + kMgParts + 1);
+}
+
+cudaError_t mg_clean(const Dims& g, const MgPlan& plan0, double* scratch, double* const* bq, bool cc, int cycles,
+                     int nsm, cudaStream_t st, long long* launches)
+{
+    long long nl = 0;
+    MgPlan plan = plan0;
+    const long long T = plan.total;
+    const long long nc = plan.lev[plan.nlev - 1].cells;
+    for (int l = 0; l < plan.nlev; l++) {
+        MgLevel& L = plan.lev[l];
+        L.phi = scratch + L.offset;
+        L.rhs = scratch + T + L.offset;
+    }
+    double* cg_r = scratch + 2 * T;
+    double* cg_p = cg_r + nc;
+    double* cg_q = cg_p + nc;
+    double* part = cg_q + nc;
+    double* mean = part + kMgParts;
+    MgArgs m;
+    for (int d = 0; d < 3; d++) {
+        m.bc[d] = g.bc[d];
+        m.act[d] = g.act[d];
+    }
+    const MgLevel& F = plan.lev[0];
+    CP3 cq;
+    P3 pq;
+    for (int d = 0; d < 3; d++) {
+        cq.p[d] = bq[d];
+        pq.p[d] = bq[d];
+    }
+    const int nb = (int)((F.cells + 255) / 256 < kMgParts ? (F.cells + 255) / 256 : kMgParts);
+    nl++;
+    k_mg_div<<<nb, 256, 0, st>>>(g, cq, cc ? 1 : 0, F, m, part);
+    nl++;
+    k_mg_mean<<<1, 256, 0, st>>>(part, nb, mean, F.cells);
+    nl++;
+    k_mg_sub_mean<<<mg_grid(F.cells, nsm), 256, 0, st>>>(F, mean);
+    const int cg_it = (int)(2 * nc + 20);
+    for (int cyc = 0; cyc < cycles; cyc++) {
+        for (int l = 0; l + 1 < plan.nlev; l++) {
+            const MgLevel& L = plan.lev[l];
+            const int b = mg_grid(L.cells, nsm);
+            for (int s = 0; s < 2; s++) {
+                nl++;
+                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 0);
+                nl++;
+                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 1);
+            }
+            nl++;
+            k_mg_restrict<<<mg_grid(plan.lev[l + 1].cells, nsm), 256, 0, st>>>(L, plan.lev[l + 1], m);
+        }
+        const MgLevel& Lc = plan.lev[plan.nlev - 1];
+        // coarsest correction from zero; with a single level this is the whole solve,
+        // and further cycles would repeat it
+        nl++;
+        k_mg_coarse_cg<<<1, 1024, 0, st>>>(Lc, m, cg_r, cg_p, cg_q, cg_it);
+        if (plan.nlev == 1) break;
+        for (int l = plan.nlev - 2; l >= 0; l--) {
+            const MgLevel& L = plan.lev[l];
+            const int b = mg_grid(L.cells, nsm);
+            nl++;
+            k_mg_prolong<<<b, 256, 0, st>>>(L, plan.lev[l + 1], m);
+            for (int s = 0; s < 2; s++) {
+                nl++;
+                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 0);
+                nl++;
+                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 1);
+            }
+        }
+    }
+    nl++;
+    k_mg_correct<<<mg_grid(F.cells, nsm), 256, 0, st>>>(g, pq, cc ? 1 : 0, F, m);
+    if (launches) *launches += nl;
+    return cudaGetLastError();
+}
+
+}  // namespace grmhd

@@ -75,6 +75,8 @@ def lib():
     L.grmhd_explicit_L.argtypes = [vp, dpp, dpp, dpp, vp]
     L.grmhd_explicit_L_glm.argtypes = [vp, dpp, dpp, vp, dpp, vp]
     L.grmhd_bind_phi.argtypes = [vp, vp]
+    L.grmhd_clean_scratch_bytes.argtypes = [C.POINTER(Grid), C.POINTER(C.c_size_t)]
+    L.grmhd_clean_divb.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
     L.grmhd_diagnostics.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp]
     L.grmhd_set_timing.argtypes = [vp, C.c_int]
     L.grmhd_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
@@ -93,7 +95,8 @@ def lib():
                  "grmhd_step", "grmhd_get_prims", "grmhd_implicit", "grmhd_explicit_L", "grmhd_diagnostics",
                  "grmhd_set_timing", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
-                 "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi"):
+                 "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
+                 "grmhd_clean_divb"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -260,8 +263,21 @@ class Solver:
     def stage(self, i, dt, stream=None):
         return check(self.L.grmhd_stage(self.ctx, int(i), float(dt), _stream(stream)), "stage")
 
-    def step(self, dt, stream=None):
-        return check(self.L.grmhd_step(self.ctx, float(dt), _stream(stream)), "step")
+    def step(self, dt, stream=None, clean_cycles=0):
+        """One IMEX step; with clean_cycles > 0 the field is then cleaned (Sec. 3.3)."""
+        r = check(self.L.grmhd_step(self.ctx, float(dt), _stream(stream)), "step")
+        if clean_cycles:
+            self.clean_divb(clean_cycles, stream)
+        return r
+
+    def clean_divb(self, cycles=10, stream=None):
+        """Elliptic cleaning of the bound field arrays (multigrid, `cycles` V-cycles)."""
+        if getattr(self, "_mg_scratch", None) is None:
+            n = C.c_size_t(0)
+            check(self.L.grmhd_clean_scratch_bytes(C.byref(self.grid), C.byref(n)), "clean_scratch_bytes")
+            self._mg_scratch = torch.empty(max(n.value, 1), dtype=torch.uint8, device=self.device)
+        check(self.L.grmhd_clean_divb(self.ctx, int(cycles), C.c_void_p(self._mg_scratch.data_ptr()),
+                                      self._mg_scratch.numel(), _stream(stream)), "clean_divb")
 
     def get_prims(self, stream=None):
         out = [torch.zeros(self.shape, dtype=torch.float64, device=self.device) for _ in range(8)]

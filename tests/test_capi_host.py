@@ -153,3 +153,20 @@ def test_invalid_divergence_scheme_rejected(lib, case):
     assert not ctx.value
     lib.grmhd_last_error.restype = C.c_char_p
     assert len(lib.grmhd_last_error()) > 0
+
+
+def test_clean_scratch_bytes(lib):
+    """Multigrid plan of the elliptic cleaning: phi and rhs on every level (each
+    halving all active extents while they are even and >= 4), three CG vectors of the
+    coarsest level, 1024 partial sums and the mean; too coarse a grid is refused."""
+    for ndim, n, levels in (((2, (512, 512, 1), [512 * 512 // 4 ** k for k in range(9)]),
+                             (1, (400, 1, 1), [400, 200, 100, 50, 25]),
+                             (3, (19, 13, 7), [19 * 13 * 7]))):
+        g = _grid(ndim, n)
+        b = C.c_size_t()
+        assert lib.grmhd_clean_scratch_bytes(C.byref(g), C.byref(b)) == 0
+        want = 8 * (2 * sum(levels) + 3 * levels[-1] + 1024 + 1)
+        assert b.value == -(-want // 256) * 256, (ndim, b.value, want)
+    g = _grid(2, (1000, 1000, 1))     # coarsest 125 x 125 cells
+    b = C.c_size_t()
+    assert lib.grmhd_clean_scratch_bytes(C.byref(g), C.byref(b)) == -1
