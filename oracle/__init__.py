@@ -102,7 +102,7 @@ class Grid:
     ``gamma``, atmosphere floor ``rho_atm``/``p_atm`` (0: none).  Inactive directions
     have one cell and no ghosts."""
 
-    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0, xi=0.0):
+    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0, xi=0.0, emf="resistive"):
         n = list(n) + [1] * (3 - len(n))
         dx = list(dx) + [1.0] * (3 - len(dx))
         bc = list(bc) + ["periodic"] * (3 - len(bc))
@@ -115,7 +115,8 @@ class Grid:
         self.N = [self.n[d] + 2 * self.ng[d] for d in range(3)]
         self._gi = (C.c_int * 7)(ndim, *self.n, *self.bc)
         self.rho_atm, self.p_atm, self.xi = float(rho_atm), float(p_atm), float(xi)
-        self._gd = (C.c_double * 7)(*self.dx, self.gamma, self.rho_atm, self.p_atm, self.xi)
+        self.emf = {"resistive": 0, "ideal": 1}[emf] if isinstance(emf, str) else int(emf)
+        self._gd = (C.c_double * 8)(*self.dx, self.gamma, self.rho_atm, self.p_atm, self.xi, float(self.emf))
 
     @property
     def shape(self):
@@ -294,10 +295,12 @@ class State:
         return prim
 
 
-def from_problem(prob):
+def from_problem(prob, emf="resistive"):
     """Oracle state from a ``paper_2110_03732_gb300.problems.Problem``: face q_B from
-    the edge potential (oracle curl) or taken as given."""
-    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0))
+    the edge potential (oracle curl) or taken as given.  ``emf="ideal"`` takes the
+    ideal-limit edge EMF of App. A."""
+    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0),
+                emf)
     if prob.A_edge is not None:
         bf = curl_A(grid, [np.ascontiguousarray(a, dtype=np.float64) for a in prob.A_edge])
     else:

@@ -25,6 +25,7 @@
  *   GLM hyperbolic cleaning (cell-centred B, Phi) Sec. 3.1 (q_Phi, f_Phi, s_Phi, s_B)
  *   B from an edge vector potential               Sec. 4
  *   MC limiter + HLL defaults                     Sec. 5 (opening paragraph)
+ *   ideal-limit HLL UCT (transport velocities)    App. A (steps i-iv)
  *
  * Readings where the paper is silent or garbled (each also listed in the design doc):
  *   - IMEX sum limits: q(i) = q^n + dt sum_{j<i} at_ij L(j) + dt sum_{j<=i} a_ij R(j),
@@ -71,6 +72,7 @@ typedef struct {
     double rho_atm;    /* atmosphere density (0: no atmosphere treatment) */
     double p_atm;      /* atmosphere pressure */
     double xi;         /* mean-field dynamo parameter (uniform) */
+    int emf;           /* edge EMF: 0 = resistive UCT (Sec. 3.2), 1 = ideal-limit UCT (App. A) */
     long ncell;        /* padded cells */
 } OGrid;
 
@@ -89,6 +91,7 @@ static void grid_setup(OGrid* g, const int* gi, const double* gd)
     g->rho_atm = gd[4];
     g->p_atm = gd[5];
     g->xi = gd[6];
+    g->emf = (int)gd[7];
     g->ncell = (long)g->N[0] * g->N[1] * g->N[2];
 }
 
@@ -598,7 +601,23 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
     /* face states and HLL fluxes, direction by direction; the flux for the 8
      * cell-centred variables lives at face index f (between cells f-1 and f) */
     double* F[3][NQ];
+    /* App. A step (ii): HLL-weighted transverse transport velocities vbar^j at the
+     * d-faces (ideal EMF only); in an inactive direction d the "face" is the cell and
+     * vbar^j is the cell's vhat^j = alpha v^j (beta = 0) */
+    double* vbar[3][3];
     for (int d = 0; d < 3; d++) for (int v = 0; v < NQ; v++) F[d][v] = NULL;
+    for (int d = 0; d < 3; d++)
+        for (int j = 0; j < 3; j++) {
+            vbar[d][j] = NULL;
+            if (g->emf != 1 || j == d) continue;
+            vbar[d][j] = dalloc(nc);
+            if (g->act[d]) continue;
+            for (long c = 0; c < nc; c++) {
+                double gg = pow(psi_at(X->psi, c), 4), uu = 0;
+                for (int k = 0; k < 3; k++) uu += gg * prim[1 + k][c] * prim[1 + k][c];
+                vbar[d][j][c] = alp_at(X->alp, c) * prim[1 + j][c] / sqrt(1.0 + uu);
+            }
+        }
     for (int d = 0; d < 3; d++) {
         if (!g->act[d]) continue;
         for (int v = 0; v < NQ; v++) F[d][v] = dalloc(nc);
@@ -629,6 +648,18 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
             double cp = fmax(0.0, lp), cm = fmax(0.0, -lm);
             for (int v = 0; v < NQ; v++)
                 F[d][v][c] = (cp * FL[v] + cm * FR[v] - cp * cm * (qR[v] - qL[v])) / (cp + cm);
+            if (g->emf == 1) {
+                /* App. A steps (i)-(ii): vhat^j = alpha v^j of the L and R states,
+                 * vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+) */
+                double uuL = 0, uuR = 0;
+                for (int k = 0; k < 3; k++) { uuL += gf * recL[1 + k] * recL[1 + k]; uuR += gf * recR[1 + k] * recR[1 + k]; }
+                double WL = sqrt(1.0 + uuL), WR = sqrt(1.0 + uuR);
+                for (int j = 0; j < 3; j++) {
+                    if (j == d) continue;
+                    double vL = alf * recL[1 + j] / WL, vR = alf * recR[1 + j] / WR;
+                    vbar[d][j][c] = (cm * vR + cp * vL) / (cm + cp);
+                }
+            }
         }
     }
     /* cell-centred L: flux divergence + non-stiff sources */
@@ -736,6 +767,30 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
                 }
             }
             double cap = ca, cam = ca, cbp = cb, cbm = cb;
+            if (g->emf == 1) {
+                /* App. A steps (iii)-(iv): vbar^a of the b-faces reconstructed along a,
+                 * vbar^b of the a-faces along b (with q_B^b along a, q_B^a along b) */
+                double vaL, vaR, vbL, vbR;
+                const double* va = vbar[b][a];
+                const double* vb = vbar[a][b];
+                if (g->act[a]) {
+                    long m2 = shift(g, c, a, -2), m1 = shift(g, c, a, -1), p1 = shift(g, c, a, 1);
+                    vaL = va[m1] + 0.5 * mc_slope(va[m2], va[m1], va[c]);
+                    vaR = va[c] - 0.5 * mc_slope(va[m1], va[c], va[p1]);
+                } else {
+                    vaL = vaR = va[c];
+                }
+                if (g->act[b]) {
+                    long m2 = shift(g, c, b, -2), m1 = shift(g, c, b, -1), p1 = shift(g, c, b, 1);
+                    vbL = vb[m1] + 0.5 * mc_slope(vb[m2], vb[m1], vb[c]);
+                    vbR = vb[c] - 0.5 * mc_slope(vb[m1], vb[c], vb[p1]);
+                } else {
+                    vbL = vbR = vb[c];
+                }
+                Eh[cc][c] = -(cam * vaR * qBbR + cap * vaL * qBbL - cam * cap * (qBbR - qBbL)) / (cam + cap)
+                            + (cbm * vbR * qBaR + cbp * vbL * qBaL - cbm * cbp * (qBaR - qBaL)) / (cbm + cbp);
+                continue;
+            }
             /* step (v): hat{E}^{XY} = alpha E_c^{XY} (beta = 0) */
             double hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
             /* step (vii): Londrillo & Del Zanna (2004) */
@@ -768,6 +823,7 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
     for (int d = 0; d < 3; d++) {
         free(Bc[d]); free(Ecov[d]); free(Eh[d]);
         for (int v = 0; v < NQ; v++) free(F[d][v]);
+        for (int j = 0; j < 3; j++) free(vbar[d][j]);
     }
 }
 
