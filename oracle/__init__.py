@@ -76,6 +76,7 @@ def lib():
                                        dp, dp, dp, C.c_double, dpp, ip]
             L.orc_step_glm.restype = C.c_int
             L.orc_divb_cc.argtypes = [ip, dp, dpp, dp]
+            L.orc_face_states.argtypes = [ip, dp, dp, C.c_int, dp, dp]
             _lib = L
     return _lib
 
@@ -102,7 +103,7 @@ class Grid:
     ``gamma``, atmosphere floor ``rho_atm``/``p_atm`` (0: none).  Inactive directions
     have one cell and no ghosts."""
 
-    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0, xi=0.0, emf="resistive"):
+    def __init__(self, ndim, n, dx, bc, gamma, rho_atm=0.0, p_atm=0.0, xi=0.0, emf="resistive", rec="mc"):
         n = list(n) + [1] * (3 - len(n))
         dx = list(dx) + [1.0] * (3 - len(dx))
         bc = list(bc) + ["periodic"] * (3 - len(bc))
@@ -116,7 +117,9 @@ class Grid:
         self._gi = (C.c_int * 7)(ndim, *self.n, *self.bc)
         self.rho_atm, self.p_atm, self.xi = float(rho_atm), float(p_atm), float(xi)
         self.emf = {"resistive": 0, "ideal": 1}[emf] if isinstance(emf, str) else int(emf)
-        self._gd = (C.c_double * 8)(*self.dx, self.gamma, self.rho_atm, self.p_atm, self.xi, float(self.emf))
+        self.rec = {"mc": 0, "ppm": 1}[rec] if isinstance(rec, str) else int(rec)
+        self._gd = (C.c_double * 9)(*self.dx, self.gamma, self.rho_atm, self.p_atm, self.xi, float(self.emf),
+                                    float(self.rec))
 
     @property
     def shape(self):
@@ -295,12 +298,12 @@ class State:
         return prim
 
 
-def from_problem(prob, emf="resistive"):
+def from_problem(prob, emf="resistive", rec="mc"):
     """Oracle state from a ``paper_2110_03732_gb300.problems.Problem``: face q_B from
     the edge potential (oracle curl) or taken as given.  ``emf="ideal"`` takes the
     ideal-limit edge EMF of App. A."""
     grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0),
-                emf)
+                emf, rec)
     if prob.A_edge is not None:
         bf = curl_A(grid, [np.ascontiguousarray(a, dtype=np.float64) for a in prob.A_edge])
     else:
@@ -407,10 +410,21 @@ class GLMState:
         self.t += dt
 
 
-def from_problem_glm(prob, kappa=None):
+def face_states(grid, a, d):
+    """Left/right states at the lower d-face of every cell (test export of the
+    reconstruction)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    L = grid.zeros()
+    R = grid.zeros()
+    lib().orc_face_states(grid.gi, grid.gd, _dp(a), int(d), _dp(L), _dp(R))
+    return L, R
+
+
+def from_problem_glm(prob, kappa=None, rec="mc"):
     """GLM oracle state from a Problem: cell-centred q_B from ``prob.A_cell`` (oracle
     central curl) or ``prob.bcell``; q_Phi = psi^6 ``prob.phi`` (0 if None)."""
-    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0))
+    grid = Grid(prob.ndim, prob.n, prob.dx, prob.bc, prob.gamma, prob.rho_atm, prob.p_atm, getattr(prob, "xi", 0.0),
+                rec=rec)
     if prob.A_cell is not None:
         qB = curl_A_cc(grid, [np.ascontiguousarray(a, dtype=np.float64) for a in prob.A_cell])
     else:

@@ -26,6 +26,7 @@
  *   B from an edge vector potential               Sec. 4
  *   MC limiter + HLL defaults                     Sec. 5 (opening paragraph)
  *   ideal-limit HLL UCT (transport velocities)    App. A (steps i-iv)
+ *   PPM reconstruction (named for the star runs)  Sec. 5; Colella & Woodward (1984)
  *
  * Readings where the paper is silent or garbled (each also listed in the design doc):
  *   - IMEX sum limits: q(i) = q^n + dt sum_{j<i} at_ij L(j) + dt sum_{j<=i} a_ij R(j),
@@ -73,6 +74,7 @@ typedef struct {
     double p_atm;      /* atmosphere pressure */
     double xi;         /* mean-field dynamo parameter (uniform) */
     int emf;           /* edge EMF: 0 = resistive UCT (Sec. 3.2), 1 = ideal-limit UCT (App. A) */
+    int rec;           /* reconstruction: 0 = MC (Sec. 5 default), 1 = PPM (Sec. 5, star runs) */
     long ncell;        /* padded cells */
 } OGrid;
 
@@ -92,6 +94,7 @@ static void grid_setup(OGrid* g, const int* gi, const double* gd)
     g->p_atm = gd[5];
     g->xi = gd[6];
     g->emf = (int)gd[7];
+    g->rec = (int)gd[8];
     g->ncell = (long)g->N[0] * g->N[1] * g->N[2];
 }
 
@@ -475,6 +478,69 @@ static double mc_slope(double um, double u0, double up)
     return minmod3(2.0 * (u0 - um), 0.5 * (up - um), 2.0 * (up - u0));
 }
 
+/* index of the cell s steps from c along d; beyond the two stored ghost layers (the PPM
+ * stencil reaches three) periodic wraps, outflow takes the boundary cell, fixed the
+ * outermost stored ghost */
+static long nb_cell(const OGrid* g, long c, int d, int s)
+{
+    int ijk[3];
+    coords(g, c, ijk);
+    int m = ijk[d] + s;
+    if (m < 0 || m >= g->N[d]) {
+        int lo = g->ng[d], hi = g->ng[d] + g->n[d] - 1;
+        if (g->bc[d] == BC_PERIODIC) m = lo + (((m - lo) % g->n[d]) + g->n[d]) % g->n[d];
+        else if (g->bc[d] == BC_OUTFLOW) m = m < lo ? lo : hi;
+        else m = m < 0 ? 0 : g->N[d] - 1;
+    }
+    ijk[d] = m;
+    return at(g, ijk[0], ijk[1], ijk[2]);
+}
+
+/* PPM (Colella & Woodward 1984, their interface interpolation and monotonicity
+ * constraints, no steepening or flattening): the interface value between cells j and
+ * j+1 from cells j-1..j+2, with the monotone slope delta_m a = the MC slope */
+static double ppm_iface(double am, double a0, double ap, double app)
+{
+    return a0 + 0.5 * (ap - a0) - (mc_slope(a0, ap, app) - mc_slope(am, a0, ap)) / 6.0;
+}
+
+/* the parabola in cell a0 with edge values (*aL, *aR), limited to be monotone */
+static void ppm_limit(double a0, double* aL, double* aR)
+{
+    if ((*aR - a0) * (a0 - *aL) <= 0.0) {
+        *aL = a0;
+        *aR = a0;
+        return;
+    }
+    double dd = *aR - *aL, m6 = 6.0 * (a0 - 0.5 * (*aL + *aR));
+    if (dd * m6 > dd * dd) *aL = 3.0 * a0 - 2.0 * *aR;
+    else if (-dd * dd > dd * m6) *aR = 3.0 * a0 - 2.0 * *aL;
+}
+
+/* left and right states at the lower d-face of cell c of the array a (values of the
+ * cells around, or of the faces of another direction, which are cells along d) */
+static void face_lr(const OGrid* g, const double* a, long c, int d, double* L, double* R)
+{
+    if (g->rec == 1) {
+        double v[6];
+        for (int s = 0; s < 6; s++) v[s] = a[nb_cell(g, c, d, s - 3)];
+        /* cells c-3..c+2 = v[0..5]; interfaces c-3/2, c-1/2, c+1/2 */
+        double im = ppm_iface(v[0], v[1], v[2], v[3]);
+        double i0 = ppm_iface(v[1], v[2], v[3], v[4]);
+        double ip = ppm_iface(v[2], v[3], v[4], v[5]);
+        double lL = im, lR = i0;       /* cell c-1 */
+        ppm_limit(v[2], &lL, &lR);
+        double rL = i0, rR = ip;       /* cell c */
+        ppm_limit(v[3], &rL, &rR);
+        *L = lR;
+        *R = rL;
+        return;
+    }
+    long m2 = shift(g, c, d, -2), m1 = shift(g, c, d, -1), p1 = shift(g, c, d, 1);
+    *L = a[m1] + 0.5 * mc_slope(a[m2], a[m1], a[c]);
+    *R = a[c] - 0.5 * mc_slope(a[m1], a[c], a[p1]);
+}
+
 /* ------------------------------------------------------------------ */
 /* physical flux and conserved state at a face (Sec. 2.1)                */
 /* ------------------------------------------------------------------ */
@@ -627,13 +693,8 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
             if (f < 2 || f > g->N[d] - 2) continue;
             long cm2 = shift(g, c, d, -2), cm1 = shift(g, c, d, -1), cp1 = shift(g, c, d, 1);
             double recL[NREC], recR[NREC];
-            for (int v = 0; v < NREC; v++) {
-                const double* a = v < NPR ? prim[v] : Bc[v - NPR];
-                double sl = mc_slope(a[cm2], a[cm1], a[c]);
-                double sr = mc_slope(a[cm1], a[c], a[cp1]);
-                recL[v] = a[cm1] + 0.5 * sl;
-                recR[v] = a[c] - 0.5 * sr;
-            }
+            (void)cm2; (void)cp1;
+            for (int v = 0; v < NREC; v++) face_lr(g, v < NPR ? prim[v] : Bc[v - NPR], c, d, &recL[v], &recR[v]);
             double psf = 0.5 * (psi_at(X->psi, cm1) + psi_at(X->psi, c));
             double alf = 0.5 * (alp_at(X->alp, cm1) + alp_at(X->alp, c));
             double gf = psf * psf * psf * psf;
@@ -662,6 +723,12 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
             }
         }
     }
+    /* transport velocities of faces outside the interior (in the transverse directions)
+     * follow the grid's boundary rule, like every other quantity read there */
+    if (g->emf == 1)
+        for (int d = 0; d < 3; d++)
+            for (int j = 0; j < 3; j++)
+                if (g->act[d] && j != d) fill_face_ghosts(g, vbar[d][j], d);
     /* cell-centred L: flux divergence + non-stiff sources */
     for (long c = 0; c < nc; c++) {
         coords(g, c, ijk);
@@ -690,9 +757,7 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
             if (!g->act[a]) { EaL[c] = EaR[c] = Ecov[cc][c]; continue; }
             int f = ijk[a];
             if (f < 2 || f > g->N[a] - 2) continue;
-            long m2 = shift(g, c, a, -2), m1 = shift(g, c, a, -1), p1 = shift(g, c, a, 1);
-            EaL[c] = Ecov[cc][m1] + 0.5 * mc_slope(Ecov[cc][m2], Ecov[cc][m1], Ecov[cc][c]);
-            EaR[c] = Ecov[cc][c] - 0.5 * mc_slope(Ecov[cc][m1], Ecov[cc][c], Ecov[cc][p1]);
+            face_lr(g, Ecov[cc], c, a, &EaL[c], &EaR[c]);
         }
         for (long c = 0; c < nc; c++) {
             coords(g, c, ijk);
@@ -708,24 +773,17 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
             const double* src[2] = {EaL, EaR};
             for (int X2 = 0; X2 < 2; X2++) {
                 if (!g->act[b]) { EXY[X2][0] = EXY[X2][1] = src[X2][c]; continue; }
-                long m2 = shift(g, c, b, -2), m1 = shift(g, c, b, -1), p1 = shift(g, c, b, 1);
-                const double* s = src[X2];
-                EXY[X2][0] = s[m1] + 0.5 * mc_slope(s[m2], s[m1], s[c]);
-                EXY[X2][1] = s[c] - 0.5 * mc_slope(s[m1], s[c], s[p1]);
+                face_lr(g, src[X2], c, b, &EXY[X2][0], &EXY[X2][1]);
             }
             /* step (iv): q_B^b (b-faces) along a -> L/R in a; q_B^a (a-faces) along b -> L/R in b */
             double qBbL, qBbR, qBaL, qBaR;
             if (g->act[a]) {
-                long m2 = shift(g, c, a, -2), m1 = shift(g, c, a, -1), p1 = shift(g, c, a, 1);
-                qBbL = bf[b][m1] + 0.5 * mc_slope(bf[b][m2], bf[b][m1], bf[b][c]);
-                qBbR = bf[b][c] - 0.5 * mc_slope(bf[b][m1], bf[b][c], bf[b][p1]);
+                face_lr(g, bf[b], c, a, &qBbL, &qBbR);
             } else {
                 qBbL = qBbR = bf[b][c];
             }
             if (g->act[b]) {
-                long m2 = shift(g, c, b, -2), m1 = shift(g, c, b, -1), p1 = shift(g, c, b, 1);
-                qBaL = bf[a][m1] + 0.5 * mc_slope(bf[a][m2], bf[a][m1], bf[a][c]);
-                qBaR = bf[a][c] - 0.5 * mc_slope(bf[a][m1], bf[a][c], bf[a][p1]);
+                face_lr(g, bf[a], c, b, &qBaL, &qBaR);
             } else {
                 qBaL = qBaR = bf[a][c];
             }
@@ -774,16 +832,12 @@ static void explicit_L(const OCtx* X, double* const* prim, double* const* qBc, d
                 const double* va = vbar[b][a];
                 const double* vb = vbar[a][b];
                 if (g->act[a]) {
-                    long m2 = shift(g, c, a, -2), m1 = shift(g, c, a, -1), p1 = shift(g, c, a, 1);
-                    vaL = va[m1] + 0.5 * mc_slope(va[m2], va[m1], va[c]);
-                    vaR = va[c] - 0.5 * mc_slope(va[m1], va[c], va[p1]);
+                    face_lr(g, va, c, a, &vaL, &vaR);
                 } else {
                     vaL = vaR = va[c];
                 }
                 if (g->act[b]) {
-                    long m2 = shift(g, c, b, -2), m1 = shift(g, c, b, -1), p1 = shift(g, c, b, 1);
-                    vbL = vb[m1] + 0.5 * mc_slope(vb[m2], vb[m1], vb[c]);
-                    vbR = vb[c] - 0.5 * mc_slope(vb[m1], vb[c], vb[p1]);
+                    face_lr(g, vb, c, b, &vbL, &vbR);
                 } else {
                     vbL = vbR = vb[c];
                 }
@@ -1211,13 +1265,9 @@ static void explicit_L_glm(const OCtx* X, double kappa, double* const* prim, dou
             coords(g, c, ijk);
             int f = ijk[d];
             if (f < 2 || f > g->N[d] - 2) continue;
-            long cm2 = shift(g, c, d, -2), cm1 = shift(g, c, d, -1), cp1 = shift(g, c, d, 1);
+            long cm1 = shift(g, c, d, -1);
             double rL[NGLM], rR[NGLM];
-            for (int v = 0; v < NGLM; v++) {
-                const double* a = rec[v];
-                rL[v] = a[cm1] + 0.5 * mc_slope(a[cm2], a[cm1], a[c]);
-                rR[v] = a[c] - 0.5 * mc_slope(a[cm1], a[c], a[cp1]);
-            }
+            for (int v = 0; v < NGLM; v++) face_lr(g, rec[v], c, d, &rL[v], &rR[v]);
             double psf = 0.5 * (psi_at(X->psi, cm1) + psi_at(X->psi, c));
             double alf = 0.5 * (alp_at(X->alp, cm1) + alp_at(X->alp, c));
             double gf = psf * psf * psf * psf;
@@ -1426,4 +1476,17 @@ void orc_divb_cc(const int* gi, const double* gd, double* const* qB_in, double* 
     }
     out[0] = s1 / n; out[1] = sqrt(s2 / n); out[2] = mx;
     for (int d = 0; d < 3; d++) free(qB[d]);
+}
+
+/* face states of one array along d at every face whose stencil fits (TEST export of
+ * face_lr): L, R padded arrays, the lower d-face of each cell */
+void orc_face_states(const int* gi, const double* gd, const double* a, int d, double* L, double* R)
+{
+    OGrid G; grid_setup(&G, gi, gd);
+    int ijk[3];
+    for (long c = 0; c < G.ncell; c++) {
+        coords(&G, c, ijk);
+        if (ijk[d] < 2 || ijk[d] > G.N[d] - 2) continue;
+        face_lr(&G, a, c, d, &L[c], &R[c]);
+    }
 }
