@@ -60,6 +60,18 @@ enum { GRMHD_PREC_FP64 = 0, GRMHD_PREC_MIXED = 1 };
  * constrained transport (Sec. 3.2), or cell-centred fields with GLM hyperbolic
  * cleaning (Sec. 3.1). */
 enum { GRMHD_DIVB_CT = 0, GRMHD_DIVB_GLM = 1 };
+/* Edge EMF of the CT update: the resistive UCT of Sec. 3.2 (reconstructed electric
+ * field), or the ideal-limit HLL UCT of App. A (Ehat = -vhat x q_B from HLL-weighted
+ * transverse transport velocities stored at the faces and q_B, both reconstructed to
+ * the edges).  The ideal EMF is valid where the stiff implicit solve drives E to
+ * -v x B (eta -> 0). */
+enum { GRMHD_EMF_RESISTIVE = 0, GRMHD_EMF_IDEAL = 1 };
+/* Reconstruction of every face and edge state: the MC limiter (the default of Sec. 5)
+ * or PPM (named in Sec. 5 for the star runs; Colella & Woodward's interface
+ * interpolation with the MC slope and their monotonicity limits, reaching one cell
+ * past the two ghost layers, where periodic wraps, outflow takes the boundary cell
+ * and fixed the outermost stored ghost). */
+enum { GRMHD_REC_MC = 0, GRMHD_REC_PPM = 1 };
 
 /* Uniform Cartesian grid (Sec. 5 test set-ups).  bc: per direction; FIXED keeps the
  * ghost values that init wrote (Sec. 5, "values at the outer boundaries are kept
@@ -105,6 +117,11 @@ typedef struct {
                           + q_B^i d_i alpha and s_B^i = -psi^6 alpha gamma^{ij} d_j Phi.
                           FP64 only; not accepted by the batched executor */
     double kappa_b;    /* GLM damping kappa_B >= 0 (Sec. 3.1); unused by CT */
+    int emf;           /* GRMHD_EMF_RESISTIVE (0, default) or GRMHD_EMF_IDEAL (App. A):
+                          CT, FP64, no FIXED boundary; not accepted by the batched
+                          executor */
+    int rec;           /* GRMHD_REC_MC (0, default) or GRMHD_REC_PPM: FP64, CT with the
+                          resistive EMF or GLM; not accepted by the batched executor */
 } grmhd_params;
 
 /* IMEX-SSP2(2,2,2) of Sec. 2.3 (Pareschi & Russo), gamma = 1 - 1/sqrt(2). */

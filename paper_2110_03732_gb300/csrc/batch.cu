@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) kb_flux(const ProbStage* __restrict__ P, 
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
         for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x)
-            flux_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, flux_of<T>(ps, D), t);
+            flux_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, flux_of<T>(ps, D), nullptr, t);
     }
 }
 
@@ -314,6 +314,10 @@ grmhd_status grmhd_batch_scratch_bytes(grmhd_ctx* const* ctxs, int n, size_t* by
         if (!ctxs[p] || !ctx_bound(ctxs[p])) return batch_fail(GRMHD_ERR_STATE, "every context must be bound");
         if (ctx_glm(ctxs[p]))
             return batch_fail(GRMHD_ERR_ARG, "batched execution supports constrained transport (GRMHD_DIVB_CT) only");
+        if (ctx_ideal(ctxs[p]))
+            return batch_fail(GRMHD_ERR_ARG, "batched execution takes the resistive edge EMF only");
+        if (ctx_ppm(ctxs[p]))
+            return batch_fail(GRMHD_ERR_ARG, "batched execution takes the MC reconstruction only");
         s = ctx_stages(ctxs[p]);
     }
     *bytes = rup(sizeof(ProbStage) * (size_t)n * s) + rup(sizeof(Chunk) * chunk_capacity(ctxs, n));

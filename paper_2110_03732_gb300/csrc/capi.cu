@@ -71,6 +71,9 @@ struct grmhd_ctx_s {
     double eta_u;
     double xi;           // mean-field dynamo parameter (0: none)
     bool glm;            // GLM cleaning with cell-centred B (Sec. 3.1) instead of CT
+    bool ideal;          // ideal-limit edge EMF (App. A)
+    bool ppm;            // PPM reconstruction instead of MC
+    double* vbar[3][2];  // its transport velocities at the d-faces (FP32 scratch block)
     double kappa;        // GLM damping kappa_B
     double* qphi;        // GLM: bound q_Phi
     long long launches;
@@ -280,7 +283,8 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
             for (int v = 0; v < 8; v++) fo.p[v] = c->F32[d][v];
             e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st);
         } else {
-            e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st);
+            e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
+                            c->ppm);
         }
         tend(c, tk, st);
         c->launches++;
@@ -290,7 +294,8 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         if (!emf_needed(g, k)) continue;
         const int tk = tbegin(c, KIND_EMF, st);
         if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh32[k], c->nsm, st);
-        else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st);
+        else if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
+        else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "emf kernel");
@@ -329,7 +334,7 @@ grmhd_status explicit_part_glm(grmhd_ctx* c, CP8 prim, CP3 qB, const double* qph
         if (!g.act[d]) continue;
         for (int v = 0; v < 12; v++) fa.F[v] = c->F[d][v];
         const int tk = tbegin(c, KIND_FLUX, st);
-        e = launch_glm_flux(g, d, fa, c->nsm, st);
+        e = launch_glm_flux(g, d, fa, c->nsm, st, c->ppm);
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "GLM flux kernel");
@@ -433,6 +438,19 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
         return fail(GRMHD_ERR_ARG, "GLM cleaning runs in FP64 only");
     if (par->divb == GRMHD_DIVB_GLM && !(par->kappa_b >= 0.0))
         return fail(GRMHD_ERR_ARG, "kappa_b must be >= 0");
+    if (par->emf != GRMHD_EMF_RESISTIVE && par->emf != GRMHD_EMF_IDEAL)
+        return fail(GRMHD_ERR_ARG, "emf must be GRMHD_EMF_RESISTIVE or GRMHD_EMF_IDEAL");
+    if (par->rec != GRMHD_REC_MC && par->rec != GRMHD_REC_PPM)
+        return fail(GRMHD_ERR_ARG, "rec must be GRMHD_REC_MC or GRMHD_REC_PPM");
+    if (par->rec == GRMHD_REC_PPM && (par->precision != GRMHD_PREC_FP64 || par->emf == GRMHD_EMF_IDEAL))
+        return fail(GRMHD_ERR_ARG, "PPM runs in FP64 with the resistive EMF or GLM");
+    if (par->emf == GRMHD_EMF_IDEAL) {
+        if (par->divb != GRMHD_DIVB_CT || par->precision != GRMHD_PREC_FP64)
+            return fail(GRMHD_ERR_ARG, "the ideal-limit EMF needs constrained transport in FP64");
+        for (int d = 0; d < grid->ndim; d++)
+            if (grid->bc[d] == GRMHD_BC_FIXED)
+                return fail(GRMHD_ERR_ARG, "the ideal-limit EMF does not take FIXED boundaries");
+    }
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -455,6 +473,8 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
     c->nsm = nsm;
     c->mixed = par->precision == GRMHD_PREC_MIXED;
     c->glm = par->divb == GRMHD_DIVB_GLM;
+    c->ideal = par->emf == GRMHD_EMF_IDEAL;
+    c->ppm = par->rec == GRMHD_REC_PPM;
     c->kappa = c->glm ? par->kappa_b : 0.0;
     *out = c;
     return GRMHD_OK;
@@ -519,6 +539,12 @@ grmhd_status grmhd_bind(grmhd_ctx* c, double* const* q, double* const* bface, vo
     const size_t need = carve(nullptr, c->g, c->tab.s, c->grid.ndim, nullptr, c->glm);
     if (scratch_bytes < need) return fail(GRMHD_ERR_SCRATCH, "scratch smaller than grmhd_scratch_bytes");
     carve(c, c->g, c->tab.s, c->grid.ndim, (char*)scratch, c->glm);
+    // ideal-limit EMF (FP64 only): its two transport-velocity arrays per direction take
+    // the FP32 flux block of that direction, which the FP64 path leaves unused (each
+    // pair of consecutive FP32 arrays spans at least one FP64 array)
+    for (int d = 0; d < 3; d++)
+        for (int k = 0; k < 2; k++)
+            c->vbar[d][k] = (c->ideal && d < c->grid.ndim) ? (double*)c->F32[d][2 * k] : nullptr;
     for (int v = 0; v < 8; v++) c->q[v] = q[v];
     for (int v = 0; v < 3; v++) c->bf[v] = bface[v];
     c->bound = true;
@@ -825,6 +851,8 @@ bool ctx_bound(const grmhd_ctx* c) { return c->bound; }
 bool ctx_mixed(const grmhd_ctx* c) { return c->mixed; }
 bool ctx_any_fixed(const grmhd_ctx* c) { return c->any_fixed; }
 bool ctx_glm(const grmhd_ctx* c) { return c->glm; }
+bool ctx_ideal(const grmhd_ctx* c) { return c->ideal; }
+bool ctx_ppm(const grmhd_ctx* c) { return c->ppm; }
 int ctx_stages(const grmhd_ctx* c) { return c->tab.s; }
 int ctx_nsm(const grmhd_ctx* c) { return c->nsm; }
 

@@ -14,6 +14,8 @@ bool ctx_bound(const grmhd_ctx* c);
 bool ctx_mixed(const grmhd_ctx* c);
 bool ctx_any_fixed(const grmhd_ctx* c);
 bool ctx_glm(const grmhd_ctx* c);
+bool ctx_ideal(const grmhd_ctx* c);
+bool ctx_ppm(const grmhd_ctx* c);
 int ctx_stages(const grmhd_ctx* c);
 int ctx_nsm(const grmhd_ctx* c);
 bool ctx_same_scheme(const grmhd_ctx* a, const grmhd_ctx* b);

@@ -24,9 +24,11 @@
 
 namespace grmhd {
 
-template <int D, bool M>
+// P: PPM reconstruction (cells c-3..c+2) instead of MC (c-2..c+1)
+template <int D, bool M, bool P = false>
 __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& a, long long t)
 {
+    constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? a.psi : nullptr;
     const double* __restrict__ alp = M ? a.alp : nullptr;
     constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
@@ -35,38 +37,52 @@ __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& 
     c[0] = g.ng[0] + (int)(t % e0);
     c[1] = g.ng[1] + (int)((t / e0) % e1);
     c[2] = g.ng[2] + (int)(t / ((long long)e0 * e1));
-    long long mi[4], ri[4];
+    long long mi[NS], ri[NS];
 #pragma unroll
-    for (int s = 0; s < 4; s++) {
+    for (int s = 0; s < NS; s++) {
         int cs[3] = {c[0], c[1], c[2]};
-        cs[D] += s - 2;
+        cs[D] = P ? ext_cell(g, D, c[D] + s - OFF) : c[D] + s - OFF;
         mi[s] = cell_at(g, cs);
         ri[s] = lin(g, cs[0], cs[1], cs[2]);
     }
-    double ip6[4];
+    double ip6[NS];
 #pragma unroll
-    for (int s = 0; s < 4; s++) {
+    for (int s = 0; s < NS; s++) {
         const double ps = psi ? psi[ri[s]] : 1.0;
         const double p2 = ps * ps;
         ip6[s] = 1.0 / (p2 * p2 * p2);
     }
+    // MC or PPM face states of w[0..NS-1]
+    auto rec = [&](const double* w, double& L, double& R) {
+        if (P) ppm_face<double>(w, L, R);
+        else mc_face<double>(w[0], w[1], w[2], w[NS - 1], L, R);
+    };
     double prL[8], prR[8], BL[3], BR[3], phL, phR;
 #pragma unroll
     for (int v = 0; v < 8; v++) {
         const double* __restrict__ x = a.prim[v];
-        mc_face<double>(x[mi[0]], x[mi[1]], x[mi[2]], x[mi[3]], prL[v], prR[v]);
+        double w[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) w[s] = x[mi[s]];
+        rec(w, prL[v], prR[v]);
     }
 #pragma unroll
     for (int e = 0; e < 3; e++) {
         const double* __restrict__ x = a.qB[e];
-        mc_face<double>(x[mi[0]] * ip6[0], x[mi[1]] * ip6[1], x[mi[2]] * ip6[2], x[mi[3]] * ip6[3], BL[e], BR[e]);
+        double w[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) w[s] = x[mi[s]] * ip6[s];
+        rec(w, BL[e], BR[e]);
     }
     {
         const double* __restrict__ x = a.qphi;
-        mc_face<double>(x[mi[0]] * ip6[0], x[mi[1]] * ip6[1], x[mi[2]] * ip6[2], x[mi[3]] * ip6[3], phL, phR);
+        double w[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) w[s] = x[mi[s]] * ip6[s];
+        rec(w, phL, phR);
     }
-    const double psf = psi ? 0.5 * (psi[ri[1]] + psi[ri[2]]) : 1.0;
-    const double alf = alp ? 0.5 * (alp[ri[1]] + alp[ri[2]]) : 1.0;
+    const double psf = psi ? 0.5 * (psi[ri[OFF - 1]] + psi[ri[OFF]]) : 1.0;
+    const double alf = alp ? 0.5 * (alp[ri[OFF - 1]] + alp[ri[OFF]]) : 1.0;
     const double pf2 = psf * psf, pf4 = pf2 * pf2, pf6 = pf4 * pf2;
     FaceState sL, sR;
     face_state<double>(prL, BL, D, psf, alf, g.gh, sL);
@@ -102,13 +118,13 @@ __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& 
         a.F[8 + v][o] = (cs * fL[v] + cs * fR[v] - cs * cs * (qR[v] - qL[v])) / (cs + cs);
 }
 
-template <int D, bool M>
+template <int D, bool M, bool P = false>
 __global__ void __launch_bounds__(128) k_glm_flux(Dims g, GlmFluxArgs a)
 {
     const long long tot = (long long)(g.n[0] + (D == 0)) * (g.n[1] + (D == 1)) * (g.n[2] + (D == 2));
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        glm_flux_item<D, M>(g, a, t);
+        glm_flux_item<D, M, P>(g, a, t);
 }
 
 __device__ __forceinline__ void glm_out(const GlmUpdateArgs& a, int v, long long o, double L, bool has_r)
@@ -200,11 +216,17 @@ static int glm_grid(long long work, int threads, int nsm)
     return (int)b;
 }
 
-cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st)
+cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st, bool ppm)
 {
     const long long work = (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
     const int b = glm_grid(work, 128, nsm);
     const bool m = a.psi || a.alp;
+    if (ppm) {
+        if (d == 0) m ? k_glm_flux<0, true, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<0, false, true><<<b, 128, 0, st>>>(g, a);
+        else if (d == 1) m ? k_glm_flux<1, true, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<1, false, true><<<b, 128, 0, st>>>(g, a);
+        else m ? k_glm_flux<2, true, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<2, false, true><<<b, 128, 0, st>>>(g, a);
+        return cudaGetLastError();
+    }
     if (d == 0) m ? k_glm_flux<0, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<0, false><<<b, 128, 0, st>>>(g, a);
     else if (d == 1) m ? k_glm_flux<1, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<1, false><<<b, 128, 0, st>>>(g, a);
     else m ? k_glm_flux<2, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<2, false><<<b, 128, 0, st>>>(g, a);

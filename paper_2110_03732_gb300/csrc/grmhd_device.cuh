@@ -145,6 +145,59 @@ __device__ __forceinline__ void mc_face(T a0, T a1, T a2, T a3, T& L, T& R)
     R = a2 - minmod3<T>(d0, T(0.25) * (a3 - a1), dp);
 }
 
+// PPM (Colella & Woodward 1984: interface interpolation with the MC slope and the
+// monotonicity limits of the parabola, no steepening or flattening).  a[0..5] are the
+// cells c-3..c+2; L is the right edge of cell c-1, R the left edge of cell c.
+template <typename T>
+__device__ __forceinline__ T ppm_iface(T am, T a0, T ap, T app)
+{
+    // the MC slope is twice the half slope minmod(D-, (a+ - a-)/4, D+)
+    const T s0 = T(2) * minmod3<T>(a0 - am, T(0.25) * (ap - am), ap - a0);
+    const T s1 = T(2) * minmod3<T>(ap - a0, T(0.25) * (app - a0), app - ap);
+    return a0 + T(0.5) * (ap - a0) - (s1 - s0) / T(6);
+}
+
+template <typename T>
+__device__ __forceinline__ void ppm_limit(T a0, T& aL, T& aR)
+{
+    if ((aR - a0) * (a0 - aL) <= T(0)) {
+        aL = a0;
+        aR = a0;
+        return;
+    }
+    const T dd = aR - aL, m6 = T(6) * (a0 - T(0.5) * (aL + aR));
+    if (dd * m6 > dd * dd) aL = T(3) * a0 - T(2) * aR;
+    else if (-dd * dd > dd * m6) aR = T(3) * a0 - T(2) * aL;
+}
+
+template <typename T>
+__device__ __forceinline__ void ppm_face(const T* a, T& L, T& R)
+{
+    const T im = ppm_iface<T>(a[0], a[1], a[2], a[3]);
+    const T i0 = ppm_iface<T>(a[1], a[2], a[3], a[4]);
+    const T ip = ppm_iface<T>(a[2], a[3], a[4], a[5]);
+    T lL = im, lR = i0, rL = i0, rR = ip;
+    ppm_limit<T>(a[2], lL, lR);
+    ppm_limit<T>(a[3], rL, rR);
+    L = lR;
+    R = rL;
+}
+
+// coordinate m along d brought inside the padded array: the PPM stencil reaches one
+// cell past the two stored ghost layers, where periodic wraps, outflow takes the
+// boundary cell and fixed the outermost stored ghost.  Inside the array m is kept.
+__device__ __forceinline__ int ext_cell(const Dims& g, int d, int m)
+{
+    if (!g.act[d] || (m >= 0 && m < g.N[d])) return m;
+    const int lo = g.ng[d], n = g.n[d];
+    if (g.bc[d] == BC_PERIODIC) {
+        int r = (m - lo) % n;
+        return lo + (r < 0 ? r + n : r);
+    }
+    if (g.bc[d] == BC_OUTFLOW) return m < lo ? lo : lo + n - 1;
+    return m < 0 ? 0 : g.N[d] - 1;
+}
+
 // ---------------------------------------------------------------------------
 // physical state at a face in the orthonormal frame (Sec. 2.1)
 // ---------------------------------------------------------------------------
@@ -153,6 +206,7 @@ template <typename T>
 struct FaceStateT {
     T q[8];    // densitised conserved: D, S_1..3, tau, E^1..3
     T f[8];    // flux of the same along the face normal
+    T W;       // Lorentz factor of the state
 };
 using FaceState = FaceStateT<double>;
 
@@ -168,6 +222,7 @@ __device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi
 #pragma unroll
     for (int i = 0; i < 3; i++) { u[i] = p2 * pr[1 + i]; E[i] = p2 * pr[5 + i]; Bh[i] = p2 * B[i]; }
     const T W = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    s.W = W;
     const T iW = T(1) / W;
     const T rhoh = rho + gh * p;
     const T D = rho * W;

@@ -142,10 +142,14 @@ __device__ __forceinline__ float cell_qB_in(const Dims&, const PrimIn<float>& pa
     return pa.p[8 + e][mi];
 }
 
-template <int D, bool M, typename T>
+// vbar (may be NULL): the two transverse transport-velocity arrays of the ideal-limit
+// EMF (App. A) for the D-faces, components (D+1)%3 and (D+2)%3.  P: PPM reconstruction
+// (six cells c-3..c+2) instead of MC (four cells c-2..c+1).
+template <int D, bool M, typename T, bool P = false>
 __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
-                                          const double* alp_in, const FluxOut<T>& F, long long t)
+                                          const double* alp_in, const FluxOut<T>& F, double* const* vbar, long long t)
 {
+    constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? psi_in : nullptr;
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
@@ -154,11 +158,13 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
     c[0] = g.ng[0] + (int)(t % e0);
     c[1] = g.ng[1] + (int)((t / e0) % e1);
     c[2] = g.ng[2] + (int)(t / ((long long)e0 * e1));
-    long long mi[4], ri[4];
+    long long mi[NS], ri[NS];
+    int cd[NS];
 #pragma unroll
-    for (int s = 0; s < 4; s++) {
+    for (int s = 0; s < NS; s++) {
         int cs[3] = {c[0], c[1], c[2]};
-        cs[D] += s - 2;
+        cs[D] = P ? ext_cell(g, D, c[D] + s - OFF) : c[D] + s - OFF;
+        cd[s] = cs[D];
         mi[s] = cell_at(g, cs);
         ri[s] = lin(g, cs[0], cs[1], cs[2]);
     }
@@ -166,25 +172,33 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
 #pragma unroll
     for (int v = 0; v < 8; v++) {
         const T* a = prim.p[v];
-        mc_face<T>(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3]], prL[v], prR[v]);
+        if (P) {
+            T w[6];
+#pragma unroll
+            for (int s = 0; s < 6; s++) w[s] = a[mi[s < NS ? s : 0]];
+            ppm_face<T>(w, prL[v], prR[v]);
+        } else {
+            mc_face<T>(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3 < NS ? 3 : 0]], prL[v], prR[v]);
+        }
     }
     // transverse cell-centred B (primitive = q_B / psi^6 at the cell)
 #pragma unroll
     for (int tt = 0; tt < 2; tt++) {
         const int e = tt == 0 ? T1 : T2;
-        T b[4];
+        T b[NS];
 #pragma unroll
-        for (int s = 0; s < 4; s++) {
+        for (int s = 0; s < NS; s++) {
             int cs[3] = {c[0], c[1], c[2]};
-            cs[D] += s - 2;
+            cs[D] = cd[s];
             const T ps = psi ? (T)psi[ri[s]] : T(1);
             const T p2 = ps * ps;
             b[s] = (T)cell_qB_in(g, prim, bf, e, cs, mi[s]) / (p2 * p2 * p2);
         }
-        mc_face<T>(b[0], b[1], b[2], b[3], BL[e], BR[e]);
+        if (P) ppm_face<T>(b, BL[e], BR[e]);
+        else mc_face<T>(b[0], b[1], b[2], b[NS - 1], BL[e], BR[e]);
     }
-    const T psf = psi ? (T)(0.5 * (psi[ri[1]] + psi[ri[2]])) : T(1);
-    const T alf = alp ? (T)(0.5 * (alp[ri[1]] + alp[ri[2]])) : T(1);
+    const T psf = psi ? (T)(0.5 * (psi[ri[OFF - 1]] + psi[ri[OFF]])) : T(1);
+    const T alf = alp ? (T)(0.5 * (alp[ri[OFF - 1]] + alp[ri[OFF]])) : T(1);
     const T pf2 = psf * psf;
     const T bn = (T)bf.p[D][face_at(g, D, c)] / (pf2 * pf2 * pf2);
     BL[D] = bn;
@@ -198,16 +212,27 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
 #pragma unroll
     for (int v = 0; v < 8; v++)
         F.p[v][o] = (cs * sL.f[v] + cs * sR.f[v] - cs * cs * (sR.q[v] - sL.q[v])) / (cs + cs);
+    if (vbar && vbar[0]) {
+        // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
+        // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+)
+        const double al = (double)alf, c = (double)cs;
+        const double vL1 = al * (double)prL[1 + T1] / (double)sL.W, vR1 = al * (double)prR[1 + T1] / (double)sR.W;
+        const double vL2 = al * (double)prL[1 + T2] / (double)sL.W, vR2 = al * (double)prR[1 + T2] / (double)sR.W;
+        vbar[0][o] = (c * vR1 + c * vL1) / (c + c);
+        vbar[1][o] = (c * vR2 + c * vL2) / (c + c);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // upwind constrained transport (Sec. 3.2): item t = C-edge t
 // ---------------------------------------------------------------------------
 
-template <int C, bool M, typename T>
+// P: PPM reconstruction (six cells or faces per pass) instead of MC (four)
+template <int C, bool M, typename T, bool P = false>
 __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
                                          const double* alp_in, T* __restrict__ Eh, long long t)
 {
+    constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? psi_in : nullptr;
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
@@ -221,22 +246,23 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
     c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
     // steps (ii)-(iii): covariant E_C = psi^4 E^C, to A-faces then along B
-    T s[2][4];   // [X = A-side L/R][B offset -2..+1]
-    const int nb = ba ? 4 : 1;
+    T s[2][NS];   // [X = A-side L/R][B offset -OFF..+OFF-1]
+    const int nb = ba ? NS : 1;
     for (int ob = 0; ob < nb; ob++) {
         int cb[3] = {c[0], c[1], c[2]};
-        if (ba) cb[B] += ob - 2;
+        if (ba) cb[B] = P ? ext_cell(g, B, c[B] + ob - OFF) : c[B] + ob - OFF;
         if (aa) {
-            T v[4];
+            T v[NS];
 #pragma unroll
-            for (int sa = 0; sa < 4; sa++) {
+            for (int sa = 0; sa < NS; sa++) {
                 int cs[3] = {cb[0], cb[1], cb[2]};
-                cs[A] += sa - 2;
+                cs[A] = P ? ext_cell(g, A, cb[A] + sa - OFF) : cb[A] + sa - OFF;
                 const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
                 const T p2 = ps * ps;
                 v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
             }
-            mc_face<T>(v[0], v[1], v[2], v[3], s[0][ob], s[1][ob]);
+            if (P) ppm_face<T>(v, s[0][ob], s[1][ob]);
+            else mc_face<T>(v[0], v[1], v[2], v[NS - 1], s[0][ob], s[1][ob]);
         } else {
             const T ps = psi ? (T)psi[lin(g, cb[0], cb[1], cb[2])] : T(1);
             const T p2 = ps * ps;
@@ -246,32 +272,35 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     T EXY[2][2];
 #pragma unroll
     for (int X = 0; X < 2; X++) {
-        if (ba) mc_face<T>(s[X][0], s[X][1], s[X][2], s[X][3], EXY[X][0], EXY[X][1]);
-        else EXY[X][0] = EXY[X][1] = s[X][0];
+        if (!ba) EXY[X][0] = EXY[X][1] = s[X][0];
+        else if (P) ppm_face<T>(s[X], EXY[X][0], EXY[X][1]);
+        else mc_face<T>(s[X][0], s[X][1], s[X][2], s[X][NS - 1], EXY[X][0], EXY[X][1]);
     }
     // step (iv): q_B^B (B-faces) along A, q_B^A (A-faces) along B
     T qBbL, qBbR, qBaL, qBaR;
     if (aa) {
-        T v[4];
+        T v[NS];
 #pragma unroll
-        for (int sa = 0; sa < 4; sa++) {
+        for (int sa = 0; sa < NS; sa++) {
             int cs[3] = {c[0], c[1], c[2]};
-            cs[A] += sa - 2;
+            cs[A] = P ? ext_cell(g, A, c[A] + sa - OFF) : c[A] + sa - OFF;
             v[sa] = (T)bf.p[B][face_at(g, B, cs)];
         }
-        mc_face<T>(v[0], v[1], v[2], v[3], qBbL, qBbR);
+        if (P) ppm_face<T>(v, qBbL, qBbR);
+        else mc_face<T>(v[0], v[1], v[2], v[NS - 1], qBbL, qBbR);
     } else {
         qBbL = qBbR = (T)bf.p[B][face_at(g, B, c)];
     }
     if (ba) {
-        T v[4];
+        T v[NS];
 #pragma unroll
-        for (int sb = 0; sb < 4; sb++) {
+        for (int sb = 0; sb < NS; sb++) {
             int cs[3] = {c[0], c[1], c[2]};
-            cs[B] += sb - 2;
+            cs[B] = P ? ext_cell(g, B, c[B] + sb - OFF) : c[B] + sb - OFF;
             v[sb] = (T)bf.p[A][face_at(g, A, cs)];
         }
-        mc_face<T>(v[0], v[1], v[2], v[3], qBaL, qBaR);
+        if (P) ppm_face<T>(v, qBaL, qBaR);
+        else mc_face<T>(v[0], v[1], v[2], v[NS - 1], qBaL, qBaR);
     } else {
         qBaL = qBaR = (T)bf.p[A][face_at(g, A, c)];
     }
@@ -313,6 +342,112 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
     Eh[i0] = (ca * cb * hLL + ca * cb * hLR + ca * cb * hRL + ca * cb * hRR) / ((ca + ca) * (cb + cb)) +
              ca * ca / (ca + ca) * (qBbR - qBbL) - cb * cb / (cb + cb) * (qBaR - qBaL);
+}
+
+// ---------------------------------------------------------------------------
+// ideal-limit edge EMF (App. A), FP64: item t = C-edge t (as emf_item)
+// ---------------------------------------------------------------------------
+
+// transport velocity vhat^j = alpha v^j of the cell at padded coordinates cs (the
+// "face" value in an inactive direction)
+__device__ __forceinline__ double cell_vhat(const Dims& g, const CP8& prim, const double* __restrict__ psi,
+                                            const double* __restrict__ alp, int j, const int* cs)
+{
+    const long long mi = cell_at(g, cs), ri = lin(g, cs[0], cs[1], cs[2]);
+    const double ps = psi ? psi[ri] : 1.0;
+    const double p4 = ps * ps * ps * ps;
+    const double u0 = prim.p[1][mi], u1 = prim.p[2][mi], u2 = prim.p[3][mi];
+    const double W = sqrt(1.0 + p4 * (u0 * u0 + u1 * u1 + u2 * u2));
+    return (alp ? alp[ri] : 1.0) * prim.p[1 + j][mi] / W;
+}
+
+// vb[d][k]: transport velocities at the d-faces, component (d + 1 + k) % 3
+template <int C, bool M>
+__device__ __forceinline__ void emf_ideal_item(const Dims& g, const CP8& prim, const CP3& bf, const double* psi_in,
+                                               const double* alp_in, const double* const (*vb)[2],
+                                               double* __restrict__ Eh, long long t)
+{
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    const double* __restrict__ alp = M ? alp_in : nullptr;
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    const bool aa = g.act[A], ba = g.act[B];
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) e[d] = (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    int c[3];
+    c[0] = g.ng[0] + (int)(t % e[0]);
+    c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
+    c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+    // step (iii): q_B^B and vbar^A (both at B-faces) along A; q_B^A and vbar^B (A-faces)
+    // along B.  vbar^A is component A = B + 2 of the B-faces, vbar^B component B = A + 1
+    // of the A-faces.
+    double qBbL, qBbR, qBaL, qBaR, vaL, vaR, vbL, vbR;
+    {
+        double q[4], v[4];
+        const int ns = aa ? 4 : 1;
+        for (int sa = 0; sa < ns; sa++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            if (aa) cs[A] += sa - 2;
+            const long long fi = face_at(g, B, cs);
+            q[sa] = bf.p[B][fi];
+            v[sa] = ba ? vb[B][1][fi] : cell_vhat(g, prim, psi, alp, A, cs);
+        }
+        if (aa) {
+            mc_face<double>(q[0], q[1], q[2], q[3], qBbL, qBbR);
+            mc_face<double>(v[0], v[1], v[2], v[3], vaL, vaR);
+        } else {
+            qBbL = qBbR = q[0];
+            vaL = vaR = v[0];
+        }
+    }
+    {
+        double q[4], v[4];
+        const int ns = ba ? 4 : 1;
+        for (int sb = 0; sb < ns; sb++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            if (ba) cs[B] += sb - 2;
+            const long long fi = face_at(g, A, cs);
+            q[sb] = bf.p[A][fi];
+            v[sb] = aa ? vb[A][0][fi] : cell_vhat(g, prim, psi, alp, B, cs);
+        }
+        if (ba) {
+            mc_face<double>(q[0], q[1], q[2], q[3], qBaL, qBaR);
+            mc_face<double>(v[0], v[1], v[2], v[3], vbL, vbR);
+        } else {
+            qBaL = qBaR = q[0];
+            vbL = vbR = v[0];
+        }
+    }
+    // speeds: each direction takes the larger alpha sqrt(gamma^dd) of its two faces at
+    // the edge (1 in an inactive direction)
+    const long long i0 = lin(g, c[0], c[1], c[2]);
+    const long long sA = aa ? g.st[A] : 0, sB = ba ? g.st[B] : 0;
+    double ca = 1.0, cb = 1.0;
+    if (alp || psi) {
+        if (aa) {
+            double cmax = 0.0;
+            for (int tt = 0; tt < (ba ? 2 : 1); tt++) {
+                const long long cf = i0 - tt * sB, cfm = cf - sA;
+                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+                cmax = fmax(cmax, alf / (psf * psf));
+            }
+            ca = cmax;
+        }
+        if (ba) {
+            double cmax = 0.0;
+            for (int tt = 0; tt < (aa ? 2 : 1); tt++) {
+                const long long cf = i0 - tt * sA, cfm = cf - sB;
+                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+                cmax = fmax(cmax, alf / (psf * psf));
+            }
+            cb = cmax;
+        }
+    }
+    // step (iv), the upwind formula of App. A (sqrt(gamma_hat) = 1)
+    Eh[i0] = -(ca * vaR * qBbR + ca * vaL * qBbL - ca * ca * (qBbR - qBbL)) / (ca + ca) +
+             (cb * vbR * qBaR + cb * vbL * qBaL - cb * cb * (qBaR - qBaL)) / (cb + cb);
 }
 
 // ---------------------------------------------------------------------------

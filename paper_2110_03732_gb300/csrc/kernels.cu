@@ -45,13 +45,13 @@ __global__ void __launch_bounds__(128) k_implicit_cc(Dims g, ImpArgs a)
 // face fluxes
 // ---------------------------------------------------------------------------
 
-template <int D, bool M, typename T>
+template <int D, bool M, typename T, bool P = false>
 __global__ void __launch_bounds__(128) k_flux(Dims g, FluxArgs<T> a)
 {
     const long long tot = (long long)(g.n[0] + (D == 0)) * (g.n[1] + (D == 1)) * (g.n[2] + (D == 2));
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        flux_item<D, M, T>(g, a.prim, a.bf, a.psi, a.alp, a.F, t);
+        flux_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) k_flux(Dims g, FluxArgs<T> a)
 // index that is lower in a = C+1 and b = C+2
 // ---------------------------------------------------------------------------
 
-template <int C, bool M, typename T>
+template <int C, bool M, typename T, bool P = false>
 __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
 {
     long long tot = 1;
@@ -67,7 +67,26 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
     for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        emf_item<C, M, T>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+        emf_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+}
+
+// ideal-limit edge EMF (App. A) from the stored transport velocities
+struct VbarArgs {
+    const double* p[3][2];
+};
+
+template <int C, bool M>
+__global__ void __launch_bounds__(128) k_emf_ideal(Dims g, EmfArgs<double> a, VbarArgs vb)
+{
+    long long tot = 1;
+#pragma unroll
+    for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    CP8 prim;
+#pragma unroll
+    for (int v = 0; v < 8; v++) prim.p[v] = a.prim.p[v];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x)
+        emf_ideal_item<C, M>(g, prim, a.bf, a.psi, a.alp, vb.p, a.Eh, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -398,17 +417,28 @@ static long long emf_work(const Dims& g, int c)
 }
 
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
-                        cudaStream_t st)
+                        cudaStream_t st, double* const* vbar, bool ppm)
 {
     FluxArgs<double> a;
     for (int v = 0; v < 8; v++) {
         a.prim.p[v] = prim.p[v];
         a.F.p[v] = F.p[v];
     }
+    a.vbar[0] = vbar ? vbar[0] : nullptr;
+    a.vbar[1] = vbar ? vbar[1] : nullptr;
     a.bf = bf;
     a.psi = psi;
     a.alp = alp;
-    flux_dispatch<double>(g, d, psi || alp, grid_for(flux_work(g, d), 128, nsm), st, a);
+    const int b = grid_for(flux_work(g, d), 128, nsm);
+    if (ppm) {
+        // PPM (FP64 only)
+        const bool m = psi || alp;
+        if (d == 0) m ? k_flux<0, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<0, false, double, true><<<b, 128, 0, st>>>(g, a);
+        else if (d == 1) m ? k_flux<1, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<1, false, double, true><<<b, 128, 0, st>>>(g, a);
+        else m ? k_flux<2, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, double, true><<<b, 128, 0, st>>>(g, a);
+        return cudaGetLastError();
+    }
+    flux_dispatch<double>(g, d, psi || alp, b, st, a);
     return cudaGetLastError();
 }
 
@@ -416,6 +446,7 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
                           const double* alp, FluxOut<float> F, int nsm, cudaStream_t st)
 {
     FluxArgs<float> a;
+    a.vbar[0] = a.vbar[1] = nullptr;
     a.prim = prim;
     a.bf = bf;
     a.psi = psi;
@@ -426,7 +457,7 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
 }
 
 cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
-                       int nsm, cudaStream_t st)
+                       int nsm, cudaStream_t st, bool ppm)
 {
     EmfArgs<double> a;
     for (int v = 0; v < 8; v++) a.prim.p[v] = prim.p[v];
@@ -434,7 +465,35 @@ cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi
     a.psi = psi;
     a.alp = alp;
     a.Eh = Eh;
-    emf_dispatch<double>(g, c, psi || alp, grid_for(emf_work(g, c), 128, nsm), st, a);
+    const int b = grid_for(emf_work(g, c), 128, nsm);
+    if (ppm) {
+        const bool m = psi || alp;
+        if (c == 0) m ? k_emf<0, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<0, false, double, true><<<b, 128, 0, st>>>(g, a);
+        else if (c == 1) m ? k_emf<1, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<1, false, double, true><<<b, 128, 0, st>>>(g, a);
+        else m ? k_emf<2, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, double, true><<<b, 128, 0, st>>>(g, a);
+        return cudaGetLastError();
+    }
+    emf_dispatch<double>(g, c, psi || alp, b, st, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp,
+                             const double* const (*vb)[2], double* Eh, int nsm, cudaStream_t st)
+{
+    EmfArgs<double> a;
+    for (int v = 0; v < 8; v++) a.prim.p[v] = prim.p[v];
+    a.bf = bf;
+    a.psi = psi;
+    a.alp = alp;
+    a.Eh = Eh;
+    VbarArgs v;
+    for (int d = 0; d < 3; d++)
+        for (int k = 0; k < 2; k++) v.p[d][k] = vb[d][k];
+    const int b = grid_for(emf_work(g, c), 128, nsm);
+    const bool m = psi || alp;
+    if (c == 0) m ? k_emf_ideal<0, true><<<b, 128, 0, st>>>(g, a, v) : k_emf_ideal<0, false><<<b, 128, 0, st>>>(g, a, v);
+    else if (c == 1) m ? k_emf_ideal<1, true><<<b, 128, 0, st>>>(g, a, v) : k_emf_ideal<1, false><<<b, 128, 0, st>>>(g, a, v);
+    else m ? k_emf_ideal<2, true><<<b, 128, 0, st>>>(g, a, v) : k_emf_ideal<2, false><<<b, 128, 0, st>>>(g, a, v);
     return cudaGetLastError();
 }
 

@@ -43,6 +43,7 @@ struct FluxArgs {
     const double* psi;
     const double* alp;
     FluxOut<T> F;
+    double* vbar[2];        // ideal-limit EMF: transverse transport velocities (or NULL)
 };
 
 template <typename T>
@@ -81,10 +82,15 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
                          const double* alp, float* Eh, int nsm, cudaStream_t st);
 cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
+// ppm: PPM reconstruction instead of MC (FP64 only)
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
-                        cudaStream_t st);
+                        cudaStream_t st, double* const* vbar = nullptr, bool ppm = false);
+// ideal-limit edge EMF (App. A): vb[d][k] are the transport velocities of the d-faces,
+// component (d + 1 + k) % 3 (NULL for inactive directions)
+cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp,
+                             const double* const (*vb)[2], double* Eh, int nsm, cudaStream_t st);
 cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
-                       int nsm, cudaStream_t st);
+                       int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_curlA(const Dims& g, CP3 A, P3 bf, int nsm, cudaStream_t st);
 cudaError_t launch_prim2con(const Dims& g, CP8 prim, CP3 bf, const double* psi, P8 q, int nsm, cudaStream_t st);
@@ -128,7 +134,7 @@ struct GlmUpdateArgs {
 };
 
 cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st);
-cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st);
+cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_glm_update(const Dims& g, const GlmUpdateArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_curlA_cc(const Dims& g, CP3 A, P3 qB, int nsm, cudaStream_t st);
 cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, P8 q, int nsm, cudaStream_t st);

@@ -38,7 +38,10 @@ class Tableau(C.Structure):
 class Params(C.Structure):
     _fields_ = [("gamma_eos", C.c_double), ("cfl", C.c_double), ("newton_tol", C.c_double),
                 ("newton_kmax", C.c_int), ("precision", C.c_int), ("rho_atm", C.c_double), ("p_atm", C.c_double),
-                ("divb", C.c_int), ("kappa_b", C.c_double)]
+                ("divb", C.c_int), ("kappa_b", C.c_double), ("emf", C.c_int), ("rec", C.c_int)]
+
+EMF = {"resistive": 0, "ideal": 1}
+REC = {"mc": 0, "ppm": 1}
 
 DIVB = {"ct": 0, "glm": 1}
 
@@ -153,7 +156,8 @@ class Solver:
     q_Phi; ``kappa`` is the damping kappa_B."""
 
     def __init__(self, ndim, n, lo, hi, bc, gamma, cfl=0.4, tableau=None, device="cuda", newton_tol=0.0,
-                 newton_kmax=0, rho_atm=0.0, p_atm=0.0, precision="fp64", divb="ct", kappa=0.0):
+                 newton_kmax=0, rho_atm=0.0, p_atm=0.0, precision="fp64", divb="ct", kappa=0.0, emf="resistive",
+                 rec="mc"):
         self.L = lib()
         self.grid = make_grid(ndim, n, lo, hi, bc)
         self.tab = ssp2() if tableau is None else tableau
@@ -161,7 +165,8 @@ class Solver:
         self.precision = prec
         self.glm = (DIVB[divb] if isinstance(divb, str) else int(divb)) == DIVB["glm"]
         self.par = Params(float(gamma), float(cfl), float(newton_tol), int(newton_kmax), prec, float(rho_atm),
-                          float(p_atm), DIVB["glm"] if self.glm else DIVB["ct"], float(kappa))
+                          float(p_atm), DIVB["glm"] if self.glm else DIVB["ct"], float(kappa),
+                          EMF[emf] if isinstance(emf, str) else int(emf), REC[rec] if isinstance(rec, str) else int(rec))
         self.device = torch.device(device)
         ng = [2 if d < ndim else 0 for d in range(3)]
         self.N = [self.grid.n[d] + 2 * ng[d] for d in range(3)]

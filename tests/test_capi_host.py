@@ -170,3 +170,41 @@ def test_clean_scratch_bytes(lib):
     g = _grid(2, (1000, 1000, 1))     # coarsest 125 x 125 cells
     b = C.c_size_t()
     assert lib.grmhd_clean_scratch_bytes(C.byref(g), C.byref(b)) == -1
+
+
+@pytest.mark.parametrize("case", ["bad_emf", "ideal_mixed", "ideal_glm", "ideal_fixed"])
+def test_invalid_emf_rejected(lib, case):
+    from paper_2110_03732_gb300.grmhd import Params, Tableau
+    g = _grid()
+    t = Tableau()
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    p = Params(5.0 / 3.0, 0.4, 0.0, 0, 0, 0.0, 0.0, 0, 0.0, 1, 0)
+    if case == "bad_emf":
+        p.emf = 2
+    elif case == "ideal_mixed":
+        p.precision = 1
+    elif case == "ideal_glm":
+        p.divb = 1
+    else:
+        g.bc[1] = 2
+    ctx = C.c_void_p()
+    assert lib.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
+    assert not ctx.value
+
+
+@pytest.mark.parametrize("case", ["bad_rec", "ppm_mixed", "ppm_ideal"])
+def test_invalid_reconstruction_rejected(lib, case):
+    from paper_2110_03732_gb300.grmhd import Params, Tableau
+    g = _grid()
+    t = Tableau()
+    lib.grmhd_tableau_ssp2(C.byref(t))
+    p = Params(5.0 / 3.0, 0.4, 0.0, 0, 0, 0.0, 0.0, 0, 0.0, 0, 1)
+    if case == "bad_rec":
+        p.rec = 5
+    elif case == "ppm_mixed":
+        p.precision = 1
+    else:
+        p.emf = 1
+    ctx = C.c_void_p()
+    assert lib.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
+    assert not ctx.value
