@@ -73,25 +73,28 @@ __device__ __forceinline__ void mg_stencil(const MgLevel& L, const MgArgs& m, co
     }
 }
 
-// red-black Gauss-Seidel half sweep of colour `color`
+// red-black Gauss-Seidel update of cell t if it has colour `color`
+__device__ __forceinline__ void mg_smooth_cell(const MgLevel& L, const MgArgs& m, int color, long long t)
+{
+    int i, j, k;
+    mg_coords(L, t, i, j, k);
+    if (((i + j + k) & 1) != color) return;
+    double nbsum, diag;
+    mg_stencil(L, m, L.phi, i, j, k, nbsum, diag);
+    if (diag > 0.0) L.phi[t] = (nbsum - L.rhs[t]) / diag;
+}
+
 __global__ void __launch_bounds__(256) k_mg_smooth(MgLevel L, MgArgs m, int color)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.cells;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i, j, k;
-        mg_coords(L, t, i, j, k);
-        if (((i + j + k) & 1) != color) continue;
-        double nbsum, diag;
-        mg_stencil(L, m, L.phi, i, j, k, nbsum, diag);
-        if (diag > 0.0) L.phi[t] = (nbsum - L.rhs[t]) / diag;
-    }
+         t += (long long)gridDim.x * blockDim.x)
+        mg_smooth_cell(L, m, color, t);
 }
 
-// coarse rhs = mean of the children's residuals rhs - L Phi; coarse Phi = 0
-__global__ void __launch_bounds__(256) k_mg_restrict(MgLevel F, MgLevel C, MgArgs m)
+// coarse rhs of cell t = mean of its children's residuals rhs - L Phi; coarse Phi = 0
+__device__ __forceinline__ void mg_restrict_cell(const MgLevel& F, const MgLevel& C, const MgArgs& m, long long t)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < C.cells;
-         t += (long long)gridDim.x * blockDim.x) {
+    {
         int I, J, K;
         mg_coords(C, t, I, J, K);
         double sum = 0.0;
@@ -111,13 +114,19 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgLevel F, MgLevel C, MgArg
     }
 }
 
+__global__ void __launch_bounds__(256) k_mg_restrict(MgLevel F, MgLevel C, MgArgs m)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < C.cells;
+         t += (long long)gridDim.x * blockDim.x)
+        mg_restrict_cell(F, C, m, t);
+}
+
 // Phi_fine += linear interpolation of the coarse correction: along each active
 // direction the child takes 3/4 of its parent and 1/4 of the parent's neighbour on its
 // side (the parent itself past a non-periodic boundary)
-__global__ void __launch_bounds__(256) k_mg_prolong(MgLevel F, MgLevel C, MgArgs m)
+__device__ __forceinline__ void mg_prolong_cell(const MgLevel& F, const MgLevel& C, const MgArgs& m, long long t)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < F.cells;
-         t += (long long)gridDim.x * blockDim.x) {
+    {
         int c[3];
         mg_coords(F, t, c[0], c[1], c[2]);
         int P[3], S[3];
@@ -148,6 +157,13 @@ __global__ void __launch_bounds__(256) k_mg_prolong(MgLevel F, MgLevel C, MgArgs
     }
 }
 
+__global__ void __launch_bounds__(256) k_mg_prolong(MgLevel F, MgLevel C, MgArgs m)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < F.cells;
+         t += (long long)gridDim.x * blockDim.x)
+        mg_prolong_cell(F, C, m, t);
+}
+
 // fixed-order block sum (blockDim.x a multiple of 32, at most 1024)
 __device__ __forceinline__ double mg_block_sum(double v, double* sh)
 {
@@ -170,10 +186,9 @@ __device__ __forceinline__ double mg_block_sum(double v, double* sh)
 // coarsest level: conjugate gradients on -lap (symmetric positive semi-definite) with
 // a mean-free right-hand side, in one block.  r, p and q are scratch vectors of the
 // level's size; iterations end at ||r|| <= 1e-15 ||b|| or after max_it.
-__global__ void __launch_bounds__(1024) k_mg_coarse_cg(MgLevel L, MgArgs m, double* __restrict__ res,
-                                                        double* __restrict__ p, double* __restrict__ q, int max_it)
+__device__ __forceinline__ void mg_cg_block(const MgLevel& L, const MgArgs& m, double* __restrict__ res,
+                                            double* __restrict__ p, double* __restrict__ q, int max_it, double* sh)
 {
-    __shared__ double sh[33];
     const long long n = L.cells;
     // b = -(rhs - mean rhs); x = 0, r = b, p = r
     double s = 0.0;
@@ -216,6 +231,43 @@ __global__ void __launch_bounds__(1024) k_mg_coarse_cg(MgLevel L, MgArgs m, doub
         rr = rn;
         for (long long t = threadIdx.x; t < n; t += blockDim.x) p[t] = res[t] + beta * p[t];
         __syncthreads();
+    }
+    __syncthreads();
+}
+
+// the levels first..nlev-1 (each at most kMgBlockCells cells) of one V-cycle in a
+// single block: down-leg smoothing and restriction, conjugate gradients on the
+// coarsest, up-leg interpolation and smoothing -- the same updates in the same order
+// as the one-launch-per-step form, with block barriers in place of launches
+struct MgTail {
+    MgLevel lev[kMgMaxLevels];
+    int first, nlev;
+};
+
+__global__ void __launch_bounds__(1024) k_mg_tail(MgTail T, MgArgs m, double* __restrict__ res,
+                                                   double* __restrict__ p, double* __restrict__ q, int max_it)
+{
+    __shared__ double sh[33];
+    for (int l = T.first; l + 1 < T.nlev; l++) {
+        const MgLevel& L = T.lev[l];
+        for (int s = 0; s < 2; s++)
+            for (int color = 0; color < 2; color++) {
+                for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_smooth_cell(L, m, color, t);
+                __syncthreads();
+            }
+        for (long long t = threadIdx.x; t < T.lev[l + 1].cells; t += blockDim.x) mg_restrict_cell(L, T.lev[l + 1], m, t);
+        __syncthreads();
+    }
+    mg_cg_block(T.lev[T.nlev - 1], m, res, p, q, max_it, sh);
+    for (int l = T.nlev - 2; l >= T.first; l--) {
+        const MgLevel& L = T.lev[l];
+        for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_prolong_cell(L, T.lev[l + 1], m, t);
+        __syncthreads();
+        for (int s = 0; s < 2; s++)
+            for (int color = 0; color < 2; color++) {
+                for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_smooth_cell(L, m, color, t);
+                __syncthreads();
+            }
     }
 }
 
@@ -392,8 +444,14 @@ cudaError_t mg_clean(const Dims& g, const MgPlan& plan0, double* scratch, double
     nl++;
     k_mg_sub_mean<<<mg_grid(F.cells, nsm), 256, 0, st>>>(F, mean);
     const int cg_it = (int)(2 * nc + 20);
+    // levels of at most kMgBlockCells cells run inside one block (k_mg_tail)
+    MgTail tail;
+    for (int l = 0; l < plan.nlev; l++) tail.lev[l] = plan.lev[l];
+    tail.nlev = plan.nlev;
+    tail.first = plan.nlev - 1;
+    while (tail.first > 0 && plan.lev[tail.first - 1].cells <= kMgBlockCells) tail.first--;
     for (int cyc = 0; cyc < cycles; cyc++) {
-        for (int l = 0; l + 1 < plan.nlev; l++) {
+        for (int l = 0; l < tail.first; l++) {
             const MgLevel& L = plan.lev[l];
             const int b = mg_grid(L.cells, nsm);
             for (int s = 0; s < 2; s++) {
@@ -405,13 +463,12 @@ cudaError_t mg_clean(const Dims& g, const MgPlan& plan0, double* scratch, double
             nl++;
             k_mg_restrict<<<mg_grid(plan.lev[l + 1].cells, nsm), 256, 0, st>>>(L, plan.lev[l + 1], m);
         }
-        const MgLevel& Lc = plan.lev[plan.nlev - 1];
-        // coarsest correction from zero; with a single level this is the whole solve,
-        // and further cycles would repeat it
+        // the small levels and the coarsest solve (from zero); with a single level this
+        // is the whole solve, and further cycles would repeat it
         nl++;
-        k_mg_coarse_cg<<<1, 1024, 0, st>>>(Lc, m, cg_r, cg_p, cg_q, cg_it);
+        k_mg_tail<<<1, 1024, 0, st>>>(tail, m, cg_r, cg_p, cg_q, cg_it);
         if (plan.nlev == 1) break;
-        for (int l = plan.nlev - 2; l >= 0; l--) {
+        for (int l = tail.first - 1; l >= 0; l--) {
             const MgLevel& L = plan.lev[l];
             const int b = mg_grid(L.cells, nsm);
             nl++;

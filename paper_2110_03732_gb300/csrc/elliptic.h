@@ -9,6 +9,9 @@ namespace grmhd {
 
 constexpr int kMgMaxLevels = 16;
 constexpr long long kMgMaxCoarse = 4096;   // cells of the coarsest level (one thread block)
+constexpr long long kMgBlockCells = 256;   // levels this small run inside one thread block
+                                           // (one SM does 2 FP64 FMA per cycle: larger
+                                           // levels are faster as grid-wide launches)
 constexpr int kMgParts = 1024;             // partial sums of the mean
 
 // one cell-centred level (no ghosts, x fastest)

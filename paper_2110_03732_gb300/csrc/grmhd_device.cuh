@@ -154,7 +154,7 @@ __device__ __forceinline__ T ppm_iface(T am, T a0, T ap, T app)
     // the MC slope is twice the half slope minmod(D-, (a+ - a-)/4, D+)
     const T s0 = T(2) * minmod3<T>(a0 - am, T(0.25) * (ap - am), ap - a0);
     const T s1 = T(2) * minmod3<T>(ap - a0, T(0.25) * (app - a0), app - ap);
-    return a0 + T(0.5) * (ap - a0) - (s1 - s0) / T(6);
+    return a0 + T(0.5) * (ap - a0) - (s1 - s0) * T(1.0 / 6.0);
 }
 
 template <typename T>
@@ -206,7 +206,7 @@ template <typename T>
 struct FaceStateT {
     T q[8];    // densitised conserved: D, S_1..3, tau, E^1..3
     T f[8];    // flux of the same along the face normal
-    T W;       // Lorentz factor of the state
+    T iW;      // 1/W of the state
 };
 using FaceState = FaceStateT<double>;
 
@@ -222,8 +222,8 @@ __device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi
 #pragma unroll
     for (int i = 0; i < 3; i++) { u[i] = p2 * pr[1 + i]; E[i] = p2 * pr[5 + i]; Bh[i] = p2 * B[i]; }
     const T W = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    s.W = W;
     const T iW = T(1) / W;
+    s.iW = iW;
     const T rhoh = rho + gh * p;
     const T D = rho * W;
     const T U = T(0.5) * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + Bh[0] * Bh[0] + Bh[1] * Bh[1] + Bh[2] * Bh[2]);

@@ -216,8 +216,9 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
         // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
         // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+)
         const double al = (double)alf, c = (double)cs;
-        const double vL1 = al * (double)prL[1 + T1] / (double)sL.W, vR1 = al * (double)prR[1 + T1] / (double)sR.W;
-        const double vL2 = al * (double)prL[1 + T2] / (double)sL.W, vR2 = al * (double)prR[1 + T2] / (double)sR.W;
+        const double iL = (double)sL.iW, iR = (double)sR.iW;
+        const double vL1 = al * (double)prL[1 + T1] * iL, vR1 = al * (double)prR[1 + T1] * iR;
+        const double vL2 = al * (double)prL[1 + T2] * iL, vR2 = al * (double)prR[1 + T2] * iR;
         vbar[0][o] = (c * vR1 + c * vL1) / (c + c);
         vbar[1][o] = (c * vR2 + c * vL2) / (c + c);
     }
@@ -357,8 +358,7 @@ __device__ __forceinline__ double cell_vhat(const Dims& g, const CP8& prim, cons
     const double ps = psi ? psi[ri] : 1.0;
     const double p4 = ps * ps * ps * ps;
     const double u0 = prim.p[1][mi], u1 = prim.p[2][mi], u2 = prim.p[3][mi];
-    const double W = sqrt(1.0 + p4 * (u0 * u0 + u1 * u1 + u2 * u2));
-    return (alp ? alp[ri] : 1.0) * prim.p[1 + j][mi] / W;
+    return (alp ? alp[ri] : 1.0) * prim.p[1 + j][mi] * rsqrt(1.0 + p4 * (u0 * u0 + u1 * u1 + u2 * u2));
 }
 
 // vb[d][k]: transport velocities at the d-faces, component (d + 1 + k) % 3
