@@ -348,8 +348,31 @@ def run_native(args):
     # PPM reconstruction (Sec. 5) and the ideal-limit edge EMF (App. A)
     ppm, _ = time_variant(rec="ppm")
     ppm.update({"dtype": "f64", "scheme": "PPM reconstruction of every face and edge state instead of MC"})
+    ppm_mixed, _ = time_variant(rec="ppm", precision="mixed")
+    ppm_mixed.update({"dtype": "f32 PPM reconstruction/HLL/edge EMF, f64 implicit solve/sources/CT",
+                      "scheme": "PPM on the mixed-precision path"})
     ideal, _ = time_variant(emf="ideal")
     ideal.update({"dtype": "f64", "scheme": "ideal-limit HLL UCT (App. A) instead of the resistive edge EMF"})
+
+    # the 3-D magnetised star on its fixed conformally flat metric (256^3, outflow,
+    # atmosphere): the metric kernels at 17M cells; inputs far exceed L2
+    Ss = grmhd.Solver.from_problem(P.star(256), device=dev)
+    dts = Ss.compute_dt()
+    for _ in range(3):
+        Ss.step(dts)
+    torch.cuda.synchronize()
+    star_ms = []
+    for _ in range(10):
+        e0.record(stream)
+        Ss.step(dts)
+        e1.record(stream)
+        e1.synchronize()
+        star_ms.append(e0.elapsed_time(e1))
+    star_total = max_over_ranks(sum(star_ms) / 1e3, dev)
+    star = {"workload": "star_3d_256^3_fp64 (fixed conformally flat metric, outflow, atmosphere)",
+            "value": ws * Ss.cells * STAGES * 10 / star_total, "unit": UNIT, "ms_per_step": 1e3 * star_total / 10,
+            "steps": 10, "newton_failures": Ss.diagnostics()[2]}
+    del Ss
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -382,7 +405,9 @@ def run_native(args):
         "elliptic_clean": dict(clean, scheme="multigrid V(2,2), staggered projection of q_B, 512^2"),
         "glm": glm,
         "ppm": ppm,
+        "ppm_mixed": ppm_mixed,
         "ideal_emf": ideal,
+        "star": star,
     }
     if not args.no_batched:
         line["batched"] = bench_batched(grmhd, P, dev, args)

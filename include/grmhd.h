@@ -120,8 +120,9 @@ typedef struct {
     int emf;           /* GRMHD_EMF_RESISTIVE (0, default) or GRMHD_EMF_IDEAL (App. A):
                           CT, FP64, no FIXED boundary; not accepted by the batched
                           executor */
-    int rec;           /* GRMHD_REC_MC (0, default) or GRMHD_REC_PPM: FP64, CT with the
-                          resistive EMF or GLM; not accepted by the batched executor */
+    int rec;           /* GRMHD_REC_MC (0, default) or GRMHD_REC_PPM: CT with the resistive
+                          EMF (FP64, or mixed with FP32 reconstruction) or GLM (FP64); not
+                          accepted by the batched executor */
 } grmhd_params;
 
 /* IMEX-SSP2(2,2,2) of Sec. 2.3 (Pareschi & Russo), gamma = 1 - 1/sqrt(2). */

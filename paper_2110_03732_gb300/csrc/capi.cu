@@ -281,7 +281,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         if (c->mixed) {
             FluxOut<float> fo;
             for (int v = 0; v < 8; v++) fo.p[v] = c->F32[d][v];
-            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st);
+            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm);
         } else {
             e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
                             c->ppm);
@@ -293,7 +293,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     for (int k = 0; k < 3; k++) {
         if (!emf_needed(g, k)) continue;
         const int tk = tbegin(c, KIND_EMF, st);
-        if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh32[k], c->nsm, st);
+        if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh32[k], c->nsm, st, c->ppm);
         else if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
         else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
         tend(c, tk, st);
@@ -442,8 +442,8 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
         return fail(GRMHD_ERR_ARG, "emf must be GRMHD_EMF_RESISTIVE or GRMHD_EMF_IDEAL");
     if (par->rec != GRMHD_REC_MC && par->rec != GRMHD_REC_PPM)
         return fail(GRMHD_ERR_ARG, "rec must be GRMHD_REC_MC or GRMHD_REC_PPM");
-    if (par->rec == GRMHD_REC_PPM && (par->precision != GRMHD_PREC_FP64 || par->emf == GRMHD_EMF_IDEAL))
-        return fail(GRMHD_ERR_ARG, "PPM runs in FP64 with the resistive EMF or GLM");
+    if (par->rec == GRMHD_REC_PPM && par->emf == GRMHD_EMF_IDEAL)
+        return fail(GRMHD_ERR_ARG, "PPM takes the resistive EMF or GLM");
     if (par->emf == GRMHD_EMF_IDEAL) {
         if (par->divb != GRMHD_DIVB_CT || par->precision != GRMHD_PREC_FP64)
             return fail(GRMHD_ERR_ARG, "the ideal-limit EMF needs constrained transport in FP64");

@@ -443,7 +443,7 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
 }
 
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st)
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm)
 {
     FluxArgs<float> a;
     a.vbar[0] = a.vbar[1] = nullptr;
@@ -452,7 +452,15 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
     a.psi = psi;
     a.alp = alp;
     a.F = F;
-    flux_dispatch<float>(g, d, psi || alp, grid_for(flux_work(g, d), 128, nsm), st, a);
+    const int b = grid_for(flux_work(g, d), 128, nsm);
+    if (ppm) {
+        const bool m = psi || alp;
+        if (d == 0) m ? k_flux<0, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<0, false, float, true><<<b, 128, 0, st>>>(g, a);
+        else if (d == 1) m ? k_flux<1, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<1, false, float, true><<<b, 128, 0, st>>>(g, a);
+        else m ? k_flux<2, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, float, true><<<b, 128, 0, st>>>(g, a);
+        return cudaGetLastError();
+    }
+    flux_dispatch<float>(g, d, psi || alp, b, st, a);
     return cudaGetLastError();
 }
 
@@ -498,7 +506,7 @@ cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const doubl
 }
 
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                         const double* alp, float* Eh, int nsm, cudaStream_t st)
+                         const double* alp, float* Eh, int nsm, cudaStream_t st, bool ppm)
 {
     EmfArgs<float> a;
     a.prim = prim;
@@ -506,7 +514,15 @@ cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf
     a.psi = psi;
     a.alp = alp;
     a.Eh = Eh;
-    emf_dispatch<float>(g, c, psi || alp, grid_for(emf_work(g, c), 128, nsm), st, a);
+    const int b = grid_for(emf_work(g, c), 128, nsm);
+    if (ppm) {
+        const bool m = psi || alp;
+        if (c == 0) m ? k_emf<0, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<0, false, float, true><<<b, 128, 0, st>>>(g, a);
+        else if (c == 1) m ? k_emf<1, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<1, false, float, true><<<b, 128, 0, st>>>(g, a);
+        else m ? k_emf<2, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, float, true><<<b, 128, 0, st>>>(g, a);
+        return cudaGetLastError();
+    }
+    emf_dispatch<float>(g, c, psi || alp, b, st, a);
     return cudaGetLastError();
 }
 

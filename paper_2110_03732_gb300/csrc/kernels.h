@@ -78,9 +78,9 @@ struct UpdateArgs {
 
 cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st);
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                         const double* alp, float* Eh, int nsm, cudaStream_t st);
+                         const double* alp, float* Eh, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
 // ppm: PPM reconstruction instead of MC (FP64 only)
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
