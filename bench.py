@@ -306,7 +306,7 @@ def run_native(args):
         S.clean_divb(cyc)
         torch.cuda.synchronize()
         cl_ms = []
-        for _ in range(20):
+        for _ in range(min(20, max(3, args.steps))):
             flush.zero_()
             e0.record(stream)
             S.clean_divb(cyc)

@@ -145,6 +145,10 @@ __device__ __forceinline__ void mc_face(T a0, T a1, T a2, T a3, T& L, T& R)
     R = a2 - minmod3<T>(d0, T(0.25) * (a3 - a1), dp);
 }
 
+// 1/sqrt(x) through CUDA's reciprocal square root, in the precision of x
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+
 // PPM (Colella & Woodward 1984: interface interpolation with the MC slope and the
 // monotonicity limits of the parabola, no steepening or flattening).  a[0..5] are the
 // cells c-3..c+2; L is the right edge of cell c-1, R the left edge of cell c.
@@ -221,8 +225,10 @@ __device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi
     T u[3], E[3], Bh[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) { u[i] = p2 * pr[1 + i]; E[i] = p2 * pr[5 + i]; Bh[i] = p2 * B[i]; }
-    const T W = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const T iW = T(1) / W;
+    // W and 1/W from one reciprocal square root (no division)
+    const T x = T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T iW = rsqrt_t(x);
+    const T W = x * iW;
     s.iW = iW;
     const T rhoh = rho + gh * p;
     const T D = rho * W;

@@ -486,8 +486,9 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
     double u[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) u[i] = prim[1 + i][o];
-    const double W = sqrt(1.0 + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-    const double iW = 1.0 / W;
+    const double xw = 1.0 + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double iW = rsqrt(xw);
+    const double W = xw * iW;
     // Gauss law: sqrt(gamma) rho_e = div q_E by central differences
     double divqE = 0.0;
 #pragma unroll
