@@ -489,8 +489,8 @@ def bench_serving(dev, args):
 # stand (profiles/ot512_fp64_kernels.md).  The flux and EMF figures are per launch
 # (one direction / one component; the EMF value is the mean of its three launches).
 # TRAFFIC: dram read + write bytes per launch from the same capture.
-FP64_FLOPS_PER_CELL = {"implicit": 575.6, "flux": 355.7, "emf": 70.9, "update": 160.0}
-TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 23.3e6, "emf": 6.4e6, "update": 109.3e6}
+FP64_FLOPS_PER_CELL = {"implicit": 575.6, "flux": 327.6, "emf": 70.9, "update": 143.0}
+TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 23.3e6, "emf": 6.4e6, "update": 109.2e6}
 
 
 def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):
