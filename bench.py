@@ -52,7 +52,52 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--n", type=int, default=N_OT, help=argparse.SUPPRESS)
+    ap.add_argument("--case", choices=["star", "clean"], default=None,
+                    help="run one secondary workload alone on a small case (for profiling) and print its "
+                         "timings: the 3-D star with --case-n cells a side, or the multigrid cleaning of the "
+                         "--case-n^2 Orszag-Tang problem")
+    ap.add_argument("--case-n", type=int, default=96)
     return ap.parse_args()
+
+
+def run_case(args, grmhd, P, dev):
+    """One secondary workload alone, `--warmup` untimed then `--steps` timed
+    repetitions (CUDA events on the current stream)."""
+    import torch
+    n = args.case_n
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if args.case == "star":
+        S = grmhd.Solver.from_problem(P.star(n), device=dev)
+        dt = S.compute_dt()
+        for _ in range(args.warmup):
+            S.step(dt)
+        torch.cuda.synchronize()
+        S.set_timing(True)
+        S.kernel_times()
+        e0.record()
+        for _ in range(args.steps):
+            S.step(dt)
+        e1.record()
+        e1.synchronize()
+        kt = S.kernel_times()
+        return {"case": f"star_3d_{n}^3_fp64", "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                "us_per_launch": {k: 1e3 * v[0] / max(v[1], 1) for k, v in kt.items()},
+                "newton_failures": S.diagnostics()[2]}
+    S = grmhd.Solver.from_problem(P.orszag_tang(n), device=dev)
+    S.step(S.compute_dt())
+    out = {"case": f"multigrid_clean_orszag_tang_{n}^2"}
+    for cyc in (1, 4):
+        for _ in range(args.warmup):
+            S.clean_divb(cyc)
+        e0.record()
+        for _ in range(args.steps):
+            S.clean_divb(cyc)
+        e1.record()
+        e1.synchronize()
+        out[f"{cyc}_cycles_ms"] = e0.elapsed_time(e1) / args.steps
+    out["divb_max_after"] = S.diagnostics()[0][2]
+    return out
 
 
 def dist_env():
@@ -233,6 +278,9 @@ def run_native(args):
     from paper_2110_03732_gb300 import grmhd
     from paper_2110_03732_gb300 import problems as P
     _b.build()
+    if args.case:
+        print(json.dumps(run_case(args, grmhd, P, dev)), flush=True)
+        return
 
     n = args.n
     pr = P.orszag_tang(n)

@@ -98,7 +98,8 @@ typedef struct {
     double gamma_eos;  /* ideal-gas Gamma (> 1) */
     double cfl;        /* Courant number for grmhd_compute_dt */
     double newton_tol; /* Newton residual tolerance, relative to the momentum terms of
-                          f_i (Sec. 2.4); 0 -> 1e-13 */
+                          f_i (Sec. 2.4); 0 -> 1e-13 (FP64) or 1e-10
+                          (mixed, whose FP32 fluxes err near 1e-7) */
     int newton_kmax;   /* Newton iteration cap; 0 -> 50 */
     int precision;     /* GRMHD_PREC_FP64: every step in FP64.  GRMHD_PREC_MIXED: MC
                           reconstruction, HLL fluxes and the edge EMF in FP32; the

@@ -46,47 +46,77 @@ struct MgArgs {
     int act[3];
 };
 
+// cell (i, j, k) of level item t (levels hold fewer than 2^31 cells: mg_plan)
 __device__ __forceinline__ void mg_coords(const MgLevel& L, long long t, int& i, int& j, int& k)
 {
-    i = (int)(t % L.n[0]);
-    j = (int)((t / L.n[0]) % L.n[1]);
-    k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    const int u = (int)t;
+    const int r = u / L.n[0];
+    i = u - r * L.n[0];
+    j = r % L.n[1];
+    k = r / L.n[1];
 }
 
-// (L Phi)_c split as sum_nb Phi_nb / h^2 - diag Phi_c; returns the neighbour sum and
-// the diagonal
+// (L Phi)_c split as sum_nb Phi_nb / h^2 - diag Phi_c; returns the neighbour sum, the
+// diagonal and the number of neighbours missing past non-periodic boundaries (0: the
+// full stencil, whose diagonal is the level's dfull)
 __device__ __forceinline__ void mg_stencil(const MgLevel& L, const MgArgs& m, const double* __restrict__ phi, int i,
-                                           int j, int k, double& nbsum, double& diag)
+                                           int j, int k, double& nbsum, double& diag, int& miss)
 {
     nbsum = 0.0;
-    diag = 0.0;
+    miss = 0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (!m.act[d]) continue;
+        const long long lo = mg_nb(L, m.bc, i, j, k, d, -1), hi = mg_nb(L, m.bc, i, j, k, d, 1);
+        double s2;
+        if (lo >= 0 && hi >= 0) {
+            s2 = phi[lo] + phi[hi];
+        } else {
+            s2 = lo >= 0 ? phi[lo] : (hi >= 0 ? phi[hi] : 0.0);
+            miss += (lo < 0) + (hi < 0);
+        }
+        nbsum += s2 * L.ih2[d];
+    }
+    diag = L.dfull;
+    if (miss) {
+        diag = 0.0;
 #pragma unroll
-        for (int s = -1; s <= 1; s += 2) {
-            const long long nb = mg_nb(L, m.bc, i, j, k, d, s);
-            if (nb < 0) continue;
-            nbsum += phi[nb] * L.ih2[d];
-            diag += L.ih2[d];
+        for (int d = 0; d < 3; d++) {
+            if (!m.act[d]) continue;
+            if (mg_nb(L, m.bc, i, j, k, d, -1) >= 0) diag += L.ih2[d];
+            if (mg_nb(L, m.bc, i, j, k, d, 1) >= 0) diag += L.ih2[d];
         }
     }
 }
 
-// red-black Gauss-Seidel update of cell t if it has colour `color`
+// cells of colour `color` ((i + j + k) & 1) of a level, enumerated x fastest: item t
+// is the u-th such cell of row (j, k), u = t mod ceil(n_x / 2)
+__device__ __forceinline__ long long mg_half_items(const MgLevel& L)
+{
+    return (long long)((L.n[0] + 1) >> 1) * L.n[1] * L.n[2];
+}
+
+// red-black Gauss-Seidel update of item t of colour `color`.  The full stencil's
+// diagonal reciprocal is the level's; a boundary cell (fewer neighbours) divides.
 __device__ __forceinline__ void mg_smooth_cell(const MgLevel& L, const MgArgs& m, int color, long long t)
 {
-    int i, j, k;
-    mg_coords(L, t, i, j, k);
-    if (((i + j + k) & 1) != color) return;
+    const int h0 = (L.n[0] + 1) >> 1;
+    const int u = (int)t, row = u / h0;
+    const int j = row % L.n[1], k = row / L.n[1];
+    const int i = 2 * (u - row * h0) + ((color + j + k) & 1);
+    if (i >= L.n[0]) return;
+    const int c = i + L.n[0] * row;
     double nbsum, diag;
-    mg_stencil(L, m, L.phi, i, j, k, nbsum, diag);
-    if (diag > 0.0) L.phi[t] = (nbsum - L.rhs[t]) / diag;
+    int miss;
+    mg_stencil(L, m, L.phi, i, j, k, nbsum, diag, miss);
+    if (!miss) L.phi[c] = (nbsum - L.rhs[c]) * L.idiag;
+    else if (diag > 0.0) L.phi[c] = (nbsum - L.rhs[c]) / diag;
 }
 
 __global__ void __launch_bounds__(256) k_mg_smooth(MgLevel L, MgArgs m, int color)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < L.cells;
+    const long long items = mg_half_items(L);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < items;
          t += (long long)gridDim.x * blockDim.x)
         mg_smooth_cell(L, m, color, t);
 }
@@ -98,18 +128,18 @@ __device__ __forceinline__ void mg_restrict_cell(const MgLevel& F, const MgLevel
         int I, J, K;
         mg_coords(C, t, I, J, K);
         double sum = 0.0;
-        int cnt = 0;
         for (int dk = 0; dk <= m.act[2]; dk++)
             for (int dj = 0; dj <= m.act[1]; dj++)
                 for (int di = 0; di <= m.act[0]; di++) {
                     const int i = 2 * I * m.act[0] + di, j = 2 * J * m.act[1] + dj, k = 2 * K * m.act[2] + dk;
                     const long long f = i + (long long)F.n[0] * (j + (long long)F.n[1] * k);
                     double nbsum, diag;
-                    mg_stencil(F, m, F.phi, i, j, k, nbsum, diag);
+                    int miss;
+                    mg_stencil(F, m, F.phi, i, j, k, nbsum, diag, miss);
                     sum += F.rhs[f] - (nbsum - diag * F.phi[f]);
-                    cnt++;
                 }
-        C.rhs[t] = sum / cnt;
+        // 1 / (number of children), a power of two
+        C.rhs[t] = sum * ((m.act[0] ? 0.5 : 1.0) * (m.act[1] ? 0.5 : 1.0) * (m.act[2] ? 0.5 : 1.0));
         C.phi[t] = 0.0;
     }
 }
@@ -211,7 +241,8 @@ __device__ __forceinline__ void mg_cg_block(const MgLevel& L, const MgArgs& m, d
             int i, j, k;
             mg_coords(L, t, i, j, k);
             double nbsum, diag;
-            mg_stencil(L, m, p, i, j, k, nbsum, diag);
+            int miss;
+            mg_stencil(L, m, p, i, j, k, nbsum, diag, miss);
             const double v = diag * p[t] - nbsum;
             q[t] = v;
             pq += p[t] * v;
@@ -238,36 +269,75 @@ __device__ __forceinline__ void mg_cg_block(const MgLevel& L, const MgArgs& m, d
 // the levels first..nlev-1 (each at most kMgBlockCells cells) of one V-cycle in a
 // single block: down-leg smoothing and restriction, conjugate gradients on the
 // coarsest, up-leg interpolation and smoothing -- the same updates in the same order
-// as the one-launch-per-step form, with block barriers in place of launches
+// as the one-launch-per-step form, with block barriers in place of launches.  With
+// smem set the block moves these levels and the CG vectors into dynamic shared memory
+// (level `first` in from its global arrays at the start, its Phi back at the end).
 struct MgTail {
     MgLevel lev[kMgMaxLevels];
+    long long soff[kMgMaxLevels];   // with smem: offset (doubles) of each tail level's
+                                    // Phi (its rhs follows) in the shared block
+    long long scg;                  // with smem: offset of the CG vectors r, p, q
     int first, nlev;
+    int smem;
 };
+
+// level l of the tail with its arrays where the block keeps them (a register copy: the
+// kernel's parameter block itself is never written, which would move it to local memory)
+__device__ __forceinline__ MgLevel tail_level(const MgTail& T, int l, double* sm)
+{
+    MgLevel L = T.lev[l];
+    if (T.smem) {
+        L.phi = sm + T.soff[l];
+        L.rhs = L.phi + L.cells;
+    }
+    return L;
+}
 
 __global__ void __launch_bounds__(1024) k_mg_tail(MgTail T, MgArgs m, double* __restrict__ res,
                                                    double* __restrict__ p, double* __restrict__ q, int max_it)
 {
+    extern __shared__ double tail_sm[];
     __shared__ double sh[33];
-    for (int l = T.first; l + 1 < T.nlev; l++) {
-        const MgLevel& L = T.lev[l];
-        for (int s = 0; s < 2; s++)
-            for (int color = 0; color < 2; color++) {
-                for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_smooth_cell(L, m, color, t);
-                __syncthreads();
-            }
-        for (long long t = threadIdx.x; t < T.lev[l + 1].cells; t += blockDim.x) mg_restrict_cell(L, T.lev[l + 1], m, t);
+    if (T.smem) {
+        const MgLevel G = T.lev[T.first];
+        const MgLevel L = tail_level(T, T.first, tail_sm);
+        for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) {
+            L.phi[t] = G.phi[t];
+            L.rhs[t] = G.rhs[t];
+        }
+        const long long nc = T.lev[T.nlev - 1].cells;
+        res = tail_sm + T.scg;
+        p = res + nc;
+        q = p + nc;
         __syncthreads();
     }
-    mg_cg_block(T.lev[T.nlev - 1], m, res, p, q, max_it, sh);
-    for (int l = T.nlev - 2; l >= T.first; l--) {
-        const MgLevel& L = T.lev[l];
-        for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_prolong_cell(L, T.lev[l + 1], m, t);
-        __syncthreads();
+    for (int l = T.first; l + 1 < T.nlev; l++) {
+        const MgLevel L = tail_level(T, l, tail_sm), C = tail_level(T, l + 1, tail_sm);
+        const long long items = mg_half_items(L);
         for (int s = 0; s < 2; s++)
             for (int color = 0; color < 2; color++) {
-                for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_smooth_cell(L, m, color, t);
+                for (long long t = threadIdx.x; t < items; t += blockDim.x) mg_smooth_cell(L, m, color, t);
                 __syncthreads();
             }
+        for (long long t = threadIdx.x; t < C.cells; t += blockDim.x) mg_restrict_cell(L, C, m, t);
+        __syncthreads();
+    }
+    mg_cg_block(tail_level(T, T.nlev - 1, tail_sm), m, res, p, q, max_it, sh);
+    for (int l = T.nlev - 2; l >= T.first; l--) {
+        const MgLevel L = tail_level(T, l, tail_sm), C = tail_level(T, l + 1, tail_sm);
+        for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) mg_prolong_cell(L, C, m, t);
+        __syncthreads();
+        const long long items = mg_half_items(L);
+        for (int s = 0; s < 2; s++)
+            for (int color = 0; color < 2; color++) {
+                for (long long t = threadIdx.x; t < items; t += blockDim.x) mg_smooth_cell(L, m, color, t);
+                __syncthreads();
+            }
+    }
+    if (T.smem) {
+        const MgLevel G = T.lev[T.first];
+        const MgLevel L = tail_level(T, T.first, tail_sm);
+        for (long long t = threadIdx.x; t < L.cells; t += blockDim.x) G.phi[t] = L.phi[t];
     }
 }
 
@@ -356,6 +426,12 @@ __global__ void __launch_bounds__(256) k_mg_correct(Dims g, P3 bq, int cc, MgLev
     }
 }
 
+// items of one colour of a level (mg_half_items on the host)
+long long half_items(const MgLevel& L)
+{
+    return (long long)((L.n[0] + 1) / 2) * L.n[1] * L.n[2];
+}
+
 int mg_grid(long long work, int nsm)
 {
     long long b = (work + 255) / 256;
@@ -383,6 +459,15 @@ int mg_plan(const Dims& g, MgPlan* plan)
             L.ih2[d] = g.act[d] ? 1.0 / (h * h) : 0.0;
             cells *= n[d];
         }
+        // the device's summation order: per active direction, its two neighbours
+        L.dfull = 0.0;
+        for (int d = 0; d < 3; d++)
+            if (g.act[d]) {
+                L.dfull += L.ih2[d];
+                L.dfull += L.ih2[d];
+            }
+        L.idiag = L.dfull > 0.0 ? 1.0 / L.dfull : 0.0;
+        if (cells >= (1LL << 31)) return -3;
         L.cells = cells;
         L.offset = total;
         total += cells;
@@ -450,15 +535,24 @@ cudaError_t mg_clean(const Dims& g, const MgPlan& plan0, double* scratch, double
     tail.nlev = plan.nlev;
     tail.first = plan.nlev - 1;
     while (tail.first > 0 && plan.lev[tail.first - 1].cells <= kMgBlockCells) tail.first--;
+    long long soff = 0;
+    for (int l = tail.first; l < plan.nlev; l++) {
+        tail.soff[l] = soff;
+        soff += 2 * plan.lev[l].cells;
+    }
+    tail.scg = soff;
+    const size_t tail_bytes = sizeof(double) * (size_t)(soff + 3 * nc);
+    tail.smem = tail_bytes <= kMgTailSmem ? 1 : 0;
+    const size_t tail_dyn = tail.smem ? tail_bytes : 0;
     for (int cyc = 0; cyc < cycles; cyc++) {
         for (int l = 0; l < tail.first; l++) {
             const MgLevel& L = plan.lev[l];
-            const int b = mg_grid(L.cells, nsm);
+            const int bs = mg_grid(half_items(L), nsm);
             for (int s = 0; s < 2; s++) {
                 nl++;
-                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 0);
+                k_mg_smooth<<<bs, 256, 0, st>>>(L, m, 0);
                 nl++;
-                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 1);
+                k_mg_smooth<<<bs, 256, 0, st>>>(L, m, 1);
             }
             nl++;
             k_mg_restrict<<<mg_grid(plan.lev[l + 1].cells, nsm), 256, 0, st>>>(L, plan.lev[l + 1], m);
@@ -466,18 +560,18 @@ cudaError_t mg_clean(const Dims& g, const MgPlan& plan0, double* scratch, double
         // the small levels and the coarsest solve (from zero); with a single level this
         // is the whole solve, and further cycles would repeat it
         nl++;
-        k_mg_tail<<<1, 1024, 0, st>>>(tail, m, cg_r, cg_p, cg_q, cg_it);
+        k_mg_tail<<<1, 1024, tail_dyn, st>>>(tail, m, cg_r, cg_p, cg_q, cg_it);
         if (plan.nlev == 1) break;
         for (int l = tail.first - 1; l >= 0; l--) {
             const MgLevel& L = plan.lev[l];
-            const int b = mg_grid(L.cells, nsm);
+            const int b = mg_grid(L.cells, nsm), bs = mg_grid(half_items(L), nsm);
             nl++;
             k_mg_prolong<<<b, 256, 0, st>>>(L, plan.lev[l + 1], m);
             for (int s = 0; s < 2; s++) {
                 nl++;
-                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 0);
+                k_mg_smooth<<<bs, 256, 0, st>>>(L, m, 0);
                 nl++;
-                k_mg_smooth<<<b, 256, 0, st>>>(L, m, 1);
+                k_mg_smooth<<<bs, 256, 0, st>>>(L, m, 1);
             }
         }
     }

@@ -9,15 +9,19 @@ namespace grmhd {
 
 constexpr int kMgMaxLevels = 16;
 constexpr long long kMgMaxCoarse = 4096;   // cells of the coarsest level (one thread block)
-constexpr long long kMgBlockCells = 256;   // levels this small run inside one thread block
+constexpr long long kMgBlockCells = 1024;  // levels this small run inside one thread block
                                            // (one SM does 2 FP64 FMA per cycle: larger
                                            // levels are faster as grid-wide launches)
+constexpr size_t kMgTailSmem = 48 * 1024;  // the block keeps its levels in shared memory
+                                           // when they fit in this many bytes
 constexpr int kMgParts = 1024;             // partial sums of the mean
 
 // one cell-centred level (no ghosts, x fastest)
 struct MgLevel {
     int n[3];
     double ih2[3];        // 1/h^2 per active direction, 0 otherwise
+    double dfull, idiag;  // diagonal of the full (2 ndim + 1)-point stencil (summed in
+                          // the device's order) and its reciprocal
     long long cells;
     long long offset;     // of this level's arrays in the phi / rhs blocks
     double* phi;
@@ -31,7 +35,7 @@ struct MgPlan {
 };
 
 // levels for grid g: 0 on success, -1 too many levels, -2 coarsest level above
-// kMgMaxCoarse cells
+// kMgMaxCoarse cells, -3 a grid of 2^31 cells or more
 int mg_plan(const Dims& g, MgPlan* plan);
 size_t mg_scratch_bytes(const MgPlan& plan);
 // clean the three q_B arrays bq in place (staggered faces, or cell-centred if cc) with

@@ -87,12 +87,13 @@ __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& 
     FaceState sL, sR;
     face_state<double>(prL, BL, D, psf, alf, g.gh, sL);
     face_state<double>(prR, BR, D, psf, alf, g.gh, sR);
-    // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity)
+    // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity); with equal
+    // speeds (c f_L + c f_R - c^2 (q_R - q_L)) / 2c = (f_L + f_R - c (q_R - q_L)) / 2
     const double cs = alf / pf2;
     const long long o = lin(g, c[0], c[1], c[2]);
 #pragma unroll
     for (int v = 0; v < 8; v++)
-        a.F[v][o] = (cs * sL.f[v] + cs * sR.f[v] - cs * cs * (sR.q[v] - sL.q[v])) / (cs + cs);
+        a.F[v][o] = (sL.f[v] + sR.f[v] - cs * (sR.q[v] - sL.q[v])) * 0.5;
     // q_B^j = psi^6 B^j with (f_B^j)^D = eta^{jDk} alpha psi^4 E^k: 0, -alpha psi^4 E^D2,
     // +alpha psi^4 E^D1 for j = D, D1, D2; q_Phi = psi^6 Phi with (f_Phi)^D = alpha q_B^D
     const double ap4 = alf * pf4;
@@ -115,7 +116,7 @@ __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& 
     fR[3] = alf * qR[D];
 #pragma unroll
     for (int v = 0; v < 4; v++)
-        a.F[8 + v][o] = (cs * fL[v] + cs * fR[v] - cs * cs * (qR[v] - qL[v])) / (cs + cs);
+        a.F[8 + v][o] = (fL[v] + fR[v] - cs * (qR[v] - qL[v])) * 0.5;
 }
 
 template <int D, bool M, bool P = false>
@@ -182,8 +183,9 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
         double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
         sp = sp * sp;
         sm = sm * sm;
-        const double php = a.qphi[cell_at(g, cp)] / (sp * sp * sp);
-        const double phm = a.qphi[cell_at(g, cm)] / (sm * sm * sm);
+        const double sp3 = sp * sp * sp, sm3 = sm * sm * sm, r = 1.0 / (sp3 * sm3);
+        const double php = a.qphi[cell_at(g, cp)] * (sm3 * r);   // q_Phi / psi^6
+        const double phm = a.qphi[cell_at(g, cm)] * (sp3 * r);
         Lc[8 + d] -= al * p2 * ((php - phm) * (0.5 * g.idx[d]));
         if (alp) Lc[11] += a.qB[d][o] * ((alp[o + g.st[d]] - alp[o - g.st[d]]) * (0.5 * g.idx[d]));
     }

@@ -181,7 +181,15 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
             mc_face<T>(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3 < NS ? 3 : 0]], prL[v], prR[v]);
         }
     }
-    // transverse cell-centred B (primitive = q_B / psi^6 at the cell)
+    // transverse cell-centred B (primitive = q_B / psi^6 at the cell); one reciprocal
+    // of psi^6 per stencil cell serves both components
+    T ip6[NS];
+#pragma unroll
+    for (int s = 0; s < NS; s++) {
+        const T ps = psi ? (T)psi[ri[s]] : T(1);
+        const T p2 = ps * ps;
+        ip6[s] = T(1) / (p2 * p2 * p2);
+    }
 #pragma unroll
     for (int tt = 0; tt < 2; tt++) {
         const int e = tt == 0 ? T1 : T2;
@@ -190,43 +198,93 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
         for (int s = 0; s < NS; s++) {
             int cs[3] = {c[0], c[1], c[2]};
             cs[D] = cd[s];
-            const T ps = psi ? (T)psi[ri[s]] : T(1);
-            const T p2 = ps * ps;
-            b[s] = (T)cell_qB_in(g, prim, bf, e, cs, mi[s]) / (p2 * p2 * p2);
+            b[s] = (T)cell_qB_in(g, prim, bf, e, cs, mi[s]) * ip6[s];
         }
         if (P) ppm_face<T>(b, BL[e], BR[e]);
         else mc_face<T>(b[0], b[1], b[2], b[NS - 1], BL[e], BR[e]);
     }
     const T psf = psi ? (T)(0.5 * (psi[ri[OFF - 1]] + psi[ri[OFF]])) : T(1);
     const T alf = alp ? (T)(0.5 * (alp[ri[OFF - 1]] + alp[ri[OFF]])) : T(1);
-    const T pf2 = psf * psf;
-    const T bn = (T)bf.p[D][face_at(g, D, c)] / (pf2 * pf2 * pf2);
-    BL[D] = bn;
-    BR[D] = bn;
+    const T pf2 = psf * psf, ipf2 = T(1) / pf2;
+    // orthonormal-frame states at the face: u_hat = psi^2 u, E_hat = psi^2 E,
+    // B_hat = psi^2 B (normal: q_B / psi^4)
+    BL[D] = BR[D] = (T)bf.p[D][face_at(g, D, c)] * (ipf2 * ipf2);
+    if (psi) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            prL[1 + i] *= pf2;
+            prR[1 + i] *= pf2;
+            prL[5 + i] *= pf2;
+            prR[5 + i] *= pf2;
+            if (i != D) {
+                BL[i] *= pf2;
+                BR[i] *= pf2;
+            }
+        }
+    }
+    // HLL with c+ = c- = c = alpha sqrt(gamma^DD) = alpha / psi^2 (Sec. 2.5, maximal
+    // diffusivity): (c f_L + c f_R - c^2 (q_R - q_L)) / 2c = (f_L + f_R - c (q_R - q_L)) / 2.
+    // Each densitised q_v is psi^k_v times its flat-space (psi = alpha = 1) value and its
+    // flux alpha psi^(k_v - 2) times, k = 6, 8, 8, 8, 6, 4, 4, 4: the HLL flux is then
+    // alpha psi^(k_v - 2) times the flat-space HLL flux (unit speed) of the
+    // orthonormal states.
     FaceStateT<T> sL, sR;
-    face_state<T>(prL, BL, D, psf, alf, (T)g.gh, sL);
-    face_state<T>(prR, BR, D, psf, alf, (T)g.gh, sR);
-    // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity)
-    const T cs = alf / pf2;
+    face_state<T>(prL, BL, D, T(1), T(1), (T)g.gh, sL);
+    face_state<T>(prR, BR, D, T(1), T(1), (T)g.gh, sR);
+    const T h2 = T(0.5) * alf * pf2, h4 = h2 * pf2, h6 = h4 * pf2;
     const long long o = lin(g, c[0], c[1], c[2]);
 #pragma unroll
-    for (int v = 0; v < 8; v++)
-        F.p[v][o] = (cs * sL.f[v] + cs * sR.f[v] - cs * cs * (sR.q[v] - sL.q[v])) / (cs + cs);
+    for (int v = 0; v < 8; v++) {
+        const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
+        F.p[v][o] = (sL.f[v] + sR.f[v] - (sR.q[v] - sL.q[v])) * hv;
+    }
     if (vbar && vbar[0]) {
         // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
-        // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+)
-        const double al = (double)alf, c = (double)cs;
+        // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+), their mean for c+ = c-;
+        // v^j = u_hat^j / (psi^2 W)
+        const double al = (double)(alf * ipf2);
         const double iL = (double)sL.iW, iR = (double)sR.iW;
         const double vL1 = al * (double)prL[1 + T1] * iL, vR1 = al * (double)prR[1 + T1] * iR;
         const double vL2 = al * (double)prL[1 + T2] * iL, vR2 = al * (double)prR[1 + T2] * iR;
-        vbar[0][o] = (c * vR1 + c * vL1) / (c + c);
-        vbar[1][o] = (c * vR2 + c * vL2) / (c + c);
+        vbar[0][o] = (vR1 + vL1) * 0.5;
+        vbar[1][o] = (vR2 + vL2) * 0.5;
     }
 }
 
 // ---------------------------------------------------------------------------
 // upwind constrained transport (Sec. 3.2): item t = C-edge t
 // ---------------------------------------------------------------------------
+
+// Face speeds at a C-edge (Sec. 2.5: c = alpha sqrt(gamma^dd) = alpha / psi^2 at a face,
+// whose alpha and psi are the means of the two cells beside it): cab[0] the larger of
+// the (up to two) A-faces touching the edge, cab[1] likewise for the B-faces; 1 in an
+// inactive direction.  The larger of a0/q0 and a1/q1 is picked by comparing a0 q1 with
+// a1 q0, and both quotients come from one reciprocal.
+__device__ __forceinline__ void edge_speeds(const double* __restrict__ psi, const double* __restrict__ alp,
+                                            long long i0, bool aa, bool ba, long long sA, long long sB,
+                                            double* cab)
+{
+    double num[2] = {1.0, 1.0}, den[2] = {1.0, 1.0};
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const bool act = k == 0 ? aa : ba, oth = k == 0 ? ba : aa;
+        if (!act) continue;
+        const long long sn = k == 0 ? sA : sB, so = k == 0 ? sB : sA;
+        for (int tt = 0; tt < (oth ? 2 : 1); tt++) {
+            const long long cf = i0 - tt * so, cfm = cf - sn;
+            const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
+            const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
+            const double q = psf * psf;
+            if (tt == 0 || alf * den[k] > num[k] * q) {
+                num[k] = alf;
+                den[k] = q;
+            }
+        }
+    }
+    const double r = 1.0 / (den[0] * den[1]);
+    cab[0] = num[0] * den[1] * r;
+    cab[1] = num[1] * den[0] * r;
+}
 
 // P: PPM reconstruction (six cells or faces per pass) instead of MC (four)
 template <int C, bool M, typename T, bool P = false>
@@ -310,39 +368,25 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     const long long sA = aa ? g.st[A] : 0, sB = ba ? g.st[B] : 0;
     T ale = T(1), ca = T(1), cb = T(1);
     if (alp || psi) {
-        int nce = 1;
-        double sum = alp ? alp[i0] : 1.0;
-        if (aa) { sum += alp ? alp[i0 - sA] : 1.0; nce++; }
+        // mean of the 1, 2 or 4 cells around the edge
+        double sum = alp ? alp[i0] : 1.0, w = 1.0;
+        if (aa) { sum += alp ? alp[i0 - sA] : 1.0; w = 0.5; }
         if (ba) {
-            sum += alp ? alp[i0 - sB] : 1.0; nce++;
-            if (aa) { sum += alp ? alp[i0 - sA - sB] : 1.0; nce++; }
+            sum += alp ? alp[i0 - sB] : 1.0;
+            if (aa) sum += alp ? alp[i0 - sA - sB] : 1.0;
+            w *= 0.5;
         }
-        ale = (T)(sum / nce);
-        if (aa) {
-            double cmax = 0.0;
-            for (int tt = 0; tt < (ba ? 2 : 1); tt++) {
-                const long long cf = i0 - tt * sB, cfm = cf - sA;
-                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
-                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-                cmax = fmax(cmax, alf / (psf * psf));
-            }
-            ca = (T)cmax;
-        }
-        if (ba) {
-            double cmax = 0.0;
-            for (int tt = 0; tt < (aa ? 2 : 1); tt++) {
-                const long long cf = i0 - tt * sA, cfm = cf - sB;
-                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
-                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-                cmax = fmax(cmax, alf / (psf * psf));
-            }
-            cb = (T)cmax;
-        }
+        ale = (T)(sum * w);
+        double cab[2];
+        edge_speeds(psi, alp, i0, aa, ba, sA, sB, cab);
+        ca = (T)cab[0];
+        cb = (T)cab[1];
     }
-    // steps (v)-(vii): hat{E}^{XY} = alpha E_C^{XY}; Londrillo & Del Zanna (2004)
+    // steps (v)-(vii): hat{E}^{XY} = alpha E_C^{XY}; Londrillo & Del Zanna (2004) with
+    // c+ = c- in each direction, where the four-state weights are all 1/4 and the
+    // diffusive coefficients c^2/2c are c/2
     const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
-    Eh[i0] = (ca * cb * hLL + ca * cb * hLR + ca * cb * hRL + ca * cb * hRR) / ((ca + ca) * (cb + cb)) +
-             ca * ca / (ca + ca) * (qBbR - qBbL) - cb * cb / (cb + cb) * (qBaR - qBaL);
+    Eh[i0] = (hLL + hLR + hRL + hRR) * T(0.25) + (T(0.5) * ca) * (qBbR - qBbL) - (T(0.5) * cb) * (qBaR - qBaL);
 }
 
 // ---------------------------------------------------------------------------
@@ -424,30 +468,16 @@ __device__ __forceinline__ void emf_ideal_item(const Dims& g, const CP8& prim, c
     const long long sA = aa ? g.st[A] : 0, sB = ba ? g.st[B] : 0;
     double ca = 1.0, cb = 1.0;
     if (alp || psi) {
-        if (aa) {
-            double cmax = 0.0;
-            for (int tt = 0; tt < (ba ? 2 : 1); tt++) {
-                const long long cf = i0 - tt * sB, cfm = cf - sA;
-                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
-                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-                cmax = fmax(cmax, alf / (psf * psf));
-            }
-            ca = cmax;
-        }
-        if (ba) {
-            double cmax = 0.0;
-            for (int tt = 0; tt < (aa ? 2 : 1); tt++) {
-                const long long cf = i0 - tt * sA, cfm = cf - sB;
-                const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
-                const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-                cmax = fmax(cmax, alf / (psf * psf));
-            }
-            cb = cmax;
-        }
+        double cab[2];
+        edge_speeds(psi, alp, i0, aa, ba, sA, sB, cab);
+        ca = cab[0];
+        cb = cab[1];
     }
-    // step (iv), the upwind formula of App. A (sqrt(gamma_hat) = 1)
-    Eh[i0] = -(ca * vaR * qBbR + ca * vaL * qBbL - ca * ca * (qBbR - qBbL)) / (ca + ca) +
-             (cb * vbR * qBaR + cb * vbL * qBaL - cb * cb * (qBaR - qBaL)) / (cb + cb);
+    // step (iv), the upwind formula of App. A (sqrt(gamma_hat) = 1); with c+ = c- each
+    // term (c v_R q_R + c v_L q_L - c^2 (q_R - q_L)) / 2c is
+    // (v_R q_R + v_L q_L - c (q_R - q_L)) / 2
+    Eh[i0] = -(vaR * qBbR + vaL * qBbL - ca * (qBbR - qBbL)) * 0.5 +
+             (vbR * qBaR + vbL * qBaL - cb * (qBaR - qBaL)) * 0.5;
 }
 
 // ---------------------------------------------------------------------------
@@ -512,12 +542,13 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
         //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
         //   s_tau = -psi^4 S_hat_i d_i alpha
         const double rho = prim[0][o], p = prim[4][o];
+        const double ip4 = 1.0 / p4, ips = ps * p2 * ip4;   // psi^-4, psi^-1
         double uh[3], Eh[3], Bh[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             uh[i] = p2 * u[i];
             Eh[i] = p2 * prim[5 + i][o];
-            Bh[i] = p2 * (CC ? bsrc[i][o] : cell_qB(g, bsrc[i], i, c)) / p6;
+            Bh[i] = (CC ? bsrc[i][o] : cell_qB(g, bsrc[i], i, c)) * ip4;   // psi^2 q_B / psi^6
         }
         const double rhoh = rho + g.gh * p;
         const double U = 0.5 * (Eh[0] * Eh[0] + Eh[1] * Eh[1] + Eh[2] * Eh[2] + Bh[0] * Bh[0] +
@@ -537,7 +568,7 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
             const double pp = psi ? psi[o + g.st[i]] : 1.0, pm = psi ? psi[o - g.st[i]] : 1.0;
             const double dal = (ap - am) * (0.5 * g.idx[i]);
             const double dps = (pp - pm) * (0.5 * g.idx[i]);
-            Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps / ps) * tr);
+            Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps * ips) * tr);
             Lc[4] -= p4 * S[i] * dal;
         }
     }
