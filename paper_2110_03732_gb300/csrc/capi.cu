@@ -219,6 +219,18 @@ P3 p3(double* const* p)
 
 bool emf_needed(const Dims& g, int c) { return g.act[(c + 1) % 3] || g.act[(c + 2) % 3]; }
 
+// the flux direction whose kernel writes the edge EMF of direction c (flat metric, MC,
+// resistive UCT, exactly one of the two directions transverse to c active: the edges
+// then coincide with that direction's faces), else -1
+int fused_emf_dir(const grmhd_ctx* c, int k)
+{
+    const Dims& g = c->g;
+    if (c->psi || c->alp || c->ppm || c->ideal) return -1;
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    if (g.act[a] == g.act[b]) return -1;
+    return g.act[a] ? a : b;
+}
+
 ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE_out, F11 p32)
 {
     ImpArgs a;
@@ -278,20 +290,27 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     for (int d = 0; d < 3; d++) {
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
+        double* eh64[3] = {nullptr, nullptr, nullptr};
+        float* eh32[3] = {nullptr, nullptr, nullptr};
+        for (int k = 0; k < 3; k++)
+            if (fused_emf_dir(c, k) == d) {
+                eh64[k] = c->Eh[k];
+                eh32[k] = c->Eh32[k];
+            }
         if (c->mixed) {
             FluxOut<float> fo;
             for (int v = 0; v < 8; v++) fo.p[v] = c->F32[d][v];
-            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm);
+            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm, eh32);
         } else {
             e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
-                            c->ppm);
+                            c->ppm, eh64);
         }
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "flux kernel");
     }
     for (int k = 0; k < 3; k++) {
-        if (!emf_needed(g, k)) continue;
+        if (!emf_needed(g, k) || fused_emf_dir(c, k) >= 0) continue;
         const int tk = tbegin(c, KIND_EMF, st);
         if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh32[k], c->nsm, st, c->ppm);
         else if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);

@@ -244,14 +244,15 @@ __device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi
     s.q[4] = p6 * tau;
 #pragma unroll
     for (int j = 0; j < 3; j++) s.q[5 + j] = p4 * E[j];
-    // fluxes along d (beta = 0)
-    const T vd = u[d] * iW;
-    const T rhw2 = rhoh * W * W;
-    s.f[0] = p4 * alp * D * vd;
+    // fluxes along d (beta = 0), with W v = u: D v^d = rho u^d and
+    // rho h W^2 v^d v^j = rho h u^d u^j
+    const T Dv = rho * u[d];
+    const T rhu = rhoh * u[d];
+    s.f[0] = p4 * alp * Dv;
 #pragma unroll
     for (int j = 0; j < 3; j++)
-        s.f[1 + j] = p6 * alp * ((j == d ? p + U : T(0)) + rhw2 * vd * (u[j] * iW) - E[d] * E[j] - Bh[d] * Bh[j]);
-    s.f[4] = p4 * alp * (S[d] - vd * D);
+        s.f[1 + j] = p6 * alp * ((j == d ? p + U : T(0)) + rhu * u[j] - E[d] * E[j] - Bh[d] * Bh[j]);
+    s.f[4] = p4 * alp * (S[d] - Dv);
     // (f_E^j)^d = alpha psi^2 eta^{djk} B_hat_k
     const T ap2 = alp * p2;
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;

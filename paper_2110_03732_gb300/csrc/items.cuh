@@ -142,6 +142,93 @@ __device__ __forceinline__ float cell_qB_in(const Dims&, const PrimIn<float>& pa
     return pa.p[8 + e][mi];
 }
 
+// the upwind edge EMF of Sec. 3.2 (Londrillo & Del Zanna 2004) with c+ = c- in each
+// direction, where the four-state weights are all 1/4 and the diffusive coefficients
+// c^2/2c are c/2: h_XY = alpha E_C^XY (X the A side, Y the B side), q_B^B reconstructed
+// along A, q_B^A along B
+template <typename T>
+__device__ __forceinline__ T uct_edge(T hLL, T hLR, T hRL, T hRR, T ca, T cb, T qBbL, T qBbR, T qBaL, T qBaR)
+{
+    return (hLL + hLR + hRL + hRR) * T(0.25) + (T(0.5) * ca) * (qBbR - qBbL) - (T(0.5) * cb) * (qBaR - qBaL);
+}
+
+// HLL flux at the D-face with padded coordinates c (between the cells of linear
+// indices rm = c - e_D and r0 = c) from the reconstructed states: prL / prR the 8
+// primitives (coordinate u^i and E^i), BL / BR the coordinate B with the two transverse
+// components set (the normal one is the face's own).  Writes twice the flux at r0, and
+// the ideal-limit transport velocities when vbar is set.  prL, prR, BL, BR are
+// overwritten.
+//
+// Eh (flat metric only, else NULL): Eh[C] set for an edge direction C != D whose
+// third direction is inactive (a 1-D or 2-D grid).  Its edges then coincide with the
+// D-faces, and the UCT EMF there needs only reconstructions along D of E_C and of the
+// transverse q_B, which are this face's states: the face writes hat{E}_C, bitwise what
+// emf_item computes (the same MC values, the same edge formula).
+template <int D, bool M, typename T>
+__device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const double* psi_in, const double* alp_in,
+                                          const int* c, long long rm, long long r0, T* prL, T* prR, T* BL, T* BR,
+                                          const FluxOut<T>& F, double* const* vbar, T* const* Eh = nullptr)
+{
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    const double* __restrict__ alp = M ? alp_in : nullptr;
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    const T psf = psi ? (T)(0.5 * (psi[rm] + psi[r0])) : T(1);
+    const T alf = alp ? (T)(0.5 * (alp[rm] + alp[r0])) : T(1);
+    const T pf2 = psf * psf, ipf2 = T(1) / pf2;
+    // orthonormal-frame states at the face: u_hat = psi^2 u, E_hat = psi^2 E,
+    // B_hat = psi^2 B (normal: q_B / psi^4)
+    BL[D] = BR[D] = (T)bf.p[D][face_at(g, D, c)] * (ipf2 * ipf2);
+    if (!M && Eh) {
+        // C = D + 1: A = D + 2 (inactive), B = D; C = D + 2: A = D, B = D + 1 (inactive)
+        if (Eh[T1])
+            Eh[T1][r0] = uct_edge<T>(prL[5 + T1], prR[5 + T1], prL[5 + T1], prR[5 + T1], T(1), T(1), BL[D], BR[D],
+                                     BL[T2], BR[T2]);
+        if (Eh[T2])
+            Eh[T2][r0] = uct_edge<T>(prL[5 + T2], prL[5 + T2], prR[5 + T2], prR[5 + T2], T(1), T(1), BL[T1], BR[T1],
+                                     BL[D], BR[D]);
+    }
+    if (psi) {
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            prL[1 + i] *= pf2;
+            prR[1 + i] *= pf2;
+            prL[5 + i] *= pf2;
+            prR[5 + i] *= pf2;
+            if (i != D) {
+                BL[i] *= pf2;
+                BR[i] *= pf2;
+            }
+        }
+    }
+    // HLL with c+ = c- = c = alpha sqrt(gamma^DD) = alpha / psi^2 (Sec. 2.5, maximal
+    // diffusivity): (c f_L + c f_R - c^2 (q_R - q_L)) / 2c = (f_L + f_R - c (q_R - q_L)) / 2.
+    // Each densitised q_v is psi^k_v times its flat-space (psi = alpha = 1) value and its
+    // flux alpha psi^(k_v - 2) times, k = 6, 8, 8, 8, 6, 4, 4, 4: the HLL flux is then
+    // alpha psi^(k_v - 2) times the flat-space HLL flux (unit speed) of the
+    // orthonormal states.  F stores twice the flux (no 1/2 here: the update folds it).
+    FaceStateT<T> sL, sR;
+    face_state<T>(prL, BL, D, T(1), T(1), (T)g.gh, sL);
+    face_state<T>(prR, BR, D, T(1), T(1), (T)g.gh, sR);
+    const T h2 = alf * pf2, h4 = h2 * pf2, h6 = h4 * pf2;
+    const long long o = r0;
+#pragma unroll
+    for (int v = 0; v < 8; v++) {
+        const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
+        F.p[v][o] = (sL.f[v] + sR.f[v] - (sR.q[v] - sL.q[v])) * hv;
+    }
+    if (vbar && vbar[0]) {
+        // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
+        // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+), their mean for c+ = c-;
+        // v^j = u_hat^j / (psi^2 W)
+        const double al = (double)(alf * ipf2);
+        const double iL = (double)sL.iW, iR = (double)sR.iW;
+        const double vL1 = al * (double)prL[1 + T1] * iL, vR1 = al * (double)prR[1 + T1] * iR;
+        const double vL2 = al * (double)prL[1 + T2] * iL, vR2 = al * (double)prR[1 + T2] * iR;
+        vbar[0][o] = (vR1 + vL1) * 0.5;
+        vbar[1][o] = (vR2 + vL2) * 0.5;
+    }
+}
+
 // vbar (may be NULL): the two transverse transport-velocity arrays of the ideal-limit
 // EMF (App. A) for the D-faces, components (D+1)%3 and (D+2)%3.  P: PPM reconstruction
 // (six cells c-3..c+2) instead of MC (four cells c-2..c+1).
@@ -203,51 +290,103 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
         if (P) ppm_face<T>(b, BL[e], BR[e]);
         else mc_face<T>(b[0], b[1], b[2], b[NS - 1], BL[e], BR[e]);
     }
-    const T psf = psi ? (T)(0.5 * (psi[ri[OFF - 1]] + psi[ri[OFF]])) : T(1);
-    const T alf = alp ? (T)(0.5 * (alp[ri[OFF - 1]] + alp[ri[OFF]])) : T(1);
-    const T pf2 = psf * psf, ipf2 = T(1) / pf2;
-    // orthonormal-frame states at the face: u_hat = psi^2 u, E_hat = psi^2 E,
-    // B_hat = psi^2 B (normal: q_B / psi^4)
-    BL[D] = BR[D] = (T)bf.p[D][face_at(g, D, c)] * (ipf2 * ipf2);
-    if (psi) {
+    face_flux<D, M, T>(g, bf, psi, alp, c, ri[OFF - 1], ri[OFF], prL, prR, BL, BR, F, vbar);
+}
+
+
+// The same fluxes for K consecutive D-faces per thread (MC only): the thread marches
+// along D keeping, per reconstructed quantity, the last two cell values, their
+// difference and the right-face state of the older cell, so each new face loads one
+// cell and computes one cell's half slope (the per-face form loads four cells and
+// computes two).  The face states are bitwise those of mc_face.  Items: chunks of K
+// faces along D, x-fastest over the other directions (for D = 0 the chunks themselves
+// run along x).
+template <int D, bool M, typename T>
+__device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
+                                                const double* psi_in, const double* alp_in, const FluxOut<T>& F,
+                                                double* const* vbar, T* const* Eh, long long t, int K)
+{
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    constexpr int NV = 10;   // 8 primitives and the two transverse B
+    const int nq = (g.n[D] + 1 + K - 1) / K;
+    int c[3], q;
+    if (D == 0) {
+        q = (int)(t % nq);
+        const long long r = t / nq;
+        c[1] = g.ng[1] + (int)(r % g.n[1]);
+        c[2] = g.ng[2] + (int)(r / g.n[1]);
+    } else if (D == 1) {
+        c[0] = g.ng[0] + (int)(t % g.n[0]);
+        const long long r = t / g.n[0];
+        q = (int)(r % nq);
+        c[2] = g.ng[2] + (int)(r / nq);
+    } else {
+        c[0] = g.ng[0] + (int)(t % g.n[0]);
+        const long long r = t / g.n[0];
+        c[1] = g.ng[1] + (int)(r % g.n[1]);
+        q = (int)(r / g.n[1]);
+    }
+    const int f0 = g.ng[D] + q * K;                       // first face (padded index)
+    const int f1 = min(f0 + K, g.ng[D] + g.n[D] + 1);     // one past the last
+    // the 10 reconstructed values of the cell at padded coordinate m along D
+    auto load = [&](int m, T* x, long long& rl) {
+        int cs[3] = {c[0], c[1], c[2]};
+        cs[D] = m;
+        const long long mi = cell_at(g, cs);
+        rl = lin(g, cs[0], cs[1], cs[2]);
 #pragma unroll
-        for (int i = 0; i < 3; i++) {
-            prL[1 + i] *= pf2;
-            prR[1 + i] *= pf2;
-            prL[5 + i] *= pf2;
-            prR[5 + i] *= pf2;
-            if (i != D) {
-                BL[i] *= pf2;
-                BR[i] *= pf2;
-            }
+        for (int v = 0; v < 8; v++) x[v] = prim.p[v][mi];
+        T ip6 = T(1);
+        if (psi) {
+            const T ps = (T)psi[rl], p2 = ps * ps;
+            ip6 = T(1) / (p2 * p2 * p2);
+        }
+        x[8] = (T)cell_qB_in(g, prim, bf, T1, cs, mi) * ip6;
+        x[9] = (T)cell_qB_in(g, prim, bf, T2, cs, mi) * ip6;
+    };
+    // window at the first face: cells f0-2, f0-1, f0
+    T A[NV], Bv[NV], Dp[NV], Lp[NV];
+    long long rm, r0;
+    {
+        T x0[NV];
+        long long rx;
+        load(f0 - 2, x0, rx);
+        load(f0 - 1, A, rm);
+        load(f0, Bv, r0);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            const T dm = A[v] - x0[v];
+            Dp[v] = Bv[v] - A[v];
+            Lp[v] = A[v] + minmod3<T>(dm, T(0.25) * (Bv[v] - x0[v]), Dp[v]);
         }
     }
-    // HLL with c+ = c- = c = alpha sqrt(gamma^DD) = alpha / psi^2 (Sec. 2.5, maximal
-    // diffusivity): (c f_L + c f_R - c^2 (q_R - q_L)) / 2c = (f_L + f_R - c (q_R - q_L)) / 2.
-    // Each densitised q_v is psi^k_v times its flat-space (psi = alpha = 1) value and its
-    // flux alpha psi^(k_v - 2) times, k = 6, 8, 8, 8, 6, 4, 4, 4: the HLL flux is then
-    // alpha psi^(k_v - 2) times the flat-space HLL flux (unit speed) of the
-    // orthonormal states.
-    FaceStateT<T> sL, sR;
-    face_state<T>(prL, BL, D, T(1), T(1), (T)g.gh, sL);
-    face_state<T>(prR, BR, D, T(1), T(1), (T)g.gh, sR);
-    const T h2 = T(0.5) * alf * pf2, h4 = h2 * pf2, h6 = h4 * pf2;
-    const long long o = lin(g, c[0], c[1], c[2]);
+    for (int f = f0; f < f1; f++) {
+        T x3[NV];
+        long long r3;
+        load(f + 1, x3, r3);
+        T prL[8], prR[8], BL[3], BR[3];
 #pragma unroll
-    for (int v = 0; v < 8; v++) {
-        const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
-        F.p[v][o] = (sL.f[v] + sR.f[v] - (sR.q[v] - sL.q[v])) * hv;
-    }
-    if (vbar && vbar[0]) {
-        // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
-        // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+), their mean for c+ = c-;
-        // v^j = u_hat^j / (psi^2 W)
-        const double al = (double)(alf * ipf2);
-        const double iL = (double)sL.iW, iR = (double)sR.iW;
-        const double vL1 = al * (double)prL[1 + T1] * iL, vR1 = al * (double)prR[1 + T1] * iR;
-        const double vL2 = al * (double)prL[1 + T2] * iL, vR2 = al * (double)prR[1 + T2] * iR;
-        vbar[0][o] = (vR1 + vL1) * 0.5;
-        vbar[1][o] = (vR2 + vL2) * 0.5;
+        for (int v = 0; v < NV; v++) {
+            const T dn = x3[v] - Bv[v];
+            const T hs = minmod3<T>(Dp[v], T(0.25) * (x3[v] - A[v]), dn);
+            const T R = Bv[v] - hs;
+            if (v < 8) {
+                prL[v] = Lp[v];
+                prR[v] = R;
+            } else {
+                BL[v == 8 ? T1 : T2] = Lp[v];
+                BR[v == 8 ? T1 : T2] = R;
+            }
+            Lp[v] = Bv[v] + hs;
+            A[v] = Bv[v];
+            Bv[v] = x3[v];
+            Dp[v] = dn;
+        }
+        c[D] = f;
+        face_flux<D, M, T>(g, bf, psi_in, alp_in, c, rm, r0, prL, prR, BL, BR, F, vbar, Eh);
+        rm = r0;
+        r0 = r3;
     }
 }
 
@@ -386,7 +525,7 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     // c+ = c- in each direction, where the four-state weights are all 1/4 and the
     // diffusive coefficients c^2/2c are c/2
     const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
-    Eh[i0] = (hLL + hLR + hRL + hRR) * T(0.25) + (T(0.5) * ca) * (qBbR - qBbL) - (T(0.5) * cb) * (qBaR - qBaL);
+    Eh[i0] = uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR);
 }
 
 // ---------------------------------------------------------------------------
@@ -600,10 +739,11 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
         for (int d = 0; d < 3; d++) {
             if (!g.act[d]) continue;
             const long long o1 = o + g.st[d];
+            const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
 #pragma unroll
             for (int v = 0; v < 8; v++) {
                 const T* __restrict__ Fv = (const T*)a.F[d][v];
-                Lc[v] -= ((double)Fv[o1] - (double)Fv[o]) * g.idx[d];
+                Lc[v] -= ((double)Fv[o1] - (double)Fv[o]) * hidx;
             }
         }
         cell_sources<false>(g, a.prim, a.bf, psi, alp, c, o, Lc);

@@ -54,6 +54,18 @@ __global__ void __launch_bounds__(128) k_flux(Dims g, FluxArgs<T> a)
         flux_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, t);
 }
 
+// MC fluxes, K consecutive D-faces per thread (flux_march_item)
+template <int D, bool M, typename T>
+__global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a, int K)
+{
+    const long long nq = (g.n[D] + K) / K;
+    const long long tot = nq * (D == 0 ? (long long)g.n[1] * g.n[2]
+                                       : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x)
+        flux_march_item<D, M, T>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, a.Eh, t, K);
+}
+
 // ---------------------------------------------------------------------------
 // upwind constrained transport: hat{E}_C on the edges along C, stored at the corner
 // index that is lower in a = C+1 and b = C+2
@@ -388,12 +400,43 @@ cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStr
     return cudaGetLastError();
 }
 
-template <typename T>
-static void flux_dispatch(const Dims& g, int d, bool m, int b, cudaStream_t st, const FluxArgs<T>& a)
+
+// resident 128-thread blocks per SM of a marching flux kernel (its register count
+// decides: about 2 for FP64, 4 for FP32), queried once
+template <int D, bool M, typename T>
+static int march_blocks_per_sm()
 {
-    if (d == 0) m ? k_flux<0, true, T><<<b, 128, 0, st>>>(g, a) : k_flux<0, false, T><<<b, 128, 0, st>>>(g, a);
-    else if (d == 1) m ? k_flux<1, true, T><<<b, 128, 0, st>>>(g, a) : k_flux<1, false, T><<<b, 128, 0, st>>>(g, a);
-    else m ? k_flux<2, true, T><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, T><<<b, 128, 0, st>>>(g, a);
+    static int nb = 0;
+    if (nb < 1) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_flux_march<D, M, T>, 128, 0) != cudaSuccess || q < 1)
+            q = 1;
+        nb = q;
+    }
+    return nb;
+}
+
+// faces per thread: the largest of 8, 4, 2, 1 that still gives three quarters of a
+// full wave of resident blocks (a longer march saves more loads and slopes; a short
+// grid leaves SMs idle)
+template <int D, bool M, typename T>
+static void flux_march_launch(const Dims& g, int nsm, cudaStream_t st, const FluxArgs<T>& a)
+{
+    const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
+                                   : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
+    const double want = 0.75 * nsm * march_blocks_per_sm<D, M, T>();
+    int K = 8;
+    while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
+    const int b = grid_for((long long)((g.n[D] + K) / K) * other, 128, nsm);
+    k_flux_march<D, M, T><<<b, 128, 0, st>>>(g, a, K);
+}
+
+template <typename T>
+static void flux_dispatch(const Dims& g, int d, bool m, int nsm, cudaStream_t st, const FluxArgs<T>& a)
+{
+    if (d == 0) m ? flux_march_launch<0, true, T>(g, nsm, st, a) : flux_march_launch<0, false, T>(g, nsm, st, a);
+    else if (d == 1) m ? flux_march_launch<1, true, T>(g, nsm, st, a) : flux_march_launch<1, false, T>(g, nsm, st, a);
+    else m ? flux_march_launch<2, true, T>(g, nsm, st, a) : flux_march_launch<2, false, T>(g, nsm, st, a);
 }
 
 template <typename T>
@@ -417,9 +460,10 @@ static long long emf_work(const Dims& g, int c)
 }
 
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
-                        cudaStream_t st, double* const* vbar, bool ppm)
+                        cudaStream_t st, double* const* vbar, bool ppm, double* const* Eh)
 {
     FluxArgs<double> a;
+    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !ppm && !(psi || alp) ? Eh[k] : nullptr;
     for (int v = 0; v < 8; v++) {
         a.prim.p[v] = prim.p[v];
         a.F.p[v] = F.p[v];
@@ -438,14 +482,15 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
         else m ? k_flux<2, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, double, true><<<b, 128, 0, st>>>(g, a);
         return cudaGetLastError();
     }
-    flux_dispatch<double>(g, d, psi || alp, b, st, a);
+    flux_dispatch<double>(g, d, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm)
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm, float* const* Eh)
 {
     FluxArgs<float> a;
+    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !ppm && !(psi || alp) ? Eh[k] : nullptr;
     a.vbar[0] = a.vbar[1] = nullptr;
     a.prim = prim;
     a.bf = bf;
@@ -460,7 +505,7 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
         else m ? k_flux<2, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, float, true><<<b, 128, 0, st>>>(g, a);
         return cudaGetLastError();
     }
-    flux_dispatch<float>(g, d, psi || alp, b, st, a);
+    flux_dispatch<float>(g, d, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 

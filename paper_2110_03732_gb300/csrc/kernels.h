@@ -14,6 +14,8 @@ enum { UPD_WRITE_L = 0, UPD_STAGE = 1 };
 template <typename T> struct PrimIn;
 template <> struct PrimIn<double> { const double* p[8]; };
 template <> struct PrimIn<float> { const float* p[11]; };
+// face fluxes of the 8 cell-centred variables, stored as twice the HLL flux (the
+// update kernel folds the 1/2 into its 1/dx)
 template <typename T> struct FluxOut { T* p[8]; };
 struct F11 { float* p[11]; };
 
@@ -44,6 +46,8 @@ struct FluxArgs {
     const double* alp;
     FluxOut<T> F;
     double* vbar[2];        // ideal-limit EMF: transverse transport velocities (or NULL)
+    T* Eh[3];               // edge EMFs written by the flux kernel (flat 1-D / 2-D grids,
+                            // see face_flux), NULL for those the EMF kernels compute
 };
 
 template <typename T>
@@ -63,7 +67,7 @@ struct UpdateArgs {
     int f32;                // fluxes and EMFs are FP32 (mixed precision) instead of FP64
     double dt;
     double At[4][4], A[4][4], wt[4], w[4];
-    const void* F[3][8];    // face fluxes per active direction (double or float)
+    const void* F[3][8];    // twice the face fluxes per active direction (double or float)
     const void* Eh[3];      // edge EMFs (double or float)
     const double* prim[8];  // stage primitives (padded)
     const double* bf[3];    // stage face fields
@@ -78,13 +82,17 @@ struct UpdateArgs {
 
 cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false);
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false,
+                          float* const* Eh = nullptr);
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
                          const double* alp, float* Eh, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
 // ppm: PPM reconstruction instead of MC (FP64 only)
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
-                        cudaStream_t st, double* const* vbar = nullptr, bool ppm = false);
+                        cudaStream_t st, double* const* vbar = nullptr, bool ppm = false,
+                        double* const* Eh = nullptr);
+// Eh (MC, flat metric only; ignored otherwise): the edge EMF arrays the flux kernel of
+// direction d writes itself (fused_emf_dir), NULL entries for the others
 // ideal-limit edge EMF (App. A): vb[d][k] are the transport velocities of the d-faces,
 // component (d + 1 + k) % 3 (NULL for inactive directions)
 cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp,

@@ -54,10 +54,14 @@ def test_batch_bitwise_equals_alone(G, precision):
             s.step(dt)
         B.step()
     torch.cuda.synchronize()
+    # the single-problem path runs other kernels (the marching MC flux kernel) whose
+    # roundings differ from the batched per-item ones: FP64 agrees to 1e-10, the mixed
+    # path's FP32 fluxes to their round-off
+    tol = 1e-10 if precision == "fp64" else 1e-6
     for i, (a, b, c) in enumerate(zip(alone, inmix, single)):
         for x, y, z in zip(states(a), states(b), states(c)):
             assert torch.equal(x, y), (precision, probs[i].name)
-            assert rel_l1(y, z) <= 1e-10, (precision, probs[i].name)
+            assert rel_l1(y, z) <= tol, (precision, probs[i].name)
         assert b.diagnostics()[2] == 0
 
 
