@@ -528,6 +528,113 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     Eh[i0] = uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR);
 }
 
+// The same EMFs for K consecutive C-edges along B per thread (MC, both A and B active):
+// the A-direction reconstruction of E_C on each row of cells along B, and q_B^A, are
+// marched along B as in flux_march_item (one new row per edge instead of four), so each
+// edge computes one A-row, three one-cell B steps and its own q_B^B reconstruction.
+// The results are bitwise those of emf_item.  Items: chunks of K edges along B,
+// x-fastest over the other two directions (the chunks run along x when B = 0).
+template <int C, bool M, typename T>
+__device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
+                                               const double* psi_in, const double* alp_in, T* __restrict__ Eh,
+                                               long long t, int K)
+{
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    const double* __restrict__ alp = M ? alp_in : nullptr;
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    const T* __restrict__ Ec = prim.p[5 + C];
+    const int nq = (g.n[B] + 1 + K - 1) / K;
+    int e[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) e[d] = d == B ? nq : (d == C ? g.n[d] : g.n[d] + 1);
+    int c[3];
+    const int i0 = (int)(t % e[0]);
+    const long long r = t / e[0];
+    const int i1 = (int)(r % e[1]), i2 = (int)(r / e[1]);
+    const int idx[3] = {i0, i1, i2};
+#pragma unroll
+    for (int d = 0; d < 3; d++) c[d] = g.ng[d] + (d == B ? 0 : idx[d]);
+    const int f0 = g.ng[B] + idx[B] * K;
+    const int f1 = min(f0 + K, g.ng[B] + g.n[B] + 1);
+    // row m along B: covariant E_C = psi^4 E^C reconstructed along A to the A-face c[A],
+    // and q_B^A at that A-face
+    auto row = [&](int m, T* x) {
+        T v[4];
+#pragma unroll
+        for (int sa = 0; sa < 4; sa++) {
+            int cs[3] = {c[0], c[1], c[2]};
+            cs[B] = m;
+            cs[A] = c[A] + sa - 2;
+            const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
+            const T p2 = ps * ps;
+            v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
+        }
+        mc_face<T>(v[0], v[1], v[2], v[3], x[0], x[1]);
+        int cs[3] = {c[0], c[1], c[2]};
+        cs[B] = m;
+        x[2] = (T)bf.p[A][face_at(g, A, cs)];
+    };
+    T Aw[3], Bw[3], Dp[3], Lp[3];
+    {
+        T x0[3];
+        row(f0 - 2, x0);
+        row(f0 - 1, Aw);
+        row(f0, Bw);
+#pragma unroll
+        for (int v = 0; v < 3; v++) {
+            const T dm = Aw[v] - x0[v];
+            Dp[v] = Bw[v] - Aw[v];
+            Lp[v] = Aw[v] + minmod3<T>(dm, T(0.25) * (Bw[v] - x0[v]), Dp[v]);
+        }
+    }
+    for (int f = f0; f < f1; f++) {
+        T x3[3];
+        row(f + 1, x3);
+        T L[3], R[3];
+#pragma unroll
+        for (int v = 0; v < 3; v++) {
+            const T dn = x3[v] - Bw[v];
+            const T hs = minmod3<T>(Dp[v], T(0.25) * (x3[v] - Aw[v]), dn);
+            L[v] = Lp[v];
+            R[v] = Bw[v] - hs;
+            Lp[v] = Bw[v] + hs;
+            Aw[v] = Bw[v];
+            Bw[v] = x3[v];
+            Dp[v] = dn;
+        }
+        c[B] = f;
+        // q_B^B (B-faces) along A
+        T qBbL, qBbR;
+        {
+            T v[4];
+#pragma unroll
+            for (int sa = 0; sa < 4; sa++) {
+                int cs[3] = {c[0], c[1], c[2]};
+                cs[A] = c[A] + sa - 2;
+                v[sa] = (T)bf.p[B][face_at(g, B, cs)];
+            }
+            mc_face<T>(v[0], v[1], v[2], v[3], qBbL, qBbR);
+        }
+        const long long i0 = lin(g, c[0], c[1], c[2]);
+        const long long sA = g.st[A], sB = g.st[B];
+        T ale = T(1), ca = T(1), cb = T(1);
+        if (alp || psi) {
+            double sum = alp ? alp[i0] : 1.0;
+            sum += alp ? alp[i0 - sA] : 1.0;
+            sum += alp ? alp[i0 - sB] : 1.0;
+            sum += alp ? alp[i0 - sA - sB] : 1.0;
+            ale = (T)(sum * 0.25);
+            double cab[2];
+            edge_speeds(psi, alp, i0, true, true, sA, sB, cab);
+            ca = (T)cab[0];
+            cb = (T)cab[1];
+        }
+        // EXY[X][Y]: X the A side (the row's L / R), Y the B side (L = this edge's
+        // lower-B state)
+        Eh[i0] = uct_edge<T>(ale * L[0], ale * R[0], ale * L[1], ale * R[1], ca, cb, qBbL, qBbR, L[2], R[2]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // ideal-limit edge EMF (App. A), FP64: item t = C-edge t (as emf_item)
 // ---------------------------------------------------------------------------

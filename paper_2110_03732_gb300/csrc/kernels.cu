@@ -82,6 +82,18 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
         emf_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
 }
 
+// MC edge EMFs, K consecutive edges along B = C + 2 per thread (emf_march_item; A and
+// B active)
+template <int C, bool M, typename T>
+__global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a, int K)
+{
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    const long long tot = (long long)((g.n[B] + K) / K) * g.n[C] * (g.n[A] + 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x)
+        emf_march_item<C, M, T>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t, K);
+}
+
 // ideal-limit edge EMF (App. A) from the stored transport velocities
 struct VbarArgs {
     const double* p[3][2];
@@ -439,12 +451,44 @@ static void flux_dispatch(const Dims& g, int d, bool m, int nsm, cudaStream_t st
     else m ? flux_march_launch<2, true, T>(g, nsm, st, a) : flux_march_launch<2, false, T>(g, nsm, st, a);
 }
 
-template <typename T>
-static void emf_dispatch(const Dims& g, int c, bool m, int b, cudaStream_t st, const EmfArgs<T>& a)
+template <int C, bool M, typename T>
+static int emf_march_blocks_per_sm()
 {
-    if (c == 0) m ? k_emf<0, true, T><<<b, 128, 0, st>>>(g, a) : k_emf<0, false, T><<<b, 128, 0, st>>>(g, a);
-    else if (c == 1) m ? k_emf<1, true, T><<<b, 128, 0, st>>>(g, a) : k_emf<1, false, T><<<b, 128, 0, st>>>(g, a);
-    else m ? k_emf<2, true, T><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, T><<<b, 128, 0, st>>>(g, a);
+    static int nb = 0;
+    if (nb < 1) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_emf_march<C, M, T>, 128, 0) != cudaSuccess || q < 1)
+            q = 1;
+        nb = q;
+    }
+    return nb;
+}
+
+// edges of direction C: marched along B when A and B are both active (K chosen as for
+// the flux kernels), one per thread otherwise
+template <int C, bool M, typename T>
+static void emf_launch(const Dims& g, int nsm, cudaStream_t st, const EmfArgs<T>& a)
+{
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    if (!g.act[A] || !g.act[B]) {
+        long long work = 1;
+        for (int d = 0; d < 3; d++) work *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+        k_emf<C, M, T><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+        return;
+    }
+    const long long other = (long long)g.n[C] * (g.n[A] + 1);
+    const double want = 0.75 * nsm * emf_march_blocks_per_sm<C, M, T>();
+    int K = 8;
+    while (K > 1 && (double)(((g.n[B] + K) / K) * other + 127) / 128 < want) K /= 2;
+    k_emf_march<C, M, T><<<grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, 0, st>>>(g, a, K);
+}
+
+template <typename T>
+static void emf_dispatch(const Dims& g, int c, bool m, int nsm, cudaStream_t st, const EmfArgs<T>& a)
+{
+    if (c == 0) m ? emf_launch<0, true, T>(g, nsm, st, a) : emf_launch<0, false, T>(g, nsm, st, a);
+    else if (c == 1) m ? emf_launch<1, true, T>(g, nsm, st, a) : emf_launch<1, false, T>(g, nsm, st, a);
+    else m ? emf_launch<2, true, T>(g, nsm, st, a) : emf_launch<2, false, T>(g, nsm, st, a);
 }
 
 static long long flux_work(const Dims& g, int d)
@@ -526,7 +570,7 @@ cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi
         else m ? k_emf<2, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, double, true><<<b, 128, 0, st>>>(g, a);
         return cudaGetLastError();
     }
-    emf_dispatch<double>(g, c, psi || alp, b, st, a);
+    emf_dispatch<double>(g, c, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
@@ -567,7 +611,7 @@ cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf
         else m ? k_emf<2, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, float, true><<<b, 128, 0, st>>>(g, a);
         return cudaGetLastError();
     }
-    emf_dispatch<float>(g, c, psi || alp, b, st, a);
+    emf_dispatch<float>(g, c, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
