@@ -736,14 +736,19 @@ __device__ __forceinline__ void out_value(const UpdateArgs& a, int v, long long 
         a.L[v][o] = L;
         return;
     }
+    // base_k += dt (At[k][i] L + A[k][i] R), acc += dt (wt[i] L + w[i] R), with the
+    // dt products formed on the host; q^n is read at stage 0 only
     const double r = has_r ? a.R[v - 5][o] : 0.0;
-    const double qn = a.qn[v][o];
+    const double qn = a.stage == 0 ? a.qn[v][o] : 0.0;
     for (int k = a.stage + 1; k < a.s; k++) {
         const double prev = a.stage == 0 ? qn : a.base[k][v][o];
-        a.base[k][v][o] = prev + a.dt * (a.At[k][a.stage] * L + a.A[k][a.stage] * r);
+        double nb = prev + a.cL[k] * L;
+        if (has_r) nb += a.cR[k] * r;
+        a.base[k][v][o] = nb;
     }
     const double prev = a.stage == 0 ? qn : a.acc[v][o];
-    const double nv = prev + a.dt * (a.wt[a.stage] * L + a.w[a.stage] * r);
+    double nv = prev + a.cwL * L;
+    if (has_r) nv += a.cwR * r;
     if (a.stage == a.s - 1) a.qn[v][o] = nv;
     else a.acc[v][o] = nv;
 }

@@ -67,6 +67,8 @@ struct UpdateArgs {
     int f32;                // fluxes and EMFs are FP32 (mixed precision) instead of FP64
     double dt;
     double At[4][4], A[4][4], wt[4], w[4];
+    double cL[4], cR[4];    // dt At[k][stage], dt A[k][stage]: this stage's terms in base k
+    double cwL, cwR;        // dt wt[stage], dt w[stage]: its terms in the final combination
     const void* F[3][8];    // twice the face fluxes per active direction (double or float)
     const void* Eh[3];      // edge EMFs (double or float)
     const double* prim[8];  // stage primitives (padded)
