@@ -61,6 +61,10 @@ struct grmhd_ctx_s {
     float* p32[11];      // mixed precision: FP32 stage primitives + cell-centred q_B
     float* F32[3][8];    // mixed precision: FP32 face fluxes
     float* Eh32[3];      // mixed precision: FP32 edge EMFs
+    float* hs[4][3];     // per stage: its last Newton root u (orthonormal, FP32) ...
+    float* hd[4][3];     // ... and that root minus the one before (the start guess is
+                         // their sum: a linear extrapolation over steps)
+    bool hist;           // hs / hd hold valid history (set by grmhd_init_from_prims)
     bool mixed;
     double* red_part;
     double* red_out;
@@ -156,6 +160,13 @@ size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base, bool glm 
         for (int v = 0; v < 12; v++) { char* p = take(arr); if (c) c->acc[v] = (double*)p; }
         for (int d = 0; d < ndim; d++)
             for (int v = 0; v < 12; v++) { char* p = take(arr); if (c) c->F[d][v] = (double*)p; }
+        const size_t arr32 = round_up(sizeof(float) * (size_t)g.ncell);
+        for (int k = 0; k < s; k++)
+            for (int v = 0; v < 3; v++) {
+                char* p = take(arr32);
+                char* q = take(arr32);
+                if (c) { c->hs[k][v] = (float*)p; c->hd[k][v] = (float*)q; }
+            }
         { char* p = take(sizeof(double) * kRedBlocks * 11); if (c) c->red_part = (double*)p; }
         { char* p = take(sizeof(double) * 16); if (c) c->red_out = (double*)p; }
         { char* p = take(sizeof(unsigned long long)); if (c) c->nfail = (unsigned long long*)p; }
@@ -174,6 +185,12 @@ size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base, bool glm 
     for (int d = 0; d < ndim; d++)
         for (int v = 0; v < 8; v++) { char* p = take(arr32); if (c) c->F32[d][v] = (float*)p; }
     for (int v = 0; v < 3; v++) { char* p = take(arr32); if (c) c->Eh32[v] = (float*)p; }
+    for (int k = 0; k < s; k++)
+        for (int v = 0; v < 3; v++) {
+            char* p = take(arr32);
+            char* q = take(arr32);
+            if (c) { c->hs[k][v] = (float*)p; c->hd[k][v] = (float*)q; }
+        }
     { char* p = take(sizeof(double) * kRedBlocks * 11); if (c) c->red_part = (double*)p; }
     { char* p = take(sizeof(double) * 16); if (c) c->red_out = (double*)p; }
     { char* p = take(sizeof(unsigned long long)); if (c) c->nfail = (unsigned long long*)p; }
@@ -251,6 +268,7 @@ ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE
     a.xi = c->xi;
     a.p32 = p32;
     a.nfail = c->nfail;
+    for (int v = 0; v < 3; v++) a.hs[v] = a.hd[v] = nullptr;
     return a;
 }
 
@@ -611,6 +629,23 @@ grmhd_status grmhd_set_dynamo(grmhd_ctx* c, double xi)
     return GRMHD_OK;
 }
 
+// Newton start history of every stage: the initial velocity, no trend
+static grmhd_status init_history(grmhd_ctx* c, const double* const* prim, cudaStream_t st)
+{
+    for (int k = 0; k < c->tab.s; k++) {
+        P3f hs, hd;
+        for (int v = 0; v < 3; v++) {
+            hs.p[v] = c->hs[k][v];
+            hd.p[v] = c->hd[k][v];
+        }
+        cudaError_t e = launch_hist_init(c->g, prim[1], prim[2], prim[3], c->psi, hs, hd, c->nsm, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "history kernel");
+    }
+    c->hist = true;
+    return GRMHD_OK;
+}
+
 grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, const double* const* A_edge,
                                    grmhd_stream_t stream)
 {
@@ -635,7 +670,7 @@ grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, cons
         e = launch_prim2con_cc(g, cp8c(prim), cp3(c->bf), c->psi, p8(c->q), c->nsm, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "prim2con kernel");
-        return GRMHD_OK;
+        return init_history(c, prim, st);
     }
     if (A_edge) {
         for (int v = 0; v < 3; v++) {
@@ -658,7 +693,7 @@ grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, cons
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "prim_to32 kernel");
     }
-    return GRMHD_OK;
+    return init_history(c, prim, st);
 }
 
 grmhd_status grmhd_compute_dt(grmhd_ctx* c, double* dt, grmhd_stream_t stream)
@@ -896,6 +931,11 @@ void ctx_stage_args(grmhd_ctx* c, int i, double dt, ImpArgs* ia, UpdateArgs* a)
     double* const* fb = i == 0 ? c->bf : c->base[i] + 8;
     const double a_dt = c->tab.A[i * S + i] * dt;
     *ia = imp_args(c, cp8(qb), cp3(fb), a_dt, p8(c->prim), p3(c->R), p3(nullptr), f11(c));
+    if (c->hist)
+        for (int v = 0; v < 3; v++) {
+            ia->hs[v] = c->hs[i][v];
+            ia->hd[v] = c->hd[i][v];
+        }
     memset(a, 0, sizeof *a);
     a->mode = UPD_STAGE;
     a->stage = i;
@@ -945,16 +985,26 @@ grmhd_status batch_fail(grmhd_status s, const char* msg)
     return s;
 }
 
+// the Newton starting points (primitives and the FP32 start history) and the failure
+// count, to host memory and back
 cudaError_t ctx_save_guess(grmhd_ctx* c, std::vector<double>& host, cudaStream_t st)
 {
-    const size_t n = (size_t)c->g.ncell;
-    host.resize(8 * n + 1);
+    const size_t n = (size_t)c->g.ncell, nh = (size_t)c->tab.s * 6 * ((n + 1) / 2);
+    host.resize(8 * n + 1 + nh);
     for (int v = 0; v < 8; v++) {
         cudaError_t e = cudaMemcpyAsync(host.data() + v * n, c->prim[v], n * sizeof(double), cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) return e;
     }
     cudaError_t e = cudaMemcpyAsync(host.data() + 8 * n, c->nfail, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
+    float* h = (float*)(host.data() + 8 * n + 1);
+    for (int k = 0; k < c->tab.s; k++)
+        for (int v = 0; v < 3; v++) {
+            e = cudaMemcpyAsync(h, c->hs[k][v], n * sizeof(float), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h + n, c->hd[k][v], n * sizeof(float), cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return e;
+            h += 2 * n;
+        }
     return cudaStreamSynchronize(st);
 }
 
@@ -967,5 +1017,13 @@ cudaError_t ctx_restore_guess(grmhd_ctx* c, const std::vector<double>& host, cud
     }
     cudaError_t e = cudaMemcpyAsync(c->nfail, host.data() + 8 * n, sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
+    const float* h = (const float*)(host.data() + 8 * n + 1);
+    for (int k = 0; k < c->tab.s; k++)
+        for (int v = 0; v < 3; v++) {
+            e = cudaMemcpyAsync(c->hs[k][v], h, n * sizeof(float), cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->hd[k][v], h + n, n * sizeof(float), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            h += 2 * n;
+        }
     return cudaStreamSynchronize(st);
 }

@@ -60,13 +60,23 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     double u[3];
     Eval e;
     bool atmo = false;
+    // Newton start: this stage's last root plus its last change (a linear extrapolation
+    // over steps, kept in FP32: it is only a start) when the history is kept, else the
+    // latest primitives
+    const bool hist = a.hs[0] != nullptr;
+    float hsv[3] = {0.0f, 0.0f, 0.0f};
     if (rho_atm > 0.0 && ci.D < 10.0 * rho_atm) {
-        atmo = true;
+        atmo = true;   // (its history is left as it is)
     } else {
         bool fin = true;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            u[i] = p2 * prim.p[1 + i][id];
+            if (hist) {
+                hsv[i] = a.hs[i][id];
+                u[i] = (double)(hsv[i] + a.hd[i][id]);
+            } else {
+                u[i] = p2 * prim.p[1 + i][id];
+            }
             if (!(fabs(u[i]) < 1e30)) fin = false;
         }
         if (!fin) u[0] = u[1] = u[2] = 0.0;
@@ -122,6 +132,11 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
         const double qEn = p4 * e.E[i];
         if (R.p[0]) R.p[i][id] = a_dt > 0.0 ? (qEn - qEs[i]) / a_dt : 0.0;
         if (qE_out.p[0]) qE_out.p[i][id] = qEn;
+        if (hist && !atmo) {
+            const float un = (float)u[i];
+            a.hd[i][id] = un - hsv[i];
+            a.hs[i][id] = un;
+        }
     }
 }
 

@@ -404,6 +404,26 @@ cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_hist_init(long long n, const double* __restrict__ u1,
+                                                   const double* __restrict__ u2, const double* __restrict__ u3,
+                                                   const double* __restrict__ psi, P3f hs, P3f hd)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const double p2 = psi ? psi[t] * psi[t] : 1.0;
+        hs.p[0][t] = (float)(p2 * u1[t]);
+        hs.p[1][t] = (float)(p2 * u2[t]);
+        hs.p[2][t] = (float)(p2 * u3[t]);
+        hd.p[0][t] = hd.p[1][t] = hd.p[2][t] = 0.0f;
+    }
+}
+
+cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, const double* u3, const double* psi,
+                             P3f hs, P3f hd, int nsm, cudaStream_t st)
+{
+    k_hist_init<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g.ncell, u1, u2, u3, psi, hs, hd);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st)
 {
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];

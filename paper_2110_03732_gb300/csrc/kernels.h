@@ -36,7 +36,11 @@ struct ImpArgs {
     double xi;              // mean-field dynamo parameter
     F11 p32;                // FP32 copy for the mixed path (or NULL)
     unsigned long long* nfail;
+    float* hs[3];           // this stage's last Newton root u (orthonormal), or NULL ...
+    float* hd[3];           // ... and its change from the one before: start at hs + hd
 };
+
+struct P3f { float* p[3]; };
 
 template <typename T>
 struct FluxArgs {
@@ -83,6 +87,10 @@ struct UpdateArgs {
 };
 
 cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st);
+// Newton start history at initialisation: hs = psi^2 u (the orthonormal velocity of the
+// coordinate u1..u3), hd = 0, on every cell
+cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, const double* u3, const double* psi,
+                             P3f hs, P3f hd, int nsm, cudaStream_t st);
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
                           const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false,
                           float* const* Eh = nullptr);

@@ -82,12 +82,14 @@ def test_scratch_bytes_formula(lib):
         arr = -(-8 * ncell // 256) * 256
         narr = 8 + 3 + 11 * (t.s - 1) + 11 + 8 * ndim + 3
         arr32 = -(-4 * ncell // 256) * 256
-        narr32 = 11 + 8 * ndim + 3
+        # FP32: stage primitives + cell q_B, fluxes, edge EMFs, and per stage the Newton
+        # start history (last root and its change, 3 components each)
+        narr32 = 11 + 8 * ndim + 3 + 6 * t.s
         small = -(-8 * 1024 * 11 // 256) * 256 + 256 + 256
         ct = narr * arr + narr32 * arr32 + small
         # GLM layout: 12 cell-centred variables per stage base, running sum and flux
-        # direction, no edge EMFs and no FP32 arrays
-        glm = (8 + 3 + 12 * (t.s - 1) + 12 + 12 * ndim) * arr + small
+        # direction, no edge EMFs; of the FP32 arrays only the start history
+        glm = (8 + 3 + 12 * (t.s - 1) + 12 + 12 * ndim) * arr + 6 * t.s * arr32 + small
         assert b.value == max(ct, glm)
 
 
