@@ -152,13 +152,24 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 // PPM (Colella & Woodward 1984: interface interpolation with the MC slope and the
 // monotonicity limits of the parabola, no steepening or flattening).  a[0..5] are the
 // cells c-3..c+2; L is the right edge of cell c-1, R the left edge of cell c.
+// the MC slope of cell a0 (twice the half slope minmod(D-, (a+ - a-)/4, D+))
+template <typename T>
+__device__ __forceinline__ T ppm_slope(T am, T a0, T ap)
+{
+    return T(2) * minmod3<T>(a0 - am, T(0.25) * (ap - am), ap - a0);
+}
+
+// the interface value between cells a0 and ap with slopes s0, s1
+template <typename T>
+__device__ __forceinline__ T ppm_iface_s(T a0, T ap, T s0, T s1)
+{
+    return a0 + T(0.5) * (ap - a0) - (s1 - s0) * T(1.0 / 6.0);
+}
+
 template <typename T>
 __device__ __forceinline__ T ppm_iface(T am, T a0, T ap, T app)
 {
-    // the MC slope is twice the half slope minmod(D-, (a+ - a-)/4, D+)
-    const T s0 = T(2) * minmod3<T>(a0 - am, T(0.25) * (ap - am), ap - a0);
-    const T s1 = T(2) * minmod3<T>(ap - a0, T(0.25) * (app - a0), app - ap);
-    return a0 + T(0.5) * (ap - a0) - (s1 - s0) * T(1.0 / 6.0);
+    return ppm_iface_s<T>(a0, ap, ppm_slope<T>(am, a0, ap), ppm_slope<T>(a0, ap, app));
 }
 
 template <typename T>

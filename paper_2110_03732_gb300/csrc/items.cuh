@@ -309,18 +309,85 @@ __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, 
 }
 
 
-// The same fluxes for K consecutive D-faces per thread (MC only): the thread marches
-// along D keeping, per reconstructed quantity, the last two cell values, their
-// difference and the right-face state of the older cell, so each new face loads one
-// cell and computes one cell's half slope (the per-face form loads four cells and
-// computes two).  The face states are bitwise those of mc_face.  Items: chunks of K
-// faces along D, x-fastest over the other directions (for D = 0 the chunks themselves
-// run along x).
-template <int D, bool M, typename T>
+// Marching reconstruction along a line of cells, one quantity: the face states of the
+// faces f0, f0+1, ... from one new cell per face.  MC keeps the last two cell values,
+// their difference and the older cell's right-face state; PPM keeps the last two cell
+// values, the newer one's MC slope, the interface value below it and the limited right
+// edge of the cell before.  Each step returns the states of face f (between cells f-1
+// and f): bitwise those of mc_face / ppm_face, whose slopes and interface values are
+// the same expressions, each now evaluated once.
+template <typename T, bool P>
+struct LineRec;
+
+template <typename T>
+struct LineRec<T, false> {
+    static constexpr int NINIT = 3, AHEAD = 1;   // cells f0-2..f0 first; step f loads f+1
+    T a, b, d, l;
+    __device__ __forceinline__ void init(const T* x)
+    {
+        a = x[1];
+        b = x[2];
+        d = b - a;
+        l = a + minmod3<T>(a - x[0], T(0.25) * (b - x[0]), d);
+    }
+    __device__ __forceinline__ void step(T x, T& L, T& R)
+    {
+        const T dn = x - b;
+        const T hs = minmod3<T>(d, T(0.25) * (x - a), dn);
+        L = l;
+        R = b - hs;
+        l = b + hs;
+        a = b;
+        b = x;
+        d = dn;
+    }
+};
+
+template <typename T>
+struct LineRec<T, true> {
+    static constexpr int NINIT = 5, AHEAD = 2;   // cells f0-3..f0+1 first; step f loads f+2
+    T a0, a1, s0, ip, lr;                        // a_f, a_f+1, slope_f, I_f-1/2, right edge_f-1
+    __device__ __forceinline__ void init(const T* x)
+    {
+        const T sm2 = ppm_slope<T>(x[0], x[1], x[2]);
+        const T sm1 = ppm_slope<T>(x[1], x[2], x[3]);
+        s0 = ppm_slope<T>(x[2], x[3], x[4]);
+        T lL = ppm_iface_s<T>(x[1], x[2], sm2, sm1);
+        ip = ppm_iface_s<T>(x[2], x[3], sm1, s0);
+        T lR = ip;
+        ppm_limit<T>(x[2], lL, lR);
+        lr = lR;
+        a0 = x[3];
+        a1 = x[4];
+    }
+    __device__ __forceinline__ void step(T x, T& L, T& R)
+    {
+        const T s1 = ppm_slope<T>(a0, a1, x);
+        const T in = ppm_iface_s<T>(a0, a1, s0, s1);
+        T rL = ip, rR = in;
+        ppm_limit<T>(a0, rL, rR);
+        L = lr;
+        R = rL;
+        lr = rR;
+        ip = in;
+        s0 = s1;
+        a0 = a1;
+        a1 = x;
+    }
+};
+
+// The same fluxes for K consecutive D-faces per thread (MC, or PPM when P): the thread
+// marches along D with one LineRec per reconstructed quantity, so each new face loads
+// one cell and reconstructs once (the per-face forms load four or six cells and
+// compute two MC slopes, or three interface values and two parabola limits).  Items:
+// chunks of K faces along D, x-fastest over the other directions (for D = 0 the chunks
+// themselves run along x).
+template <int D, bool M, typename T, bool P = false>
 __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
                                                 const double* psi_in, const double* alp_in, const FluxOut<T>& F,
                                                 double* const* vbar, T* const* Eh, long long t, int K)
 {
+    using Rec = LineRec<T, P>;
     const double* __restrict__ psi = M ? psi_in : nullptr;
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     constexpr int NV = 10;   // 8 primitives and the two transverse B
@@ -344,64 +411,50 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
     }
     const int f0 = g.ng[D] + q * K;                       // first face (padded index)
     const int f1 = min(f0 + K, g.ng[D] + g.n[D] + 1);     // one past the last
-    // the 10 reconstructed values of the cell at padded coordinate m along D
-    auto load = [&](int m, T* x, long long& rl) {
+    // the 10 reconstructed values of the cell at padded coordinate m along D (PPM's
+    // stencil reaches a third ghost: ext_cell maps it)
+    auto load = [&](int m, T* x) {
         int cs[3] = {c[0], c[1], c[2]};
-        cs[D] = m;
+        cs[D] = P ? ext_cell(g, D, m) : m;
         const long long mi = cell_at(g, cs);
-        rl = lin(g, cs[0], cs[1], cs[2]);
 #pragma unroll
         for (int v = 0; v < 8; v++) x[v] = prim.p[v][mi];
         T ip6 = T(1);
         if (psi) {
-            const T ps = (T)psi[rl], p2 = ps * ps;
+            const T ps = (T)psi[lin(g, cs[0], cs[1], cs[2])], p2 = ps * ps;
             ip6 = T(1) / (p2 * p2 * p2);
         }
         x[8] = (T)cell_qB_in(g, prim, bf, T1, cs, mi) * ip6;
         x[9] = (T)cell_qB_in(g, prim, bf, T2, cs, mi) * ip6;
     };
-    // window at the first face: cells f0-2, f0-1, f0
-    T A[NV], Bv[NV], Dp[NV], Lp[NV];
-    long long rm, r0;
+    Rec rec[NV];
     {
-        T x0[NV];
-        long long rx;
-        load(f0 - 2, x0, rx);
-        load(f0 - 1, A, rm);
-        load(f0, Bv, r0);
+        T w[Rec::NINIT][NV];
+#pragma unroll
+        for (int k = 0; k < Rec::NINIT; k++) load(f0 - Rec::NINIT + Rec::AHEAD + k, w[k]);
 #pragma unroll
         for (int v = 0; v < NV; v++) {
-            const T dm = A[v] - x0[v];
-            Dp[v] = Bv[v] - A[v];
-            Lp[v] = A[v] + minmod3<T>(dm, T(0.25) * (Bv[v] - x0[v]), Dp[v]);
+            T x[Rec::NINIT];
+#pragma unroll
+            for (int k = 0; k < Rec::NINIT; k++) x[k] = w[k][v];
+            rec[v].init(x);
         }
     }
+    int cm[3] = {c[0], c[1], c[2]};
+    cm[D] = f0 - 1;
+    long long rm = lin(g, cm[0], cm[1], cm[2]);
     for (int f = f0; f < f1; f++) {
-        T x3[NV];
-        long long r3;
-        load(f + 1, x3, r3);
+        T x[NV];
+        load(f + Rec::AHEAD, x);
         T prL[8], prR[8], BL[3], BR[3];
 #pragma unroll
-        for (int v = 0; v < NV; v++) {
-            const T dn = x3[v] - Bv[v];
-            const T hs = minmod3<T>(Dp[v], T(0.25) * (x3[v] - A[v]), dn);
-            const T R = Bv[v] - hs;
-            if (v < 8) {
-                prL[v] = Lp[v];
-                prR[v] = R;
-            } else {
-                BL[v == 8 ? T1 : T2] = Lp[v];
-                BR[v == 8 ? T1 : T2] = R;
-            }
-            Lp[v] = Bv[v] + hs;
-            A[v] = Bv[v];
-            Bv[v] = x3[v];
-            Dp[v] = dn;
-        }
+        for (int v = 0; v < 8; v++) rec[v].step(x[v], prL[v], prR[v]);
+        rec[8].step(x[8], BL[T1], BR[T1]);
+        rec[9].step(x[9], BL[T2], BR[T2]);
         c[D] = f;
-        face_flux<D, M, T>(g, bf, psi_in, alp_in, c, rm, r0, prL, prR, BL, BR, F, vbar, Eh);
+        const long long r0 = lin(g, c[0], c[1], c[2]);
+        face_flux<D, M, T>(g, bf, psi_in, alp_in, c, rm, r0, prL, prR, BL, BR, F, vbar, P ? nullptr : Eh);
         rm = r0;
-        r0 = r3;
     }
 }
 
@@ -543,17 +596,19 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     Eh[i0] = uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR);
 }
 
-// The same EMFs for K consecutive C-edges along B per thread (MC, both A and B active):
-// the A-direction reconstruction of E_C on each row of cells along B, and q_B^A, are
-// marched along B as in flux_march_item (one new row per edge instead of four), so each
-// edge computes one A-row, three one-cell B steps and its own q_B^B reconstruction.
-// The results are bitwise those of emf_item.  Items: chunks of K edges along B,
-// x-fastest over the other two directions (the chunks run along x when B = 0).
-template <int C, bool M, typename T>
+// The same EMFs for K consecutive C-edges along B per thread (MC, or PPM when P; A and
+// B both active): the A-direction reconstruction of E_C on each row of cells along B,
+// and q_B^A, are marched along B with LineRec (one new row per edge instead of four or
+// six), so each edge computes one A-row, three one-cell B steps and its own q_B^B
+// reconstruction.  The results are bitwise those of emf_item.  Items: chunks of K edges
+// along B, x-fastest over the other two directions (the chunks run along x when B = 0).
+template <int C, bool M, typename T, bool P = false>
 __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
                                                const double* psi_in, const double* alp_in, T* __restrict__ Eh,
                                                long long t, int K)
 {
+    using Rec = LineRec<T, P>;
+    constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? psi_in : nullptr;
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
@@ -571,64 +626,61 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
     for (int d = 0; d < 3; d++) c[d] = g.ng[d] + (d == B ? 0 : idx[d]);
     const int f0 = g.ng[B] + idx[B] * K;
     const int f1 = min(f0 + K, g.ng[B] + g.n[B] + 1);
+    // a face state along A from the NS values v (cells or faces c[A]-OFF..)
+    auto recA = [&](const T* v, T& L, T& R) {
+        if (P) ppm_face<T>(v, L, R);
+        else mc_face<T>(v[0], v[1], v[2], v[NS - 1], L, R);
+    };
     // row m along B: covariant E_C = psi^4 E^C reconstructed along A to the A-face c[A],
     // and q_B^A at that A-face
     auto row = [&](int m, T* x) {
-        T v[4];
+        const int mb = P ? ext_cell(g, B, m) : m;
+        T v[NS];
 #pragma unroll
-        for (int sa = 0; sa < 4; sa++) {
+        for (int sa = 0; sa < NS; sa++) {
             int cs[3] = {c[0], c[1], c[2]};
-            cs[B] = m;
-            cs[A] = c[A] + sa - 2;
+            cs[B] = mb;
+            cs[A] = P ? ext_cell(g, A, c[A] + sa - OFF) : c[A] + sa - OFF;
             const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
             const T p2 = ps * ps;
             v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
         }
-        mc_face<T>(v[0], v[1], v[2], v[3], x[0], x[1]);
+        recA(v, x[0], x[1]);
         int cs[3] = {c[0], c[1], c[2]};
-        cs[B] = m;
+        cs[B] = mb;
         x[2] = (T)bf.p[A][face_at(g, A, cs)];
     };
-    T Aw[3], Bw[3], Dp[3], Lp[3];
+    Rec rec[3];
     {
-        T x0[3];
-        row(f0 - 2, x0);
-        row(f0 - 1, Aw);
-        row(f0, Bw);
+        T w[Rec::NINIT][3];
+#pragma unroll
+        for (int k = 0; k < Rec::NINIT; k++) row(f0 - Rec::NINIT + Rec::AHEAD + k, w[k]);
 #pragma unroll
         for (int v = 0; v < 3; v++) {
-            const T dm = Aw[v] - x0[v];
-            Dp[v] = Bw[v] - Aw[v];
-            Lp[v] = Aw[v] + minmod3<T>(dm, T(0.25) * (Bw[v] - x0[v]), Dp[v]);
+            T x[Rec::NINIT];
+#pragma unroll
+            for (int k = 0; k < Rec::NINIT; k++) x[k] = w[k][v];
+            rec[v].init(x);
         }
     }
     for (int f = f0; f < f1; f++) {
         T x3[3];
-        row(f + 1, x3);
+        row(f + Rec::AHEAD, x3);
         T L[3], R[3];
 #pragma unroll
-        for (int v = 0; v < 3; v++) {
-            const T dn = x3[v] - Bw[v];
-            const T hs = minmod3<T>(Dp[v], T(0.25) * (x3[v] - Aw[v]), dn);
-            L[v] = Lp[v];
-            R[v] = Bw[v] - hs;
-            Lp[v] = Bw[v] + hs;
-            Aw[v] = Bw[v];
-            Bw[v] = x3[v];
-            Dp[v] = dn;
-        }
+        for (int v = 0; v < 3; v++) rec[v].step(x3[v], L[v], R[v]);
         c[B] = f;
         // q_B^B (B-faces) along A
         T qBbL, qBbR;
         {
-            T v[4];
+            T v[NS];
 #pragma unroll
-            for (int sa = 0; sa < 4; sa++) {
+            for (int sa = 0; sa < NS; sa++) {
                 int cs[3] = {c[0], c[1], c[2]};
-                cs[A] = c[A] + sa - 2;
+                cs[A] = P ? ext_cell(g, A, c[A] + sa - OFF) : c[A] + sa - OFF;
                 v[sa] = (T)bf.p[B][face_at(g, B, cs)];
             }
-            mc_face<T>(v[0], v[1], v[2], v[3], qBbL, qBbR);
+            recA(v, qBbL, qBbR);
         }
         const long long i0 = lin(g, c[0], c[1], c[2]);
         const long long sA = g.st[A], sB = g.st[B];

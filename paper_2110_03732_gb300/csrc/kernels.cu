@@ -3,9 +3,11 @@
 //
 //   k_implicit   Sec. 2.4: per-cell Newton on u coupled to the implicit E update;
 //                writes stage primitives and the stiff rate R = (q_E - q_E,base)/(a_ii dt)
-//   k_flux<D>    Sec. 2.1 + Sec. 5 defaults: MC reconstruction to the D-faces, HLL flux
-//                with the maximal-diffusivity speeds of Sec. 2.5
-//   k_emf<C>     Sec. 3.2 steps (i)-(vii): upwind (UCT-HLL) edge EMF hat{E}_C
+//   k_flux_march<D>  Sec. 2.1 + Sec. 5 defaults: MC (or PPM) reconstruction to the
+//                D-faces, marched along D, and the HLL flux with the maximal-diffusivity
+//                speeds of Sec. 2.5 (on flat 1-D / 2-D grids also the degenerate edge EMFs)
+//   k_emf_march<C>, k_emf<C>  Sec. 3.2 steps (i)-(vii): upwind (UCT-HLL) edge EMF
+//                hat{E}_C, marched along C + 2 when both transverse directions are active
 //   k_update<M>  flux divergence + non-stiff sources (Sec. 2.1) and the CT face update
 //                (Sec. 3.2); writes L, or folds it straight into the IMEX stage bases and
 //                the final combination (Sec. 2.3)
@@ -45,17 +47,8 @@ __global__ void __launch_bounds__(128) k_implicit_cc(Dims g, ImpArgs a)
 // face fluxes
 // ---------------------------------------------------------------------------
 
+// MC (or PPM) fluxes, K consecutive D-faces per thread (flux_march_item)
 template <int D, bool M, typename T, bool P = false>
-__global__ void __launch_bounds__(128) k_flux(Dims g, FluxArgs<T> a)
-{
-    const long long tot = (long long)(g.n[0] + (D == 0)) * (g.n[1] + (D == 1)) * (g.n[2] + (D == 2));
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x)
-        flux_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, t);
-}
-
-// MC fluxes, K consecutive D-faces per thread (flux_march_item)
-template <int D, bool M, typename T>
 __global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a, int K)
 {
     const long long nq = (g.n[D] + K) / K;
@@ -63,7 +56,7 @@ __global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a, int K
                                        : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        flux_march_item<D, M, T>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, a.Eh, t, K);
+        flux_march_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, a.Eh, t, K);
 }
 
 // ---------------------------------------------------------------------------
@@ -82,16 +75,16 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
         emf_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
 }
 
-// MC edge EMFs, K consecutive edges along B = C + 2 per thread (emf_march_item; A and
-// B active)
-template <int C, bool M, typename T>
+// MC (or PPM) edge EMFs, K consecutive edges along B = C + 2 per thread
+// (emf_march_item; A and B active)
+template <int C, bool M, typename T, bool P = false>
 __global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a, int K)
 {
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     const long long tot = (long long)((g.n[B] + K) / K) * g.n[C] * (g.n[A] + 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        emf_march_item<C, M, T>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t, K);
+        emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t, K);
 }
 
 // ideal-limit edge EMF (App. A) from the stored transport velocities
@@ -435,13 +428,14 @@ cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStr
 
 // resident 128-thread blocks per SM of a marching flux kernel (its register count
 // decides: about 2 for FP64, 4 for FP32), queried once
-template <int D, bool M, typename T>
+template <int D, bool M, typename T, bool P>
 static int march_blocks_per_sm()
 {
     static int nb = 0;
     if (nb < 1) {
         int q = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_flux_march<D, M, T>, 128, 0) != cudaSuccess || q < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_flux_march<D, M, T, P>, 128, 0) != cudaSuccess ||
+            q < 1)
             q = 1;
         nb = q;
     }
@@ -451,33 +445,34 @@ static int march_blocks_per_sm()
 // faces per thread: the largest of 8, 4, 2, 1 that still gives three quarters of a
 // full wave of resident blocks (a longer march saves more loads and slopes; a short
 // grid leaves SMs idle)
-template <int D, bool M, typename T>
+template <int D, bool M, typename T, bool P>
 static void flux_march_launch(const Dims& g, int nsm, cudaStream_t st, const FluxArgs<T>& a)
 {
     const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
                                    : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
-    const double want = 0.75 * nsm * march_blocks_per_sm<D, M, T>();
+    const double want = 0.75 * nsm * march_blocks_per_sm<D, M, T, P>();
     int K = 8;
     while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
     const int b = grid_for((long long)((g.n[D] + K) / K) * other, 128, nsm);
-    k_flux_march<D, M, T><<<b, 128, 0, st>>>(g, a, K);
+    k_flux_march<D, M, T, P><<<b, 128, 0, st>>>(g, a, K);
 }
 
-template <typename T>
+template <typename T, bool P>
 static void flux_dispatch(const Dims& g, int d, bool m, int nsm, cudaStream_t st, const FluxArgs<T>& a)
 {
-    if (d == 0) m ? flux_march_launch<0, true, T>(g, nsm, st, a) : flux_march_launch<0, false, T>(g, nsm, st, a);
-    else if (d == 1) m ? flux_march_launch<1, true, T>(g, nsm, st, a) : flux_march_launch<1, false, T>(g, nsm, st, a);
-    else m ? flux_march_launch<2, true, T>(g, nsm, st, a) : flux_march_launch<2, false, T>(g, nsm, st, a);
+    if (d == 0) m ? flux_march_launch<0, true, T, P>(g, nsm, st, a) : flux_march_launch<0, false, T, P>(g, nsm, st, a);
+    else if (d == 1) m ? flux_march_launch<1, true, T, P>(g, nsm, st, a) : flux_march_launch<1, false, T, P>(g, nsm, st, a);
+    else m ? flux_march_launch<2, true, T, P>(g, nsm, st, a) : flux_march_launch<2, false, T, P>(g, nsm, st, a);
 }
 
-template <int C, bool M, typename T>
+template <int C, bool M, typename T, bool P>
 static int emf_march_blocks_per_sm()
 {
     static int nb = 0;
     if (nb < 1) {
         int q = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_emf_march<C, M, T>, 128, 0) != cudaSuccess || q < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_emf_march<C, M, T, P>, 128, 0) != cudaSuccess ||
+            q < 1)
             q = 1;
         nb = q;
     }
@@ -486,34 +481,29 @@ static int emf_march_blocks_per_sm()
 
 // edges of direction C: marched along B when A and B are both active (K chosen as for
 // the flux kernels), one per thread otherwise
-template <int C, bool M, typename T>
+template <int C, bool M, typename T, bool P>
 static void emf_launch(const Dims& g, int nsm, cudaStream_t st, const EmfArgs<T>& a)
 {
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     if (!g.act[A] || !g.act[B]) {
         long long work = 1;
         for (int d = 0; d < 3; d++) work *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
-        k_emf<C, M, T><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+        k_emf<C, M, T, P><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
         return;
     }
     const long long other = (long long)g.n[C] * (g.n[A] + 1);
-    const double want = 0.75 * nsm * emf_march_blocks_per_sm<C, M, T>();
+    const double want = 0.75 * nsm * emf_march_blocks_per_sm<C, M, T, P>();
     int K = 8;
     while (K > 1 && (double)(((g.n[B] + K) / K) * other + 127) / 128 < want) K /= 2;
-    k_emf_march<C, M, T><<<grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, 0, st>>>(g, a, K);
+    k_emf_march<C, M, T, P><<<grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, 0, st>>>(g, a, K);
 }
 
-template <typename T>
+template <typename T, bool P>
 static void emf_dispatch(const Dims& g, int c, bool m, int nsm, cudaStream_t st, const EmfArgs<T>& a)
 {
-    if (c == 0) m ? emf_launch<0, true, T>(g, nsm, st, a) : emf_launch<0, false, T>(g, nsm, st, a);
-    else if (c == 1) m ? emf_launch<1, true, T>(g, nsm, st, a) : emf_launch<1, false, T>(g, nsm, st, a);
-    else m ? emf_launch<2, true, T>(g, nsm, st, a) : emf_launch<2, false, T>(g, nsm, st, a);
-}
-
-static long long flux_work(const Dims& g, int d)
-{
-    return (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
+    if (c == 0) m ? emf_launch<0, true, T, P>(g, nsm, st, a) : emf_launch<0, false, T, P>(g, nsm, st, a);
+    else if (c == 1) m ? emf_launch<1, true, T, P>(g, nsm, st, a) : emf_launch<1, false, T, P>(g, nsm, st, a);
+    else m ? emf_launch<2, true, T, P>(g, nsm, st, a) : emf_launch<2, false, T, P>(g, nsm, st, a);
 }
 
 static long long emf_work(const Dims& g, int c)
@@ -537,16 +527,8 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
     a.bf = bf;
     a.psi = psi;
     a.alp = alp;
-    const int b = grid_for(flux_work(g, d), 128, nsm);
-    if (ppm) {
-        // PPM (FP64 only)
-        const bool m = psi || alp;
-        if (d == 0) m ? k_flux<0, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<0, false, double, true><<<b, 128, 0, st>>>(g, a);
-        else if (d == 1) m ? k_flux<1, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<1, false, double, true><<<b, 128, 0, st>>>(g, a);
-        else m ? k_flux<2, true, double, true><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, double, true><<<b, 128, 0, st>>>(g, a);
-        return cudaGetLastError();
-    }
-    flux_dispatch<double>(g, d, psi || alp, nsm, st, a);
+    if (ppm) flux_dispatch<double, true>(g, d, psi || alp, nsm, st, a);
+    else flux_dispatch<double, false>(g, d, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
@@ -561,15 +543,8 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
     a.psi = psi;
     a.alp = alp;
     a.F = F;
-    const int b = grid_for(flux_work(g, d), 128, nsm);
-    if (ppm) {
-        const bool m = psi || alp;
-        if (d == 0) m ? k_flux<0, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<0, false, float, true><<<b, 128, 0, st>>>(g, a);
-        else if (d == 1) m ? k_flux<1, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<1, false, float, true><<<b, 128, 0, st>>>(g, a);
-        else m ? k_flux<2, true, float, true><<<b, 128, 0, st>>>(g, a) : k_flux<2, false, float, true><<<b, 128, 0, st>>>(g, a);
-        return cudaGetLastError();
-    }
-    flux_dispatch<float>(g, d, psi || alp, nsm, st, a);
+    if (ppm) flux_dispatch<float, true>(g, d, psi || alp, nsm, st, a);
+    else flux_dispatch<float, false>(g, d, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
@@ -582,15 +557,8 @@ cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi
     a.psi = psi;
     a.alp = alp;
     a.Eh = Eh;
-    const int b = grid_for(emf_work(g, c), 128, nsm);
-    if (ppm) {
-        const bool m = psi || alp;
-        if (c == 0) m ? k_emf<0, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<0, false, double, true><<<b, 128, 0, st>>>(g, a);
-        else if (c == 1) m ? k_emf<1, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<1, false, double, true><<<b, 128, 0, st>>>(g, a);
-        else m ? k_emf<2, true, double, true><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, double, true><<<b, 128, 0, st>>>(g, a);
-        return cudaGetLastError();
-    }
-    emf_dispatch<double>(g, c, psi || alp, nsm, st, a);
+    if (ppm) emf_dispatch<double, true>(g, c, psi || alp, nsm, st, a);
+    else emf_dispatch<double, false>(g, c, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
@@ -623,15 +591,8 @@ cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf
     a.psi = psi;
     a.alp = alp;
     a.Eh = Eh;
-    const int b = grid_for(emf_work(g, c), 128, nsm);
-    if (ppm) {
-        const bool m = psi || alp;
-        if (c == 0) m ? k_emf<0, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<0, false, float, true><<<b, 128, 0, st>>>(g, a);
-        else if (c == 1) m ? k_emf<1, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<1, false, float, true><<<b, 128, 0, st>>>(g, a);
-        else m ? k_emf<2, true, float, true><<<b, 128, 0, st>>>(g, a) : k_emf<2, false, float, true><<<b, 128, 0, st>>>(g, a);
-        return cudaGetLastError();
-    }
-    emf_dispatch<float>(g, c, psi || alp, nsm, st, a);
+    if (ppm) emf_dispatch<float, true>(g, c, psi || alp, nsm, st, a);
+    else emf_dispatch<float, false>(g, c, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 
