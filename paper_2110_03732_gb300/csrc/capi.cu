@@ -408,7 +408,11 @@ void glm_stage_args(grmhd_ctx* c, int i, double dt, GlmUpdateArgs* a)
         }
         a->wt[r] = c->tab.wt[r];
         a->w[r] = c->tab.w[r];
+        a->cL[r] = dt * c->tab.At[r * S + i];
+        a->cR[r] = dt * c->tab.A[r * S + i];
     }
+    a->cwL = dt * c->tab.wt[i];
+    a->cwR = dt * c->tab.w[i];
     for (int v = 0; v < 3; v++) a->R[v] = c->R[v];
     for (int v = 0; v < 8; v++) a->qn[v] = c->q[v];
     for (int v = 0; v < 3; v++) a->qn[8 + v] = c->bf[v];

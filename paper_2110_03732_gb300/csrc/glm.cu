@@ -24,65 +24,20 @@
 
 namespace grmhd {
 
-// P: PPM reconstruction (cells c-3..c+2) instead of MC (c-2..c+1)
-template <int D, bool M, bool P = false>
-__device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& a, long long t)
+// HLL fluxes of the 12 variables at the D-face with padded coordinates c (between the
+// cells of linear indices rm and r0 = c - e_D, c) from the reconstructed states:
+// prL / prR the 8 primitives, BL / BR the coordinate B = q_B / psi^6, phL / phR
+// Phi = q_Phi / psi^6.  Writes twice the flux (the update folds the 1/2).
+template <int D, bool M>
+__device__ __forceinline__ void glm_face_flux(const Dims& g, const GlmFluxArgs& a, long long rm, long long r0,
+                                              const double* prL, const double* prR, const double* BL,
+                                              const double* BR, double phL, double phR)
 {
-    constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? a.psi : nullptr;
     const double* __restrict__ alp = M ? a.alp : nullptr;
     constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
-    const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1);
-    int c[3];
-    c[0] = g.ng[0] + (int)(t % e0);
-    c[1] = g.ng[1] + (int)((t / e0) % e1);
-    c[2] = g.ng[2] + (int)(t / ((long long)e0 * e1));
-    long long mi[NS], ri[NS];
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        int cs[3] = {c[0], c[1], c[2]};
-        cs[D] = P ? ext_cell(g, D, c[D] + s - OFF) : c[D] + s - OFF;
-        mi[s] = cell_at(g, cs);
-        ri[s] = lin(g, cs[0], cs[1], cs[2]);
-    }
-    double ip6[NS];
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        const double ps = psi ? psi[ri[s]] : 1.0;
-        const double p2 = ps * ps;
-        ip6[s] = 1.0 / (p2 * p2 * p2);
-    }
-    // MC or PPM face states of w[0..NS-1]
-    auto rec = [&](const double* w, double& L, double& R) {
-        if (P) ppm_face<double>(w, L, R);
-        else mc_face<double>(w[0], w[1], w[2], w[NS - 1], L, R);
-    };
-    double prL[8], prR[8], BL[3], BR[3], phL, phR;
-#pragma unroll
-    for (int v = 0; v < 8; v++) {
-        const double* __restrict__ x = a.prim[v];
-        double w[NS];
-#pragma unroll
-        for (int s = 0; s < NS; s++) w[s] = x[mi[s]];
-        rec(w, prL[v], prR[v]);
-    }
-#pragma unroll
-    for (int e = 0; e < 3; e++) {
-        const double* __restrict__ x = a.qB[e];
-        double w[NS];
-#pragma unroll
-        for (int s = 0; s < NS; s++) w[s] = x[mi[s]] * ip6[s];
-        rec(w, BL[e], BR[e]);
-    }
-    {
-        const double* __restrict__ x = a.qphi;
-        double w[NS];
-#pragma unroll
-        for (int s = 0; s < NS; s++) w[s] = x[mi[s]] * ip6[s];
-        rec(w, phL, phR);
-    }
-    const double psf = psi ? 0.5 * (psi[ri[OFF - 1]] + psi[ri[OFF]]) : 1.0;
-    const double alf = alp ? 0.5 * (alp[ri[OFF - 1]] + alp[ri[OFF]]) : 1.0;
+    const double psf = psi ? 0.5 * (psi[rm] + psi[r0]) : 1.0;
+    const double alf = alp ? 0.5 * (alp[rm] + alp[r0]) : 1.0;
     const double pf2 = psf * psf, pf4 = pf2 * pf2, pf6 = pf4 * pf2;
     FaceState sL, sR;
     face_state<double>(prL, BL, D, psf, alf, g.gh, sL);
@@ -90,10 +45,9 @@ __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& 
     // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity); with equal
     // speeds (c f_L + c f_R - c^2 (q_R - q_L)) / 2c = (f_L + f_R - c (q_R - q_L)) / 2
     const double cs = alf / pf2;
-    const long long o = lin(g, c[0], c[1], c[2]);
+    const long long o = r0;
 #pragma unroll
-    for (int v = 0; v < 8; v++)
-        a.F[v][o] = (sL.f[v] + sR.f[v] - cs * (sR.q[v] - sL.q[v])) * 0.5;
+    for (int v = 0; v < 8; v++) a.F[v][o] = sL.f[v] + sR.f[v] - cs * (sR.q[v] - sL.q[v]);
     // q_B^j = psi^6 B^j with (f_B^j)^D = eta^{jDk} alpha psi^4 E^k: 0, -alpha psi^4 E^D2,
     // +alpha psi^4 E^D1 for j = D, D1, D2; q_Phi = psi^6 Phi with (f_Phi)^D = alpha q_B^D
     const double ap4 = alf * pf4;
@@ -115,17 +69,76 @@ __device__ __forceinline__ void glm_flux_item(const Dims& g, const GlmFluxArgs& 
     fL[3] = alf * qL[D];
     fR[3] = alf * qR[D];
 #pragma unroll
-    for (int v = 0; v < 4; v++)
-        a.F[8 + v][o] = (fL[v] + fR[v] - cs * (qR[v] - qL[v])) * 0.5;
+    for (int v = 0; v < 4; v++) a.F[8 + v][o] = fL[v] + fR[v] - cs * (qR[v] - qL[v]);
+}
+
+// MC (or PPM when P) reconstruction of the 8 primitives, B^i = q_B^i / psi^6 and
+// Phi = q_Phi / psi^6 to K consecutive D-faces per thread, marched along D with one
+// LineRec per quantity (as flux_march_item)
+template <int D, bool M, bool P>
+__device__ __forceinline__ void glm_flux_march_item(const Dims& g, const GlmFluxArgs& a, long long t, int K)
+{
+    using Rec = LineRec<double, P>;
+    const double* __restrict__ psi = M ? a.psi : nullptr;
+    constexpr int NV = 12;
+    int c[3], f0, f1;
+    march_coords<D>(g, t, K, c, f0, f1);
+    auto load = [&](int m, double* x) {
+        int cs[3] = {c[0], c[1], c[2]};
+        cs[D] = P ? ext_cell(g, D, m) : m;
+        const long long mi = cell_at(g, cs);
+#pragma unroll
+        for (int v = 0; v < 8; v++) x[v] = a.prim[v][mi];
+        double ip6 = 1.0;
+        if (psi) {
+            const double ps = psi[lin(g, cs[0], cs[1], cs[2])], p2 = ps * ps;
+            ip6 = 1.0 / (p2 * p2 * p2);
+        }
+#pragma unroll
+        for (int e = 0; e < 3; e++) x[8 + e] = a.qB[e][mi] * ip6;
+        x[11] = a.qphi[mi] * ip6;
+    };
+    Rec rec[NV];
+    {
+        double w[Rec::NINIT][NV];
+#pragma unroll
+        for (int k = 0; k < Rec::NINIT; k++) load(f0 - Rec::NINIT + Rec::AHEAD + k, w[k]);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+            double x[Rec::NINIT];
+#pragma unroll
+            for (int k = 0; k < Rec::NINIT; k++) x[k] = w[k][v];
+            rec[v].init(x);
+        }
+    }
+    int cm[3] = {c[0], c[1], c[2]};
+    cm[D] = f0 - 1;
+    long long rm = lin(g, cm[0], cm[1], cm[2]);
+    for (int f = f0; f < f1; f++) {
+        double x[NV];
+        load(f + Rec::AHEAD, x);
+        double prL[8], prR[8], BL[3], BR[3], phL, phR;
+#pragma unroll
+        for (int v = 0; v < 8; v++) rec[v].step(x[v], prL[v], prR[v]);
+#pragma unroll
+        for (int e = 0; e < 3; e++) rec[8 + e].step(x[8 + e], BL[e], BR[e]);
+        rec[11].step(x[11], phL, phR);
+        c[D] = f;
+        const long long r0 = lin(g, c[0], c[1], c[2]);
+        glm_face_flux<D, M>(g, a, rm, r0, prL, prR, BL, BR, phL, phR);
+        rm = r0;
+    }
 }
 
 template <int D, bool M, bool P = false>
-__global__ void __launch_bounds__(128) k_glm_flux(Dims g, GlmFluxArgs a)
+__global__ void __launch_bounds__(128) k_glm_flux(Dims g, GlmFluxArgs a, int K)
 {
-    const long long tot = (long long)(g.n[0] + (D == 0)) * (g.n[1] + (D == 1)) * (g.n[2] + (D == 2));
+    const long long nq = (g.n[D] + K) / K;
+    const long long tot = nq * (D == 0 ? (long long)g.n[1] * g.n[2]
+                                       : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        glm_flux_item<D, M, P>(g, a, t);
+        glm_flux_march_item<D, M, P>(g, a, t, K);
 }
 
 __device__ __forceinline__ void glm_out(const GlmUpdateArgs& a, int v, long long o, double L, bool has_r)
@@ -134,14 +147,18 @@ __device__ __forceinline__ void glm_out(const GlmUpdateArgs& a, int v, long long
         a.L[v][o] = L;
         return;
     }
+    // as out_value: host-formed dt products, q^n read at stage 0 only
     const double r = has_r ? a.R[v - 5][o] : 0.0;
-    const double qn = a.qn[v][o];
+    const double qn = a.stage == 0 ? a.qn[v][o] : 0.0;
     for (int k = a.stage + 1; k < a.s; k++) {
         const double prev = a.stage == 0 ? qn : a.base[k][v][o];
-        a.base[k][v][o] = prev + a.dt * (a.At[k][a.stage] * L + a.A[k][a.stage] * r);
+        double nb = prev + a.cL[k] * L;
+        if (has_r) nb += a.cR[k] * r;
+        a.base[k][v][o] = nb;
     }
     const double prev = a.stage == 0 ? qn : a.acc[v][o];
-    const double nv = prev + a.dt * (a.wt[a.stage] * L + a.w[a.stage] * r);
+    double nv = prev + a.cwL * L;
+    if (has_r) nv += a.cwR * r;
     if (a.stage == a.s - 1) a.qn[v][o] = nv;
     else a.acc[v][o] = nv;
 }
@@ -163,10 +180,11 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
     for (int d = 0; d < 3; d++) {
         if (!g.act[d]) continue;
         const long long o1 = o + g.st[d];
+        const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
 #pragma unroll
         for (int v = 0; v < 12; v++) {
             const double* __restrict__ Fv = a.F[d][v];
-            Lc[v] -= (Fv[o1] - Fv[o]) * g.idx[d];
+            Lc[v] -= (Fv[o1] - Fv[o]) * hidx;
         }
     }
     cell_sources<true>(g, a.prim, a.qB, psi, alp, c, o, Lc);
@@ -218,20 +236,44 @@ static int glm_grid(long long work, int threads, int nsm)
     return (int)b;
 }
 
+template <int D, bool M, bool P>
+static int glm_blocks_per_sm()
+{
+    static int nb = 0;
+    if (nb < 1) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_glm_flux<D, M, P>, 128, 0) != cudaSuccess || q < 1)
+            q = 1;
+        nb = q;
+    }
+    return nb;
+}
+
+// faces per thread as for the staggered-field flux kernels
+template <int D, bool M, bool P>
+static void glm_flux_launch(const Dims& g, const GlmFluxArgs& a, int nsm, cudaStream_t st)
+{
+    const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
+                                   : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
+    const double want = 0.75 * nsm * glm_blocks_per_sm<D, M, P>();
+    int K = 8;
+    while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
+    k_glm_flux<D, M, P><<<glm_grid((long long)((g.n[D] + K) / K) * other, 128, nsm), 128, 0, st>>>(g, a, K);
+}
+
+template <bool P>
+static void glm_flux_dispatch(const Dims& g, int d, bool m, const GlmFluxArgs& a, int nsm, cudaStream_t st)
+{
+    if (d == 0) m ? glm_flux_launch<0, true, P>(g, a, nsm, st) : glm_flux_launch<0, false, P>(g, a, nsm, st);
+    else if (d == 1) m ? glm_flux_launch<1, true, P>(g, a, nsm, st) : glm_flux_launch<1, false, P>(g, a, nsm, st);
+    else m ? glm_flux_launch<2, true, P>(g, a, nsm, st) : glm_flux_launch<2, false, P>(g, a, nsm, st);
+}
+
 cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st, bool ppm)
 {
-    const long long work = (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
-    const int b = glm_grid(work, 128, nsm);
     const bool m = a.psi || a.alp;
-    if (ppm) {
-        if (d == 0) m ? k_glm_flux<0, true, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<0, false, true><<<b, 128, 0, st>>>(g, a);
-        else if (d == 1) m ? k_glm_flux<1, true, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<1, false, true><<<b, 128, 0, st>>>(g, a);
-        else m ? k_glm_flux<2, true, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<2, false, true><<<b, 128, 0, st>>>(g, a);
-        return cudaGetLastError();
-    }
-    if (d == 0) m ? k_glm_flux<0, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<0, false><<<b, 128, 0, st>>>(g, a);
-    else if (d == 1) m ? k_glm_flux<1, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<1, false><<<b, 128, 0, st>>>(g, a);
-    else m ? k_glm_flux<2, true><<<b, 128, 0, st>>>(g, a) : k_glm_flux<2, false><<<b, 128, 0, st>>>(g, a);
+    if (ppm) glm_flux_dispatch<true>(g, d, m, a, nsm, st);
+    else glm_flux_dispatch<false>(g, d, m, a, nsm, st);
     return cudaGetLastError();
 }
 

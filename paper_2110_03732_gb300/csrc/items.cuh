@@ -376,23 +376,14 @@ struct LineRec<T, true> {
     }
 };
 
-// The same fluxes for K consecutive D-faces per thread (MC, or PPM when P): the thread
-// marches along D with one LineRec per reconstructed quantity, so each new face loads
-// one cell and reconstructs once (the per-face forms load four or six cells and
-// compute two MC slopes, or three interface values and two parabola limits).  Items:
-// chunks of K faces along D, x-fastest over the other directions (for D = 0 the chunks
-// themselves run along x).
-template <int D, bool M, typename T, bool P = false>
-__device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
-                                                const double* psi_in, const double* alp_in, const FluxOut<T>& F,
-                                                double* const* vbar, T* const* Eh, long long t, int K)
+// item t of a face march along D in chunks of K: the padded coordinates c of the
+// line (c[D] unset) and its faces f0 .. f1-1 (padded indices).  Chunks along D,
+// x-fastest over the other directions; for D = 0 the chunks themselves run along x.
+template <int D>
+__device__ __forceinline__ void march_coords(const Dims& g, long long t, int K, int* c, int& f0, int& f1)
 {
-    using Rec = LineRec<T, P>;
-    const double* __restrict__ psi = M ? psi_in : nullptr;
-    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    constexpr int NV = 10;   // 8 primitives and the two transverse B
     const int nq = (g.n[D] + 1 + K - 1) / K;
-    int c[3], q;
+    int q;
     if (D == 0) {
         q = (int)(t % nq);
         const long long r = t / nq;
@@ -409,8 +400,28 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
         c[1] = g.ng[1] + (int)(r % g.n[1]);
         q = (int)(r / g.n[1]);
     }
-    const int f0 = g.ng[D] + q * K;                       // first face (padded index)
-    const int f1 = min(f0 + K, g.ng[D] + g.n[D] + 1);     // one past the last
+    c[D] = 0;
+    f0 = g.ng[D] + q * K;
+    f1 = min(f0 + K, g.ng[D] + g.n[D] + 1);
+}
+
+// The same fluxes for K consecutive D-faces per thread (MC, or PPM when P): the thread
+// marches along D with one LineRec per reconstructed quantity, so each new face loads
+// one cell and reconstructs once (the per-face forms load four or six cells and
+// compute two MC slopes, or three interface values and two parabola limits).  Items:
+// chunks of K faces along D, x-fastest over the other directions (for D = 0 the chunks
+// themselves run along x).
+template <int D, bool M, typename T, bool P = false>
+__device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
+                                                const double* psi_in, const double* alp_in, const FluxOut<T>& F,
+                                                double* const* vbar, T* const* Eh, long long t, int K)
+{
+    using Rec = LineRec<T, P>;
+    const double* __restrict__ psi = M ? psi_in : nullptr;
+    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
+    constexpr int NV = 10;   // 8 primitives and the two transverse B
+    int c[3], f0, f1;
+    march_coords<D>(g, t, K, c, f0, f1);
     // the 10 reconstructed values of the cell at padded coordinate m along D (PPM's
     // stencil reaches a third ghost: ext_cell maps it)
     auto load = [&](int m, T* x) {

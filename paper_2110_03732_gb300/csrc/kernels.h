@@ -129,7 +129,7 @@ struct GlmFluxArgs {
     const double* qphi;     // stage q_Phi
     const double* psi;
     const double* alp;
-    double* F[12];          // face fluxes of the 12 variables along the launch direction
+    double* F[12];          // twice the face fluxes of the 12 variables along the launch direction
 };
 
 struct GlmUpdateArgs {
@@ -138,7 +138,8 @@ struct GlmUpdateArgs {
     double dt;
     double kappa;           // kappa_B, the damping of Phi
     double At[4][4], A[4][4], wt[4], w[4];
-    const double* F[3][12];
+    double cL[4], cR[4], cwL, cwR;   // the dt products of UpdateArgs
+    const double* F[3][12];  // twice the face fluxes
     const double* prim[8];
     const double* qB[3];
     const double* qphi;
