@@ -31,12 +31,14 @@ struct ProbStage {
     CP3 bfs;
     const double* psi;
     const double* alp;
-    FluxOut<double> F64[3];
-    FluxOut<float> F32[3];
+    FluxOut<double> F64[3];   // fluxes and edge EMFs: FP64 for both precisions
     double* Eh64[3];
-    float* Eh32[3];
+    double* fe64[3][3];   // [D][C]: edge EMFs written by the D-flux kernel (flat 1-D / 2-D)
     UpdateArgs upd;
 };
+
+// faces (edges) per item of the batched flux (EMF) kernels: each item marches K of them
+constexpr int kMarch = 4;
 
 struct Chunk {
     int prob;
@@ -76,19 +78,7 @@ __global__ void __launch_bounds__(256) kb_implicit(const ProbStage* __restrict__
 template <typename T> __device__ __forceinline__ const PrimIn<T>& prim_of(const ProbStage& ps);
 template <> __device__ __forceinline__ const PrimIn<double>& prim_of<double>(const ProbStage& ps) { return ps.p64; }
 template <> __device__ __forceinline__ const PrimIn<float>& prim_of<float>(const ProbStage& ps) { return ps.p32; }
-template <typename T> __device__ __forceinline__ const FluxOut<T>& flux_of(const ProbStage& ps, int d);
-template <> __device__ __forceinline__ const FluxOut<double>& flux_of<double>(const ProbStage& ps, int d)
-{
-    return ps.F64[d];
-}
-template <> __device__ __forceinline__ const FluxOut<float>& flux_of<float>(const ProbStage& ps, int d)
-{
-    return ps.F32[d];
-}
-template <typename T> __device__ __forceinline__ T* emf_of(const ProbStage& ps, int c);
-template <> __device__ __forceinline__ double* emf_of<double>(const ProbStage& ps, int c) { return ps.Eh64[c]; }
-template <> __device__ __forceinline__ float* emf_of<float>(const ProbStage& ps, int c) { return ps.Eh32[c]; }
-
+// item t: kMarch consecutive D-faces (flux_march_item)
 template <int D, bool M, typename T>
 __global__ void __launch_bounds__(256) kb_flux(const ProbStage* __restrict__ P, int s, int stage,
                                               const Chunk* __restrict__ ch, int nch)
@@ -97,10 +87,13 @@ __global__ void __launch_bounds__(256) kb_flux(const ProbStage* __restrict__ P, 
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
         for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x)
-            flux_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, flux_of<T>(ps, D), nullptr, t);
+            flux_march_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.F64[D], nullptr, ps.fe64[D], t,
+                                     kMarch);
     }
 }
 
+// item t: kMarch consecutive C-edges along C + 2 when both transverse directions are
+// active (emf_march_item), else one edge (emf_item)
 template <int C, bool M, typename T>
 __global__ void __launch_bounds__(256) kb_emf(const ProbStage* __restrict__ P, int s, int stage,
                                              const Chunk* __restrict__ ch, int nch)
@@ -108,34 +101,42 @@ __global__ void __launch_bounds__(256) kb_emf(const ProbStage* __restrict__ P, i
     for (int i = blockIdx.x; i < nch; i += gridDim.x) {
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
-        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x)
-            emf_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, emf_of<T>(ps, C), t);
+        const bool march = ps.g.act[(C + 1) % 3] && ps.g.act[(C + 2) % 3];
+        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) {
+            if (march) emf_march_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t, kMarch);
+            else emf_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t);
+        }
     }
 }
 
-template <bool M, typename T>
+template <bool M>
 __global__ void __launch_bounds__(256) kb_update(const ProbStage* __restrict__ P, int s, int stage,
                                                 const Chunk* __restrict__ ch, int nch)
 {
     for (int i = blockIdx.x; i < nch; i += gridDim.x) {
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
-        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) update_item<M, T>(ps.g, ps.upd, t);
+        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) update_item<M>(ps.g, ps.upd, t);
     }
 }
 
 // items of one problem for a work-list kind (0 = not run)
-long long items_of(const Dims& g, int kind)
+long long items_of(const grmhd_ctx* cx, int kind)
 {
+    const Dims& g = ctx_dims(cx);
     if (kind == WL_IMP) return (long long)g.n[0] * g.n[1] * g.n[2];
     if (kind >= WL_FLUX && kind < WL_FLUX + 3) {
         const int d = kind - WL_FLUX;
         if (!g.act[d]) return 0;
-        return (long long)(g.n[0] + (d == 0)) * (g.n[1] + (d == 1)) * (g.n[2] + (d == 2));
+        long long other = 1;
+        for (int e = 0; e < 3; e++)
+            if (e != d) other *= g.n[e];
+        return (long long)((g.n[d] + kMarch) / kMarch) * other;
     }
     if (kind >= WL_EMF && kind < WL_EMF + 3) {
-        const int c = kind - WL_EMF;
-        if (!(g.act[(c + 1) % 3] || g.act[(c + 2) % 3])) return 0;
+        const int c = kind - WL_EMF, a = (c + 1) % 3, bd = (c + 2) % 3;
+        if (!(g.act[a] || g.act[bd]) || ctx_fused_emf_dir(cx, c) >= 0) return 0;
+        if (g.act[a] && g.act[bd]) return (long long)((g.n[bd] + kMarch) / kMarch) * g.n[c] * (g.n[a] + 1);
         long long w = 1;
         for (int d = 0; d < 3; d++) w *= (d == c) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
         return w;
@@ -174,7 +175,7 @@ grmhd_status build_lists(grmhd_batch* b, cudaStream_t st)
             for (int p = 0; p < b->n; p++) {
                 const grmhd_ctx* c = b->ctx[p];
                 if ((ctx_metric(c) ? 1 : 0) != m) continue;
-                const long long w = items_of(ctx_dims(c), kind);
+                const long long w = items_of(c, kind);
                 for (long long a = 0; a < w; a += b->cfg[kind].items) {
                     Chunk k;
                     k.prob = p;
@@ -207,19 +208,18 @@ void fill_desc(grmhd_batch* b, int p, double dt)
         ps.psi = ps.imp.psi;
         ps.alp = ps.imp.alp;
         for (int d = 0; d < 3; d++) {
-            for (int v = 0; v < 8; v++) {
-                ps.F64[d].p[v] = ctx_flux64(c, d, v);
-                ps.F32[d].p[v] = ctx_flux32(c, d, v);
-            }
+            for (int v = 0; v < 8; v++) ps.F64[d].p[v] = ctx_flux64(c, d, v);
             ps.Eh64[d] = ctx_emf64(c, d);
-            ps.Eh32[d] = ctx_emf32(c, d);
         }
-        ps.upd.f32 = b->mixed ? 1 : 0;
+        for (int k = 0; k < 3; k++) {
+            const int d = ctx_fused_emf_dir(c, k);
+            if (d < 0) continue;
+            ps.fe64[d][k] = ctx_emf64(c, k);
+        }
         for (int d = 0; d < 3; d++)
             for (int v = 0; v < 8; v++)
-                ps.upd.F[d][v] = !ps.g.act[d] ? nullptr
-                                 : b->mixed ? (const void*)ps.F32[d].p[v] : (const void*)ps.F64[d].p[v];
-        for (int k = 0; k < 3; k++) ps.upd.Eh[k] = b->mixed ? (const void*)ps.Eh32[k] : (const void*)ps.Eh64[k];
+                ps.upd.F[d][v] = !ps.g.act[d] ? nullptr : ps.F64[d].p[v];
+        for (int k = 0; k < 3; k++) ps.upd.Eh[k] = ps.Eh64[k];
         for (int v = 0; v < 8; v++) ps.upd.prim[v] = ps.imp.prim.p[v];
         for (int k = 0; k < 3; k++) ps.upd.bf[k] = ps.bfs.p[k];
         ps.upd.psi = ps.psi;
@@ -280,13 +280,8 @@ cudaError_t launch_stage(grmhd_batch* b, int stage, cudaStream_t st, unsigned ma
         if (!(mask >> kind & 1u) || !b->cnt[kind][m]) continue;
         const Chunk* ch = b->d_chunks + b->off[kind][m];
         const int nch = b->cnt[kind][m], th = b->cfg[kind].threads, gr = grid_of(b, kind, m);
-        if (b->mixed) {
-            if (m) kb_update<true, float><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
-            else kb_update<false, float><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
-        } else {
-            if (m) kb_update<true, double><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
-            else kb_update<false, double><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
-        }
+        if (m) kb_update<true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        else kb_update<false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
     }
     return cudaGetLastError();
 }
@@ -296,7 +291,7 @@ size_t chunk_capacity(grmhd_ctx* const* ctxs, int n)
     size_t cap = 0;
     for (int kind = 0; kind < WL_KINDS; kind++)
         for (int p = 0; p < n; p++) {
-            const long long w = items_of(ctx_dims(ctxs[p]), kind);
+            const long long w = items_of(ctxs[p], kind);
             cap += (size_t)((w + kMinItems - 1) / kMinItems);
         }
     return cap;

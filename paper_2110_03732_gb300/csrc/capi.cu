@@ -59,8 +59,8 @@ struct grmhd_ctx_s {
     double* F[3][12];      // FP64 face fluxes (8; 12 for GLM)
     double* Eh[3];
     float* p32[11];      // mixed precision: FP32 stage primitives + cell-centred q_B
-    float* F32[3][8];    // mixed precision: FP32 face fluxes
-    float* Eh32[3];      // mixed precision: FP32 edge EMFs
+    double* vblk[3][2];  // per active direction, two FP64 arrays (the ideal-limit EMF's
+                         // transport velocities)
     float* hs[4][3];     // per stage: its last Newton root u (orthonormal, FP32) ...
     float* hd[4][3];     // ... and that root minus the one before (the start guess is
                          // their sum: a linear extrapolation over steps)
@@ -77,7 +77,7 @@ struct grmhd_ctx_s {
     bool glm;            // GLM cleaning with cell-centred B (Sec. 3.1) instead of CT
     bool ideal;          // ideal-limit edge EMF (App. A)
     bool ppm;            // PPM reconstruction instead of MC
-    double* vbar[3][2];  // its transport velocities at the d-faces (FP32 scratch block)
+    double* vbar[3][2];  // its transport velocities at the d-faces (vblk, or NULL)
     double kappa;        // GLM damping kappa_B
     double* qphi;        // GLM: bound q_Phi
     long long launches;
@@ -180,11 +180,10 @@ size_t carve(grmhd_ctx* c, const Dims& g, int s, int ndim, char* base, bool glm 
     for (int d = 0; d < ndim; d++)
         for (int v = 0; v < 8; v++) { char* p = take(arr); if (c) c->F[d][v] = (double*)p; }
     for (int v = 0; v < 3; v++) { char* p = take(arr); if (c) c->Eh[v] = (double*)p; }
+    for (int d = 0; d < ndim; d++)
+        for (int k = 0; k < 2; k++) { char* p = take(arr); if (c) c->vblk[d][k] = (double*)p; }
     const size_t arr32 = round_up(sizeof(float) * (size_t)g.ncell);
     for (int v = 0; v < 11; v++) { char* p = take(arr32); if (c) c->p32[v] = (float*)p; }
-    for (int d = 0; d < ndim; d++)
-        for (int v = 0; v < 8; v++) { char* p = take(arr32); if (c) c->F32[d][v] = (float*)p; }
-    for (int v = 0; v < 3; v++) { char* p = take(arr32); if (c) c->Eh32[v] = (float*)p; }
     for (int k = 0; k < s; k++)
         for (int v = 0; v < 3; v++) {
             char* p = take(arr32);
@@ -309,16 +308,13 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
         double* eh64[3] = {nullptr, nullptr, nullptr};
-        float* eh32[3] = {nullptr, nullptr, nullptr};
         for (int k = 0; k < 3; k++)
-            if (fused_emf_dir(c, k) == d) {
-                eh64[k] = c->Eh[k];
-                eh32[k] = c->Eh32[k];
-            }
+            if (fused_emf_dir(c, k) == d) eh64[k] = c->Eh[k];
         if (c->mixed) {
-            FluxOut<float> fo;
-            for (int v = 0; v < 8; v++) fo.p[v] = c->F32[d][v];
-            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm, eh32);
+            // FP32 arithmetic, FP64 results (widened once when stored)
+            FluxOut<double> fo;
+            for (int v = 0; v < 8; v++) fo.p[v] = c->F[d][v];
+            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm, eh64);
         } else {
             e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
                             c->ppm, eh64);
@@ -330,18 +326,16 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     for (int k = 0; k < 3; k++) {
         if (!emf_needed(g, k) || fused_emf_dir(c, k) >= 0) continue;
         const int tk = tbegin(c, KIND_EMF, st);
-        if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh32[k], c->nsm, st, c->ppm);
+        if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
         else if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
         else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "emf kernel");
     }
-    a.f32 = c->mixed ? 1 : 0;
     for (int d = 0; d < 3; d++)
-        for (int v = 0; v < 8; v++)
-            a.F[d][v] = !g.act[d] ? nullptr : c->mixed ? (const void*)c->F32[d][v] : (const void*)c->F[d][v];
-    for (int k = 0; k < 3; k++) a.Eh[k] = c->mixed ? (const void*)c->Eh32[k] : (const void*)c->Eh[k];
+        for (int v = 0; v < 8; v++) a.F[d][v] = !g.act[d] ? nullptr : c->F[d][v];
+    for (int k = 0; k < 3; k++) a.Eh[k] = c->Eh[k];
     for (int v = 0; v < 8; v++) a.prim[v] = prim.p[v];
     for (int k = 0; k < 3; k++) a.bf[k] = bfs.p[k];
     a.psi = c->psi;
@@ -582,12 +576,9 @@ grmhd_status grmhd_bind(grmhd_ctx* c, double* const* q, double* const* bface, vo
     const size_t need = carve(nullptr, c->g, c->tab.s, c->grid.ndim, nullptr, c->glm);
     if (scratch_bytes < need) return fail(GRMHD_ERR_SCRATCH, "scratch smaller than grmhd_scratch_bytes");
     carve(c, c->g, c->tab.s, c->grid.ndim, (char*)scratch, c->glm);
-    // ideal-limit EMF (FP64 only): its two transport-velocity arrays per direction take
-    // the FP32 flux block of that direction, which the FP64 path leaves unused (each
-    // pair of consecutive FP32 arrays spans at least one FP64 array)
+    // ideal-limit EMF: its two transport-velocity arrays per direction
     for (int d = 0; d < 3; d++)
-        for (int k = 0; k < 2; k++)
-            c->vbar[d][k] = (c->ideal && d < c->grid.ndim) ? (double*)c->F32[d][2 * k] : nullptr;
+        for (int k = 0; k < 2; k++) c->vbar[d][k] = (c->ideal && d < c->grid.ndim) ? c->vblk[d][k] : nullptr;
     for (int v = 0; v < 8; v++) c->q[v] = q[v];
     for (int v = 0; v < 3; v++) c->bf[v] = bface[v];
     c->bound = true;
@@ -967,9 +958,8 @@ void ctx_stage_args(grmhd_ctx* c, int i, double dt, ImpArgs* ia, UpdateArgs* a)
 
 float* ctx_p32(grmhd_ctx* c, int v) { return c->p32[v]; }
 double* ctx_flux64(grmhd_ctx* c, int d, int v) { return d < c->grid.ndim ? c->F[d][v] : nullptr; }
-float* ctx_flux32(grmhd_ctx* c, int d, int v) { return d < c->grid.ndim ? c->F32[d][v] : nullptr; }
 double* ctx_emf64(grmhd_ctx* c, int k) { return c->Eh[k]; }
-float* ctx_emf32(grmhd_ctx* c, int k) { return c->Eh32[k]; }
+int ctx_fused_emf_dir(const grmhd_ctx* c, int k) { return fused_emf_dir(c, k); }
 
 cudaError_t ctx_copy_fixed_faces(grmhd_ctx* c, cudaStream_t st)
 {

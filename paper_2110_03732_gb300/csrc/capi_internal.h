@@ -24,9 +24,9 @@ bool ctx_same_scheme(const grmhd_ctx* a, const grmhd_ctx* b);
 void ctx_stage_args(grmhd_ctx* c, int i, double dt, grmhd::ImpArgs* imp, grmhd::UpdateArgs* upd);
 float* ctx_p32(grmhd_ctx* c, int v);
 double* ctx_flux64(grmhd_ctx* c, int d, int v);
-float* ctx_flux32(grmhd_ctx* c, int d, int v);
 double* ctx_emf64(grmhd_ctx* c, int k);
-float* ctx_emf32(grmhd_ctx* c, int k);
+// the flux direction whose kernel writes the edge EMF of direction k, or -1
+int ctx_fused_emf_dir(const grmhd_ctx* c, int k);
 // FIXED boundaries: copy the bound face fields into the later stages' face arrays
 cudaError_t ctx_copy_fixed_faces(grmhd_ctx* c, cudaStream_t st);
 grmhd_status batch_fail(grmhd_status s, const char* msg);

@@ -182,7 +182,7 @@ __device__ __forceinline__ T uct_edge(T hLL, T hLR, T hRL, T hRR, T ca, T cb, T 
 template <int D, bool M, typename T>
 __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const double* psi_in, const double* alp_in,
                                           const int* c, long long rm, long long r0, T* prL, T* prR, T* BL, T* BR,
-                                          const FluxOut<T>& F, double* const* vbar, T* const* Eh = nullptr)
+                                          const FluxOut<double>& F, double* const* vbar, double* const* Eh = nullptr)
 {
     const double* __restrict__ psi = M ? psi_in : nullptr;
     const double* __restrict__ alp = M ? alp_in : nullptr;
@@ -196,11 +196,11 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     if (!M && Eh) {
         // C = D + 1: A = D + 2 (inactive), B = D; C = D + 2: A = D, B = D + 1 (inactive)
         if (Eh[T1])
-            Eh[T1][r0] = uct_edge<T>(prL[5 + T1], prR[5 + T1], prL[5 + T1], prR[5 + T1], T(1), T(1), BL[D], BR[D],
-                                     BL[T2], BR[T2]);
+            Eh[T1][r0] = (double)uct_edge<T>(prL[5 + T1], prR[5 + T1], prL[5 + T1], prR[5 + T1], T(1), T(1), BL[D],
+                                             BR[D], BL[T2], BR[T2]);
         if (Eh[T2])
-            Eh[T2][r0] = uct_edge<T>(prL[5 + T2], prL[5 + T2], prR[5 + T2], prR[5 + T2], T(1), T(1), BL[T1], BR[T1],
-                                     BL[D], BR[D]);
+            Eh[T2][r0] = (double)uct_edge<T>(prL[5 + T2], prL[5 + T2], prR[5 + T2], prR[5 + T2], T(1), T(1),
+                                             BL[T1], BR[T1], BL[D], BR[D]);
     }
     if (psi) {
 #pragma unroll
@@ -229,7 +229,7 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
 #pragma unroll
     for (int v = 0; v < 8; v++) {
         const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
-        F.p[v][o] = (sL.f[v] + sR.f[v] - (sR.q[v] - sL.q[v])) * hv;
+        F.p[v][o] = (double)((sL.f[v] + sR.f[v] - (sR.q[v] - sL.q[v])) * hv);
     }
     if (vbar && vbar[0]) {
         // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
@@ -249,7 +249,7 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
 // (six cells c-3..c+2) instead of MC (four cells c-2..c+1).
 template <int D, bool M, typename T, bool P = false>
 __device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
-                                          const double* alp_in, const FluxOut<T>& F, double* const* vbar, long long t)
+                                          const double* alp_in, const FluxOut<double>& F, double* const* vbar, long long t)
 {
     constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? psi_in : nullptr;
@@ -413,8 +413,8 @@ __device__ __forceinline__ void march_coords(const Dims& g, long long t, int K, 
 // themselves run along x).
 template <int D, bool M, typename T, bool P = false>
 __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
-                                                const double* psi_in, const double* alp_in, const FluxOut<T>& F,
-                                                double* const* vbar, T* const* Eh, long long t, int K)
+                                                const double* psi_in, const double* alp_in, const FluxOut<double>& F,
+                                                double* const* vbar, double* const* Eh, long long t, int K)
 {
     using Rec = LineRec<T, P>;
     const double* __restrict__ psi = M ? psi_in : nullptr;
@@ -507,7 +507,7 @@ __device__ __forceinline__ void edge_speeds(const double* __restrict__ psi, cons
 // P: PPM reconstruction (six cells or faces per pass) instead of MC (four)
 template <int C, bool M, typename T, bool P = false>
 __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
-                                         const double* alp_in, T* __restrict__ Eh, long long t)
+                                         const double* alp_in, double* __restrict__ Eh, long long t)
 {
     constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
     const double* __restrict__ psi = M ? psi_in : nullptr;
@@ -604,7 +604,7 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     // c+ = c- in each direction, where the four-state weights are all 1/4 and the
     // diffusive coefficients c^2/2c are c/2
     const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
-    Eh[i0] = uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR);
+    Eh[i0] = (double)uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR);
 }
 
 // The same EMFs for K consecutive C-edges along B per thread (MC, or PPM when P; A and
@@ -615,7 +615,7 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
 // along B, x-fastest over the other two directions (the chunks run along x when B = 0).
 template <int C, bool M, typename T, bool P = false>
 __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
-                                               const double* psi_in, const double* alp_in, T* __restrict__ Eh,
+                                               const double* psi_in, const double* alp_in, double* __restrict__ Eh,
                                                long long t, int K)
 {
     using Rec = LineRec<T, P>;
@@ -709,7 +709,8 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
         }
         // EXY[X][Y]: X the A side (the row's L / R), Y the B side (L = this edge's
         // lower-B state)
-        Eh[i0] = uct_edge<T>(ale * L[0], ale * R[0], ale * L[1], ale * R[1], ca, cb, qBbL, qBbR, L[2], R[2]);
+        Eh[i0] = (double)uct_edge<T>(ale * L[0], ale * R[0], ale * L[1], ale * R[1], ca, cb, qBbL, qBbR, L[2],
+                                     R[2]);
     }
 }
 
@@ -903,7 +904,7 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
     }
 }
 
-template <bool M, typename T>
+template <bool M>
 __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, long long t)
 {
     // flat metric: alpha = psi = 1 known at compile time
@@ -932,8 +933,8 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
             const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
 #pragma unroll
             for (int v = 0; v < 8; v++) {
-                const T* __restrict__ Fv = (const T*)a.F[d][v];
-                Lc[v] -= ((double)Fv[o1] - (double)Fv[o]) * hidx;
+                const double* __restrict__ Fv = a.F[d][v];
+                Lc[v] -= (Fv[o1] - Fv[o]) * hidx;
             }
         }
         cell_sources<false>(g, a.prim, a.bf, psi, alp, c, o, Lc);
@@ -953,10 +954,10 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
         }
         if (!ok) continue;
         double r = 0.0;
-        const T* __restrict__ Ec = (const T*)a.Eh[fc];
-        const T* __restrict__ Eb = (const T*)a.Eh[fb];
-        if (g.act[fb]) r -= ((double)Ec[o + g.st[fb]] - (double)Ec[o]) * g.idx[fb];
-        if (g.act[fc]) r += ((double)Eb[o + g.st[fc]] - (double)Eb[o]) * g.idx[fc];
+        const double* __restrict__ Ec = a.Eh[fc];
+        const double* __restrict__ Eb = a.Eh[fb];
+        if (g.act[fb]) r -= (Ec[o + g.st[fb]] - Ec[o]) * g.idx[fb];
+        if (g.act[fc]) r += (Eb[o + g.st[fc]] - Eb[o]) * g.idx[fc];
         out_value(a, 8 + fa, o, r, false);
     }
 }

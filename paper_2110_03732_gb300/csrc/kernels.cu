@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(128) k_emf_ideal(Dims g, EmfArgs<double> a, Vb
 // update: cell-centred L (flux divergence + non-stiff sources) and face L_B (CT)
 // ---------------------------------------------------------------------------
 
-template <bool M, typename T>
+template <bool M>
 __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
 {
     long long tot = 1;
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
     for (int d = 0; d < 3; d++) tot *= g.act[d] ? g.n[d] + 1 : 1;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        update_item<M, T>(g, a, t);
+        update_item<M>(g, a, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -533,7 +533,7 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
 }
 
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm, float* const* Eh)
+                          const double* alp, FluxOut<double> F, int nsm, cudaStream_t st, bool ppm, double* const* Eh)
 {
     FluxArgs<float> a;
     for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !ppm && !(psi || alp) ? Eh[k] : nullptr;
@@ -583,7 +583,7 @@ cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const doubl
 }
 
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                         const double* alp, float* Eh, int nsm, cudaStream_t st, bool ppm)
+                         const double* alp, double* Eh, int nsm, cudaStream_t st, bool ppm)
 {
     EmfArgs<float> a;
     a.prim = prim;
@@ -601,13 +601,8 @@ cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStrea
     long long work = 1;
     for (int d = 0; d < 3; d++) work *= g.act[d] ? g.n[d] + 1 : 1;
     const int b = grid_for(work, 128, nsm);
-    if (a.f32) {
-        if (a.psi || a.alp) k_update<true, float><<<b, 128, 0, st>>>(g, a);
-        else k_update<false, float><<<b, 128, 0, st>>>(g, a);
-    } else {
-        if (a.psi || a.alp) k_update<true, double><<<b, 128, 0, st>>>(g, a);
-        else k_update<false, double><<<b, 128, 0, st>>>(g, a);
-    }
+    if (a.psi || a.alp) k_update<true><<<b, 128, 0, st>>>(g, a);
+    else k_update<false><<<b, 128, 0, st>>>(g, a);
     return cudaGetLastError();
 }
 

@@ -14,8 +14,9 @@ enum { UPD_WRITE_L = 0, UPD_STAGE = 1 };
 template <typename T> struct PrimIn;
 template <> struct PrimIn<double> { const double* p[8]; };
 template <> struct PrimIn<float> { const float* p[11]; };
-// face fluxes of the 8 cell-centred variables, stored as twice the HLL flux (the
-// update kernel folds the 1/2 into its 1/dx)
+// face fluxes of the 8 cell-centred variables, stored in FP64 as twice the HLL flux
+// (the update kernel folds the 1/2 into its 1/dx); the mixed path's FP32 fluxes are
+// widened once, when stored
 template <typename T> struct FluxOut { T* p[8]; };
 struct F11 { float* p[11]; };
 
@@ -48,9 +49,9 @@ struct FluxArgs {
     CP3 bf;
     const double* psi;
     const double* alp;
-    FluxOut<T> F;
+    FluxOut<double> F;
     double* vbar[2];        // ideal-limit EMF: transverse transport velocities (or NULL)
-    T* Eh[3];               // edge EMFs written by the flux kernel (flat 1-D / 2-D grids,
+    double* Eh[3];          // edge EMFs written by the flux kernel (flat 1-D / 2-D grids,
                             // see face_flux), NULL for those the EMF kernels compute
 };
 
@@ -60,7 +61,7 @@ struct EmfArgs {
     CP3 bf;
     const double* psi;
     const double* alp;
-    T* Eh;
+    double* Eh;             // edge EMFs (FP64 also on the mixed path)
 };
 
 // Arguments of the update kernel.  Variables 0..7 are cell-centred (D, S_1..3, tau,
@@ -68,13 +69,12 @@ struct EmfArgs {
 struct UpdateArgs {
     int mode;               // UPD_WRITE_L: L -> L[]; UPD_STAGE: fold into base/acc/qn
     int stage, s;
-    int f32;                // fluxes and EMFs are FP32 (mixed precision) instead of FP64
     double dt;
     double At[4][4], A[4][4], wt[4], w[4];
     double cL[4], cR[4];    // dt At[k][stage], dt A[k][stage]: this stage's terms in base k
     double cwL, cwR;        // dt wt[stage], dt w[stage]: its terms in the final combination
-    const void* F[3][8];    // twice the face fluxes per active direction (double or float)
-    const void* Eh[3];      // edge EMFs (double or float)
+    const double* F[3][8];  // twice the face fluxes per active direction
+    const double* Eh[3];    // edge EMFs
     const double* prim[8];  // stage primitives (padded)
     const double* bf[3];    // stage face fields
     const double* psi;
@@ -92,10 +92,10 @@ cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream
 cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, const double* u3, const double* psi,
                              P3f hs, P3f hd, int nsm, cudaStream_t st);
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false,
-                          float* const* Eh = nullptr);
+                          const double* alp, FluxOut<double> F, int nsm, cudaStream_t st, bool ppm = false,
+                          double* const* Eh = nullptr);
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                         const double* alp, float* Eh, int nsm, cudaStream_t st, bool ppm = false);
+                         const double* alp, double* Eh, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
 // ppm: PPM reconstruction instead of MC (FP64 only)
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,

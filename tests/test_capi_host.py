@@ -80,11 +80,13 @@ def test_scratch_bytes_formula(lib):
         for d in range(3):
             ncell *= n[d] + 4 if d < ndim else 1
         arr = -(-8 * ncell // 256) * 256
-        narr = 8 + 3 + 11 * (t.s - 1) + 11 + 8 * ndim + 3
+        # FP64: primitives, stiff rates, later stage bases, running sum, fluxes, edge
+        # EMFs and two transport-velocity arrays per direction (ideal-limit EMF)
+        narr = 8 + 3 + 11 * (t.s - 1) + 11 + 8 * ndim + 3 + 2 * ndim
         arr32 = -(-4 * ncell // 256) * 256
-        # FP32: stage primitives + cell q_B, fluxes, edge EMFs, and per stage the Newton
-        # start history (last root and its change, 3 components each)
-        narr32 = 11 + 8 * ndim + 3 + 6 * t.s
+        # FP32: stage primitives + cell q_B, and per stage the Newton start history (last
+        # root and its change, 3 components each)
+        narr32 = 11 + 6 * t.s
         small = -(-8 * 1024 * 11 // 256) * 256 + 256 + 256
         ct = narr * arr + narr32 * arr32 + small
         # GLM layout: 12 cell-centred variables per stage base, running sum and flux
