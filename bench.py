@@ -534,11 +534,14 @@ def bench_serving(dev, args):
 
 # FP64 flops per cell per launch of each kernel kind (2 * DFMA + DADD + DMUL thread
 # instructions / cells), counted by ncu on the 512^2 workload for the kernels as they
-# stand (profiles/ot512_fp64_kernels.md).  The flux and EMF figures are per launch
-# (one direction / one component; the EMF value is the mean of its three launches).
-# TRAFFIC: dram read + write bytes per launch from the same capture.
-FP64_FLOPS_PER_CELL = {"implicit": 575.6, "flux": 327.6, "emf": 70.9, "update": 143.0}
-TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 23.3e6, "emf": 6.4e6, "update": 109.2e6}
+# stand (profiles/ot512_fp64_kernels.md).  The flux figure is per launch (one
+# direction); the EMF one is the single EMF launch of a flat 2-D stage (the other two
+# components come out of the flux kernels); the implicit one is a launch after the
+# Newton start history has filled (from the third step on).
+# TRAFFIC: dram read + write bytes per launch from the same capture (flux: the mean of
+# its two directions).
+FP64_FLOPS_PER_CELL = {"implicit": 525.3, "flux": 269.4, "emf": 95.4, "update": 121.0}
+TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 29.2e6, "emf": 6.4e6, "update": 86.2e6}
 
 
 def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):
