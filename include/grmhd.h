@@ -241,6 +241,20 @@ grmhd_status grmhd_clean_divb(grmhd_ctx* ctx, int cycles, void* scratch, size_t 
 /* Kernels launched by this context since create (host-side count). */
 long long grmhd_launch_count(const grmhd_ctx* ctx);
 
+/* Checkpoint / resume (not in the paper).  The state q^n and the face fields belong to
+ * the caller, who saves them.  Beside them the context keeps the starting point of the
+ * implicit solve (Sec. 2.4): the last stage primitives and, per stage, the last root
+ * and its change over the previous step (FP32), all in its scratch.  The root of every
+ * later solve does not depend on them beyond the Newton tolerance, but a bitwise
+ * resume needs them: grmhd_start_bytes gives their size, grmhd_save_start copies them
+ * to dst and grmhd_load_start back from src (device or host memory, stream-ordered
+ * copies; dst / src at least start_bytes long, 8-byte aligned).  A blob loads only
+ * into a context of the same grid, tableau and divergence scheme (the size is
+ * checked).  The Newton failure count is not part of it. */
+grmhd_status grmhd_start_bytes(const grmhd_ctx* ctx, size_t* bytes);
+grmhd_status grmhd_save_start(grmhd_ctx* ctx, void* dst, size_t bytes, grmhd_stream_t stream);
+grmhd_status grmhd_load_start(grmhd_ctx* ctx, const void* src, size_t bytes, grmhd_stream_t stream);
+
 /* Optional per-kernel timing (not part of the paper's method: measurement only).
  * When enabled, CUDA events are recorded on the launching stream around every
  * stage kernel (at most 64 launches between two grmhd_kernel_times calls; later

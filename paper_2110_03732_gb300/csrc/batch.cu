@@ -381,6 +381,7 @@ grmhd_status grmhd_batch_set_dt(grmhd_batch* b, const double* dt, grmhd_stream_t
 
 grmhd_status grmhd_batch_step(grmhd_batch* b, grmhd_stream_t stream)
 {
+    NvtxRange nv("grmhd_batch_step");
     if (!b) return batch_fail(GRMHD_ERR_ARG, "batch is NULL");
     for (int p = 0; p < b->n; p++)
         if (!(b->dt[p] > 0.0)) return batch_fail(GRMHD_ERR_STATE, "call grmhd_batch_set_dt before stepping");

@@ -711,6 +711,7 @@ grmhd_status grmhd_compute_dt(grmhd_ctx* c, double* dt, grmhd_stream_t stream)
 
 grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
 {
+    NvtxRange nv("grmhd_stage");
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     if (i < 0 || i >= c->tab.s) return fail(GRMHD_ERR_ARG, "stage index out of range");
@@ -751,6 +752,7 @@ grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
 
 grmhd_status grmhd_step(grmhd_ctx* c, double dt, grmhd_stream_t stream)
 {
+    NvtxRange nv("grmhd_step");
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     for (int i = 0; i < c->tab.s; i++) {
@@ -872,6 +874,7 @@ grmhd_status grmhd_clean_scratch_bytes(const grmhd_grid* grid, size_t* bytes)
 
 grmhd_status grmhd_clean_divb(grmhd_ctx* c, int cycles, void* scratch, size_t scratch_bytes, grmhd_stream_t stream)
 {
+    NvtxRange nv("grmhd_clean_divb");
     grmhd_status s = need_bound(c);
     if (s != GRMHD_OK) return s;
     if (cycles < 1 || cycles > 1000) return fail(GRMHD_ERR_ARG, "cycles must be in 1..1000");
@@ -888,6 +891,67 @@ grmhd_status grmhd_clean_divb(grmhd_ctx* c, int cycles, void* scratch, size_t sc
 }
 
 long long grmhd_launch_count(const grmhd_ctx* c) { return c ? c->launches : 0; }
+
+// the start blob: 8 FP64 primitive arrays, then per stage 3 + 3 FP32 history arrays
+static size_t start_bytes(const grmhd_ctx* c)
+{
+    const size_t n = (size_t)c->g.ncell;
+    return 8 * n * sizeof(double) + (size_t)c->tab.s * 6 * n * sizeof(float);
+}
+
+// copy the start arrays to (save) or from (load) the blob p, in blob order
+static cudaError_t start_copy(grmhd_ctx* c, char* p, bool save, cudaStream_t st)
+{
+    const size_t n = (size_t)c->g.ncell;
+    auto cp = [&](void* arr, size_t bytes) -> cudaError_t {
+        cudaError_t e = save ? cudaMemcpyAsync(p, arr, bytes, cudaMemcpyDefault, st)
+                             : cudaMemcpyAsync(arr, p, bytes, cudaMemcpyDefault, st);
+        p += bytes;
+        return e;
+    };
+    for (int v = 0; v < 8; v++) {
+        const cudaError_t e = cp(c->prim[v], n * sizeof(double));
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = 0; k < c->tab.s; k++)
+        for (int v = 0; v < 3; v++) {
+            cudaError_t e = cp(c->hs[k][v], n * sizeof(float));
+            if (e == cudaSuccess) e = cp(c->hd[k][v], n * sizeof(float));
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+grmhd_status grmhd_start_bytes(const grmhd_ctx* c, size_t* bytes)
+{
+    if (!c || !bytes) return fail(GRMHD_ERR_ARG, "grmhd_start_bytes: context or bytes is NULL");
+    *bytes = start_bytes(c);
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_save_start(grmhd_ctx* c, void* dst, size_t bytes, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!dst || (uintptr_t)dst % 8) return fail(GRMHD_ERR_ARG, "dst must be non-NULL and 8-byte aligned");
+    if (bytes < start_bytes(c)) return fail(GRMHD_ERR_ARG, "dst is smaller than grmhd_start_bytes");
+    if (!c->hist) return fail(GRMHD_ERR_STATE, "call grmhd_init_from_prims first");
+    const cudaError_t e = start_copy(c, (char*)dst, true, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_load_start(grmhd_ctx* c, const void* src, size_t bytes, grmhd_stream_t stream)
+{
+    grmhd_status s = need_bound(c);
+    if (s != GRMHD_OK) return s;
+    if (!src || (uintptr_t)src % 8) return fail(GRMHD_ERR_ARG, "src must be non-NULL and 8-byte aligned");
+    if (bytes != start_bytes(c)) return fail(GRMHD_ERR_ARG, "src is not a start blob of this grid and tableau");
+    const cudaError_t e = start_copy(c, (char*)src, false, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    c->hist = true;
+    return GRMHD_OK;
+}
 
 const char* grmhd_last_error(void) { return g_err; }
 

@@ -5,8 +5,19 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/grmhd.h"
 #include "kernels.h"
+
+// NVTX range around a host call (visible to nsys / ncu range filters; a no-op when no
+// tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 const grmhd::Dims& ctx_dims(const grmhd_ctx* c);
 bool ctx_metric(const grmhd_ctx* c);

@@ -92,6 +92,9 @@ def lib():
     L.grmhd_batch_destroy.argtypes = [vp]
     L.grmhd_launch_count.argtypes = [vp]
     L.grmhd_launch_count.restype = C.c_longlong
+    L.grmhd_start_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+    L.grmhd_save_start.argtypes = [vp, vp, C.c_size_t, vp]
+    L.grmhd_load_start.argtypes = [vp, vp, C.c_size_t, vp]
     L.grmhd_last_error.restype = C.c_char_p
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
                  "grmhd_set_metric", "grmhd_set_eta", "grmhd_set_dynamo", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
@@ -99,7 +102,7 @@ def lib():
                  "grmhd_set_timing", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
                  "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
-                 "grmhd_clean_divb"):
+                 "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -326,6 +329,35 @@ class Solver:
 
     def launch_count(self):
         return int(self.L.grmhd_launch_count(self.ctx))
+
+    # -- checkpoint / resume -------------------------------------------------
+    def checkpoint(self, stream=None):
+        """Everything a bitwise resume needs, as CPU tensors: the state q^n, the face
+        (or cell) q_B, q_Phi for GLM, and the context's Newton start blob
+        (grmhd_save_start).  The grid, parameters, metric and eta are the caller's
+        set-up and are not included."""
+        n = C.c_size_t()
+        check(self.L.grmhd_start_bytes(self.ctx, C.byref(n)), "start_bytes")
+        blob = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        check(self.L.grmhd_save_start(self.ctx, C.c_void_p(blob.data_ptr()), n.value, _stream(stream)), "save_start")
+        ck = {"q": [t.cpu() for t in self.q], "bf": [t.cpu() for t in self.bf], "start": blob.cpu()}
+        if self.phi is not None:
+            ck["phi"] = self.phi.cpu()
+        return ck
+
+    def restore(self, ck, stream=None):
+        """Load a checkpoint taken from a solver of the same grid, tableau and scheme
+        (the library checks the start blob's size first)."""
+        blob = ck["start"].to(self.device)
+        check(self.L.grmhd_load_start(self.ctx, C.c_void_p(blob.data_ptr()), blob.numel(), _stream(stream)),
+              "load_start")
+        for t, s in zip(self.q, ck["q"]):
+            t.copy_(s)
+        for t, s in zip(self.bf, ck["bf"]):
+            t.copy_(s)
+        if self.phi is not None:
+            self.phi.copy_(ck["phi"])
+        torch.cuda.current_stream(self.device).synchronize()
 
     KERNEL_KINDS = ("implicit", "flux", "emf", "update")
 
