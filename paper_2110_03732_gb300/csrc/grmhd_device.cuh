@@ -500,23 +500,10 @@ __device__ __forceinline__ CellF cell_f32(const CellIn& c)
     return f;
 }
 
-// Newton direction x = -J^{-1} f with J formed and inverted in FP32 (62x the FP64
-// rate on GB300).  The root is fixed by the FP64 residual f, so a direction accurate
-// to ~1e-6 only turns quadratic convergence into fast linear convergence.  Everything
-// J needs is recomputed in FP32 from the FP32 velocity and the per-cell constants,
-// except the two FP64 quantities that can cancel (w_t and tau + D - U).  J is
-// normalised by w_t and f by the power of two nearest below its scale M (an exact
-// rescaling), keeping every float O(1).  Returns false when the FP32 system is
-// singular or the direction is not finite (the caller then uses the FP64 Jacobian).
-__device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf, const double* u, const Eval& e,
-                                               double* x)
+// E(u) and dE_i/du_j in FP32 at the FP32 velocity uf (W = Wf, 1/W = iWf)
+__device__ __forceinline__ void efield_f32(const CellIn& c, const CellF& cf, const float* uf, float Wf, float iWf,
+                                           float* Ef, float dE[3][3])
 {
-    float uf[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) uf[i] = (float)u[i];
-    const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
-    const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
-    float Ef[3], dE[3][3];
     if (c.etat >= 0.0 && c.xi != 0.0) {
         DynT<float> dy;
         dyn_coeffs<float>(Wf, cf.etat, cf.xi, dy, true);
@@ -558,11 +545,19 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf,
             for (int j = 0; j < 3; j++) dE[i][j] = 0.0f;
         }
     }
+}
+
+// y = -(J / w_t)^{-1} fs in FP32, J at uf from E, dE, w_t and tau + D - U (= base);
+// false when singular
+__device__ __forceinline__ bool solve_f32(const CellF& cf, const float* uf, float Wf, float iWf, float uu,
+                                          const float* Ef, const float (*dE)[3], float wt, float base, const float* fs,
+                                          float* y)
+{
     // normalise J by 1/w_t (J = w_t I + ...):
     //   J_ij / w_t = delta_ij + u_i (dw_t/du_j)/w_t + (dE/du_j x B)_i / w_t
     //   (dw_t/du_j)/w_t = ((tau + D - U)/w_t u_j/W - W dU_j/w_t - 2 u_j) / (W^2 - 1/Gamma_hat)
-    const float scf = 1.0f / (float)e.wt;
-    const float basef = (float)(c.tau + c.D - e.U) * scf;
+    const float scf = 1.0f / wt;
+    const float basef = base * scf;
     const float idenf = 1.0f / (uu + 1.0f - cf.igh);
     float J[3][3];
 #pragma unroll
@@ -577,12 +572,6 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf,
         J[2][j] = uf[2] * dw + cz;
     }
     J[0][0] += 1.0f; J[1][1] += 1.0f; J[2][2] += 1.0f;
-    // f scaled by 2^-k with 2^k <= M < 2^(k+1): the exponent field of M, read as an integer
-    const int ek = (int)(mag_hi(e.M) >> 20);
-    const bool scale = ek >= 1 && ek <= 2045;
-    const double down = scale ? __hiloint2double((2046 - ek) << 20, 0) : 1.0;
-    const double up = scale ? __hiloint2double(ek << 20, 0) : 1.0;
-    const float f0 = (float)(e.f[0] * down), f1 = (float)(e.f[1] * down), f2 = (float)(e.f[2] * down);
     const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
     const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
     const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
@@ -595,11 +584,84 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf,
     const float c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
     const float c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
     const float c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    y[0] = (c00 * fs[0] + c10 * fs[1] + c20 * fs[2]) * id;
+    y[1] = (c01 * fs[0] + c11 * fs[1] + c21 * fs[2]) * id;
+    y[2] = (c02 * fs[0] + c12 * fs[1] + c22 * fs[2]) * id;
+    return true;
+}
+
+// Newton direction x = -J^{-1} f with J formed and inverted in FP32 (62x the FP64
+// rate on GB300).  The root is fixed by the FP64 residual f, so a direction accurate
+// to ~1e-6 only turns quadratic convergence into fast linear convergence.  Everything
+// J needs is recomputed in FP32 from the FP32 velocity and the per-cell constants,
+// except the two FP64 quantities that can cancel (w_t and tau + D - U).  J is
+// normalised by w_t and f by the power of two nearest below its scale M (an exact
+// rescaling), keeping every float O(1).  Returns false when the FP32 system is
+// singular or the direction is not finite (the caller then uses the FP64 Jacobian).
+__device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf, const double* u, const Eval& e,
+                                               double* x)
+{
+    float uf[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) uf[i] = (float)u[i];
+    const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+    const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
+    float Ef[3], dE[3][3];
+    efield_f32(c, cf, uf, Wf, iWf, Ef, dE);
+    // f scaled by 2^-k with 2^k <= M < 2^(k+1): the exponent field of M, read as an integer
+    const int ek = (int)(mag_hi(e.M) >> 20);
+    const bool scale = ek >= 1 && ek <= 2045;
+    const double down = scale ? __hiloint2double((2046 - ek) << 20, 0) : 1.0;
+    const double up = scale ? __hiloint2double(ek << 20, 0) : 1.0;
+    const float fs[3] = {(float)(e.f[0] * down), (float)(e.f[1] * down), (float)(e.f[2] * down)};
+    float y[3];
+    if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, (float)e.wt, (float)(c.tau + c.D - e.U), fs, y)) return false;
     // (J / w_t) y = -(f 2^-k) / w_t  ->  x = 2^k y
-    x[0] = up * (double)((c00 * f0 + c10 * f1 + c20 * f2) * id);
-    x[1] = up * (double)((c01 * f0 + c11 * f1 + c21 * f2) * id);
-    x[2] = up * (double)((c02 * f0 + c12 * f1 + c22 * f2) * id);
+    x[0] = up * (double)y[0];
+    x[1] = up * (double)y[1];
+    x[2] = up * (double)y[2];
     return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
+}
+
+// One Newton step done wholly in FP32 (residual, Jacobian and solve) from the start u:
+// the residual of a start within ~1e-6 of the root is then accurate to a few per cent,
+// enough to bring the start to FP32 accuracy (~1e-7) before the FP64 iteration, which
+// then needs one FP64 evaluation fewer.  u is moved only when the step is finite and
+// within the step bound; the FP64 iteration fixes the root as before.
+__device__ __forceinline__ void newton_step_f32(const CellIn& c, const CellF& cf, double* u)
+{
+    float uf[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) uf[i] = (float)u[i];
+    const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+    const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
+    float Ef[3], dE[3][3];
+    efield_f32(c, cf, uf, Wf, iWf, Ef, dE);
+    const float U = 0.5f * (Ef[0] * Ef[0] + Ef[1] * Ef[1] + Ef[2] * Ef[2] + cf.B[0] * cf.B[0] + cf.B[1] * cf.B[1] +
+                            cf.B[2] * cf.B[2]);
+    const float Sf[3] = {(float)c.S[0], (float)c.S[1], (float)c.S[2]};
+    const float Df = (float)c.D;
+    const float base = (float)(c.tau + c.D) - U;
+    const float wt = (Wf * base - Df * cf.igh) / (uu + 1.0f - cf.igh);
+    const float x0 = Ef[1] * cf.B[2] - Ef[2] * cf.B[1];
+    const float x1 = Ef[2] * cf.B[0] - Ef[0] * cf.B[2];
+    const float x2 = Ef[0] * cf.B[1] - Ef[1] * cf.B[0];
+    // f / M with M the momentum scale (as in evaluate)
+    const float M = fmaxf(fmaxf(fmaxf(fabsf(Sf[0]), fabsf(Sf[1])), fmaxf(fabsf(Sf[2]), fabsf(x0))),
+                          fmaxf(fmaxf(fabsf(x1), fabsf(x2)),
+                                fmaxf(fabsf(wt * uf[0]), fmaxf(fabsf(wt * uf[1]), fabsf(wt * uf[2])))));
+    if (!(wt > 0.0f) || !(M > 0.0f) || !(M < 1e30f)) return;
+    const float iM = 1.0f / M;
+    const float fs[3] = {(wt * uf[0] - Sf[0] + x0) * iM, (wt * uf[1] - Sf[1] + x1) * iM,
+                         (wt * uf[2] - Sf[2] + x2) * iM};
+    float y[3];
+    if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, wt, base, fs, y)) return;
+    const float dx[3] = {y[0] * M, y[1] * M, y[2] * M};
+    const float nx2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    if (!(nx2 <= 1e4f * fmaxf(1.0f, uu))) return;   // also rejects NaN
+    u[0] += (double)dx[0];
+    u[1] += (double)dx[1];
+    u[2] += (double)dx[2];
 }
 
 // Globally convergent Newton (backtracking on |f|^2 with the Armijo condition and a
@@ -609,6 +671,10 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf,
 __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol)
 {
     const CellF cf = cell_f32(c);
+    // the FP32 first step saves an FP64 evaluation only when the tolerance lies below
+    // what one FP64 iteration reaches from a start ~1e-6 off (~1e-12): the FP64 path's
+    // 1e-13, not the mixed path's 1e-10
+    if (tol < 1e-11) newton_step_f32(c, cf, u);
     evaluate(c, u, e);
     for (int it = 1; it <= kmax; it++) {
         double dx[3];

@@ -25,7 +25,7 @@ namespace grmhd {
 // ---------------------------------------------------------------------------
 
 template <bool M>
-__global__ void __launch_bounds__(128) k_implicit(Dims g, ImpArgs a)
+__global__ void __launch_bounds__(128, 3) k_implicit(Dims g, ImpArgs a)
 {
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(128) k_implicit(Dims g, ImpArgs a)
 
 // the same solve with cell-centred q_B (GLM variant, Sec. 3.1)
 template <bool M>
-__global__ void __launch_bounds__(128) k_implicit_cc(Dims g, ImpArgs a)
+__global__ void __launch_bounds__(128, 3) k_implicit_cc(Dims g, ImpArgs a)
 {
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
