@@ -244,71 +244,6 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     }
 }
 
-// vbar (may be NULL): the two transverse transport-velocity arrays of the ideal-limit
-// EMF (App. A) for the D-faces, components (D+1)%3 and (D+2)%3.  P: PPM reconstruction
-// (six cells c-3..c+2) instead of MC (four cells c-2..c+1).
-template <int D, bool M, typename T, bool P = false>
-__device__ __forceinline__ void flux_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf, const double* psi_in,
-                                          const double* alp_in, const FluxOut<double>& F, double* const* vbar, long long t)
-{
-    constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
-    const double* __restrict__ psi = M ? psi_in : nullptr;
-    const double* __restrict__ alp = M ? alp_in : nullptr;
-    constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    const int e0 = g.n[0] + (D == 0), e1 = g.n[1] + (D == 1);
-    int c[3];
-    c[0] = g.ng[0] + (int)(t % e0);
-    c[1] = g.ng[1] + (int)((t / e0) % e1);
-    c[2] = g.ng[2] + (int)(t / ((long long)e0 * e1));
-    long long mi[NS], ri[NS];
-    int cd[NS];
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        int cs[3] = {c[0], c[1], c[2]};
-        cs[D] = P ? ext_cell(g, D, c[D] + s - OFF) : c[D] + s - OFF;
-        cd[s] = cs[D];
-        mi[s] = cell_at(g, cs);
-        ri[s] = lin(g, cs[0], cs[1], cs[2]);
-    }
-    T prL[8], prR[8], BL[3], BR[3];
-#pragma unroll
-    for (int v = 0; v < 8; v++) {
-        const T* a = prim.p[v];
-        if (P) {
-            T w[6];
-#pragma unroll
-            for (int s = 0; s < 6; s++) w[s] = a[mi[s < NS ? s : 0]];
-            ppm_face<T>(w, prL[v], prR[v]);
-        } else {
-            mc_face<T>(a[mi[0]], a[mi[1]], a[mi[2]], a[mi[3 < NS ? 3 : 0]], prL[v], prR[v]);
-        }
-    }
-    // transverse cell-centred B (primitive = q_B / psi^6 at the cell); one reciprocal
-    // of psi^6 per stencil cell serves both components
-    T ip6[NS];
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        const T ps = psi ? (T)psi[ri[s]] : T(1);
-        const T p2 = ps * ps;
-        ip6[s] = T(1) / (p2 * p2 * p2);
-    }
-#pragma unroll
-    for (int tt = 0; tt < 2; tt++) {
-        const int e = tt == 0 ? T1 : T2;
-        T b[NS];
-#pragma unroll
-        for (int s = 0; s < NS; s++) {
-            int cs[3] = {c[0], c[1], c[2]};
-            cs[D] = cd[s];
-            b[s] = (T)cell_qB_in(g, prim, bf, e, cs, mi[s]) * ip6[s];
-        }
-        if (P) ppm_face<T>(b, BL[e], BR[e]);
-        else mc_face<T>(b[0], b[1], b[2], b[NS - 1], BL[e], BR[e]);
-    }
-    face_flux<D, M, T>(g, bf, psi, alp, c, ri[OFF - 1], ri[OFF], prL, prR, BL, BR, F, vbar);
-}
-
-
 // Marching reconstruction along a line of cells, one quantity: the face states of the
 // faces f0, f0+1, ... from one new cell per face.  MC keeps the last two cell values,
 // their difference and the older cell's right-face state; PPM keeps the last two cell
