@@ -235,13 +235,14 @@ P3 p3(double* const* p)
 
 bool emf_needed(const Dims& g, int c) { return g.act[(c + 1) % 3] || g.act[(c + 2) % 3]; }
 
-// the flux direction whose kernel writes the edge EMF of direction c (flat metric, MC,
+// the flux direction whose kernel writes the edge EMF of direction c (flat metric,
 // resistive UCT, exactly one of the two directions transverse to c active: the edges
-// then coincide with that direction's faces), else -1
+// then coincide with that direction's faces, and the MC or PPM face states the flux
+// kernel holds are the reconstructions the EMF needs), else -1
 int fused_emf_dir(const grmhd_ctx* c, int k)
 {
     const Dims& g = c->g;
-    if (c->psi || c->alp || c->ppm || c->ideal) return -1;
+    if (c->psi || c->alp || c->ideal) return -1;
     const int a = (k + 1) % 3, b = (k + 2) % 3;
     if (g.act[a] == g.act[b]) return -1;
     return g.act[a] ? a : b;

@@ -178,7 +178,7 @@ __device__ __forceinline__ T uct_edge(T hLL, T hLR, T hRL, T hRR, T ca, T cb, T 
 // third direction is inactive (a 1-D or 2-D grid).  Its edges then coincide with the
 // D-faces, and the UCT EMF there needs only reconstructions along D of E_C and of the
 // transverse q_B, which are this face's states: the face writes hat{E}_C, bitwise what
-// emf_item computes (the same MC values, the same edge formula).
+// emf_item computes (the same MC or PPM values, the same edge formula).
 template <int D, bool M, typename T>
 __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const double* psi_in, const double* alp_in,
                                           const int* c, long long rm, long long r0, T* prL, T* prR, T* BL, T* BR,
@@ -399,7 +399,7 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
         rec[9].step(x[9], BL[T2], BR[T2]);
         c[D] = f;
         const long long r0 = lin(g, c[0], c[1], c[2]);
-        face_flux<D, M, T>(g, bf, psi_in, alp_in, c, rm, r0, prL, prR, BL, BR, F, vbar, P ? nullptr : Eh);
+        face_flux<D, M, T>(g, bf, psi_in, alp_in, c, rm, r0, prL, prR, BL, BR, F, vbar, Eh);
         rm = r0;
     }
 }

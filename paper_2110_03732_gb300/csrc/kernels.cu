@@ -517,7 +517,7 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
                         cudaStream_t st, double* const* vbar, bool ppm, double* const* Eh)
 {
     FluxArgs<double> a;
-    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !ppm && !(psi || alp) ? Eh[k] : nullptr;
+    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !(psi || alp) ? Eh[k] : nullptr;
     for (int v = 0; v < 8; v++) {
         a.prim.p[v] = prim.p[v];
         a.F.p[v] = F.p[v];
@@ -536,7 +536,7 @@ cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 b
                           const double* alp, FluxOut<double> F, int nsm, cudaStream_t st, bool ppm, double* const* Eh)
 {
     FluxArgs<float> a;
-    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !ppm && !(psi || alp) ? Eh[k] : nullptr;
+    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !(psi || alp) ? Eh[k] : nullptr;
     a.vbar[0] = a.vbar[1] = nullptr;
     a.prim = prim;
     a.bf = bf;

@@ -101,7 +101,7 @@ cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, 
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
                         cudaStream_t st, double* const* vbar = nullptr, bool ppm = false,
                         double* const* Eh = nullptr);
-// Eh (MC, flat metric only; ignored otherwise): the edge EMF arrays the flux kernel of
+// Eh (flat metric only; ignored otherwise): the edge EMF arrays the flux kernel of
 // direction d writes itself (fused_emf_dir), NULL entries for the others
 // ideal-limit edge EMF (App. A): vb[d][k] are the transport velocities of the d-faces,
 // component (d + 1 + k) % 3 (NULL for inactive directions)
