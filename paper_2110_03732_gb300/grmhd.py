@@ -178,8 +178,11 @@ class Solver:
         self.ng = ng
         self.cells = self.grid.n[0] * self.grid.n[1] * self.grid.n[2]
         opts = dict(dtype=torch.float64, device=self.device)
-        self.q = [torch.zeros(self.shape, **opts) for _ in range(8)]
-        self.bf = [torch.zeros(self.shape, **opts) for _ in range(3)]
+        # the state in one block (q 0..7, the three field arrays, q_Phi for GLM), so that
+        # it moves between host and device in one copy; q, bf and phi are views into it
+        self.state = torch.zeros((12 if self.glm else 11,) + self.shape, **opts)
+        self.q = [self.state[v] for v in range(8)]
+        self.bf = [self.state[8 + d] for d in range(3)]
         nbytes = scratch_bytes(self.grid, self.tab)
         # torch's caching allocator returns 512-byte aligned blocks
         self.scratch = torch.zeros(nbytes, dtype=torch.uint8, device=self.device)
@@ -193,7 +196,7 @@ class Solver:
         check(self.L.grmhd_bind(ctx, pq, pb, C.c_void_p(self.scratch.data_ptr()), nbytes), "bind")
         self.phi = None
         if self.glm:
-            self.phi = torch.zeros(self.shape, **opts)
+            self.phi = self.state[11]
             check(self.L.grmhd_bind_phi(ctx, C.c_void_p(self.phi.data_ptr())), "bind_phi")
         self.alpha = self.psi = self.eta = None
         self.eta_u = 0.0
