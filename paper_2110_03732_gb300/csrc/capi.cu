@@ -11,6 +11,7 @@
 #include "capi_internal.h"
 #include "elliptic.h"
 #include "kernels.h"
+#include "launch.cuh"
 
 using namespace grmhd;
 
@@ -81,8 +82,11 @@ struct grmhd_ctx_s {
     double kappa;        // GLM damping kappa_B
     double* qphi;        // GLM: bound q_Phi
     long long launches;
+    // programmatic dependent launch of the stage kernels (launch.cuh)
+    bool overlap;
     // optional per-kernel timing: events around each launch, folded on request
     bool timing;
+    bool ev_made;
     int npend;
     cudaEvent_t ev[64][2];
     int ev_kind[64];
@@ -278,6 +282,16 @@ F11 f11(grmhd_ctx* c)
     for (int v = 0; v < 11; v++) r.p[v] = c->mixed ? c->p32[v] : nullptr;
     return r;
 }
+
+// programmatic dependent launch for the kernels launched while it lives (the stage
+// kernels open with grid_dep_sync, launch.cuh); restores the previous setting
+struct OverlapScope {
+    bool prev;
+    explicit OverlapScope(bool on) : prev(grmhd::launch_overlap) { grmhd::launch_overlap = on; }
+    ~OverlapScope() { grmhd::launch_overlap = prev; }
+    OverlapScope(const OverlapScope&) = delete;
+    OverlapScope& operator=(const OverlapScope&) = delete;
+};
 
 // kernel kinds for the timing hooks
 enum { KIND_IMPLICIT = 0, KIND_FLUX = 1, KIND_EMF = 2, KIND_UPDATE = 3 };
@@ -520,7 +534,7 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
 
 grmhd_status grmhd_destroy(grmhd_ctx* ctx)
 {
-    if (ctx && ctx->timing)
+    if (ctx && ctx->ev_made)
         for (int i = 0; i < 64; i++) {
             cudaEventDestroy(ctx->ev[i][0]);
             cudaEventDestroy(ctx->ev[i][1]);
@@ -533,22 +547,35 @@ grmhd_status grmhd_set_timing(grmhd_ctx* c, int enable)
 {
     if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
     if (enable && !c->timing) {
-        for (int i = 0; i < 64; i++)
-            for (int k = 0; k < 2; k++) {
-                cudaError_t e = cudaEventCreate(&c->ev[i][k]);
-                if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
-            }
+        if (!c->ev_made) {
+            for (int i = 0; i < 64; i++)
+                for (int k = 0; k < 2; k++) {
+                    cudaError_t e = cudaEventCreate(&c->ev[i][k]);
+                    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+                }
+            c->ev_made = true;
+        }
         c->timing = true;
         c->npend = 0;
         for (int k = 0; k < 4; k++) { c->t_ms[k] = 0.0; c->t_n[k] = 0; }
+    } else if (!enable && c->timing) {
+        // events already recorded stay readable until the next grmhd_set_timing(1)
+        c->timing = false;
     }
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_set_launch_overlap(grmhd_ctx* c, int enable)
+{
+    if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
+    c->overlap = enable != 0;
     return GRMHD_OK;
 }
 
 grmhd_status grmhd_kernel_times(grmhd_ctx* c, double* ms, long long* launches)
 {
     if (!c) return fail(GRMHD_ERR_ARG, "context is NULL");
-    if (!c->timing) return fail(GRMHD_ERR_STATE, "timing is off: call grmhd_set_timing first");
+    if (!c->ev_made) return fail(GRMHD_ERR_STATE, "timing is off: call grmhd_set_timing first");
     for (int i = 0; i < c->npend; i++) {
         cudaError_t e = cudaEventSynchronize(c->ev[i][1]);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
@@ -720,6 +747,8 @@ grmhd_status grmhd_stage(grmhd_ctx* c, int i, double dt, grmhd_stream_t stream)
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (c->glm && !c->qphi) return fail(GRMHD_ERR_STATE, "call grmhd_bind_phi first");
+    // events recorded between the launches would serialise them anyway
+    const OverlapScope ov(c->overlap && !c->timing);
     if (i == 0 && c->any_fixed) {
         e = ctx_copy_fixed_faces(c, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");

@@ -21,6 +21,7 @@
 #include "grmhd_device.cuh"
 #include "items.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace grmhd {
 
@@ -133,6 +134,7 @@ __device__ __forceinline__ void glm_flux_march_item(const Dims& g, const GlmFlux
 template <int D, bool M, bool P = false>
 __global__ void __launch_bounds__(128) k_glm_flux(Dims g, GlmFluxArgs a, int K)
 {
+    grid_dep_sync();
     const long long nq = (g.n[D] + K) / K;
     const long long tot = nq * (D == 0 ? (long long)g.n[1] * g.n[2]
                                        : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
@@ -213,6 +215,7 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
 
 __global__ void __launch_bounds__(128) k_glm_update_flat(Dims g, GlmUpdateArgs a)
 {
+    grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
@@ -221,6 +224,7 @@ __global__ void __launch_bounds__(128) k_glm_update_flat(Dims g, GlmUpdateArgs a
 
 __global__ void __launch_bounds__(128) k_glm_update_metric(Dims g, GlmUpdateArgs a)
 {
+    grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
@@ -258,7 +262,7 @@ static void glm_flux_launch(const Dims& g, const GlmFluxArgs& a, int nsm, cudaSt
     const double want = 0.75 * nsm * glm_blocks_per_sm<D, M, P>();
     int K = 8;
     while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
-    k_glm_flux<D, M, P><<<glm_grid((long long)((g.n[D] + K) / K) * other, 128, nsm), 128, 0, st>>>(g, a, K);
+    launch_k(k_glm_flux<D, M, P>, glm_grid((long long)((g.n[D] + K) / K) * other, 128, nsm), 128, st, g, a, K);
 }
 
 template <bool P>
@@ -280,8 +284,7 @@ cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm,
 cudaError_t launch_glm_update(const Dims& g, const GlmUpdateArgs& a, int nsm, cudaStream_t st)
 {
     const int b = glm_grid((long long)g.n[0] * g.n[1] * g.n[2], 128, nsm);
-    if (a.psi || a.alp) k_glm_update_metric<<<b, 128, 0, st>>>(g, a);
-    else k_glm_update_flat<<<b, 128, 0, st>>>(g, a);
+    launch_k(a.psi || a.alp ? k_glm_update_metric : k_glm_update_flat, b, 128, st, g, a);
     return cudaGetLastError();
 }
 

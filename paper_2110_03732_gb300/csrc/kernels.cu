@@ -17,8 +17,11 @@
 #include "grmhd_device.cuh"
 #include "items.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace grmhd {
+
+thread_local bool launch_overlap = false;
 
 // ---------------------------------------------------------------------------
 // implicit step
@@ -27,6 +30,7 @@ namespace grmhd {
 template <bool M>
 __global__ void __launch_bounds__(128, 3) k_implicit(Dims g, ImpArgs a)
 {
+    grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
@@ -37,6 +41,7 @@ __global__ void __launch_bounds__(128, 3) k_implicit(Dims g, ImpArgs a)
 template <bool M>
 __global__ void __launch_bounds__(128, 3) k_implicit_cc(Dims g, ImpArgs a)
 {
+    grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
@@ -51,6 +56,7 @@ __global__ void __launch_bounds__(128, 3) k_implicit_cc(Dims g, ImpArgs a)
 template <int D, bool M, typename T, bool P = false>
 __global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a, int K)
 {
+    grid_dep_sync();
     const long long nq = (g.n[D] + K) / K;
     const long long tot = nq * (D == 0 ? (long long)g.n[1] * g.n[2]
                                        : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
@@ -67,6 +73,7 @@ __global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a, int K
 template <int C, bool M, typename T, bool P = false>
 __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
 {
+    grid_dep_sync();
     long long tot = 1;
 #pragma unroll
     for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
@@ -80,6 +87,7 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
 template <int C, bool M, typename T, bool P = false>
 __global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a, int K)
 {
+    grid_dep_sync();
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     const long long tot = (long long)((g.n[B] + K) / K) * g.n[C] * (g.n[A] + 1);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
@@ -95,6 +103,7 @@ struct VbarArgs {
 template <int C, bool M>
 __global__ void __launch_bounds__(128) k_emf_ideal(Dims g, EmfArgs<double> a, VbarArgs vb)
 {
+    grid_dep_sync();
     long long tot = 1;
 #pragma unroll
     for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
@@ -113,6 +122,7 @@ __global__ void __launch_bounds__(128) k_emf_ideal(Dims g, EmfArgs<double> a, Vb
 template <bool M>
 __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
 {
+    grid_dep_sync();
     long long tot = 1;
 #pragma unroll
     for (int d = 0; d < 3; d++) tot *= g.act[d] ? g.n[d] + 1 : 1;
@@ -392,8 +402,7 @@ static int grid_for(long long work, int threads, int nsm)
 cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st)
 {
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
-    if (a.psi || a.alp) k_implicit<true><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
-    else k_implicit<false><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+    launch_k(a.psi || a.alp ? k_implicit<true> : k_implicit<false>, grid_for(work, 128, nsm), 128, st, g, a);
     return cudaGetLastError();
 }
 
@@ -420,8 +429,8 @@ cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, 
 cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st)
 {
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
-    if (a.psi || a.alp) k_implicit_cc<true><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
-    else k_implicit_cc<false><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+    launch_k(a.psi || a.alp ? k_implicit_cc<true> : k_implicit_cc<false>, grid_for(work, 128, nsm), 128, st, g,
+             a);
     return cudaGetLastError();
 }
 
@@ -454,7 +463,7 @@ static void flux_march_launch(const Dims& g, int nsm, cudaStream_t st, const Flu
     int K = 8;
     while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
     const int b = grid_for((long long)((g.n[D] + K) / K) * other, 128, nsm);
-    k_flux_march<D, M, T, P><<<b, 128, 0, st>>>(g, a, K);
+    launch_k(k_flux_march<D, M, T, P>, b, 128, st, g, a, K);
 }
 
 template <typename T, bool P>
@@ -488,14 +497,14 @@ static void emf_launch(const Dims& g, int nsm, cudaStream_t st, const EmfArgs<T>
     if (!g.act[A] || !g.act[B]) {
         long long work = 1;
         for (int d = 0; d < 3; d++) work *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
-        k_emf<C, M, T, P><<<grid_for(work, 128, nsm), 128, 0, st>>>(g, a);
+        launch_k(k_emf<C, M, T, P>, grid_for(work, 128, nsm), 128, st, g, a);
         return;
     }
     const long long other = (long long)g.n[C] * (g.n[A] + 1);
     const double want = 0.75 * nsm * emf_march_blocks_per_sm<C, M, T, P>();
     int K = 8;
     while (K > 1 && (double)(((g.n[B] + K) / K) * other + 127) / 128 < want) K /= 2;
-    k_emf_march<C, M, T, P><<<grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, 0, st>>>(g, a, K);
+    launch_k(k_emf_march<C, M, T, P>, grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, st, g, a, K);
 }
 
 template <typename T, bool P>
@@ -576,9 +585,9 @@ cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const doubl
         for (int k = 0; k < 2; k++) v.p[d][k] = vb[d][k];
     const int b = grid_for(emf_work(g, c), 128, nsm);
     const bool m = psi || alp;
-    if (c == 0) m ? k_emf_ideal<0, true><<<b, 128, 0, st>>>(g, a, v) : k_emf_ideal<0, false><<<b, 128, 0, st>>>(g, a, v);
-    else if (c == 1) m ? k_emf_ideal<1, true><<<b, 128, 0, st>>>(g, a, v) : k_emf_ideal<1, false><<<b, 128, 0, st>>>(g, a, v);
-    else m ? k_emf_ideal<2, true><<<b, 128, 0, st>>>(g, a, v) : k_emf_ideal<2, false><<<b, 128, 0, st>>>(g, a, v);
+    if (c == 0) launch_k(m ? k_emf_ideal<0, true> : k_emf_ideal<0, false>, b, 128, st, g, a, v);
+    else if (c == 1) launch_k(m ? k_emf_ideal<1, true> : k_emf_ideal<1, false>, b, 128, st, g, a, v);
+    else launch_k(m ? k_emf_ideal<2, true> : k_emf_ideal<2, false>, b, 128, st, g, a, v);
     return cudaGetLastError();
 }
 
@@ -601,8 +610,7 @@ cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStrea
     long long work = 1;
     for (int d = 0; d < 3; d++) work *= g.act[d] ? g.n[d] + 1 : 1;
     const int b = grid_for(work, 128, nsm);
-    if (a.psi || a.alp) k_update<true><<<b, 128, 0, st>>>(g, a);
-    else k_update<false><<<b, 128, 0, st>>>(g, a);
+    launch_k(a.psi || a.alp ? k_update<true> : k_update<false>, b, 128, st, g, a);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,47 @@
+// Launch of the stage kernels with programmatic dependent launch (sm_90 and later).
+//
+// The kernels of one IMEX stage run back to back on one stream, each reading what the
+// one before wrote.  Launched with the programmatic-stream-serialisation attribute, a
+// kernel may be scheduled while its predecessor is still draining its last blocks:
+// every stage kernel opens with grid_dep_sync(), which waits until the preceding grid
+// has completed and its memory is visible (griddepcontrol.wait) and only then lets the
+// next grid be scheduled (griddepcontrol.launch_dependents).  So at most two grids are
+// in flight, the waiting grid's blocks hold no more than the slots its predecessor has
+// already given up, and no kernel touches memory before its predecessor has finished;
+// what is hidden is the launch latency between the two.  Kernels launched without the
+// attribute (every launch while launch_overlap is off) see both instructions as no-ops.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <utility>
+
+namespace grmhd {
+
+// set by the C API for the duration of a stage (one context per thread)
+extern thread_local bool launch_overlap;
+
+__device__ __forceinline__ void grid_dep_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// k<<<grid, block, 0, st>>>(args...), with the programmatic attribute when
+// launch_overlap is set.  k must open with grid_dep_sync().
+template <typename... P, typename... A>
+inline cudaError_t launch_k(void (*k)(P...), int grid, int block, cudaStream_t st, A&&... args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = launch_overlap ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
+}  // namespace grmhd

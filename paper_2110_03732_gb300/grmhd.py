@@ -82,6 +82,7 @@ def lib():
     L.grmhd_clean_divb.argtypes = [vp, C.c_int, vp, C.c_size_t, vp]
     L.grmhd_diagnostics.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_longlong), vp]
     L.grmhd_set_timing.argtypes = [vp, C.c_int]
+    L.grmhd_set_launch_overlap.argtypes = [vp, C.c_int]
     L.grmhd_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
     L.grmhd_batch_scratch_bytes.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_size_t)]
     L.grmhd_batch_create.argtypes = [C.POINTER(vp), C.c_int, vp, C.c_size_t, C.POINTER(vp)]
@@ -99,7 +100,7 @@ def lib():
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
                  "grmhd_set_metric", "grmhd_set_eta", "grmhd_set_dynamo", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
                  "grmhd_step", "grmhd_get_prims", "grmhd_implicit", "grmhd_explicit_L", "grmhd_diagnostics",
-                 "grmhd_set_timing", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
+                 "grmhd_set_timing", "grmhd_set_launch_overlap", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
                  "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
                  "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start"):
@@ -156,11 +157,12 @@ class Solver:
     ``q`` (8 tensors) and ``bf`` (3 tensors) are the padded, densitised conserved
     cell and face fields; the library updates them in place.  With ``divb="glm"``
     (GLM cleaning, Sec. 3.1) ``bf`` holds cell-centred q_B and ``phi`` the evolved
-    q_Phi; ``kappa`` is the damping kappa_B."""
+    q_Phi; ``kappa`` is the damping kappa_B.  ``launch_overlap`` launches the stage
+    kernels with programmatic dependent launch (bitwise the same results)."""
 
     def __init__(self, ndim, n, lo, hi, bc, gamma, cfl=0.4, tableau=None, device="cuda", newton_tol=0.0,
                  newton_kmax=0, rho_atm=0.0, p_atm=0.0, precision="fp64", divb="ct", kappa=0.0, emf="resistive",
-                 rec="mc"):
+                 rec="mc", launch_overlap=True):
         self.L = lib()
         self.grid = make_grid(ndim, n, lo, hi, bc)
         self.tab = ssp2() if tableau is None else tableau
@@ -191,6 +193,7 @@ class Solver:
             check(self.L.grmhd_create(C.byref(self.grid), C.byref(self.par), C.byref(self.tab), C.byref(ctx)),
                   "create")
         self.ctx = ctx
+        self.set_launch_overlap(launch_overlap)
         pq, self._kq = _ptrs(self.q)
         pb, self._kb = _ptrs(self.bf)
         check(self.L.grmhd_bind(ctx, pq, pb, C.c_void_p(self.scratch.data_ptr()), nbytes), "bind")
@@ -366,6 +369,10 @@ class Solver:
 
     def set_timing(self, on=True):
         check(self.L.grmhd_set_timing(self.ctx, int(on)), "set_timing")
+
+    def set_launch_overlap(self, on=True):
+        """Programmatic dependent launch of the stage kernels (bitwise the same results)."""
+        check(self.L.grmhd_set_launch_overlap(self.ctx, int(on)), "set_launch_overlap")
 
     def kernel_times(self):
         """Cumulative (ms, launches) per kernel kind since timing was enabled."""
