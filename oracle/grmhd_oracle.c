@@ -28,7 +28,7 @@
  *   ideal-limit HLL UCT (transport velocities)    App. A (steps i-iv)
  *   PPM reconstruction (named for the star runs)  Sec. 5; Colella & Woodward (1984)
  *
- * Readings where the paper is silent or garbled (each also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - IMEX sum limits: q(i) = q^n + dt sum_{j<i} at_ij L(j) + dt sum_{j<=i} a_ij R(j),
  *     q^{n+1} = q^n + dt sum_i (wt_i L(i) + w_i R(i))  (Pareschi-Russo form).
  *   - eta_tilde = eta / (alpha a_ii dt) inside stage i.

@@ -120,7 +120,7 @@ def _lorentz_u(vx, vy, vz):
 
 
 # --------------------------------------------------------------------------
-# BASELINE workloads
+# benchmark workloads (shock tube, Orszag-Tang, magnetised star)
 # --------------------------------------------------------------------------
 
 def shock_tube(n=400, eta=1e-3, with_B=True):
