@@ -262,6 +262,9 @@ ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE
     a.eta = c->eta;
     a.eta_u = c->eta_u;
     a.a_dt = a_dt;
+    a.ia_dt = a_dt > 0.0 ? 1.0 / a_dt : 0.0;
+    a.ighf = (float)c->g.igh;
+    a.xif = (float)c->xi;
     a.prim = prim;
     a.R = R;
     a.qE_out = qE_out;

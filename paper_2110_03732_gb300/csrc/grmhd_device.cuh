@@ -281,7 +281,22 @@ struct CellIn {
     double etat;                        // eta / (alpha a_ii dt); < 0: E held fixed
     double xi;                          // mean-field dynamo parameter (Sec. 2.2)
     double gh, igh;
+    float ighf, xif;                    // FP32 copies of igh and xi (kernel constants)
+    // set by cell_derive, once per cell: which E(u) applies, and the pieces of the
+    // residual that do not depend on u
+    int emode;                          // 0: E held fixed, 1: resistive, 2: with the dynamo
+    double tD, B2h, Digh, etEs[3];      // tau + D, |B|^2 / 2, D / Gamma_hat, eta_t E*
 };
+
+__device__ __forceinline__ void cell_derive(CellIn& c)
+{
+    c.emode = !(c.etat >= 0.0) ? 0 : (c.xi != 0.0 ? 2 : 1);
+    c.tD = c.tau + c.D;
+    c.B2h = 0.5 * (c.B[0] * c.B[0] + c.B[1] * c.B[1] + c.B[2] * c.B[2]);
+    c.Digh = c.D * c.igh;
+#pragma unroll
+    for (int i = 0; i < 3; i++) c.etEs[i] = c.etat * c.Es[i];
+}
 
 // A_k(W) of Sec. 2.4 for the dynamo parameter xi, and their W-derivatives:
 //   A_0 = W + eta_t + xi^2 (W^2 - 1)/p,  A_1 = eta_t/q + xi^2 eta_t W/(p q),
@@ -351,7 +366,7 @@ __device__ __forceinline__ unsigned mag_hi(double x) { return (unsigned)__double
 __device__ __forceinline__ double from_hi(unsigned h) { return __hiloint2double((int)h, 0); }
 
 struct Eval {
-    double W, E[3], wt, U, A1, iWe, iden, Esu, f[3], g;
+    double W, iW, E[3], wt, U, A1, iWe, iden, Esu, f[3], g;
     double fm;   // max |f_i| (high-word maximum: within 2^-20 below the exact one)
     double M;    // momentum scale of f: max(|S_i|, |(E x B)_i|, |w_t u_i|), likewise
 };
@@ -361,8 +376,10 @@ struct Eval {
 __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval& e)
 {
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    e.W = sqrt(1.0 + uu);
-    if (c.etat >= 0.0 && c.xi != 0.0) {
+    const double Wsq = 1.0 + uu;   // W^2
+    e.iW = rsqrt(Wsq);
+    e.W = Wsq * e.iW;
+    if (c.emode == 2) {
         // A_0 E = eta_t E* + A_1 (E*.u) u + A_2 u x E* + A_3 B + A_4 (B.u) u + A_5 u x B
         Dyn dy;
         dyn_coeffs(e.W, c.etat, c.xi, dy, false);
@@ -379,28 +396,27 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
         for (int i = 0; i < 3; i++)
             e.E[i] = (c.etat * c.Es[i] + (a + b) * u[i] + dy.A[2] * uxEs[i] + dy.A[3] * c.B[i] + dy.A[5] * uxB[i]) *
                      e.iWe;
-    } else if (c.etat >= 0.0) {
+    } else if (c.emode == 1) {
         // the three reciprocals 1/(W + eta_t), 1/(1 + eta_t W) and 1/(W^2 - 1/Gamma_hat)
         // from one division: r = 1/(a b d), 1/a = r b d, ...  (a, b >= 1 and d > 0, so
         // the product neither overflows nor cancels)
-        const double a = e.W + c.etat, b = 1.0 + c.etat * e.W, d = uu + 1.0 - c.igh;
+        const double a = e.W + c.etat, b = 1.0 + c.etat * e.W, d = Wsq - c.igh;
         const double ab = a * b, r = 1.0 / (ab * d);
         e.iWe = r * (b * d);
         e.A1 = c.etat * (r * (a * d));
         e.iden = r * ab;
         e.Esu = c.Es[0] * u[0] + c.Es[1] * u[1] + c.Es[2] * u[2];
         const double ae = e.A1 * e.Esu;
-        e.E[0] = (c.etat * c.Es[0] + ae * u[0] - (u[1] * c.B[2] - u[2] * c.B[1])) * e.iWe;
-        e.E[1] = (c.etat * c.Es[1] + ae * u[1] - (u[2] * c.B[0] - u[0] * c.B[2])) * e.iWe;
-        e.E[2] = (c.etat * c.Es[2] + ae * u[2] - (u[0] * c.B[1] - u[1] * c.B[0])) * e.iWe;
+        e.E[0] = (c.etEs[0] + ae * u[0] - (u[1] * c.B[2] - u[2] * c.B[1])) * e.iWe;
+        e.E[1] = (c.etEs[1] + ae * u[1] - (u[2] * c.B[0] - u[0] * c.B[2])) * e.iWe;
+        e.E[2] = (c.etEs[2] + ae * u[2] - (u[0] * c.B[1] - u[1] * c.B[0])) * e.iWe;
     } else {
         e.iWe = 0.0; e.A1 = 0.0; e.Esu = 0.0;
         e.E[0] = c.Es[0]; e.E[1] = c.Es[1]; e.E[2] = c.Es[2];
     }
-    e.U = 0.5 * (e.E[0] * e.E[0] + e.E[1] * e.E[1] + e.E[2] * e.E[2] + c.B[0] * c.B[0] + c.B[1] * c.B[1] +
-                 c.B[2] * c.B[2]);
-    if (!(c.etat >= 0.0) || c.xi != 0.0) e.iden = 1.0 / (uu + 1.0 - c.igh);
-    e.wt = (e.W * (c.tau + c.D - e.U) - c.D * c.igh) * e.iden;
+    e.U = 0.5 * (e.E[0] * e.E[0] + e.E[1] * e.E[1] + e.E[2] * e.E[2]) + c.B2h;
+    if (c.emode != 1) e.iden = 1.0 / (Wsq - c.igh);
+    e.wt = (e.W * (c.tD - e.U) - c.Digh) * e.iden;
     const double x0 = e.E[1] * c.B[2] - e.E[2] * c.B[1];
     const double x1 = e.E[2] * c.B[0] - e.E[0] * c.B[2];
     const double x2 = e.E[0] * c.B[1] - e.E[1] * c.B[0];
@@ -417,13 +433,13 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
 // Jacobian J_ij = w_t delta_ij + u_i dw_t/du_j + (dE/du_j x B)_i
 __device__ __forceinline__ void jacobian(const CellIn& c, const double* u, const Eval& e, double J[3][3])
 {
-    const double iW = 1.0 / e.W;
+    const double iW = e.iW;
     double dE[3][3];   // dE_i / du_j
-    if (c.etat >= 0.0 && c.xi != 0.0) {
+    if (c.emode == 2) {
         Dyn dy;
         dyn_coeffs(e.W, c.etat, c.xi, dy, true);
         dE_dynamo<double>(dy.A, dy.Ad, e.W, u, e.E, c.Es, c.B, dE);
-    } else if (c.etat >= 0.0) {
+    } else if (c.emode == 1) {
         // W (W + eta_t) dE_i/du_j = -E_i u_j + A_1 W u_i E*_j + (A_1 W delta_ij - A_1^2 u_i u_j)(E*.u)
         //                          - W eps_ijl B_l
         const double A1 = e.A1, a2 = A1 * A1 * e.Esu * iW;
@@ -444,7 +460,7 @@ __device__ __forceinline__ void jacobian(const CellIn& c, const double* u, const
 #pragma unroll
             for (int j = 0; j < 3; j++) dE[i][j] = 0.0;
     }
-    const double base = c.tau + c.D - e.U;
+    const double base = c.tD - e.U;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         const double dU = e.E[0] * dE[0][j] + e.E[1] * dE[1][j] + e.E[2] * dE[2][j];
@@ -481,6 +497,42 @@ __device__ __forceinline__ bool newton_dir(const double J[3][3], const double* f
     return true;
 }
 
+// binary64 <-> binary32 on the integer pipe.  On GB300 the hardware conversions issue
+// on the FP64 pipe, which bounds the implicit solve; these re-bias the exponent field
+// (1023 -> 127) and move the mantissa with integer instructions.  d2f rounds the 29
+// dropped mantissa bits half away from zero (IEEE round-to-nearest-even differs only
+// at exact ties).  Zero keeps its sign; values outside the normal binary32 range
+// (denormal, infinite, NaN) take the hardware conversion.  Used for the FP32 copies
+// of the Newton solve, where only the size of the rounding matters.
+__device__ __forceinline__ float d2f_int(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e - 897u > 253u) {
+        if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+        return (float)x;
+    }
+    const unsigned f = ((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) +
+                       ((lo >> 28) & 1u);
+    return __uint_as_float(f);
+}
+
+__device__ __forceinline__ double f2d_int(float v)
+{
+    const unsigned f = __float_as_uint(v);
+    const unsigned e = (f >> 23) & 0xffu;
+    if (e - 1u >= 254u) {
+        if ((f << 1) == 0u) return __hiloint2double((int)(f & 0x80000000u), 0);
+        return (double)v;
+    }
+    return __hiloint2double((int)((f & 0x80000000u) | ((e + 896u) << 20) | ((f >> 3) & 0xfffffu)), (int)(f << 29));
+}
+
+// three floats passed by value (an FP32 copy of u), so they stay in registers
+struct F3 {
+    float x[3];
+};
+
 // FP32 copies of the per-cell constants of the solve, converted once per cell
 struct CellF {
     float Es[3], B[3], etat, xi, igh;
@@ -491,12 +543,12 @@ __device__ __forceinline__ CellF cell_f32(const CellIn& c)
     CellF f;
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        f.Es[i] = (float)c.Es[i];
-        f.B[i] = (float)c.B[i];
+        f.Es[i] = d2f_int(c.Es[i]);
+        f.B[i] = d2f_int(c.B[i]);
     }
-    f.etat = (float)c.etat;
-    f.xi = (float)c.xi;
-    f.igh = (float)c.igh;
+    f.etat = d2f_int(c.etat);
+    f.xi = c.xif;
+    f.igh = c.ighf;
     return f;
 }
 
@@ -504,7 +556,7 @@ __device__ __forceinline__ CellF cell_f32(const CellIn& c)
 __device__ __forceinline__ void efield_f32(const CellIn& c, const CellF& cf, const float* uf, float Wf, float iWf,
                                            float* Ef, float dE[3][3])
 {
-    if (c.etat >= 0.0 && c.xi != 0.0) {
+    if (c.emode == 2) {
         DynT<float> dy;
         dyn_coeffs<float>(Wf, cf.etat, cf.xi, dy, true);
         const float s = 1.0f / dy.A[0];
@@ -519,7 +571,7 @@ __device__ __forceinline__ void efield_f32(const CellIn& c, const CellF& cf, con
         for (int i = 0; i < 3; i++)
             Ef[i] = (cf.etat * cf.Es[i] + ab * uf[i] + dy.A[2] * uxEs[i] + dy.A[3] * cf.B[i] + dy.A[5] * uxB[i]) * s;
         dE_dynamo<float>(dy.A, dy.Ad, Wf, uf, Ef, cf.Es, cf.B, dE);
-    } else if (c.etat >= 0.0) {
+    } else if (c.emode == 1) {
         const float s = 1.0f / (Wf + cf.etat);
         const float A1 = cf.etat / (1.0f + cf.etat * Wf);
         const float Esu = cf.Es[0] * uf[0] + cf.Es[1] * uf[1] + cf.Es[2] * uf[2];
@@ -599,11 +651,11 @@ __device__ __forceinline__ bool solve_f32(const CellF& cf, const float* uf, floa
 // rescaling), keeping every float O(1).  Returns false when the FP32 system is
 // singular or the direction is not finite (the caller then uses the FP64 Jacobian).
 __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf, const double* u, const Eval& e,
-                                               double* x)
+                                               double* x, bool has_uin, const F3& uin)
 {
     float uf[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) uf[i] = (float)u[i];
+    for (int i = 0; i < 3; i++) uf[i] = has_uin ? uin.x[i] : d2f_int(u[i]);
     const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
     const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
     float Ef[3], dE[3][3];
@@ -613,13 +665,13 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf,
     const bool scale = ek >= 1 && ek <= 2045;
     const double down = scale ? __hiloint2double((2046 - ek) << 20, 0) : 1.0;
     const double up = scale ? __hiloint2double(ek << 20, 0) : 1.0;
-    const float fs[3] = {(float)(e.f[0] * down), (float)(e.f[1] * down), (float)(e.f[2] * down)};
+    const float fs[3] = {d2f_int(e.f[0] * down), d2f_int(e.f[1] * down), d2f_int(e.f[2] * down)};
     float y[3];
-    if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, (float)e.wt, (float)(c.tau + c.D - e.U), fs, y)) return false;
+    if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, d2f_int(e.wt), d2f_int(c.tD - e.U), fs, y)) return false;
     // (J / w_t) y = -(f 2^-k) / w_t  ->  x = 2^k y
-    x[0] = up * (double)y[0];
-    x[1] = up * (double)y[1];
-    x[2] = up * (double)y[2];
+    x[0] = up * f2d_int(y[0]);
+    x[1] = up * f2d_int(y[1]);
+    x[2] = up * f2d_int(y[2]);
     return isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]);
 }
 
@@ -627,21 +679,25 @@ __device__ __forceinline__ bool newton_dir_f32(const CellIn& c, const CellF& cf,
 // the residual of a start within ~1e-6 of the root is then accurate to a few per cent,
 // enough to bring the start to FP32 accuracy (~1e-7) before the FP64 iteration, which
 // then needs one FP64 evaluation fewer.  u is moved only when the step is finite and
-// within the step bound; the FP64 iteration fixes the root as before.
-__device__ __forceinline__ void newton_step_f32(const CellIn& c, const CellF& cf, double* u)
+// within the step bound; the FP64 iteration fixes the root as before.  uin: the FP32
+// value of u when the caller has it (has_uin; else converted here); when u moves, uout
+// gets the FP32 sum, within an FP32 rounding of the new u (all the next FP32 direction
+// needs).  Returns whether u moved.
+__device__ __forceinline__ bool newton_step_f32(const CellIn& c, const CellF& cf, double* u, bool has_uin,
+                                                const F3& uin, F3& uout)
 {
     float uf[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) uf[i] = (float)u[i];
+    for (int i = 0; i < 3; i++) uf[i] = has_uin ? uin.x[i] : d2f_int(u[i]);
     const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
     const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
     float Ef[3], dE[3][3];
     efield_f32(c, cf, uf, Wf, iWf, Ef, dE);
     const float U = 0.5f * (Ef[0] * Ef[0] + Ef[1] * Ef[1] + Ef[2] * Ef[2] + cf.B[0] * cf.B[0] + cf.B[1] * cf.B[1] +
                             cf.B[2] * cf.B[2]);
-    const float Sf[3] = {(float)c.S[0], (float)c.S[1], (float)c.S[2]};
-    const float Df = (float)c.D;
-    const float base = (float)(c.tau + c.D) - U;
+    const float Sf[3] = {d2f_int(c.S[0]), d2f_int(c.S[1]), d2f_int(c.S[2])};
+    const float Df = d2f_int(c.D);
+    const float base = d2f_int(c.tD) - U;
     const float wt = (Wf * base - Df * cf.igh) / (uu + 1.0f - cf.igh);
     const float x0 = Ef[1] * cf.B[2] - Ef[2] * cf.B[1];
     const float x1 = Ef[2] * cf.B[0] - Ef[0] * cf.B[2];
@@ -650,37 +706,50 @@ __device__ __forceinline__ void newton_step_f32(const CellIn& c, const CellF& cf
     const float M = fmaxf(fmaxf(fmaxf(fabsf(Sf[0]), fabsf(Sf[1])), fmaxf(fabsf(Sf[2]), fabsf(x0))),
                           fmaxf(fmaxf(fabsf(x1), fabsf(x2)),
                                 fmaxf(fabsf(wt * uf[0]), fmaxf(fabsf(wt * uf[1]), fabsf(wt * uf[2])))));
-    if (!(wt > 0.0f) || !(M > 0.0f) || !(M < 1e30f)) return;
+    if (!(wt > 0.0f) || !(M > 0.0f) || !(M < 1e30f)) return false;
     const float iM = 1.0f / M;
     const float fs[3] = {(wt * uf[0] - Sf[0] + x0) * iM, (wt * uf[1] - Sf[1] + x1) * iM,
                          (wt * uf[2] - Sf[2] + x2) * iM};
     float y[3];
-    if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, wt, base, fs, y)) return;
+    if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, wt, base, fs, y)) return false;
     const float dx[3] = {y[0] * M, y[1] * M, y[2] * M};
     const float nx2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
-    if (!(nx2 <= 1e4f * fmaxf(1.0f, uu))) return;   // also rejects NaN
-    u[0] += (double)dx[0];
-    u[1] += (double)dx[1];
-    u[2] += (double)dx[2];
+    if (!(nx2 <= 1e4f * fmaxf(1.0f, uu))) return false;   // also rejects NaN
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        u[i] += f2d_int(dx[i]);
+        uout.x[i] = uf[i] + dx[i];
+    }
+    return true;
 }
 
 // Globally convergent Newton (backtracking on |f|^2 with the Armijo condition and a
 // bounded step).  u: in = initial guess, out = solution.  Converged when |f| is at
 // `tol` against its own momentum scale M, or when the step no longer moves u.
-// Returns iterations, or -1.
-__device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol)
+// Returns iterations, or -1.  uin: the FP32 value of the start when the caller has it
+// (has_uin; the start is then exactly that value).
+__device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol, bool has_uin,
+                                            const F3& uin)
 {
     const CellF cf = cell_f32(c);
     // the FP32 first step saves an FP64 evaluation only when the tolerance lies below
     // what one FP64 iteration reaches from a start ~1e-6 off (~1e-12): the FP64 path's
     // 1e-13, not the mixed path's 1e-10
-    if (tol < 1e-11) newton_step_f32(c, cf, u);
+    F3 uf1 = uin;   // FP32 value of u at the first direction (when has1)
+    bool has1 = has_uin;
+    if (tol < 1e-11) {
+        F3 un;
+        if (newton_step_f32(c, cf, u, has_uin, uin, un)) {
+            uf1 = un;
+            has1 = true;
+        }
+    }
     evaluate(c, u, e);
     for (int it = 1; it <= kmax; it++) {
         double dx[3];
         // FP32 directions first; the FP64 Jacobian takes over if they have not
         // converged within 10 iterations or fail
-        if (it > 10 || !newton_dir_f32(c, cf, u, e, dx)) {
+        if (it > 10 || !newton_dir_f32(c, cf, u, e, dx, it == 1 && has1, uf1)) {
             double J[3][3];
             jacobian(c, u, e, J);
             if (!newton_dir(J, e.f, dx)) return -1;

@@ -43,6 +43,8 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     ci.gh = g.gh;
     ci.igh = g.igh;
     ci.xi = a.xi;
+    ci.ighf = a.ighf;
+    ci.xif = a.xif;
     ci.D = qb.p[0][id] * ip6;
     ci.S[0] = qb.p[1][id] * ip6 * ip2;
     ci.S[1] = qb.p[2][id] * ip6 * ip2;
@@ -56,7 +58,9 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
         ci.B[i] = (CC ? bf.p[i][id] : cell_qB(g, bf.p[i], i, c)) * ip4;
     }
     const double et = eta ? eta[id] : eta_u;
-    ci.etat = a_dt > 0.0 ? et / (al * a_dt) : -1.0;
+    // flat: eta / (a_ii dt) with the host's reciprocal, no division
+    ci.etat = a_dt > 0.0 ? (M ? et / (al * a_dt) : et * a.ia_dt) : -1.0;
+    cell_derive(ci);
     double u[3];
     Eval e;
     bool atmo = false;
@@ -65,6 +69,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     // latest primitives
     const bool hist = a.hs[0] != nullptr;
     float hsv[3] = {0.0f, 0.0f, 0.0f};
+    F3 ust = {{0.0f, 0.0f, 0.0f}};
     if (rho_atm > 0.0 && ci.D < 10.0 * rho_atm) {
         atmo = true;   // (its history is left as it is)
     } else {
@@ -73,17 +78,18 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
         for (int i = 0; i < 3; i++) {
             if (hist) {
                 hsv[i] = a.hs[i][id];
-                u[i] = (double)(hsv[i] + a.hd[i][id]);
+                ust.x[i] = hsv[i] + a.hd[i][id];
+                u[i] = f2d_int(ust.x[i]);
             } else {
                 u[i] = p2 * prim.p[1 + i][id];
             }
             if (!(fabs(u[i]) < 1e30)) fin = false;
         }
         if (!fin) u[0] = u[1] = u[2] = 0.0;
-        int it = newton_solve(ci, u, e, kmax, tol);
+        int it = newton_solve(ci, u, e, kmax, tol, hist && fin, ust);
         if (it < 0 && fin) {
             u[0] = u[1] = u[2] = 0.0;
-            it = newton_solve(ci, u, e, kmax, tol);
+            it = newton_solve(ci, u, e, kmax, tol, false, ust);
         }
         if (it < 0) {
             atomicAdd(nfail, 1ull);
@@ -107,7 +113,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
         e.E[1] = ci.Es[1];
         e.E[2] = ci.Es[2];
     } else {
-        const double iW = 1.0 / e.W;
+        const double iW = e.iW;
         rho = ci.D * iW;
         pres = (e.wt * iW - rho) * g.igh;
     }
@@ -130,10 +136,10 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
         prim.p[1 + i][id] = u[i] * ip2;
         prim.p[5 + i][id] = e.E[i] * ip2;
         const double qEn = p4 * e.E[i];
-        if (R.p[0]) R.p[i][id] = a_dt > 0.0 ? (qEn - qEs[i]) / a_dt : 0.0;
+        if (R.p[0]) R.p[i][id] = a_dt > 0.0 ? (qEn - qEs[i]) * a.ia_dt : 0.0;
         if (qE_out.p[0]) qE_out.p[i][id] = qEn;
         if (hist && !atmo) {
-            const float un = (float)u[i];
+            const float un = d2f_int(u[i]);
             a.hd[i][id] = un - hsv[i];
             a.hs[i][id] = un;
         }

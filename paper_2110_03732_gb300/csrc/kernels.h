@@ -29,6 +29,8 @@ struct ImpArgs {
     const double* eta;      // per-cell resistivity or NULL
     double eta_u;
     double a_dt;            // a_ii dt (<= 0: E held fixed)
+    double ia_dt;           // 1 / (a_ii dt) (0 when a_dt <= 0)
+    float ighf, xif;        // FP32 1/Gamma_hat and xi
     P8 prim;                // in: Newton start; out: stage primitives
     P3 R;                   // stiff rates (or NULL)
     P3 qE_out;              // solved q_E (or NULL)
