@@ -560,8 +560,8 @@ def bench_serving(dev, args):
 # Newton start history has filled (from the third step on).
 # TRAFFIC: dram read + write bytes per launch from the same capture (flux: the mean of
 # its two directions).
-FP64_FLOPS_PER_CELL = {"implicit": 377.1, "flux": 269.4, "emf": 95.4, "update": 121.0}
-TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 29.6e6, "emf": 6.4e6, "update": 84.9e6}
+FP64_FLOPS_PER_CELL = {"implicit": 268.0, "flux": 270.9, "emf": 95.4, "update": 121.0}
+TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 30.3e6, "emf": 6.4e6, "update": 84.9e6}
 
 
 def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):

@@ -259,9 +259,7 @@ static void glm_flux_launch(const Dims& g, const GlmFluxArgs& a, int nsm, cudaSt
 {
     const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
                                    : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
-    const double want = 0.75 * nsm * glm_blocks_per_sm<D, M, P>();
-    int K = 8;
-    while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
+    const int K = march_len(g.n[D], other, nsm, glm_blocks_per_sm<D, M, P>(), P ? 1.0 : 0.6);
     launch_k(k_glm_flux<D, M, P>, glm_grid((long long)((g.n[D] + K) / K) * other, 128, nsm), 128, st, g, a, K);
 }
 

@@ -451,17 +451,14 @@ static int march_blocks_per_sm()
     return nb;
 }
 
-// faces per thread: the largest of 8, 4, 2, 1 that still gives three quarters of a
-// full wave of resident blocks (a longer march saves more loads and slopes; a short
-// grid leaves SMs idle)
+// faces per thread by march_len (start-up: 3 cells for MC, 5 for PPM, each about a
+// fifth of a face's work)
 template <int D, bool M, typename T, bool P>
 static void flux_march_launch(const Dims& g, int nsm, cudaStream_t st, const FluxArgs<T>& a)
 {
     const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
                                    : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
-    const double want = 0.75 * nsm * march_blocks_per_sm<D, M, T, P>();
-    int K = 8;
-    while (K > 1 && (double)(((g.n[D] + K) / K) * other + 127) / 128 < want) K /= 2;
+    const int K = march_len(g.n[D], other, nsm, march_blocks_per_sm<D, M, T, P>(), P ? 1.0 : 0.6);
     const int b = grid_for((long long)((g.n[D] + K) / K) * other, 128, nsm);
     launch_k(k_flux_march<D, M, T, P>, b, 128, st, g, a, K);
 }
@@ -501,9 +498,7 @@ static void emf_launch(const Dims& g, int nsm, cudaStream_t st, const EmfArgs<T>
         return;
     }
     const long long other = (long long)g.n[C] * (g.n[A] + 1);
-    const double want = 0.75 * nsm * emf_march_blocks_per_sm<C, M, T, P>();
-    int K = 8;
-    while (K > 1 && (double)(((g.n[B] + K) / K) * other + 127) / 128 < want) K /= 2;
+    const int K = march_len(g.n[B], other, nsm, emf_march_blocks_per_sm<C, M, T, P>(), P ? 1.0 : 0.6);
     launch_k(k_emf_march<C, M, T, P>, grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, st, g, a, K);
 }
 

@@ -44,4 +44,27 @@ inline cudaError_t launch_k(void (*k)(P...), int grid, int block, cudaStream_t s
     return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
 }
 
+// Items (faces or edges) per thread of a march over `other` lines of n + 1 items, with
+// 128-thread blocks of which bps are resident per SM: the K in 8..1 that minimises
+// (waves of resident blocks) x (K + c0), c0 being a march's start-up in items (the
+// cells reconstructed before the first item).  The kernels keep about two blocks per
+// SM and are latency- rather than throughput-limited at that occupancy, so an SM given
+// fewer blocks does not finish sooner: what counts is how many waves there are and how
+// long each thread's march is.  Ties go to the larger K (fewer loads and slopes).
+inline int march_len(int n, long long other, int nsm, int bps, double c0)
+{
+    int best = 8;
+    double best_v = 0.0;
+    for (int K = 8; K >= 1; K--) {
+        const long long blocks = (((long long)(n + K) / K) * other + 127) / 128;
+        const long long slots = (long long)nsm * (bps > 0 ? bps : 1);
+        const double v = (double)((blocks + slots - 1) / slots) * (K + c0);
+        if (K == 8 || v < best_v * (1.0 - 1e-9)) {
+            best = K;
+            best_v = v;
+        }
+    }
+    return best;
+}
+
 }  // namespace grmhd
