@@ -560,7 +560,7 @@ def bench_serving(dev, args):
 # Newton start history has filled (from the third step on).
 # TRAFFIC: dram read + write bytes per launch from the same capture (flux: the mean of
 # its two directions).
-FP64_FLOPS_PER_CELL = {"implicit": 268.0, "flux": 270.9, "emf": 95.4, "update": 121.0}
+FP64_FLOPS_PER_CELL = {"implicit": 268.1, "flux": 270.9, "emf": 84.3, "update": 121.0}
 TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 30.3e6, "emf": 6.4e6, "update": 84.9e6}
 
 
