@@ -272,6 +272,44 @@ __device__ __forceinline__ void face_state(const T* pr, const T* B, int d, T psi
     s.f[5 + d2] = -ap2 * Bh[d1];
 }
 
+// One side's half of the unit-speed HLL flux in flat space (psi = alpha = 1), in the
+// orthonormal frame: g = f + SG q, SG = +1 for the left state and -1 for the right, so
+// that f_L + f_R - (q_R - q_L) = g_L + g_R with q and f as in face_state.  Grouping by
+// state lets shared factors merge: with a = u^d + SG W,
+//   D:     rho u^d + SG rho W                                  = rho a
+//   S_j:   (p + U) delta_dj + rho h u^d u^j - E^d E^j - B^d B^j
+//          + SG (rho h W u^j + (E x B)_j)                      = rho h a u^j + ...
+//   tau:   S_d - rho u^d + SG (rho h W^2 - p + U - rho W)
+//   E^j:   eta^{djk} B_k + SG E^j
+// pr: rho, u^1..3, p, E^1..3; B: the three components; iW gets 1/W of the state.
+template <typename T, int SG>
+__device__ __forceinline__ void face_hll_half(const T* pr, const T* B, int d, T gh, T* g, T& iW)
+{
+    const T s = T(SG);
+    const T rho = pr[0], p = pr[4];
+    const T u[3] = {pr[1], pr[2], pr[3]};
+    const T E[3] = {pr[5], pr[6], pr[7]};
+    const T x = T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    iW = rsqrt_t(x);
+    const T W = x * iW;
+    const T rhoh = rho + gh * p;
+    const T hW = rhoh * W;
+    const T U = T(0.5) * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    const T X[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
+    const T a = u[d] + s * W;
+    const T K = rhoh * a;
+    g[0] = rho * a;
+#pragma unroll
+    for (int j = 0; j < 3; j++) g[1 + j] = K * u[j] - E[d] * E[j] - B[d] * B[j] + s * X[j];
+    g[1 + d] += p + U;
+    const T Sd = hW * u[d] + X[d];
+    g[4] = (Sd - rho * u[d]) + s * (W * (hW - rho) + (U - p));
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    g[5 + d] = s * E[d];
+    g[5 + d1] = B[d2] + s * E[d1];
+    g[5 + d2] = s * E[d2] - B[d1];
+}
+
 // ---------------------------------------------------------------------------
 // implicit electric field + velocity solve (Sec. 2.4), xi = 0, orthonormal frame
 // ---------------------------------------------------------------------------

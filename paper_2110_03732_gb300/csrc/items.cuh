@@ -227,22 +227,22 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     // flux alpha psi^(k_v - 2) times, k = 6, 8, 8, 8, 6, 4, 4, 4: the HLL flux is then
     // alpha psi^(k_v - 2) times the flat-space HLL flux (unit speed) of the
     // orthonormal states.  F stores twice the flux (no 1/2 here: the update folds it).
-    FaceStateT<T> sL, sR;
-    face_state<T>(prL, BL, D, T(1), T(1), (T)g.gh, sL);
-    face_state<T>(prR, BR, D, T(1), T(1), (T)g.gh, sR);
+    T gL[8], gR[8], iWL, iWR;
+    face_hll_half<T, 1>(prL, BL, D, (T)g.gh, gL, iWL);
+    face_hll_half<T, -1>(prR, BR, D, (T)g.gh, gR, iWR);
     const T h2 = alf * pf2, h4 = h2 * pf2, h6 = h4 * pf2;
     const long long o = r0;
 #pragma unroll
     for (int v = 0; v < 8; v++) {
         const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
-        F.p[v][o] = (double)((sL.f[v] + sR.f[v] - (sR.q[v] - sL.q[v])) * hv);
+        F.p[v][o] = (double)((gL[v] + gR[v]) * hv);
     }
     if (vbar && vbar[0]) {
         // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
         // vbar^j = (c- vhat^j_R + c+ vhat^j_L)/(c- + c+), their mean for c+ = c-;
         // v^j = u_hat^j / (psi^2 W)
         const double al = (double)(alf * ipf2);
-        const double iL = (double)sL.iW, iR = (double)sR.iW;
+        const double iL = (double)iWL, iR = (double)iWR;
         const double vL1 = al * (double)prL[1 + T1] * iL, vR1 = al * (double)prR[1 + T1] * iR;
         const double vL2 = al * (double)prL[1 + T2] * iL, vR2 = al * (double)prR[1 + T2] * iR;
         vbar[0][o] = (vR1 + vL1) * 0.5;
