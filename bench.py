@@ -554,14 +554,14 @@ def bench_serving(dev, args):
 
 # FP64 flops per cell per launch of each kernel kind (2 * DFMA + DADD + DMUL thread
 # instructions / cells), counted by ncu on the 512^2 workload for the kernels as they
-# stand (profiles/ot512_fp64_kernels.md).  The flux figure is per launch, the mean of
-# its two directions (x marches 5 faces per thread, y 7); the EMF one is the single EMF launch of a flat 2-D stage (the other two
+# stand (profiles/ot512_fp64_kernels.md).  The flux figure is per launch (one
+# direction; both march 7 faces per thread); the EMF one is the single EMF launch of a flat 2-D stage (the other two
 # components come out of the flux kernels); the implicit one is a launch after the
 # Newton start history has filled (from the third step on).
 # TRAFFIC: dram read + write bytes per launch from the same capture (flux: the mean of
 # its two directions).
-FP64_FLOPS_PER_CELL = {"implicit": 268.1, "flux": 258.4, "emf": 84.3, "update": 121.0}
-TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 29.9e6, "emf": 6.4e6, "update": 84.9e6}
+FP64_FLOPS_PER_CELL = {"implicit": 268.1, "flux": 255.9, "emf": 84.3, "update": 121.0}
+TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 30.4e6, "emf": 6.4e6, "update": 84.6e6}
 
 
 def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):

@@ -265,12 +265,13 @@ grmhd_status grmhd_set_timing(grmhd_ctx* ctx, int enable);
 grmhd_status grmhd_kernel_times(grmhd_ctx* ctx, double* ms, long long* launches);
 
 /* Launch overlap (not part of the paper's method: scheduling only).  When enabled,
- * grmhd_stage / grmhd_step launch their kernels with programmatic dependent launch:
- * a kernel may be scheduled while the one before it on the stream drains its last
- * blocks, and waits on the device until that one has completed and its writes are
- * visible before it reads or writes anything.  Results are bitwise those of plain
- * launches.  Ignored while per-kernel timing is on (the events between the launches
- * serialise them).  Off by default for a context made by grmhd_create. */
+ * grmhd_stage / grmhd_step launch their kernels with programmatic dependent launch: a
+ * kernel may be scheduled as soon as every block of the one before it on the stream
+ * has finished, ahead of that grid's completion and memory flush.  It waits on the
+ * device until that grid has completed and its writes are visible before it reads or
+ * writes anything.  Results are bitwise those of plain launches.  Ignored while
+ * per-kernel timing is on (the events between the launches serialise them).  Off by
+ * default for a context made by grmhd_create. */
 grmhd_status grmhd_set_launch_overlap(grmhd_ctx* ctx, int enable);
 
 /* Message of the last error on the calling thread ("" if none). */

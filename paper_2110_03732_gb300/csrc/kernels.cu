@@ -452,13 +452,18 @@ static int march_blocks_per_sm()
 }
 
 // faces per thread by march_len (start-up: 3 cells for MC, 5 for PPM, each about a
-// fifth of a face's work)
+// fifth of a face's work).  For FP64, waves are counted at no more than two resident
+// blocks per SM.  At 8 warps the FP64 flux already keeps the FP64 pipe ~75-80 % busy, and
+// a third block (where the registers allow it) adds no throughput.  A shorter march to
+// fill that block would only add start-ups: 5 faces at three blocks per SM took 123 us
+// per 512^2 launch, against 117 us for 7 faces at two.
 template <int D, bool M, typename T, bool P>
 static void flux_march_launch(const Dims& g, int nsm, cudaStream_t st, const FluxArgs<T>& a)
 {
     const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
                                    : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
-    const int K = march_len(g.n[D], other, nsm, march_blocks_per_sm<D, M, T, P>(), P ? 1.0 : 0.6);
+    const int bps = march_blocks_per_sm<D, M, T, P>();
+    const int K = march_len(g.n[D], other, nsm, sizeof(T) == 8 && bps > 2 ? 2 : bps, P ? 1.0 : 0.6);
     const int b = grid_for((long long)((g.n[D] + K) / K) * other, 128, nsm);
     launch_k(k_flux_march<D, M, T, P>, b, 128, st, g, a, K);
 }

@@ -2,14 +2,17 @@
 //
 // The kernels of one IMEX stage run back to back on one stream, each reading what the
 // one before wrote.  Launched with the programmatic-stream-serialisation attribute, a
-// kernel may be scheduled while its predecessor is still draining its last blocks:
-// every stage kernel opens with grid_dep_sync(), which waits until the preceding grid
-// has completed and its memory is visible (griddepcontrol.wait) and only then lets the
-// next grid be scheduled (griddepcontrol.launch_dependents).  So at most two grids are
-// in flight, the waiting grid's blocks hold no more than the slots its predecessor has
-// already given up, and no kernel touches memory before its predecessor has finished;
-// what is hidden is the launch latency between the two.  Kernels launched without the
-// attribute (every launch while launch_overlap is off) see both instructions as no-ops.
+// kernel may be scheduled before its predecessor has completed and flushed.  Every
+// stage kernel opens with grid_dep_sync() (griddepcontrol.wait): it waits until the
+// preceding grid has completed and its memory is visible.  No kernel triggers its
+// dependents explicitly, so each block triggers when it exits.  A kernel's blocks are
+// therefore placed only once every block of its predecessor has finished its work, and
+// what is hidden is the launch latency and the completion and flush of the grid before.
+// An early trigger (griddepcontrol.launch_dependents at the top of each kernel) was
+// slower: the next kernel's waiting blocks then sat on SMs beside running ones for the
+// whole of a launch.  Since no kernel touches memory before its predecessor has
+// finished, the results are bitwise those of plain launches.  Kernels launched without
+// the attribute (every launch while launch_overlap is off) see the wait as a no-op.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -23,7 +26,6 @@ extern thread_local bool launch_overlap;
 __device__ __forceinline__ void grid_dep_sync()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 // k<<<grid, block, 0, st>>>(args...), with the programmatic attribute when
