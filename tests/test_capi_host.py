@@ -210,3 +210,47 @@ def test_invalid_reconstruction_rejected(lib, case):
     ctx = C.c_void_p()
     assert lib.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
     assert not ctx.value
+
+
+def test_null_context_is_refused_by_every_call(lib):
+    """Every call that takes a context returns GRMHD_ERR_ARG (-1) with a message for a
+    NULL one, before touching the device."""
+    vp = C.c_void_p
+    null = vp(None)
+    buf = (C.c_double * 8)()
+    ptrs = (vp * 11)()
+    sz = C.c_size_t(0)
+    ll = (C.c_longlong * 4)()
+    calls = {
+        "grmhd_set_timing": (null, C.c_int(1)),
+        "grmhd_set_launch_overlap": (null, C.c_int(1)),
+        "grmhd_kernel_times": (null, buf, ll),
+        "grmhd_bind": (null, ptrs, ptrs, vp(1), C.c_size_t(0)),
+        "grmhd_bind_phi": (null, vp(1)),
+        "grmhd_set_metric": (null, null, null),
+        "grmhd_set_eta": (null, null, C.c_double(1.0)),
+        "grmhd_set_dynamo": (null, C.c_double(0.1)),
+        "grmhd_init_from_prims": (null, ptrs, ptrs, ptrs, null),
+        "grmhd_compute_dt": (null, buf, null),
+        "grmhd_stage": (null, C.c_int(0), C.c_double(1e-3), null),
+        "grmhd_step": (null, C.c_double(1e-3), null),
+        "grmhd_get_prims": (null, ptrs, null),
+        "grmhd_implicit": (null, C.c_double(1e-3), ptrs, ptrs, ptrs, ptrs, null),
+        "grmhd_explicit_L": (null, ptrs, ptrs, ptrs, null),
+        "grmhd_explicit_L_glm": (null, ptrs, ptrs, vp(1), ptrs, null),
+        "grmhd_diagnostics": (null, buf, buf, ll, null),
+        "grmhd_clean_divb": (null, C.c_int(1), vp(1), C.c_size_t(0), null),
+        "grmhd_start_bytes": (null, C.byref(sz)),
+        "grmhd_save_start": (null, vp(1), C.c_size_t(0), null),
+        "grmhd_load_start": (null, vp(1), C.c_size_t(0), null),
+    }
+    lib.grmhd_last_error.restype = C.c_char_p
+    for name, args in calls.items():
+        f = getattr(lib, name)
+        f.restype = C.c_int
+        assert f(*args) == -1, name
+        assert lib.grmhd_last_error(), name
+    lib.grmhd_launch_count.restype = C.c_longlong
+    assert lib.grmhd_launch_count(null) == 0
+    lib.grmhd_destroy.restype = C.c_int
+    assert lib.grmhd_destroy(null) == 0
