@@ -230,7 +230,7 @@ def test_null_context_is_refused_by_every_call(lib):
         "grmhd_set_metric": (null, null, null),
         "grmhd_set_eta": (null, null, C.c_double(1.0)),
         "grmhd_set_dynamo": (null, C.c_double(0.1)),
-        "grmhd_init_from_prims": (null, ptrs, ptrs, ptrs, null),
+        "grmhd_init_from_prims": (null, ptrs, ptrs, null),
         "grmhd_compute_dt": (null, buf, null),
         "grmhd_stage": (null, C.c_int(0), C.c_double(1e-3), null),
         "grmhd_step": (null, C.c_double(1e-3), null),
