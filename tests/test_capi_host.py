@@ -254,3 +254,36 @@ def test_null_context_is_refused_by_every_call(lib):
     assert lib.grmhd_launch_count(null) == 0
     lib.grmhd_destroy.restype = C.c_int
     assert lib.grmhd_destroy(null) == 0
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """The binding's ctypes Structures have the sizes and field offsets that a C
+    compiler gives the header's structs (a mismatch would silently corrupt them)."""
+    from paper_2110_03732_gb300.grmhd import Grid, Params, Tableau
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"grmhd_grid": Grid, "grmhd_params": Params, "grmhd_tableau": Tableau}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "grmhd.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    # grmhd.h refers to cudaStream_t only through an opaque struct pointer
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True, timeout=120)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True, timeout=30).stdout.split("\n")
+    got = {}
+    for ln in out:
+        parts = ln.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
