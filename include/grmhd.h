@@ -75,7 +75,8 @@ enum { GRMHD_REC_MC = 0, GRMHD_REC_PPM = 1 };
 
 /* Uniform Cartesian grid (Sec. 5 test set-ups).  bc: per direction; FIXED keeps the
  * ghost values that init wrote (Sec. 5, "values at the outer boundaries are kept
- * fixed").  lo/hi give the physical extent; dx = (hi - lo)/n. */
+ * fixed").  lo/hi give the physical extent (finite, lo < hi in every active
+ * direction); dx = (hi - lo)/n. */
 typedef struct {
     int ndim;      /* 1, 2 or 3 active directions */
     int n[3];      /* interior cells; ignored (taken as 1) for inactive directions */
@@ -172,7 +173,9 @@ grmhd_status grmhd_set_dynamo(grmhd_ctx* ctx, double xi);
  * GLM context: A_edge, if given, is a potential at cell centres (read on the whole
  * padded grid) and the interior cell fields become its central-difference curl
  * (Sec. 4, cell-centred case; ghost values of q_B are left as bound); q uses the
- * cell fields directly.  q_Phi is taken as bound (zero it for the usual start). */
+ * cell fields directly.  prim then holds 9 pointers: the 8 above and the primitive
+ * Phi (a padded cell array, or NULL for Phi = 0), and the bound q_Phi becomes
+ * psi^6 Phi at every padded cell (Sec. 3.1). */
 grmhd_status grmhd_init_from_prims(grmhd_ctx* ctx, const double* const* prim, const double* const* A_edge,
                                    grmhd_stream_t stream);
 
@@ -321,10 +324,11 @@ grmhd_status grmhd_batch_destroy(grmhd_batch* b);
  * is all owned by its own pool or arena, or a loop that must not allocate after
  * start-up) and so cannot provide the scratch that grmhd_bind needs.
  *
- * grid: as for grmhd_create; bface: 3 padded face arrays (device, q_B^x, q_B^y,
- * q_B^z, read-only); out: 3 device doubles written with {mean |div q_B|, rms,
- * max |div q_B|} over interior cells, the same quantities as grmhd_diagnostics.
- * Runs on `stream`; does not synchronise.
+ * grid: as for grmhd_create (finite lo < hi in every active direction); bface: 3
+ * padded face arrays (device, q_B^x, q_B^y, q_B^z, read-only; the array of an
+ * inactive direction is never read and may be NULL); out: 3 device doubles written
+ * with {mean |div q_B|, rms, max |div q_B|} over interior cells, the same quantities
+ * as grmhd_diagnostics.  Runs on `stream`; does not synchronise.
  *
  * Scratch: a fixed array inside the library (8192 rows x 3 doubles = 192 KiB) that
  * every GPU loading the library holds until the process exits; grids with more than
@@ -333,8 +337,10 @@ grmhd_status grmhd_batch_destroy(grmhd_batch* b);
  * calls share the array: calls that overlap on the GPU (on different streams, or
  * from different threads) race and must be ordered by the caller.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  It calls no
- * allocation routine. */
+ * that device current; make that first call before any stream capture.  The address
+ * is kept until the process exits: after a reset of that device (cudaDeviceReset)
+ * it is stale, so a process that resets a device must not call this entry point on
+ * it again.  It calls no allocation routine. */
 grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double* const* bface, double* out,
                                 grmhd_stream_t stream);
 

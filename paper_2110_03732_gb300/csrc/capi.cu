@@ -102,7 +102,10 @@ grmhd_status check_grid(const grmhd_grid* g)
     if (g->ndim < 1 || g->ndim > 3) return fail(GRMHD_ERR_ARG, "ndim must be 1, 2 or 3");
     for (int d = 0; d < g->ndim; d++) {
         if (g->n[d] < 1) return fail(GRMHD_ERR_ARG, "n[d] must be >= 1 in every active direction");
-        if (!(g->hi[d] > g->lo[d])) return fail(GRMHD_ERR_ARG, "hi must exceed lo in every active direction");
+        if (!std::isfinite(g->lo[d]) || !std::isfinite(g->hi[d]) || !(g->hi[d] > g->lo[d]) ||
+            !std::isfinite(g->n[d] / (g->hi[d] - g->lo[d])))
+            return fail(GRMHD_ERR_ARG, "lo and hi must be finite with hi > lo (and n/(hi - lo) finite) in every "
+                                       "active direction");
         if (g->bc[d] < 0 || g->bc[d] > 2) return fail(GRMHD_ERR_ARG, "bc must be PERIODIC, OUTFLOW or FIXED");
         if (g->bc[d] == GRMHD_BC_PERIODIC && g->n[d] < 2)
             return fail(GRMHD_ERR_ARG, "a periodic direction needs at least 2 cells");
@@ -693,7 +696,8 @@ grmhd_status grmhd_init_from_prims(grmhd_ctx* c, const double* const* prim, cons
             e = cudaMemcpyAsync(c->prim[v], prim[v], bytes, cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
         }
-        e = launch_prim2con_cc(g, cp8c(prim), cp3(c->bf), c->psi, p8(c->q), c->nsm, st);
+        // prim[8] is the primitive Phi (NULL: zero); the kernel densitises it
+        e = launch_prim2con_cc(g, cp8c(prim), cp3(c->bf), c->psi, prim[8], c->qphi, p8(c->q), c->nsm, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "prim2con kernel");
         return init_history(c, prim, st);

@@ -63,14 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_divb_rows(Dims g, CP3 bf, double* 
         c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
         c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
         const long long o = grmhd::lin(g, c[0], c[1], c[2]);
-        double dv = 0.0;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            if (!g.act[d]) continue;
-            int cu[3] = {c[0], c[1], c[2]};
-            cu[d] += 1;
-            dv += (bf.p[d][grmhd::face_at(g, d, cu)] - bf.p[d][o]) * g.idx[d];
-        }
+        const double dv = grmhd::cell_divb(g, bf.p, c, o);
         a = fabs(dv);
         s = dv * dv;
         m = fabs(dv);
@@ -137,7 +130,10 @@ grmhd_status err(grmhd_status s, const char* msg)
     return s;
 }
 
-// address of g_divb_rows on the current device, looked up once per device
+// address of g_divb_rows on the current device, looked up once per device (on the
+// first call with that device current) and kept until the process exits.  A device
+// reset unloads the module, so the kept address is stale afterwards: a process that
+// resets a device must not call grmhd_divb_noalloc on it again.
 grmhd_status rows_address(double** out)
 {
     int dev = -1;
@@ -168,8 +164,11 @@ extern "C" grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double*
     for (int d = 0; d < 3; d++) {
         g.act[d] = d < grid->ndim;
         if (g.act[d]) {
-            if (grid->n[d] < 1 || !(grid->hi[d] > grid->lo[d]) || grid->bc[d] < 0 || grid->bc[d] > 2)
-                return err(GRMHD_ERR_ARG, "grmhd_divb_noalloc: invalid grid (n >= 1, hi > lo, bc 0..2)");
+            if (grid->n[d] < 1 || !std::isfinite(grid->lo[d]) || !std::isfinite(grid->hi[d]) ||
+                !(grid->hi[d] > grid->lo[d]) || !std::isfinite(grid->n[d] / (grid->hi[d] - grid->lo[d])) ||
+                grid->bc[d] < 0 || grid->bc[d] > 2)
+                return err(GRMHD_ERR_ARG,
+                           "grmhd_divb_noalloc: invalid grid (n >= 1, finite lo < hi with finite n/(hi-lo), bc 0..2)");
             if (grid->bc[d] == GRMHD_BC_PERIODIC && grid->n[d] < 2)
                 return err(GRMHD_ERR_ARG, "grmhd_divb_noalloc: a periodic direction needs at least 2 cells");
         }
@@ -194,8 +193,9 @@ extern "C" grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double*
     if (s != GRMHD_OK) return s;
     CP3 bf;
     for (int d = 0; d < 3; d++) {
-        if (!bface[d]) return err(GRMHD_ERR_ARG, "grmhd_divb_noalloc: bface[d] is NULL");
-        bf.p[d] = bface[d];
+        // an inactive direction's array is never read and may be NULL
+        if (g.act[d] && !bface[d]) return err(GRMHD_ERR_ARG, "grmhd_divb_noalloc: bface[d] is NULL for an active d");
+        bf.p[d] = g.act[d] ? bface[d] : nullptr;
     }
     cudaStream_t st = (cudaStream_t)stream;
     k_divb_rows<<<(unsigned)rows, kThreads, 0, st>>>(g, bf, scratch);

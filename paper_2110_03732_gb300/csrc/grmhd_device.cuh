@@ -81,6 +81,22 @@ __device__ __forceinline__ long long face_at(const Dims& g, int fd, const int* c
     return lin(g, m[0], m[1], m[2]);
 }
 
+// discrete divergence of the staggered q_B at the interior cell with padded
+// coordinates c and linear index o (Sec. 3.2): sum over the active directions of
+// (upper face - lower face) / dx; the upper face is mapped by the boundary rule
+__device__ __forceinline__ double cell_divb(const Dims& g, const double* const* bf, const int* c, long long o)
+{
+    double dv = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (!g.act[d]) continue;
+        int cu[3] = {c[0], c[1], c[2]};
+        cu[d] += 1;
+        dv += (bf[d][face_at(g, d, cu)] - bf[d][o]) * g.idx[d];
+    }
+    return dv;
+}
+
 // cell-centred q_B^e of the cell at padded coordinates c: the cell is mapped first,
 // then the mean of its two e-faces (the lower face alone where the upper one lies
 // outside a fixed-boundary array); an inactive e stores the cell value itself

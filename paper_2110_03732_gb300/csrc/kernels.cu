@@ -200,8 +200,10 @@ __global__ void k_curlA_cc(Dims g, CP3 A, P3 qB)
     }
 }
 
-// prim -> cons with cell-centred q_B, every padded cell
-__global__ void k_prim2con_cc(Dims g, CP8 prim, CP3 qB, const double* __restrict__ psi, P8 q)
+// prim -> cons with cell-centred q_B, every padded cell; q_Phi = psi^6 Phi (Sec. 3.1)
+// from the primitive Phi (NULL: zero)
+__global__ void k_prim2con_cc(Dims g, CP8 prim, CP3 qB, const double* __restrict__ psi,
+                              const double* __restrict__ phi, double* __restrict__ qphi, P8 q)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < g.ncell;
          t += (long long)gridDim.x * blockDim.x) {
@@ -216,6 +218,7 @@ __global__ void k_prim2con_cc(Dims g, CP8 prim, CP3 qB, const double* __restrict
         face_state(pr, B, 0, ps, 1.0, g.gh, s);
 #pragma unroll
         for (int v = 0; v < 8; v++) q.p[v][t] = s.q[v];
+        qphi[t] = phi ? p6 * phi[t] : 0.0;
     }
 }
 
@@ -297,14 +300,7 @@ __global__ void __launch_bounds__(256) k_diag(Dims g, CP3 bf, CP8 q, double dV, 
         c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
         c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
         const long long o = lin(g, c[0], c[1], c[2]);
-        double dv = 0.0;
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            if (!g.act[d]) continue;
-            int cu[3] = {c[0], c[1], c[2]};
-            cu[d] += 1;
-            dv += (bf.p[d][face_at(g, d, cu)] - bf.p[d][o]) * g.idx[d];
-        }
+        const double dv = cell_divb(g, bf.p, c, o);
         s1 += fabs(dv);
         s2 += dv * dv;
         mx = fmax(mx, fabs(dv));
@@ -654,9 +650,10 @@ cudaError_t launch_curlA_cc(const Dims& g, CP3 A, P3 qB, int nsm, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, P8 q, int nsm, cudaStream_t st)
+cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, const double* phi, double* qphi,
+                               P8 q, int nsm, cudaStream_t st)
 {
-    k_prim2con_cc<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, prim, qB, psi, q);
+    k_prim2con_cc<<<grid_for(g.ncell, 256, nsm), 256, 0, st>>>(g, prim, qB, psi, phi, qphi, q);
     return cudaGetLastError();
 }
 

@@ -158,7 +158,8 @@ cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStr
 cudaError_t launch_glm_flux(const Dims& g, int d, const GlmFluxArgs& a, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_glm_update(const Dims& g, const GlmUpdateArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_curlA_cc(const Dims& g, CP3 A, P3 qB, int nsm, cudaStream_t st);
-cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, P8 q, int nsm, cudaStream_t st);
+cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* psi, const double* phi, double* qphi,
+                               P8 q, int nsm, cudaStream_t st);
 cudaError_t launch_diag_cc(const Dims& g, CP3 qB, CP8 q, double dV, double* part, int nblk, double* out,
                            cudaStream_t st);
 

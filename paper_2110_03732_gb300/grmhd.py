@@ -229,16 +229,14 @@ class Solver:
     def init_from_prims(self, prim, A_edge=None, bface=None, stream=None, phi=None):
         """Initial state.  CT: A_edge on edges (curl -> faces) or face q_B in bface.
         GLM: A_edge is a cell-centred potential (central curl), or bface holds the
-        cell-centred q_B; phi is the initial q_Phi (zero if None)."""
+        cell-centred q_B; phi is the initial primitive Phi (None: zero), which the
+        library densitises into q_Phi."""
         prim = [self._dev(p) for p in prim]
         if bface is not None:
             for d in range(3):
                 self.bf[d].copy_(self._dev(bface[d]))
         if self.glm:
-            if phi is None:
-                self.phi.zero_()
-            else:
-                self.phi.copy_(self._dev(phi))
+            prim = prim + [None if phi is None else self._dev(phi)]
         A = None if A_edge is None else [self._dev(a) for a in A_edge]
         pp, k1 = _ptrs(prim)
         pa, k2 = _ptrs(A) if A is not None else (None, None)
@@ -257,13 +255,9 @@ class Solver:
         if getattr(prob, "xi", 0.0):
             s.set_dynamo(prob.xi)
         if s.glm:
-            # cell-centred fields: the potential at cell centres, else q_B given at cells;
-            # q_Phi = psi^6 Phi
-            qphi = None
-            if prob.phi is not None:
-                qphi = prob.phi if prob.psi is None else prob.psi ** 6 * prob.phi
+            # cell-centred fields: the potential at cell centres, else q_B given at cells
             s.init_from_prims(prob.prim, A_edge=prob.A_cell, bface=None if prob.A_cell is not None else prob.bcell,
-                              phi=qphi)
+                              phi=prob.phi)
         else:
             s.init_from_prims(prob.prim, A_edge=prob.A_edge, bface=None if prob.A_edge is not None else prob.bface)
         return s

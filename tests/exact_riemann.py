@@ -8,7 +8,8 @@ rarefactions from the Riemann invariant
 
 along the isentrope p = K rho^Gamma.  Used as an independent pin for the oracle's
 hydrodynamics at B = E = 0 (the ideal-limit shock tube).  Self-checks of this file
-against the jump conditions and the invariant's ODE are in test_oracle_pins.py.
+against the jump conditions and the invariant's ODE are in test_oracle_physics.py
+(test_exact_riemann_solver_self_checks).
 """
 from __future__ import annotations
 
