@@ -52,10 +52,10 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--n", type=int, default=N_OT, help=argparse.SUPPRESS)
-    ap.add_argument("--case", choices=["star", "clean"], default=None,
-                    help="run one secondary workload alone on a small case (for profiling) and print its "
-                         "timings: the 3-D star with --case-n cells a side, or the multigrid cleaning of the "
-                         "--case-n^2 Orszag-Tang problem")
+    ap.add_argument("--case", choices=["star", "clean", "ot", "ot_mixed"], default=None,
+                    help="run one workload alone (for profiling) and print its timings: the 3-D star with "
+                         "--case-n cells a side, the multigrid cleaning of the --case-n^2 Orszag-Tang problem, "
+                         "or the --case-n^2 Orszag-Tang step in FP64 or mixed precision")
     ap.add_argument("--case-n", type=int, default=96)
     return ap.parse_args()
 
@@ -67,8 +67,14 @@ def run_case(args, grmhd, P, dev):
     n = args.case_n
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if args.case == "star":
-        S = grmhd.Solver.from_problem(P.star(n), device=dev)
+    if args.case in ("star", "ot", "ot_mixed"):
+        if args.case == "star":
+            S = grmhd.Solver.from_problem(P.star(n), device=dev)
+            name = f"star_3d_{n}^3_fp64"
+        else:
+            prec = "mixed" if args.case == "ot_mixed" else "fp64"
+            S = grmhd.Solver.from_problem(P.orszag_tang(n), device=dev, precision=prec)
+            name = f"orszag_tang_2d_{n}^2_{prec}"
         dt = S.compute_dt()
         for _ in range(args.warmup):
             S.step(dt)
@@ -81,7 +87,7 @@ def run_case(args, grmhd, P, dev):
         e1.record()
         e1.synchronize()
         kt = S.kernel_times()
-        return {"case": f"star_3d_{n}^3_fp64", "ms_per_step": e0.elapsed_time(e1) / args.steps,
+        return {"case": name, "ms_per_step": e0.elapsed_time(e1) / args.steps,
                 "us_per_launch": {k: 1e3 * v[0] / max(v[1], 1) for k, v in kt.items()},
                 "newton_failures": S.diagnostics()[2]}
     S = grmhd.Solver.from_problem(P.orszag_tang(n), device=dev)

@@ -110,6 +110,9 @@ grmhd_status check_grid(const grmhd_grid* g)
         if (g->bc[d] == GRMHD_BC_PERIODIC && g->n[d] < 2)
             return fail(GRMHD_ERR_ARG, "a periodic direction needs at least 2 cells");
     }
+    long long cells = 1;
+    for (int d = 0; d < g->ndim; d++) cells *= g->n[d];
+    if (cells >= (1ll << 32)) return fail(GRMHD_ERR_ARG, "grids of 2^32 or more interior cells are not supported");
     return GRMHD_OK;
 }
 
@@ -145,6 +148,8 @@ Dims make_dims(const grmhd_grid* gr, double gam)
     g.st[2] = (long long)g.N[0] * g.N[1];
     g.gh = gam / (gam - 1.0);
     g.igh = (gam - 1.0) / gam;
+    g.dv[0] = make_fastdiv((unsigned)g.n[0]);
+    g.dv[1] = make_fastdiv((unsigned)g.n[1]);
     return g;
 }
 
@@ -273,8 +278,12 @@ ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE
     a.qE_out = qE_out;
     a.kmax = c->par.newton_kmax;
     a.tol = c->par.newton_tol;
+    a.tolf = (float)c->par.newton_tol;
+    a.stiff = a_dt > 0.0;
     a.rho_atm = c->par.rho_atm;
     a.p_atm = c->par.p_atm;
+    a.atm = c->par.rho_atm > 0.0;
+    a.d_atm = 10.0 * c->par.rho_atm;
     a.xi = c->xi;
     a.p32 = p32;
     a.nfail = c->nfail;

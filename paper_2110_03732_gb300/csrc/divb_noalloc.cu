@@ -184,6 +184,8 @@ extern "C" grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double*
     g.st[1] = g.N[0];
     g.st[2] = (long long)g.N[0] * g.N[1];
     g.gh = g.igh = 0.0;
+    g.dv[0] = grmhd::make_fastdiv((unsigned)g.n[0]);
+    g.dv[1] = grmhd::make_fastdiv((unsigned)g.n[1]);
     const long long rows = (cells + kThreads - 1) / kThreads;
     if (rows > kMaxRows)
         return err(GRMHD_ERR_ARG,

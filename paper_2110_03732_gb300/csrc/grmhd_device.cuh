@@ -11,9 +11,44 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dword.cuh"
+
 namespace grmhd {
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_FIXED = 2 };
+
+// Unsigned 32-bit division by a run-time invariant d >= 1 through a multiply-high
+// (Granlund & Montgomery, PLDI 1994, the unsigned form exact for every 32-bit
+// dividend): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// t / d = (h + ((t - h) >> min(l, 1))) >> max(l - 1, 0), h = umulhi(t, m).  The
+// compiler's own division by a run-time value goes through float reciprocals and
+// conversions, which on GB300 share the FP64 pipe with the implicit solve.
+struct FastDiv {
+    unsigned m, d;
+    int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d)
+{
+    int l = 0;
+    while (l < 32 && (1ull << l) < d) l++;
+    FastDiv f;
+    f.d = d;
+    f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l - 1 > 0 ? l - 1 : 0;
+    return f;
+}
+
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned t, const FastDiv& f)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned h = __umulhi(t, f.m);
+#else
+    const unsigned h = (unsigned)(((unsigned long long)t * f.m) >> 32);
+#endif
+    return (h + ((t - h) >> f.s1)) >> f.s2;
+}
 
 // Padded grid, passed by value to every kernel.  Active directions have ng = 2 ghost
 // cells per side; inactive ones have one cell and no ghosts.  Arrays are x-fastest.
@@ -24,7 +59,20 @@ struct Dims {
     double gh;             // Gamma_hat_1 = Gamma/(Gamma - 1)
     double igh;            // 1/Gamma_hat_1
     long long ncell;       // padded cells
+    FastDiv dv[2];         // division by n[0] and by n[1] (interior cell index -> i, j, k)
 };
+
+// padded coordinates of interior cell t (x fastest); t < 2^32 (the library refuses
+// grids of 2^32 or more interior cells)
+__device__ __forceinline__ void interior_coords(const Dims& g, long long t, int* c)
+{
+    const unsigned tt = (unsigned)t;
+    const unsigned q0 = fdiv(tt, g.dv[0]);
+    const unsigned q1 = fdiv(q0, g.dv[1]);
+    c[0] = g.ng[0] + (int)(tt - q0 * (unsigned)g.n[0]);
+    c[1] = g.ng[1] + (int)(q0 - q1 * (unsigned)g.n[1]);
+    c[2] = g.ng[2] + (int)q1;
+}
 
 struct P8 { double* p[8]; };          // rho, u^1..3, p, E^1..3  (or 8 conserved)
 struct P3 { double* p[3]; };          // three face / edge / R arrays
@@ -326,6 +374,77 @@ __device__ __forceinline__ void face_hll_half(const T* pr, const T* B, int d, T 
     g[5 + d2] = s * E[d2] - B[d1];
 }
 
+// binary64 <-> binary32 on the integer pipe.  On GB300 the hardware conversions (F2F)
+// issue on the FP64 pipe at the rate of an FP64 add, and the implicit solve is bound
+// by that pipe; these re-bias the exponent field (1023 <-> 127) and move the mantissa
+// with integer instructions, and take no hardware conversion on any path (a rare
+// fallback would still be predicated into every call).  d2f rounds the 29 dropped
+// mantissa bits half away from zero (IEEE round-to-nearest-even differs only at exact
+// ties); below the normal binary32 range it flushes to a signed zero, above it gives
+// a signed infinity, and NaN stays NaN.  f2d is exact for normal floats and zero,
+// flushes binary32 denormals to a signed zero and keeps infinities and NaN.  Used for
+// the FP32 and double-word copies of the Newton solve, where only the size of the
+// rounding matters.
+__device__ __forceinline__ float d2f_int(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned sgn = hi & 0x80000000u;
+    const unsigned f = (sgn | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+    const bool nan = e == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+    const unsigned big = nan ? (sgn | 0x7fc00000u) : (sgn | 0x7f800000u);
+    return __uint_as_float(e - 897u <= 253u ? f : (e < 897u ? sgn : big));
+}
+
+__device__ __forceinline__ double f2d_int(float v)
+{
+    const unsigned f = __float_as_uint(v);
+    const unsigned e = (f >> 23) & 0xffu;
+    const unsigned sgn = f & 0x80000000u;
+    const unsigned nhi = sgn | ((e + 896u) << 20) | ((f >> 3) & 0xfffffu);
+    const unsigned shi = e == 0u ? sgn : (sgn | 0x7ff00000u | ((f & 0x7fffffu) ? 0x80000u : 0u));
+    const bool normal = e - 1u < 254u;
+    return __hiloint2double((int)(normal ? nhi : shi), (int)(normal ? (f << 29) : 0u));
+}
+
+constexpr unsigned kHi1e30 = 0x46293E59u;   // high word of 1e30 (a start beyond is discarded)
+
+// FP64 tests on the integer pipe (an FP64 compare also issues on the FP64 pipe):
+// x is finite; x > 0 (false for NaN and +inf); |x| < a bound given by its high word
+// (within 2^-20, from below)
+__device__ __forceinline__ bool finite_int(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) != 0x7ff; }
+__device__ __forceinline__ bool pos_int(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool mag_below_int(double x, unsigned bound_hi)
+{
+    return ((unsigned)__double2hiint(x) & 0x7fffffffu) < bound_hi;
+}
+
+// 1/sqrt(x) for x >= 1 and 1/x for x > 0 in FP64 from an FP32 estimate: rsqrt takes
+// two Newton steps y + y (1/2 - x y^2 / 2), each squaring the relative error (2^-22
+// -> 2^-43 -> 2^-86); the reciprocal takes one step of order three, y (1 + e + e^2)
+// with e = 1 - x y (2^-22 -> 2^-66).  Both end within an ulp or so of the exact
+// value, without the special-value branches of the library routines (their callers
+// only pass moderate positive values; the FP64 residual decides the root either way).
+__device__ __forceinline__ double rsqrt_ge1(double x)
+{
+    double y = f2d_int(rsqrtf(d2f_int(x)));
+    const double h = 0.5 * x;
+    y = fma(y, fma(-h, y * y, 0.5), y);
+    y = fma(y, fma(-h, y * y, 0.5), y);
+    return y;
+}
+
+__device__ __forceinline__ double rcp_pos(double x)
+{
+    const double y = f2d_int(__fdividef(1.0f, d2f_int(x)));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
 // ---------------------------------------------------------------------------
 // implicit electric field + velocity solve (Sec. 2.4), xi = 0, orthonormal frame
 // ---------------------------------------------------------------------------
@@ -344,7 +463,11 @@ struct CellIn {
 
 __device__ __forceinline__ void cell_derive(CellIn& c)
 {
-    c.emode = !(c.etat >= 0.0) ? 0 : (c.xi != 0.0 ? 2 : 1);
+    // E held fixed when eta_t < 0 or NaN; the dynamo form when xi != 0 (integer tests:
+    // an FP64 compare issues on the FP64 pipe)
+    const long long eb = __double_as_longlong(c.etat);
+    const bool et_ok = (eb >= 0 && eb <= 0x7ff0000000000000ll) || eb == (long long)0x8000000000000000ull;
+    c.emode = !et_ok ? 0 : ((__double_as_longlong(c.xi) << 1) != 0 ? 2 : 1);
     c.tD = c.tau + c.D;
     c.B2h = 0.5 * (c.B[0] * c.B[0] + c.B[1] * c.B[1] + c.B[2] * c.B[2]);
     c.Digh = c.D * c.igh;
@@ -431,7 +554,7 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
 {
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const double Wsq = 1.0 + uu;   // W^2
-    e.iW = rsqrt(Wsq);
+    e.iW = rsqrt_ge1(Wsq);
     e.W = Wsq * e.iW;
     if (c.emode == 2) {
         // A_0 E = eta_t E* + A_1 (E*.u) u + A_2 u x E* + A_3 B + A_4 (B.u) u + A_5 u x B
@@ -455,7 +578,7 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
         // from one division: r = 1/(a b d), 1/a = r b d, ...  (a, b >= 1 and d > 0, so
         // the product neither overflows nor cancels)
         const double a = e.W + c.etat, b = 1.0 + c.etat * e.W, d = Wsq - c.igh;
-        const double ab = a * b, r = 1.0 / (ab * d);
+        const double ab = a * b, r = rcp_pos(ab * d);
         e.iWe = r * (b * d);
         e.A1 = c.etat * (r * (a * d));
         e.iden = r * ab;
@@ -469,7 +592,7 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
         e.E[0] = c.Es[0]; e.E[1] = c.Es[1]; e.E[2] = c.Es[2];
     }
     e.U = 0.5 * (e.E[0] * e.E[0] + e.E[1] * e.E[1] + e.E[2] * e.E[2]) + c.B2h;
-    if (c.emode != 1) e.iden = 1.0 / (Wsq - c.igh);
+    if (c.emode != 1) e.iden = rcp_pos(Wsq - c.igh);
     e.wt = (e.W * (c.tD - e.U) - c.Digh) * e.iden;
     const double x0 = e.E[1] * c.B[2] - e.E[2] * c.B[1];
     const double x1 = e.E[2] * c.B[0] - e.E[0] * c.B[2];
@@ -549,37 +672,6 @@ __device__ __forceinline__ bool newton_dir(const double J[3][3], const double* f
     x[1] = (c01 * f[0] + c11 * f[1] + c21 * f[2]) * id;
     x[2] = (c02 * f[0] + c12 * f[1] + c22 * f[2]) * id;
     return true;
-}
-
-// binary64 <-> binary32 on the integer pipe.  On GB300 the hardware conversions issue
-// on the FP64 pipe, which bounds the implicit solve; these re-bias the exponent field
-// (1023 -> 127) and move the mantissa with integer instructions.  d2f rounds the 29
-// dropped mantissa bits half away from zero (IEEE round-to-nearest-even differs only
-// at exact ties).  Zero keeps its sign; values outside the normal binary32 range
-// (denormal, infinite, NaN) take the hardware conversion.  Used for the FP32 copies
-// of the Newton solve, where only the size of the rounding matters.
-__device__ __forceinline__ float d2f_int(double x)
-{
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned e = (hi >> 20) & 0x7ffu;
-    if (e - 897u > 253u) {
-        if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
-        return (float)x;
-    }
-    const unsigned f = ((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29)) +
-                       ((lo >> 28) & 1u);
-    return __uint_as_float(f);
-}
-
-__device__ __forceinline__ double f2d_int(float v)
-{
-    const unsigned f = __float_as_uint(v);
-    const unsigned e = (f >> 23) & 0xffu;
-    if (e - 1u >= 254u) {
-        if ((f << 1) == 0u) return __hiloint2double((int)(f & 0x80000000u), 0);
-        return (double)v;
-    }
-    return __hiloint2double((int)((f & 0x80000000u) | ((e + 896u) << 20) | ((f >> 3) & 0xfffffu)), (int)(f << 29));
 }
 
 // three floats passed by value (an FP32 copy of u), so they stay in registers
@@ -777,13 +869,156 @@ __device__ __forceinline__ bool newton_step_f32(const CellIn& c, const CellF& cf
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// double-word residual (dword.cuh): the Newton corrections of the implicit solve are
+// formed on the FP32 pipe from a residual accurate to ~1e-14; only the final residual,
+// which accepts the root, is evaluated in FP64
+// ---------------------------------------------------------------------------
+
+// x as a double-word pair, on the integer pipe: hi = d2f_int(x), and lo = x - hi
+// (exact in binary64) rounded to binary32.  With L the 29 significand bits that hi
+// drops and r = L, or L - 2^29 where hi rounded up, |x| - |hi| = r 2^(e - 1075) for
+// the biased exponent e.  r (|r| <= 2^28) becomes a float as rh 2^14 + rl, each half
+// converted exactly by the 1.5 2^23 bias (rh < 2^14 and rl < 2^14 in magnitude), with
+// one rounding in the final fma.  Outside binary32's normal range, or where lo would
+// fall below it (|x| < 2^-74), lo is 0: the pair is then only binary32-accurate, which
+// the FP64 residual that accepts the root detects.
+__device__ __forceinline__ dw dw_of(double x)
+{
+    const unsigned whi = (unsigned)__double2hiint(x), wlo = (unsigned)__double2loint(x);
+    const unsigned e = (whi >> 20) & 0x7ffu;
+    const float h = d2f_int(x);
+    if (e - 949u > 201u) return {h, 0.0f};   // e outside [949, 1150]
+    const int r = (int)(wlo & 0x1fffffffu) - (int)((wlo >> 28) & 1u) * (1 << 29);
+    const float fh = __fsub_rn(__int_as_float(0x4B400000 + (r >> 14)), 12582912.0f);
+    const float fl = __fsub_rn(__int_as_float(0x4B400000 + (r & 0x3fff)), 12582912.0f);
+    const float sc = __uint_as_float((e - 948u) << 23);   // 2^(e - 1075)
+    const float l = fmaf(fh, __fmul_rn(16384.0f, sc), __fmul_rn(fl, sc));
+    return {h, (whi >> 31) ? -l : l};
+}
+
+__device__ __forceinline__ double dw_to_double(dw x) { return f2d_int(x.hi) + f2d_int(x.lo); }
+
+__device__ __forceinline__ dw dw_dot3(const dw* a, const dw* b)
+{
+    return dw_add(dw_add(dw_mul(a[0], b[0]), dw_mul(a[1], b[1])), dw_mul(a[2], b[2]));
+}
+
+// (a x b)_i = a_j b_k - a_k b_j
+__device__ __forceinline__ dw dw_cross(const dw* a, const dw* b, int i)
+{
+    const int j = (i + 1) % 3, k = (i + 2) % 3;
+    return dw_sub(dw_mul(a[j], b[k]), dw_mul(a[k], b[j]));
+}
+
+// The residual f = w_t u - S + E x B of evaluate() in double-word arithmetic, for the
+// resistive and E-fixed forms of E(u) (emode 1 and 0).  The per-cell constants are
+// split from their FP64 values on the integer pipe.  Outputs in binary32: f (each
+// accurate to ~1e-14 of the momentum scale), w_t, tau + D - U and the scale M.
+struct EvalDW {
+    float f[3], wt, base, M;
+};
+
+__device__ __forceinline__ void evaluate_dw(const CellIn& c, const dw* u, EvalDW& o)
+{
+    dw S[3], B[3], E[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        S[i] = dw_of(c.S[i]);
+        B[i] = dw_of(c.B[i]);
+    }
+    const dw Wsq = dw_add_f(dw_add(dw_add(dw_sqr(u[0]), dw_sqr(u[1])), dw_sqr(u[2])), 1.0f);
+    const dw W = dw_sqrt(Wsq);
+    if (c.emode == 1) {
+        // A_0 E = eta_t E* + A_1 (E*.u) u - u x B, A_0 = W + eta_t, A_1 = eta_t/(1 + eta_t W)
+        const dw et = dw_of(c.etat);
+        dw Es[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) Es[i] = dw_of(c.Es[i]);
+        const dw iWe = dw_rcp(dw_add(W, et));
+        const dw A1 = dw_mul(et, dw_rcp(dw_add_f(dw_mul(et, W), 1.0f)));
+        const dw ae = dw_mul(A1, dw_dot3(Es, u));
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+            E[i] = dw_mul(dw_sub(dw_add(dw_of(c.etEs[i]), dw_mul(ae, u[i])), dw_cross(u, B, i)), iWe);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; i++) E[i] = dw_of(c.Es[i]);
+    }
+    // U = |E|^2/2 + |B|^2/2;  w_t = (W (tau + D - U) - D/Gamma_hat) / (W^2 - 1/Gamma_hat)
+    const dw U = dw_add(dw_scale(dw_dot3(E, E), 0.5f), dw_of(c.B2h));
+    const dw base = dw_sub(dw_of(c.tD), U);
+    const dw wt = dw_mul(dw_sub(dw_mul(W, base), dw_of(c.Digh)), dw_rcp(dw_sub(Wsq, dw_of(c.igh))));
+    float M = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const dw x = dw_cross(E, B, i);
+        const dw w = dw_mul(wt, u[i]);
+        o.f[i] = dw_add(dw_sub(w, S[i]), x).hi;
+        M = fmaxf(M, fmaxf(fabsf(S[i].hi), fmaxf(fabsf(x.hi), fabsf(w.hi))));
+    }
+    o.wt = wt.hi;
+    o.base = base.hi;
+    o.M = M;
+}
+
+// Newton corrections from the double-word residual with the FP32 Jacobian (the
+// direction of newton_dir_f32, here at the double-word velocity), at most `nit`
+// evaluations.  It stops once |f| <= tol M / 4 in double-word arithmetic, or after a
+// step |dx|^2 <= tol max(|u|^2, 1) / 100: the FP32 Jacobian contracts the error by
+// ~1e-6 per step and the quadratic term is ~|dx|^2, so the residual after such a step
+// is already below the tolerance and the FP64 residual can accept it directly.  Steps
+// are taken only when finite and within the step bound; u (FP64) receives the result
+// only if it is finite.
+constexpr int kDwEvals = 4;   // most double-word residual evaluations per solve
+constexpr unsigned kHi1e10 = 0x4202A05Fu;   // high word of 1e10 (the bound on W)
+
+__device__ __forceinline__ void newton_refine_dw(const CellIn& c, const CellF& cf, double* u, float tol, int nit)
+{
+    dw ud[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) ud[i] = dw_of(u[i]);
+    bool moved = false;
+    for (int k = 0; k < nit; k++) {
+        EvalDW ed;
+        evaluate_dw(c, ud, ed);
+        if (!(ed.M > 0.0f) || !(ed.M < 1e30f) || !(ed.wt > 0.0f)) break;
+        const float fm = fmaxf(fabsf(ed.f[0]), fmaxf(fabsf(ed.f[1]), fabsf(ed.f[2])));
+        if (fm <= 0.25f * tol * ed.M) break;   // also false for NaN
+        const float uf[3] = {ud[0].hi, ud[1].hi, ud[2].hi};
+        const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
+        const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
+        float Ef[3], dE[3][3];
+        efield_f32(c, cf, uf, Wf, iWf, Ef, dE);
+        const float iM = 1.0f / ed.M;
+        const float fs[3] = {ed.f[0] * iM, ed.f[1] * iM, ed.f[2] * iM};
+        float y[3];
+        if (!solve_f32(cf, uf, Wf, iWf, uu, Ef, dE, ed.wt, ed.base, fs, y)) break;
+        const float dx[3] = {y[0] * ed.M, y[1] * ed.M, y[2] * ed.M};
+        const float nx2 = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        if (!(nx2 <= 1e4f * fmaxf(1.0f, uu))) break;   // also rejects NaN
+#pragma unroll
+        for (int i = 0; i < 3; i++) ud[i] = dw_add_f(ud[i], dx[i]);
+        moved = true;
+        if (nx2 <= 0.01f * tol * fmaxf(1.0f, uu)) break;
+    }
+    if (moved) {
+        const double v[3] = {dw_to_double(ud[0]), dw_to_double(ud[1]), dw_to_double(ud[2])};
+        if (finite_int(v[0]) && finite_int(v[1]) && finite_int(v[2])) {
+            u[0] = v[0];
+            u[1] = v[1];
+            u[2] = v[2];
+        }
+    }
+}
+
 // Globally convergent Newton (backtracking on |f|^2 with the Armijo condition and a
 // bounded step).  u: in = initial guess, out = solution.  Converged when |f| is at
 // `tol` against its own momentum scale M, or when the step no longer moves u.
 // Returns iterations, or -1.  uin: the FP32 value of the start when the caller has it
 // (has_uin; the start is then exactly that value).
-__device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol, bool has_uin,
-                                            const F3& uin)
+__device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol, float tolf,
+                                            bool has_uin, const F3& uin)
 {
     const CellF cf = cell_f32(c);
     // the FP32 first step saves an FP64 evaluation only when the tolerance lies below
@@ -791,7 +1026,12 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
     // 1e-13, not the mixed path's 1e-10
     F3 uf1 = uin;   // FP32 value of u at the first direction (when has1)
     bool has1 = has_uin;
-    if (tol < 1e-11) {
+    if (c.emode != 2) {
+        // Newton corrections from the double-word residual; the FP64 residual below
+        // then accepts the root, or the FP64 iteration continues from there
+        newton_refine_dw(c, cf, u, tolf, kDwEvals);
+        has1 = false;
+    } else if (tol < 1e-11) {
         F3 un;
         if (newton_step_f32(c, cf, u, has_uin, uin, un)) {
             uf1 = un;
@@ -799,6 +1039,10 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
         }
     }
     evaluate(c, u, e);
+    if (e.fm <= tol * e.M) {
+        if (!pos_int(e.wt) || !mag_below_int(e.W, kHi1e10)) return -1;
+        return 0;
+    }
     for (int it = 1; it <= kmax; it++) {
         double dx[3];
         // FP32 directions first; the FP64 Jacobian takes over if they have not
@@ -832,7 +1076,7 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
         e = et;
         const double umax = from_hi(max(mag_hi(u[0]), max(mag_hi(u[1]), mag_hi(u[2]))));
         if (e.fm <= tol * e.M || step <= 1e-15 * umax) {
-            if (!(e.wt > 0.0) || !(e.W < 1e10)) return -1;
+            if (!pos_int(e.wt) || !mag_below_int(e.W, kHi1e10)) return -1;
             return it;
         }
     }

@@ -32,9 +32,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     const F11& p32 = a.p32;
     unsigned long long* nfail = a.nfail;
     int c[3];
-    c[0] = g.ng[0] + (int)(t % g.n[0]);
-    c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
-    c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+    interior_coords(g, t, c);
     const long long id = lin(g, c[0], c[1], c[2]);
     const double ps = psi ? psi[id] : 1.0;
     const double al = alp ? alp[id] : 1.0;
@@ -59,7 +57,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     }
     const double et = eta ? eta[id] : eta_u;
     // flat: eta / (a_ii dt) with the host's reciprocal, no division
-    ci.etat = a_dt > 0.0 ? (M ? et / (al * a_dt) : et * a.ia_dt) : -1.0;
+    ci.etat = a.stiff ? (M ? et / (al * a_dt) : et * a.ia_dt) : -1.0;
     cell_derive(ci);
     double u[3];
     Eval e;
@@ -70,7 +68,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     const bool hist = a.hs[0] != nullptr;
     float hsv[3] = {0.0f, 0.0f, 0.0f};
     F3 ust = {{0.0f, 0.0f, 0.0f}};
-    if (rho_atm > 0.0 && ci.D < 10.0 * rho_atm) {
+    if (a.atm && ci.D < a.d_atm) {
         atmo = true;   // (its history is left as it is)
     } else {
         bool fin = true;
@@ -83,17 +81,17 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
             } else {
                 u[i] = p2 * prim.p[1 + i][id];
             }
-            if (!(fabs(u[i]) < 1e30)) fin = false;
+            if (!mag_below_int(u[i], kHi1e30)) fin = false;   // also NaN
         }
         if (!fin) u[0] = u[1] = u[2] = 0.0;
-        int it = newton_solve(ci, u, e, kmax, tol, hist && fin, ust);
+        int it = newton_solve(ci, u, e, kmax, tol, a.tolf, hist && fin, ust);
         if (it < 0 && fin) {
             u[0] = u[1] = u[2] = 0.0;
-            it = newton_solve(ci, u, e, kmax, tol, false, ust);
+            it = newton_solve(ci, u, e, kmax, tol, a.tolf, false, ust);
         }
         if (it < 0) {
             atomicAdd(nfail, 1ull);
-            if (!(rho_atm > 0.0)) {
+            if (!a.atm) {
                 // no atmosphere: leave the cell's primitives as they were, no stiff update
                 if (R.p[0])
 #pragma unroll
@@ -122,13 +120,14 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     if (p32.p[0]) {
         // FP32 copy for the mixed-precision explicit kernels, with the densitised
         // cell-centred q_B of the stage
-        p32.p[0][id] = (float)rho;
-        p32.p[4][id] = (float)pres;
+        // (converted on the integer pipe: a hardware conversion issues on the FP64 pipe)
+        p32.p[0][id] = d2f_int(rho);
+        p32.p[4][id] = d2f_int(pres);
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            p32.p[1 + i][id] = (float)(u[i] * ip2);
-            p32.p[5 + i][id] = (float)(e.E[i] * ip2);
-            p32.p[8 + i][id] = (float)(ci.B[i] * p4);
+            p32.p[1 + i][id] = d2f_int(u[i] * ip2);
+            p32.p[5 + i][id] = d2f_int(e.E[i] * ip2);
+            p32.p[8 + i][id] = d2f_int(ci.B[i] * p4);
         }
     }
 #pragma unroll
@@ -136,7 +135,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
         prim.p[1 + i][id] = u[i] * ip2;
         prim.p[5 + i][id] = e.E[i] * ip2;
         const double qEn = p4 * e.E[i];
-        if (R.p[0]) R.p[i][id] = a_dt > 0.0 ? (qEn - qEs[i]) * a.ia_dt : 0.0;
+        if (R.p[0]) R.p[i][id] = a.stiff ? (qEn - qEs[i]) * a.ia_dt : 0.0;
         if (qE_out.p[0]) qE_out.p[i][id] = qEn;
         if (hist && !atmo) {
             const float un = d2f_int(u[i]);

@@ -28,7 +28,7 @@ thread_local bool launch_overlap = false;
 // ---------------------------------------------------------------------------
 
 template <bool M>
-__global__ void __launch_bounds__(128, 3) k_implicit(Dims g, ImpArgs a)
+__global__ void __launch_bounds__(128, 4) k_implicit(Dims g, ImpArgs a)
 {
     grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(128, 3) k_implicit(Dims g, ImpArgs a)
 
 // the same solve with cell-centred q_B (GLM variant, Sec. 3.1)
 template <bool M>
-__global__ void __launch_bounds__(128, 3) k_implicit_cc(Dims g, ImpArgs a)
+__global__ void __launch_bounds__(128, 4) k_implicit_cc(Dims g, ImpArgs a)
 {
     grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];

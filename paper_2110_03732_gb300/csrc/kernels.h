@@ -36,6 +36,10 @@ struct ImpArgs {
     P3 qE_out;              // solved q_E (or NULL)
     int kmax;
     double tol, rho_atm, p_atm;
+    float tolf;             // tol in FP32 (for the double-word corrections)
+    int stiff;              // a_dt > 0 (else E is held fixed)
+    int atm;                // rho_atm > 0 (an atmosphere is set)
+    double d_atm;           // 10 rho_atm: cells with D below it are atmosphere
     double xi;              // mean-field dynamo parameter
     F11 p32;                // FP32 copy for the mixed path (or NULL)
     unsigned long long* nfail;
