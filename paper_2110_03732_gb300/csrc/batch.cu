@@ -87,8 +87,7 @@ __global__ void __launch_bounds__(256) kb_flux(const ProbStage* __restrict__ P, 
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
         for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x)
-            flux_march_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.F64[D], nullptr, ps.fe64[D], t,
-                                     kMarch);
+            flux_march_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.F64[D], nullptr, ps.fe64[D], t);
     }
 }
 
@@ -103,7 +102,7 @@ __global__ void __launch_bounds__(256) kb_emf(const ProbStage* __restrict__ P, i
         const ProbStage& ps = P[k.prob * s + stage];
         const bool march = ps.g.act[(C + 1) % 3] && ps.g.act[(C + 2) % 3];
         for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) {
-            if (march) emf_march_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t, kMarch);
+            if (march) emf_march_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t);
             else emf_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t);
         }
     }
@@ -201,6 +200,7 @@ void fill_desc(grmhd_batch* b, int p, double dt)
         ProbStage& ps = b->desc[(size_t)p * b->s + i];
         memset(&ps, 0, sizeof ps);
         ps.g = ctx_dims(c);
+        for (int d = 0; d < 3; d++) set_march(ps.g, d, kMarch);   // every batched march is kMarch long
         ctx_stage_args(c, i, dt, &ps.imp, &ps.upd);
         for (int v = 0; v < 8; v++) ps.p64.p[v] = ps.imp.prim.p[v];
         for (int v = 0; v < 11; v++) ps.p32.p[v] = ctx_p32(c, v);

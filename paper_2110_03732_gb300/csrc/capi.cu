@@ -148,8 +148,7 @@ Dims make_dims(const grmhd_grid* gr, double gam)
     g.st[2] = (long long)g.N[0] * g.N[1];
     g.gh = gam / (gam - 1.0);
     g.igh = (gam - 1.0) / gam;
-    g.dv[0] = make_fastdiv((unsigned)g.n[0]);
-    g.dv[1] = make_fastdiv((unsigned)g.n[1]);
+    set_divisors(g);
     return g;
 }
 

@@ -59,9 +59,7 @@ __global__ void __launch_bounds__(kThreads) k_divb_rows(Dims g, CP3 bf, double* 
     double a = 0.0, s = 0.0, m = 0.0;
     if (t < tot) {
         int c[3];
-        c[0] = g.ng[0] + (int)(t % g.n[0]);
-        c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
-        c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+        grmhd::interior_coords(g, t, c);
         const long long o = grmhd::lin(g, c[0], c[1], c[2]);
         const double dv = grmhd::cell_divb(g, bf.p, c, o);
         a = fabs(dv);
@@ -184,8 +182,7 @@ extern "C" grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double*
     g.st[1] = g.N[0];
     g.st[2] = (long long)g.N[0] * g.N[1];
     g.gh = g.igh = 0.0;
-    g.dv[0] = grmhd::make_fastdiv((unsigned)g.n[0]);
-    g.dv[1] = grmhd::make_fastdiv((unsigned)g.n[1]);
+    grmhd::set_divisors(g);
     const long long rows = (cells + kThreads - 1) / kThreads;
     if (rows > kMaxRows)
         return err(GRMHD_ERR_ARG,

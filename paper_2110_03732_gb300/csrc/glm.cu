@@ -77,13 +77,13 @@ __device__ __forceinline__ void glm_face_flux(const Dims& g, const GlmFluxArgs& 
 // Phi = q_Phi / psi^6 to K consecutive D-faces per thread, marched along D with one
 // LineRec per quantity (as flux_march_item)
 template <int D, bool M, bool P>
-__device__ __forceinline__ void glm_flux_march_item(const Dims& g, const GlmFluxArgs& a, long long t, int K)
+__device__ __forceinline__ void glm_flux_march_item(const Dims& g, const GlmFluxArgs& a, long long t)
 {
     using Rec = LineRec<double, P>;
     const double* __restrict__ psi = M ? a.psi : nullptr;
     constexpr int NV = 12;
     int c[3], f0, f1;
-    march_coords<D>(g, t, K, c, f0, f1);
+    march_coords<D>(g, t, c, f0, f1);
     auto load = [&](int m, double* x) {
         int cs[3] = {c[0], c[1], c[2]};
         cs[D] = P ? ext_cell(g, D, m) : m;
@@ -132,15 +132,15 @@ __device__ __forceinline__ void glm_flux_march_item(const Dims& g, const GlmFlux
 }
 
 template <int D, bool M, bool P = false>
-__global__ void __launch_bounds__(128) k_glm_flux(Dims g, GlmFluxArgs a, int K)
+__global__ void __launch_bounds__(128) k_glm_flux(Dims g, GlmFluxArgs a)
 {
     grid_dep_sync();
-    const long long nq = (g.n[D] + K) / K;
+    const long long nq = g.dq[D].d;   // chunks of g.mk[D] faces per line
     const long long tot = nq * (D == 0 ? (long long)g.n[1] * g.n[2]
                                        : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        glm_flux_march_item<D, M, P>(g, a, t, K);
+        glm_flux_march_item<D, M, P>(g, a, t);
 }
 
 __device__ __forceinline__ void glm_out(const GlmUpdateArgs& a, int v, long long o, double L, bool has_r)
@@ -171,9 +171,7 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
     const double* __restrict__ psi = M ? a.psi : nullptr;
     const double* __restrict__ alp = M ? a.alp : nullptr;
     int c[3];
-    c[0] = g.ng[0] + (int)(t % g.n[0]);
-    c[1] = g.ng[1] + (int)((t / g.n[0]) % g.n[1]);
-    c[2] = g.ng[2] + (int)(t / ((long long)g.n[0] * g.n[1]));
+    interior_coords(g, t, c);
     const long long o = lin(g, c[0], c[1], c[2]);
     double Lc[12];
 #pragma unroll
@@ -260,7 +258,9 @@ static void glm_flux_launch(const Dims& g, const GlmFluxArgs& a, int nsm, cudaSt
     const long long other = D == 0 ? (long long)g.n[1] * g.n[2]
                                    : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
     const int K = march_len(g.n[D], other, nsm, glm_blocks_per_sm<D, M, P>(), P ? 1.0 : 0.6);
-    launch_k(k_glm_flux<D, M, P>, glm_grid((long long)((g.n[D] + K) / K) * other, 128, nsm), 128, st, g, a, K);
+    Dims gl = g;
+    set_march(gl, D, K);
+    launch_k(k_glm_flux<D, M, P>, glm_grid((long long)gl.dq[D].d * other, 128, nsm), 128, st, gl, a);
 }
 
 template <bool P>

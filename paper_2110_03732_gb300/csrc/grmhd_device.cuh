@@ -60,18 +60,47 @@ struct Dims {
     double igh;            // 1/Gamma_hat_1
     long long ncell;       // padded cells
     FastDiv dv[2];         // division by n[0] and by n[1] (interior cell index -> i, j, k)
+    FastDiv dvp[2];        // division by n[d] + 1 (1 where inactive): face and edge indices
+    int mk[3];             // march length along d (faces or edges per thread)
+    FastDiv dq[3];         // division by the chunks per line along d, (n[d] + mk[d]) / mk[d]
 };
+
+// set the march length along d (and its chunk divisor) of a launch's copy of the grid
+inline void set_march(Dims& g, int d, int K)
+{
+    g.mk[d] = K;
+    g.dq[d] = make_fastdiv((unsigned)((g.n[d] + K) / K));
+}
+
+// the divisors of a grid whose extents n, act are set (march length 1 everywhere)
+inline void set_divisors(Dims& g)
+{
+    for (int d = 0; d < 2; d++) {
+        g.dv[d] = make_fastdiv((unsigned)g.n[d]);
+        g.dvp[d] = make_fastdiv((unsigned)(g.act[d] ? g.n[d] + 1 : 1));
+    }
+    for (int d = 0; d < 3; d++) set_march(g, d, 1);
+}
+
+// (i0, i1, i2) of index t over an x-fastest box whose first two extents have the
+// divisors f0, f1 (t < 2^32)
+__device__ __forceinline__ void box_coords(long long t, const FastDiv& f0, const FastDiv& f1, int* idx)
+{
+    const unsigned tt = (unsigned)t;
+    const unsigned q0 = fdiv(tt, f0);
+    const unsigned q1 = fdiv(q0, f1);
+    idx[0] = (int)(tt - q0 * f0.d);
+    idx[1] = (int)(q0 - q1 * f1.d);
+    idx[2] = (int)q1;
+}
 
 // padded coordinates of interior cell t (x fastest); t < 2^32 (the library refuses
 // grids of 2^32 or more interior cells)
 __device__ __forceinline__ void interior_coords(const Dims& g, long long t, int* c)
 {
-    const unsigned tt = (unsigned)t;
-    const unsigned q0 = fdiv(tt, g.dv[0]);
-    const unsigned q1 = fdiv(q0, g.dv[1]);
-    c[0] = g.ng[0] + (int)(tt - q0 * (unsigned)g.n[0]);
-    c[1] = g.ng[1] + (int)(q0 - q1 * (unsigned)g.n[1]);
-    c[2] = g.ng[2] + (int)q1;
+    box_coords(t, g.dv[0], g.dv[1], c);
+#pragma unroll
+    for (int d = 0; d < 3; d++) c[d] += g.ng[d];
 }
 
 struct P8 { double* p[8]; };          // rho, u^1..3, p, E^1..3  (or 8 conserved)
@@ -85,14 +114,25 @@ struct CP3 { const double* p[3]; };
 // the stored ghost value
 // ---------------------------------------------------------------------------
 
+// (m - lo) mod n for m - lo in [-2n, 3n): stencil indices stay within a few cells of the
+// interior and a periodic direction has n >= 2, so two conditional shifts each way
+// suffice (an integer % by a run-time n goes through float reciprocals and conversions
+// that share the FP64 pipe)
+__device__ __forceinline__ int wrap_periodic(int m, int lo, int n)
+{
+    int r = m - lo;
+    r += r < 0 ? n : 0;
+    r += r < 0 ? n : 0;
+    r -= r >= n ? n : 0;
+    r -= r >= n ? n : 0;
+    return lo + r;
+}
+
 __device__ __forceinline__ int map_cell(const Dims& g, int d, int m)
 {
     if (!g.act[d]) return 0;
     const int lo = g.ng[d], n = g.n[d];
-    if (g.bc[d] == BC_PERIODIC) {
-        int r = (m - lo) % n;
-        return lo + (r < 0 ? r + n : r);
-    }
+    if (g.bc[d] == BC_PERIODIC) return wrap_periodic(m, lo, n);
     if (g.bc[d] == BC_OUTFLOW) return m < lo ? lo : (m > lo + n - 1 ? lo + n - 1 : m);
     return m;
 }
@@ -101,10 +141,7 @@ __device__ __forceinline__ int map_face(const Dims& g, int d, int m)
 {
     if (!g.act[d]) return 0;
     const int lo = g.ng[d], n = g.n[d];
-    if (g.bc[d] == BC_PERIODIC) {
-        int r = (m - lo) % n;
-        return lo + (r < 0 ? r + n : r);
-    }
+    if (g.bc[d] == BC_PERIODIC) return wrap_periodic(m, lo, n);
     if (g.bc[d] == BC_OUTFLOW) return m < lo ? lo : (m > lo + n ? lo + n : m);
     return m;
 }
@@ -269,10 +306,7 @@ __device__ __forceinline__ int ext_cell(const Dims& g, int d, int m)
 {
     if (!g.act[d] || (m >= 0 && m < g.N[d])) return m;
     const int lo = g.ng[d], n = g.n[d];
-    if (g.bc[d] == BC_PERIODIC) {
-        int r = (m - lo) % n;
-        return lo + (r < 0 ? r + n : r);
-    }
+    if (g.bc[d] == BC_PERIODIC) return wrap_periodic(m, lo, n);
     if (g.bc[d] == BC_OUTFLOW) return m < lo ? lo : lo + n - 1;
     return m < 0 ? 0 : g.N[d] - 1;
 }
@@ -406,6 +440,11 @@ __device__ __forceinline__ double f2d_int(float v)
     const bool normal = e - 1u < 254u;
     return __hiloint2double((int)(normal ? nhi : shi), (int)(normal ? (f << 29) : 0u));
 }
+
+// a value of the stencil precision T widened to FP64 for storing: FP32 on the integer
+// pipe (exact for normal floats and zero; a denormal float is stored as zero)
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f2d_int(x); }
 
 constexpr unsigned kHi1e30 = 0x46293E59u;   // high word of 1e30 (a start beyond is discarded)
 

@@ -201,11 +201,11 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     if (!M && Eh) {
         // C = D + 1: A = D + 2 (inactive), B = D; C = D + 2: A = D, B = D + 1 (inactive)
         if (Eh[T1])
-            Eh[T1][r0] = (double)uct_edge<T>(prL[5 + T1], prR[5 + T1], prL[5 + T1], prR[5 + T1], T(1), T(1), BL[D],
-                                             BR[D], BL[T2], BR[T2]);
+            Eh[T1][r0] = to_f64(uct_edge<T>(prL[5 + T1], prR[5 + T1], prL[5 + T1], prR[5 + T1], T(1), T(1), BL[D],
+                                             BR[D], BL[T2], BR[T2]));
         if (Eh[T2])
-            Eh[T2][r0] = (double)uct_edge<T>(prL[5 + T2], prL[5 + T2], prR[5 + T2], prR[5 + T2], T(1), T(1),
-                                             BL[T1], BR[T1], BL[D], BR[D]);
+            Eh[T2][r0] = to_f64(uct_edge<T>(prL[5 + T2], prL[5 + T2], prR[5 + T2], prR[5 + T2], T(1), T(1),
+                                             BL[T1], BR[T1], BL[D], BR[D]));
     }
     if (psi) {
 #pragma unroll
@@ -234,7 +234,7 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
 #pragma unroll
     for (int v = 0; v < 8; v++) {
         const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
-        F.p[v][o] = (double)((gL[v] + gR[v]) * hv);
+        F.p[v][o] = to_f64((gL[v] + gR[v]) * hv);
     }
     if (vbar && vbar[0]) {
         // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
@@ -320,27 +320,15 @@ struct LineRec<T, true> {
 // line (c[D] unset) and its faces f0 .. f1-1 (padded indices).  Chunks along D,
 // x-fastest over the other directions; for D = 0 the chunks themselves run along x.
 template <int D>
-__device__ __forceinline__ void march_coords(const Dims& g, long long t, int K, int* c, int& f0, int& f1)
+__device__ __forceinline__ void march_coords(const Dims& g, long long t, int* c, int& f0, int& f1)
 {
-    const int nq = (g.n[D] + 1 + K - 1) / K;
-    int q;
-    if (D == 0) {
-        q = (int)(t % nq);
-        const long long r = t / nq;
-        c[1] = g.ng[1] + (int)(r % g.n[1]);
-        c[2] = g.ng[2] + (int)(r / g.n[1]);
-    } else if (D == 1) {
-        c[0] = g.ng[0] + (int)(t % g.n[0]);
-        const long long r = t / g.n[0];
-        q = (int)(r % nq);
-        c[2] = g.ng[2] + (int)(r / nq);
-    } else {
-        c[0] = g.ng[0] + (int)(t % g.n[0]);
-        const long long r = t / g.n[0];
-        c[1] = g.ng[1] + (int)(r % g.n[1]);
-        q = (int)(r / g.n[1]);
-    }
-    c[D] = 0;
+    const int K = g.mk[D];
+    int idx[3];
+    // the chunk index along D takes the place of the D coordinate in an x-fastest box
+    box_coords(t, D == 0 ? g.dq[0] : g.dv[0], D == 1 ? g.dq[1] : g.dv[1], idx);
+    const int q = idx[D];
+#pragma unroll
+    for (int d = 0; d < 3; d++) c[d] = d == D ? 0 : g.ng[d] + idx[d];
     f0 = g.ng[D] + q * K;
     f1 = min(f0 + K, g.ng[D] + g.n[D] + 1);
 }
@@ -354,14 +342,14 @@ __device__ __forceinline__ void march_coords(const Dims& g, long long t, int K, 
 template <int D, bool M, typename T, bool P = false>
 __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
                                                 const double* psi_in, const double* alp_in, const FluxOut<double>& F,
-                                                double* const* vbar, double* const* Eh, long long t, int K)
+                                                double* const* vbar, double* const* Eh, long long t)
 {
     using Rec = LineRec<T, P>;
     const double* __restrict__ psi = M ? psi_in : nullptr;
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     constexpr int NV = 10;   // 8 primitives and the two transverse B
     int c[3], f0, f1;
-    march_coords<D>(g, t, K, c, f0, f1);
+    march_coords<D>(g, t, c, f0, f1);
     // the 10 reconstructed values of the cell at padded coordinate m along D (PPM's
     // stencil reaches a third ghost: ext_cell maps it)
     auto load = [&](int m, T* x) {
@@ -454,14 +442,12 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     const bool aa = g.act[A], ba = g.act[B];
-    int e[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) e[d] = (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
     const T* __restrict__ Ec = prim.p[5 + C];
+    // edges: n[d] along C, n[d] + 1 along an active transverse d (1 if inactive)
     int c[3];
-    c[0] = g.ng[0] + (int)(t % e[0]);
-    c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
-    c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+    box_coords(t, C == 0 ? g.dv[0] : g.dvp[0], C == 1 ? g.dv[1] : g.dvp[1], c);
+#pragma unroll
+    for (int d = 0; d < 3; d++) c[d] += g.ng[d];
     // steps (ii)-(iii): covariant E_C = psi^4 E^C, to A-faces then along B
     T s[2][NS];   // [X = A-side L/R][B offset -OFF..+OFF-1]
     const int nb = ba ? NS : 1;
@@ -544,7 +530,7 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     // c+ = c- in each direction, where the four-state weights are all 1/4 and the
     // diffusive coefficients c^2/2c are c/2
     const T hLL = ale * EXY[0][0], hLR = ale * EXY[0][1], hRL = ale * EXY[1][0], hRR = ale * EXY[1][1];
-    Eh[i0] = (double)uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR);
+    Eh[i0] = to_f64(uct_edge<T>(hLL, hLR, hRL, hRR, ca, cb, qBbL, qBbR, qBaL, qBaR));
 }
 
 // The same EMFs for K consecutive C-edges along B per thread (MC, or PPM when P; A and
@@ -556,7 +542,7 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
 template <int C, bool M, typename T, bool P = false>
 __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
                                                const double* psi_in, const double* alp_in, double* __restrict__ Eh,
-                                               long long t, int K)
+                                               long long t)
 {
     using Rec = LineRec<T, P>;
     constexpr int NS = P ? 6 : 4, OFF = P ? 3 : 2;
@@ -564,15 +550,11 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     const T* __restrict__ Ec = prim.p[5 + C];
-    const int nq = (g.n[B] + 1 + K - 1) / K;
-    int e[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) e[d] = d == B ? nq : (d == C ? g.n[d] : g.n[d] + 1);
-    int c[3];
-    const int i0 = (int)(t % e[0]);
-    const long long r = t / e[0];
-    const int i1 = (int)(r % e[1]), i2 = (int)(r / e[1]);
-    const int idx[3] = {i0, i1, i2};
+    const int K = g.mk[B];
+    // x-fastest box: the chunks along B, n[C] edges along C, n[A] + 1 along A
+    int c[3], idx[3];
+    box_coords(t, B == 0 ? g.dq[0] : (C == 0 ? g.dv[0] : g.dvp[0]),
+               B == 1 ? g.dq[1] : (C == 1 ? g.dv[1] : g.dvp[1]), idx);
 #pragma unroll
     for (int d = 0; d < 3; d++) c[d] = g.ng[d] + (d == B ? 0 : idx[d]);
     const int f0 = g.ng[B] + idx[B] * K;
@@ -649,8 +631,8 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
         }
         // EXY[X][Y]: X the A side (the row's L / R), Y the B side (L = this edge's
         // lower-B state)
-        Eh[i0] = (double)uct_edge<T>(ale * L[0], ale * R[0], ale * L[1], ale * R[1], ca, cb, qBbL, qBbR, L[2],
-                                     R[2]);
+        Eh[i0] = to_f64(uct_edge<T>(ale * L[0], ale * R[0], ale * L[1], ale * R[1], ca, cb, qBbL, qBbR, L[2],
+                                     R[2]));
     }
 }
 
@@ -680,13 +662,11 @@ __device__ __forceinline__ void emf_ideal_item(const Dims& g, const CP8& prim, c
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     const bool aa = g.act[A], ba = g.act[B];
-    int e[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) e[d] = (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+    // edges: n[d] along C, n[d] + 1 along an active transverse d (1 if inactive)
     int c[3];
-    c[0] = g.ng[0] + (int)(t % e[0]);
-    c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
-    c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+    box_coords(t, C == 0 ? g.dv[0] : g.dvp[0], C == 1 ? g.dv[1] : g.dvp[1], c);
+#pragma unroll
+    for (int d = 0; d < 3; d++) c[d] += g.ng[d];
     // step (iii): q_B^B and vbar^A (both at B-faces) along A; q_B^A and vbar^B (A-faces)
     // along B.  vbar^A is component A = B + 2 of the B-faces, vbar^B component B = A + 1
     // of the A-faces.
@@ -850,13 +830,11 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
     // flat metric: alpha = psi = 1 known at compile time
     const double* __restrict__ psi = M ? a.psi : nullptr;
     const double* __restrict__ alp = M ? a.alp : nullptr;
-    int e[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) e[d] = g.act[d] ? g.n[d] + 1 : 1;
+    // cells and their upper faces: n[d] + 1 along an active d
     int c[3];
-    c[0] = g.ng[0] + (int)(t % e[0]);
-    c[1] = g.ng[1] + (int)((t / e[0]) % e[1]);
-    c[2] = g.ng[2] + (int)(t / ((long long)e[0] * e[1]));
+    box_coords(t, g.dvp[0], g.dvp[1], c);
+#pragma unroll
+    for (int d = 0; d < 3; d++) c[d] += g.ng[d];
     bool interior = true;
 #pragma unroll
     for (int d = 0; d < 3; d++)

@@ -54,15 +54,15 @@ __global__ void __launch_bounds__(128, 4) k_implicit_cc(Dims g, ImpArgs a)
 
 // MC (or PPM) fluxes, K consecutive D-faces per thread (flux_march_item)
 template <int D, bool M, typename T, bool P = false>
-__global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a, int K)
+__global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a)
 {
     grid_dep_sync();
-    const long long nq = (g.n[D] + K) / K;
+    const long long nq = g.dq[D].d;   // chunks of g.mk[D] faces per line
     const long long tot = nq * (D == 0 ? (long long)g.n[1] * g.n[2]
                                        : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        flux_march_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, a.Eh, t, K);
+        flux_march_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, a.vbar, a.Eh, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -85,14 +85,14 @@ __global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
 // MC (or PPM) edge EMFs, K consecutive edges along B = C + 2 per thread
 // (emf_march_item; A and B active)
 template <int C, bool M, typename T, bool P = false>
-__global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a, int K)
+__global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a)
 {
     grid_dep_sync();
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
-    const long long tot = (long long)((g.n[B] + K) / K) * g.n[C] * (g.n[A] + 1);
+    const long long tot = (long long)g.dq[B].d * g.n[C] * (g.n[A] + 1);   // chunks of g.mk[B] edges
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t, K);
+        emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
 }
 
 // ideal-limit edge EMF (App. A) from the stored transport velocities
@@ -460,8 +460,10 @@ static void flux_march_launch(const Dims& g, int nsm, cudaStream_t st, const Flu
                                    : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
     const int bps = march_blocks_per_sm<D, M, T, P>();
     const int K = march_len(g.n[D], other, nsm, sizeof(T) == 8 && bps > 2 ? 2 : bps, P ? 1.0 : 0.6);
-    const int b = grid_for((long long)((g.n[D] + K) / K) * other, 128, nsm);
-    launch_k(k_flux_march<D, M, T, P>, b, 128, st, g, a, K);
+    Dims gl = g;
+    set_march(gl, D, K);
+    const int b = grid_for((long long)gl.dq[D].d * other, 128, nsm);
+    launch_k(k_flux_march<D, M, T, P>, b, 128, st, gl, a);
 }
 
 template <typename T, bool P>
@@ -500,7 +502,9 @@ static void emf_launch(const Dims& g, int nsm, cudaStream_t st, const EmfArgs<T>
     }
     const long long other = (long long)g.n[C] * (g.n[A] + 1);
     const int K = march_len(g.n[B], other, nsm, emf_march_blocks_per_sm<C, M, T, P>(), P ? 1.0 : 0.6);
-    launch_k(k_emf_march<C, M, T, P>, grid_for((long long)((g.n[B] + K) / K) * other, 128, nsm), 128, st, g, a, K);
+    Dims gl = g;
+    set_march(gl, B, K);
+    launch_k(k_emf_march<C, M, T, P>, grid_for((long long)gl.dq[B].d * other, 128, nsm), 128, st, gl, a);
 }
 
 template <typename T, bool P>
