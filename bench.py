@@ -133,9 +133,15 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 ALU peak: the nominal GB300 dense FP64 rate of the profiling recipe
-# (1.25 TFLOP/s); a register-only FMA probe on this machine measured 1.19-1.20 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
+# Algorithmic bytes per 512^2 launch of the mixed-precision stencil kernels (each datum
+# once, flat 2-D grid): a flux launch reads the 10 FP32 values each face state needs
+# per cell (8 primitives and the 2 transverse cell q_B, 40 B) and writes 8 FP64 fluxes
+# and the one degenerate edge EMF it owns per face (72 B); the edge-EMF launch reads E_z
+# (FP32) and the two face q_B (FP64) per edge and writes its FP64 EMF (28 B); the update
+# reads per cell q^n or the running sum (11), the fluxes (16), the primitives its sources
+# use (u^1..3, E^1..2: 5), R (3) and the edge EMFs (3), and writes the later-stage base
+# and the running sum (22, stage 0) or q^{n+1} (11, stage 1): 55.5 doubles on average.
+MIXED_ALG_BYTES_PER_CELL = {"flux": 112.0, "emf": 28.0, "update": 55.5 * 8}
 
 
 class ClockSampler:
@@ -387,6 +393,19 @@ def run_native(args):
         clean[f"{cyc}_cycles_ms"] = float(np.median(cl_ms))
     clean["divb_max_after"] = S.diagnostics()[0][2]
 
+    def kernel_pass(Sv, steps):
+        """Per-kernel CUDA-event times over `steps` further steps (launches serialised)."""
+        Sv.set_timing(True)
+        Sv.kernel_times()
+        for _ in range(steps):
+            flush.zero_()
+            Sv.step(dt)
+            kt = Sv.kernel_times()
+        kt = Sv.kernel_times()
+        Sv.set_timing(False)
+        torch.cuda.synchronize()
+        return kt
+
     def time_variant(**kw):
         """The same workload and timing rules with another solver configuration."""
         Sv = grmhd.Solver.from_problem(pr, device=dev, **kw)
@@ -409,8 +428,10 @@ def run_native(args):
 
     # mixed precision (FP32 reconstruction, HLL and edge EMF; FP64 implicit solve,
     # sources and CT)
-    mixed, _ = time_variant(precision="mixed")
+    mixed, Sm = time_variant(precision="mixed")
     mixed["dtype"] = "f32 reconstruction/HLL/edge EMF, f64 implicit solve/sources/CT/stage combination"
+    mixed_kt = kernel_pass(Sm, args.steps)
+    del Sm
     # GLM hyperbolic cleaning (Sec. 3.1, cell-centred B, kappa_B = 1) instead of CT
     glm, Sg = time_variant(divb="glm", kappa=1.0)
     glm.update({"dtype": "f64", "kappa_b": 1.0, "divb_cell_central_max": Sg.diagnostics()[0][2],
@@ -450,12 +471,24 @@ def run_native(args):
         return
 
     pk, pk_src = peaks()
+    from paper_2110_03732_gb300 import roofline as RL
+    counts = RL.load_counts()
+    probe = grmhd.fp64_fma_rate()
     # dominant kernel by measured time inside the timed region
     kname = max(ktimes, key=lambda k: ktimes[k][0])
     kms, kn = ktimes[kname]
     k_avg_ms = kms / max(kn, 1)
     tot_kernel_ms = sum(v[0] for v in ktimes.values())
-    roof = roofline_entry(kname, k_avg_ms, cells, pk, pk_src)
+    roof = RL.alu_entry(counts, "fp64", kname, k_avg_ms, probe)
+    # mixed precision: the dominant kernel, and the FP32 stencil kernels against HBM
+    mk = max(mixed_kt, key=lambda k: mixed_kt[k][0])
+    avg = {k: v[0] / max(v[1], 1) for k, v in mixed_kt.items()}
+    mixed["kernel_ms_per_step"] = {k: v[0] / args.steps for k, v in mixed_kt.items()}
+    mixed["roofline"] = RL.alu_entry(counts, "mixed", mk, avg[mk], probe)
+    mixed["stencil_hbm"] = {k: RL.hbm_entry(counts, "mixed", k, avg[k], MIXED_ALG_BYTES_PER_CELL[k] * cells,
+                                            pk["hbm_gbs"]) for k in ("flux", "emf", "update")}
+    mixed["stencil_hbm_note"] = ("the 512^2 working set (~0.2 GB) stays in the 129 MB L2 between kernels only in "
+                                 "part; traffic is DRAM bytes per launch from the stored ncu counts")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -470,6 +503,7 @@ def run_native(args):
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
         "kernel_share": {k: v[0] / tot_kernel_ms for k, v in ktimes.items()},
         "roofline": roof,
+        "fp64_fma_probe_tflops": probe,
         "hbm_fraction_of_step": ALG_BYTES_PER_ZONE_STAGE * cells * STAGES / (ms_per_step / 1e3) / (pk["hbm_gbs"] * 1e9),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
         "gpu_launches": launches,
@@ -556,30 +590,6 @@ def bench_serving(dev, args):
     stats["unit"] = UNIT
     stats["workload"] = f"{len(reqs)} requests, Poisson 200/s, seed 0"
     return stats
-
-
-# FP64 flops per cell per launch of each kernel kind (2 * DFMA + DADD + DMUL thread
-# instructions / cells), counted by ncu on the 512^2 workload for the kernels as they
-# stand (profiles/ot512_fp64_kernels.md).  The flux figure is per launch (one
-# direction; both march 7 faces per thread); the EMF one is the single EMF launch of a flat 2-D stage (the other two
-# components come out of the flux kernels); the implicit one is a launch after the
-# Newton start history has filled (from the third step on).
-# TRAFFIC: dram read + write bytes per launch from the same capture (flux: the mean of
-# its two directions).
-FP64_FLOPS_PER_CELL = {"implicit": 268.1, "flux": 255.9, "emf": 84.3, "update": 121.0}
-TRAFFIC_PER_LAUNCH = {"implicit": 29.7e6, "flux": 30.4e6, "emf": 6.4e6, "update": 84.6e6}
-
-
-def roofline_entry(kname, k_avg_ms, cells, pk, pk_src):
-    fl = FP64_FLOPS_PER_CELL.get(kname)
-    if fl is None:
-        return {"bound": "alu", "kernel": kname, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "avg_launch_ms": k_avg_ms,
-                "note": "FP64 flop count per cell not yet measured"}
-    ach = fl * cells / (k_avg_ms / 1e3) / 1e12
-    return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_PER_LAUNCH.get(kname), "avg_launch_ms": k_avg_ms,
-            "flops_per_cell": fl, "peak_source": "nominal FP64 of the profiling recipe (probe: 1.19-1.20)"}
 
 
 def main():

@@ -280,6 +280,13 @@ grmhd_status grmhd_kernel_times(grmhd_ctx* ctx, double* ms, long long* launches)
  * default for a context made by grmhd_create. */
 grmhd_status grmhd_set_launch_overlap(grmhd_ctx* ctx, int enable);
 
+/* FP64 fused multiply-add rate of the current device in TFLOP/s (measurement only,
+ * not part of the paper's method): a register-only kernel of independent FMA chains,
+ * the best of five launches timed with CUDA events on `stream` (synchronises it).  It
+ * measures the denominator that FP64-bound kernels are compared with and changes no
+ * device setting.  GRMHD_ERR_CUDA without a device. */
+grmhd_status grmhd_fp64_fma_rate(double* tflops, grmhd_stream_t stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* grmhd_last_error(void);
 

@@ -96,6 +96,7 @@ def lib():
     L.grmhd_start_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
     L.grmhd_save_start.argtypes = [vp, vp, C.c_size_t, vp]
     L.grmhd_load_start.argtypes = [vp, vp, C.c_size_t, vp]
+    L.grmhd_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), vp]
     L.grmhd_last_error.restype = C.c_char_p
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
                  "grmhd_set_metric", "grmhd_set_eta", "grmhd_set_dynamo", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
@@ -103,7 +104,8 @@ def lib():
                  "grmhd_set_timing", "grmhd_set_launch_overlap", "grmhd_kernel_times", "grmhd_batch_scratch_bytes", "grmhd_batch_create",
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
                  "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
-                 "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start"):
+                 "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start",
+                 "grmhd_fp64_fma_rate"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -137,6 +139,14 @@ def make_grid(ndim, n, lo, hi, bc):
         b = bc[d]
         g.bc[d] = BC[b] if isinstance(b, str) else int(b)
     return g
+
+
+def fp64_fma_rate(stream=None):
+    """FP64 fused multiply-add rate of the current device in TFLOP/s (a register-only
+    probe kernel timed with CUDA events; measurement only)."""
+    r = C.c_double(0.0)
+    check(lib().grmhd_fp64_fma_rate(C.byref(r), _stream(stream)), "fp64_fma_rate")
+    return r.value
 
 
 def ssp2():

@@ -53,16 +53,77 @@ def test_clock_sampler_without_nvidia_smi():
     assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
 
 
-def test_roofline_entry_arithmetic():
-    pk = {"hbm_gbs": 7000.0}
-    cells = 512 * 512
+NCU_CSV = """==PROF== Connected
+"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_read.sum","Mbyte","20.00"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","dram__bytes_write.sum","Mbyte","10.00"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","usecond","110.00"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","sm__inst_executed_pipe_fp64.sum","inst","2,000,000"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active","%","80.00"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","smsp__sass_thread_inst_executed_op_dadd_pred_on.sum","inst","30,000,000"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","smsp__sass_thread_inst_executed_op_dfma_pred_on.sum","inst","13,000,000"
+"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7","(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","smsp__sass_thread_inst_executed_op_dmul_pred_on.sum","inst","10,000,000"
+"1","1","python3","h","void k_dt(Dims, const double *, const double *, double *)","1","7","(256, 1, 1)","(10, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","usecond","3.00"
+"""
+
+
+def test_roofline_counts_from_ncu_csv(tmp_path):
+    """The counts parser takes units into account, forms FP64 flop as 2 DFMA + DADD +
+    DMUL, keeps DRAM read + write per launch and ignores kernels outside the stage."""
+    from paper_2110_03732_gb300 import roofline as RL
+    f = tmp_path / "counts.csv"
+    f.write_text(NCU_CSV)
+    kinds, names = RL.counts_from_ncu_csv(str(f), 512 * 512)
+    assert list(kinds) == ["flux"]
+    k = kinds["flux"]
+    assert k["launches"] == 1 and k["dur_us"] == pytest.approx(110.0)
+    assert k["fp64_flop"] == pytest.approx(2 * 13e6 + 30e6 + 10e6)
+    assert k["dram_bytes"] == pytest.approx(30e6)
+    assert k["fp64_pipe_inst"] == pytest.approx(32 * 2e6)
+    assert k["fp64_flop_per_cell"] == pytest.approx(66e6 / 262144)
+
+
+def test_roofline_alu_entry_arithmetic_and_staleness(tmp_path, monkeypatch):
+    """achieved = stored FP64 flop per launch / live mean launch time, against the
+    nominal FP64 rate; a count taken on other kernel sources reports stale and no
+    traffic, and changing a kernel source makes the stored counts stale."""
+    import json
+    import shutil
+    from paper_2110_03732_gb300 import roofline as RL
+    f = tmp_path / "counts.csv"
+    f.write_text(NCU_CSV)
+    counts = RL.build_counts(str(f))
+    p = tmp_path / "roofline_counts.json"
+    p.write_text(json.dumps(counts))
+    c = RL.load_counts(str(p))
+    assert c["stale"] is False
     ms = 0.1
-    r = bench.roofline_entry("flux", ms, cells, pk, "test")
-    fl = bench.FP64_FLOPS_PER_CELL["flux"]
+    r = RL.alu_entry(c, "fp64", "flux", ms, peak_probe_tflops=1.2)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["achieved"] == pytest.approx(fl * cells / (ms / 1e3) / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.TRAFFIC_PER_LAUNCH["flux"]
+    assert r["achieved"] == pytest.approx(66e6 / (ms / 1e3) / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / RL.FP64_PEAK_TFLOPS)
+    assert r["traffic"] == pytest.approx(30e6)
+    assert r["fp64_issue_frac"] == pytest.approx(32 * 2e6 / (ms / 1e3) / RL.FP64_INST_PEAK_PER_S)
     # an unknown kernel kind reports no figure rather than a made-up one
-    u = bench.roofline_entry("unknown", ms, cells, pk, "test")
+    u = RL.alu_entry(c, "fp64", "unknown", ms)
     assert u["achieved"] is None and u["frac"] is None
+    # edit a copy of the kernel sources: the same stored counts are now stale
+    src = tmp_path / "pkg"
+    shutil.copytree(RL.HERE + "/csrc", src / "csrc")
+    monkeypatch.setattr(RL, "HERE", str(src))
+    assert RL.load_counts(str(p))["stale"] is False
+    k = src / "csrc" / "kernels.cu"
+    k.write_text(k.read_text() + "\n// edited\n")
+    c2 = RL.load_counts(str(p))
+    assert c2["stale"] is True
+    r2 = RL.alu_entry(c2, "fp64", "flux", ms)
+    assert r2["traffic"] is None and r2["counts"]["stale"] is True
+
+
+def test_hbm_entry_arithmetic():
+    from paper_2110_03732_gb300 import roofline as RL
+    r = RL.hbm_entry(None, "mixed", "flux", 0.02, 112.0 * 262144, 6780.4)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(112.0 * 262144 / 0.02e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6780.4)
+    assert r["traffic"] is None
