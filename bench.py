@@ -465,6 +465,23 @@ def run_native(args):
             "value": ws * Ss.cells * STAGES * 10 / star_total, "unit": UNIT, "ms_per_step": 1e3 * star_total / 10,
             "steps": 10, "newton_failures": Ss.diagnostics()[2]}
     del Ss
+    # the same star on the mixed-precision path
+    Ss = grmhd.Solver.from_problem(P.star(256), device=dev, precision="mixed")
+    for _ in range(3):
+        Ss.step(dts)
+    torch.cuda.synchronize()
+    sm_ms = []
+    for _ in range(10):
+        e0.record(stream)
+        Ss.step(dts)
+        e1.record(stream)
+        e1.synchronize()
+        sm_ms.append(e0.elapsed_time(e1))
+    sm_total = max_over_ranks(sum(sm_ms) / 1e3, dev)
+    star_mixed = {"workload": "star_3d_256^3_mixed (FP32 reconstruction/HLL/edge EMF)",
+                  "value": ws * Ss.cells * STAGES * 10 / sm_total, "unit": UNIT, "ms_per_step": 1e3 * sm_total / 10,
+                  "steps": 10, "newton_failures": Ss.diagnostics()[2]}
+    del Ss
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -516,7 +533,10 @@ def run_native(args):
         "ppm_mixed": ppm_mixed,
         "ideal_emf": ideal,
         "star": star,
+        "star_mixed": star_mixed,
     }
+    line["tube_run"] = bench_tube(grmhd, P, dev)
+    line["star_mixed_error"] = star_mixed_error(grmhd, P, dev)
     if not args.no_batched:
         line["batched"] = bench_batched(grmhd, P, dev, args)
         line["serving"] = bench_serving(dev, args)
@@ -575,21 +595,121 @@ def bench_batched(grmhd, P, dev, args):
     return out
 
 
+def _pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def _latency_groups(results, reqs):
+    """p50/p99 time to solution per eta decade and per kind of run."""
+    by_id = {r.rid: r for r in reqs}
+    dec, kind = {}, {}
+    for res in results:
+        info = by_id[res.rid].problem.info
+        d = int(math.floor(math.log10(info["eta"]) + 1e-12))
+        dec.setdefault(f"1e{d}..1e{d + 1}", []).append(res.time_to_solution)
+        kind.setdefault(info["kind"], []).append(res.time_to_solution)
+    f = lambda xs: {"n": len(xs), "p50_tts_s": _pct(xs, 50), "p99_tts_s": _pct(xs, 99)}
+    return {k: f(v) for k, v in sorted(dec.items())}, {k: f(v) for k, v in sorted(kind.items())}
+
+
 def bench_serving(dev, args):
-    """Seeded Poisson stream (200 requests/s) of 1-D shock tubes (400-4096 cells, to
-    t = 0.4), 2-D Orszag-Tang vortices (128^2-512^2, 100 steps) and 3-D stars
-    (64^3-128^3, 100 steps), eta log-uniform in [1e-6, 1], served by continuous
-    batching under a 150 GB device-memory budget (mixed precision)."""
+    """The serving mix: 1-D shock tubes (400-4096 cells, to t = 0.4), 2-D Orszag-Tang
+    vortices (128^2-512^2, 100 steps) and 3-D stars (64^3-128^3, 100 steps), eta
+    log-uniform in [1e-6, 1], served by continuous batching under a 150 GB device-memory
+    budget (mixed precision).
+    - capacity: the mix admitted all at once (offline), runs per second;
+    - the eta sweep at a sustainable load: a seeded Poisson stream at 80 % of that
+      capacity, with p50/p99 time to solution overall, per eta decade and per kind;
+    - overload: the stream at 200 requests/s, which queues (time to solution is then
+      mostly waiting)."""
     from paper_2110_03732_gb300 import problems as P
     from paper_2110_03732_gb300.serve import Request, Server
-    reqs = []
-    for i, (t, pr, steps) in enumerate(P.request_stream(0, args.serve_requests, rate=200.0)):
-        reqs.append(Request(i, t, pr, steps, t_end=pr.t_end if pr.ndim == 1 else None))
-    srv = Server(budget_bytes=150e9, precision="mixed", device=dev)
-    results, stats = srv.run(reqs, realtime=True)
-    stats["unit"] = UNIT
-    stats["workload"] = f"{len(reqs)} requests, Poisson 200/s, seed 0"
-    return stats
+
+    def make(seed, n, rate):
+        return [Request(i, t, pr, steps, t_end=pr.t_end if pr.ndim == 1 else None)
+                for i, (t, pr, steps) in enumerate(P.request_stream(seed, n, rate=rate))]
+
+    def serve(reqs, realtime):
+        srv = Server(budget_bytes=150e9, precision="mixed", device=dev)
+        return srv.run(reqs, realtime=realtime)
+
+    n = args.serve_requests
+    off_reqs = make(0, n, 200.0)
+    off_res, off = serve(off_reqs, realtime=False)
+    capacity = len(off_res) / off["wall_s"]
+    rate = 0.8 * capacity
+    sus_reqs = make(1, int(1.25 * n), rate)
+    sus_res, sus = serve(sus_reqs, realtime=True)
+    dec, kinds = _latency_groups(sus_res, sus_reqs)
+    ovl_reqs = make(0, n, 200.0)
+    ovl_res, ovl = serve(ovl_reqs, realtime=True)
+    out = dict(sus)
+    out.update({"unit": UNIT, "workload": f"{len(sus_reqs)} requests, Poisson {rate:.2f}/s (80 % of capacity), seed 1",
+                "arrival_rate_per_s": rate, "capacity_runs_per_s": capacity,
+                "capacity_measure": f"{len(off_reqs)} requests of the same mix admitted at once (seed 0): "
+                                    f"{off['wall_s']:.2f} s, {off['zone_updates_per_s']:.3g} zone-updates/s",
+                "by_eta_decade": dec, "by_kind": kinds,
+                "overload_200_per_s": {"requests": ovl["requests"], "wall_s": ovl["wall_s"],
+                                       "p50_tts_s": ovl["p50_tts_s"], "p99_tts_s": ovl["p99_tts_s"],
+                                       "zone_updates_per_s": ovl["zone_updates_per_s"],
+                                       "note": "arrivals far above capacity: time to solution is queueing"}})
+    return out
+
+
+def bench_tube(grmhd, P, dev, runs=10):
+    """The 1-D resistive shock tube (400 cells, eta = 1e-3, Gamma = 2, CFL 0.4) run to
+    t = 0.4 (400 IMEX steps) in FP64, start to finish through the public API: problem
+    set-up, time step, the steps and a final synchronisation, repeated `runs` times."""
+    import torch
+    pr = P.shock_tube(400)
+    lat = []
+    for _ in range(runs + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = grmhd.Solver.from_problem(pr, device=dev)
+        dt = S.compute_dt()
+        nsteps = int(math.ceil(pr.t_end / dt - 1e-9))
+        t = 0.0
+        for k in range(nsteps):
+            d = dt if k < nsteps - 1 else pr.t_end - t
+            S.step(d)
+            t += d
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+    lat = lat[1:]   # the first run pays one-time set-up
+    return {"workload": "shock_tube_1d_400 (eta 1e-3, Gamma 2) to t = 0.4, FP64", "steps": nsteps,
+            "runs": runs, "p50_run_s": _pct(lat, 50), "p99_run_s": _pct(lat, 99),
+            "ms_per_step_p50": 1e3 * _pct(lat, 50) / nsteps,
+            "newton_failures": S.diagnostics()[2]}
+
+
+def star_mixed_error(grmhd, P, dev, n=64, steps=100):
+    """Mixed precision against FP64 on the 3-D star after `steps` steps: relative L1 of
+    D and tau over the interior, and the div B maxima of both runs."""
+    import torch
+    pr = P.star(n)
+    runs = {}
+    for prec in ("fp64", "mixed"):
+        S = grmhd.Solver.from_problem(pr, device=dev, precision=prec)
+        dt = S.compute_dt()
+        for _ in range(steps):
+            S.step(dt)
+        torch.cuda.synchronize()
+        runs[prec] = (S, S.diagnostics())
+    I = runs["fp64"][0].interior()
+    out = {"workload": f"star_3d_{n}^3", "steps": steps}
+    for v, name in ((0, "D"), (4, "tau")):
+        a = runs["mixed"][0].q[v][I]
+        b = runs["fp64"][0].q[v][I]
+        out[f"rel_l1_{name}"] = float((a - b).abs().sum() / b.abs().sum())
+    out["divb_max_mixed"] = runs["mixed"][1][0][2]
+    out["divb_max_fp64"] = runs["fp64"][1][0][2]
+    out["newton_failures"] = runs["mixed"][1][2] + runs["fp64"][1][2]
+    return out
 
 
 def main():

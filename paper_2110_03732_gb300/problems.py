@@ -405,7 +405,8 @@ def request_stream(seed=0, n_requests=64, rate=200.0, tube_cells=(400, 4096), vo
     """Seeded Poisson stream of runs: (arrival time [s], Problem, number of steps).
     Kinds drawn uniformly: 1-D shock tube (cells in `tube_cells`, run to t = 0.4),
     2-D Orszag-Tang (side in `vortex_side`, `steps_2d3d` steps), 3-D star (side in
-    `star_side`, `steps_2d3d` steps); eta log-uniform in 10^eta_range for every run."""
+    `star_side`, `steps_2d3d` steps); eta log-uniform in 10^eta_range for every run.
+    Each Problem's info records the drawn eta and its kind."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -425,6 +426,8 @@ def request_stream(seed=0, n_requests=64, rate=200.0, tube_cells=(400, 4096), vo
             n = int(rng.integers(star_side[0], star_side[1] + 1))
             pr = star(n=n, eta_in=eta)
             steps = steps_2d3d
+        pr.info["eta"] = eta
+        pr.info["kind"] = ("tube", "vortex", "star")[kind]
         out.append((t, pr, steps))
     return out
 
