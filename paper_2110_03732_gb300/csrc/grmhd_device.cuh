@@ -224,6 +224,26 @@ template <> struct Bits<float> {
     static constexpr I MAG = 0x7fffffff;
 };
 
+// v * 2^K.  In FP64, exactly, by moving the exponent field on the integer pipe (a
+// multiply by a power of two would take an FP64 issue slot): normal values stay exact,
+// a result below the normal range (|v| < 2^-1020 for K = -2) flushes to a signed zero,
+// one above it becomes a signed infinity, and infinities and NaN pass unchanged.  In
+// FP32 the multiply itself (the FP32 pipe has room to spare).
+template <typename T, int K>
+__device__ __forceinline__ T scale_pow2(T v)
+{
+    if (sizeof(T) == 4) return v * (K >= 0 ? T(1 << (K >= 0 ? K : 0)) : T(1) / T(1 << (K < 0 ? -K : 0)));
+    using I = typename Bits<T>::I;
+    constexpr int MB = sizeof(T) == 8 ? 52 : 23;
+    constexpr I EMAX = sizeof(T) == 8 ? 2047 : 255;
+    const I b = Bits<T>::to(v);
+    const I e = (b >> MB) & EMAX;
+    const I sgn = b & ~Bits<T>::MAG;
+    const I moved = b + (I(K) << MB);
+    const I r = (e == EMAX) ? b : ((e != 0 && e + K >= 1) ? (e + K < EMAX ? moved : (sgn | (EMAX << MB))) : sgn);
+    return Bits<T>::from(r);
+}
+
 template <typename T>
 __device__ __forceinline__ T minmod3(T a, T b, T c)
 {
@@ -242,8 +262,8 @@ template <typename T>
 __device__ __forceinline__ void mc_face(T a0, T a1, T a2, T a3, T& L, T& R)
 {
     const T dm = a1 - a0, d0 = a2 - a1, dp = a3 - a2;
-    L = a1 + minmod3<T>(dm, T(0.25) * (a2 - a0), d0);
-    R = a2 - minmod3<T>(d0, T(0.25) * (a3 - a1), dp);
+    L = a1 + minmod3<T>(dm, scale_pow2<T, -2>(a2 - a0), d0);
+    R = a2 - minmod3<T>(d0, scale_pow2<T, -2>(a3 - a1), dp);
 }
 
 // 1/sqrt(x) through CUDA's reciprocal square root, in the precision of x
@@ -257,7 +277,7 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 template <typename T>
 __device__ __forceinline__ T ppm_slope(T am, T a0, T ap)
 {
-    return T(2) * minmod3<T>(a0 - am, T(0.25) * (ap - am), ap - a0);
+    return scale_pow2<T, 1>(minmod3<T>(a0 - am, scale_pow2<T, -2>(ap - am), ap - a0));
 }
 
 // the interface value between cells a0 and ap with slopes s0, s1
@@ -392,16 +412,17 @@ __device__ __forceinline__ void face_hll_half(const T* pr, const T* B, int d, T 
     const T W = x * iW;
     const T rhoh = rho + gh * p;
     const T hW = rhoh * W;
-    const T U = T(0.5) * (E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    // 2U = |E|^2 + |B|^2; p + U and U - p each as one fused multiply-add
+    const T U2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
     const T X[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
     const T a = u[d] + s * W;
     const T K = rhoh * a;
     g[0] = rho * a;
 #pragma unroll
     for (int j = 0; j < 3; j++) g[1 + j] = K * u[j] - E[d] * E[j] - B[d] * B[j] + s * X[j];
-    g[1 + d] += p + U;
+    g[1 + d] += T(0.5) * U2 + p;
     const T Sd = hW * u[d] + X[d];
-    g[4] = (Sd - rho * u[d]) + s * (W * (hW - rho) + (U - p));
+    g[4] = (Sd - rho * u[d]) + s * (W * (hW - rho) + (T(0.5) * U2 - p));
     const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
     g[5 + d] = s * E[d];
     g[5 + d1] = B[d2] + s * E[d1];

@@ -169,7 +169,7 @@ __device__ __forceinline__ float cell_qB_in(const Dims&, const PrimIn<float>& pa
 template <typename T>
 __device__ __forceinline__ T uct_edge(T hLL, T hLR, T hRL, T hRR, T ca, T cb, T qBbL, T qBbR, T qBaL, T qBaR)
 {
-    return (hLL + hLR + hRL + hRR) * T(0.25) + (T(0.5) * ca) * (qBbR - qBbL) - (T(0.5) * cb) * (qBaR - qBaL);
+    return scale_pow2<T, -2>(hLL + hLR + hRL + hRR) + (T(0.5) * ca) * (qBbR - qBbL) - (T(0.5) * cb) * (qBaR - qBaL);
 }
 
 // HLL flux at the D-face with padded coordinates c (between the cells of linear
@@ -268,12 +268,12 @@ struct LineRec<T, false> {
         a = x[1];
         b = x[2];
         d = b - a;
-        l = a + minmod3<T>(a - x[0], T(0.25) * (b - x[0]), d);
+        l = a + minmod3<T>(a - x[0], scale_pow2<T, -2>(b - x[0]), d);
     }
     __device__ __forceinline__ void step(T x, T& L, T& R)
     {
         const T dn = x - b;
-        const T hs = minmod3<T>(d, T(0.25) * (x - a), dn);
+        const T hs = minmod3<T>(d, scale_pow2<T, -2>(x - a), dn);
         L = l;
         R = b - hs;
         l = b + hs;
