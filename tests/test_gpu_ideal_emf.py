@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+from parity_tools import check, rel_max
 from paper_2110_03732_gb300 import problems as P
 
 torch = pytest.importorskip("torch")
@@ -51,14 +52,14 @@ def test_ideal_emf_explicit_L_parity(G, ndim, n, bc, metric):
     torch.cuda.synchronize()
     I = st.grid.interior()
     for v in range(8):
-        assert rel_l1(cpu(Lg[v])[I], Lo[v][I]) <= TOL, f"L[{v}]"
+        check(cpu(Lg[v])[I], Lo[v][I], f"L[{v}]")
     for d in range(3):
         sl = list(I)
         ax = 2 - d
         if st.grid.ndim > d and st.grid.bc[d] != 0:
             sl[ax] = slice(st.grid.ng[d], st.grid.ng[d] + st.grid.n[d] + 1)
         sl = tuple(sl)
-        assert rel_l1(cpu(Lg[8 + d])[sl], Lo[8 + d][sl]) <= TOL, f"L_B[{d}]"
+        check(cpu(Lg[8 + d])[sl], Lo[8 + d][sl], f"L_B[{d}]")
 
 
 def _steps(G, pr, nsteps):
@@ -71,9 +72,9 @@ def _steps(G, pr, nsteps):
         S.step(dt)
         torch.cuda.synchronize()
         for v in range(8):
-            assert rel_l1(cpu(S.q[v])[I], st.q[v][I]) <= TOL, (k, v)
+            check(cpu(S.q[v])[I], st.q[v][I], (k, v))
         for d in range(3):
-            assert rel_l1(cpu(S.bf[d])[I], st.bf[d][I]) <= TOL, (k, "B", d)
+            check(cpu(S.bf[d])[I], st.bf[d][I], (k, "B", d))
     divb, _, nf = S.diagnostics()
     assert nf == 0 and st.fails == 0
     return S
