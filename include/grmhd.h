@@ -287,6 +287,16 @@ grmhd_status grmhd_set_launch_overlap(grmhd_ctx* ctx, int enable);
  * device setting.  GRMHD_ERR_CUDA without a device. */
 grmhd_status grmhd_fp64_fma_rate(double* tflops, grmhd_stream_t stream);
 
+/* Index-bounds violations (diagnostic build only; not part of the paper's method).
+ * The library is also built as a checked copy (compiled with GRMHD_CHECK_BOUNDS, in
+ * _build_checked/): there every array index its kernels form from a grid position
+ * or a stride offset is checked against the padded array; one outside it is counted
+ * and the access redirected to element 0, so the kernel runs on without touching
+ * memory outside its arrays (its results are then wrong, which the count reports).
+ * This call synchronises the device and returns the count since the last reset in
+ * *count (reset != 0 clears it).  In the normal build *count is -1 (no checks). */
+grmhd_status grmhd_bounds_violations(long long* count, int reset);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* grmhd_last_error(void);
 

@@ -465,3 +465,7 @@ grmhd_status grmhd_batch_destroy(grmhd_batch* b)
 }
 
 }  // extern "C"
+
+namespace grmhd {
+GRMHD_OOB_READER(oob_batch)
+}  // namespace grmhd

@@ -900,6 +900,27 @@ grmhd_status grmhd_diagnostics(grmhd_ctx* c, double* divb, double* totals, long 
     return nf ? GRMHD_WARN_C2P_FAILED : GRMHD_OK;
 }
 
+grmhd_status grmhd_bounds_violations(long long* count, int reset)
+{
+    if (!count) return fail(GRMHD_ERR_ARG, "count is NULL");
+#ifdef GRMHD_CHECK_BOUNDS
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise before reading the bounds counters");
+    unsigned long long (*const readers[])(bool) = {oob_kernels, oob_glm, oob_elliptic, oob_batch, oob_noalloc};
+    unsigned long long total = 0;
+    for (auto rd : readers) {
+        const unsigned long long v = rd(reset != 0);
+        if (v == ~0ull) return fail(GRMHD_ERR_CUDA, "reading a bounds counter failed");
+        total += v;
+    }
+    *count = (long long)total;
+#else
+    (void)reset;
+    *count = -1;   // not a checked build
+#endif
+    return GRMHD_OK;
+}
+
 grmhd_status grmhd_clean_scratch_bytes(const grmhd_grid* grid, size_t* bytes)
 {
     grmhd_status s = check_grid(grid);

@@ -203,3 +203,7 @@ extern "C" grmhd_status grmhd_divb_noalloc(const grmhd_grid* grid, const double*
     if (e != cudaSuccess) return err(GRMHD_ERR_CUDA, "grmhd_divb_noalloc: kernel launch failed");
     return GRMHD_OK;
 }
+
+namespace grmhd {
+GRMHD_OOB_READER(oob_noalloc)
+}  // namespace grmhd

@@ -581,4 +581,6 @@ cudaError_t mg_clean(const Dims& g, const MgPlan& plan0, double* scratch, double
     return cudaGetLastError();
 }
 
+GRMHD_OOB_READER(oob_elliptic)
+
 }  // namespace grmhd

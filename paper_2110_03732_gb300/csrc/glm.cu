@@ -179,7 +179,7 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (!g.act[d]) continue;
-        const long long o1 = o + g.st[d];
+        const long long o1 = chk(g, o + g.st[d]);
         const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
 #pragma unroll
         for (int v = 0; v < 12; v++) {
@@ -198,14 +198,14 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
         int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
         cp[d] += 1;
         cm[d] -= 1;
-        double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
+        double sp = psi ? psi[chk(g, o + g.st[d])] : 1.0, sm = psi ? psi[chk(g, o - g.st[d])] : 1.0;
         sp = sp * sp;
         sm = sm * sm;
         const double sp3 = sp * sp * sp, sm3 = sm * sm * sm, r = 1.0 / (sp3 * sm3);
         const double php = a.qphi[cell_at(g, cp)] * (sm3 * r);   // q_Phi / psi^6
         const double phm = a.qphi[cell_at(g, cm)] * (sp3 * r);
         Lc[8 + d] -= al * p2 * ((php - phm) * (0.5 * g.idx[d]));
-        if (alp) Lc[11] += a.qB[d][o] * ((alp[o + g.st[d]] - alp[o - g.st[d]]) * (0.5 * g.idx[d]));
+        if (alp) Lc[11] += a.qB[d][o] * ((alp[chk(g, o + g.st[d])] - alp[chk(g, o - g.st[d])]) * (0.5 * g.idx[d]));
     }
 #pragma unroll
     for (int v = 0; v < 12; v++) glm_out(a, v, o, Lc[v], v >= 5 && v < 8);
@@ -285,5 +285,7 @@ cudaError_t launch_glm_update(const Dims& g, const GlmUpdateArgs& a, int nsm, cu
     launch_k(a.psi || a.alp ? k_glm_update_metric : k_glm_update_flat, b, 128, st, g, a);
     return cudaGetLastError();
 }
+
+GRMHD_OOB_READER(oob_glm)
 
 }  // namespace grmhd

@@ -146,9 +146,50 @@ __device__ __forceinline__ int map_face(const Dims& g, int d, int m)
     return m;
 }
 
+// Bounds-checked builds (-DGRMHD_CHECK_BOUNDS, the library's checked copy): every
+// array index made by lin() or by an explicit stride offset passes through chk(),
+// which counts an index outside [0, ncell) in a per-translation-unit device counter
+// and redirects it to index 0, so that the access stays inside the array and the
+// kernel runs on; grmhd_bounds_violations reads and clears the counters.  In the
+// normal build chk() is the identity.
+#ifdef GRMHD_CHECK_BOUNDS
+static __device__ unsigned long long g_oob_count;
+#endif
+
+__device__ __forceinline__ long long chk(const Dims& g, long long i)
+{
+#ifdef GRMHD_CHECK_BOUNDS
+    if (i < 0 || i >= g.ncell) {
+        atomicAdd(&g_oob_count, 1ull);
+        return 0;
+    }
+#else
+    (void)g;
+#endif
+    return i;
+}
+
+// host side: this translation unit's counter (0 in the normal build); reset clears it
+#ifdef GRMHD_CHECK_BOUNDS
+#define GRMHD_OOB_READER(name)                                                                  \
+    unsigned long long name(bool reset)                                                         \
+    {                                                                                           \
+        unsigned long long v = 0;                                                               \
+        if (cudaMemcpyFromSymbol(&v, g_oob_count, sizeof v) != cudaSuccess) return ~0ull;       \
+        if (reset) {                                                                            \
+            const unsigned long long z = 0;                                                     \
+            if (cudaMemcpyToSymbol(g_oob_count, &z, sizeof z) != cudaSuccess) return ~0ull;     \
+        }                                                                                       \
+        return v;                                                                               \
+    }
+#else
+#define GRMHD_OOB_READER(name) \
+    unsigned long long name(bool) { return 0; }
+#endif
+
 __device__ __forceinline__ long long lin(const Dims& g, int i, int j, int k)
 {
-    return (long long)i + g.st[1] * j + g.st[2] * k;
+    return chk(g, (long long)i + g.st[1] * j + g.st[2] * k);
 }
 
 // mapped cell index of padded coordinates c[3]
@@ -195,7 +236,7 @@ __device__ __forceinline__ double cell_qB(const Dims& g, const double* __restric
     int h = m[e] + 1;
     if (g.bc[e] == BC_PERIODIC && h == g.ng[e] + g.n[e]) h = g.ng[e];
     if (h >= g.N[e]) return bf[i0];
-    const long long i1 = i0 + (long long)(h - m[e]) * g.st[e];
+    const long long i1 = chk(g, i0 + (long long)(h - m[e]) * g.st[e]);
     return 0.5 * (bf[i0] + bf[i1]);
 }
 

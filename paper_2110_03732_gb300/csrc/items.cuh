@@ -406,9 +406,9 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
 // the (up to two) A-faces touching the edge, cab[1] likewise for the B-faces; 1 in an
 // inactive direction.  The larger of a0/q0 and a1/q1 is picked by comparing a0 q1 with
 // a1 q0, and both quotients come from one reciprocal.
-__device__ __forceinline__ void edge_speeds(const double* __restrict__ psi, const double* __restrict__ alp,
-                                            long long i0, bool aa, bool ba, long long sA, long long sB,
-                                            double* cab)
+__device__ __forceinline__ void edge_speeds(const Dims& g, const double* __restrict__ psi,
+                                            const double* __restrict__ alp, long long i0, bool aa, bool ba,
+                                            long long sA, long long sB, double* cab)
 {
     double num[2] = {1.0, 1.0}, den[2] = {1.0, 1.0};
 #pragma unroll
@@ -417,7 +417,7 @@ __device__ __forceinline__ void edge_speeds(const double* __restrict__ psi, cons
         if (!act) continue;
         const long long sn = k == 0 ? sA : sB, so = k == 0 ? sB : sA;
         for (int tt = 0; tt < (oth ? 2 : 1); tt++) {
-            const long long cf = i0 - tt * so, cfm = cf - sn;
+            const long long cf = chk(g, i0 - tt * so), cfm = chk(g, cf - sn);
             const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
             const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
             const double q = psf * psf;
@@ -514,15 +514,15 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     if (alp || psi) {
         // mean of the 1, 2 or 4 cells around the edge
         double sum = alp ? alp[i0] : 1.0, w = 1.0;
-        if (aa) { sum += alp ? alp[i0 - sA] : 1.0; w = 0.5; }
+        if (aa) { sum += alp ? alp[chk(g, i0 - sA)] : 1.0; w = 0.5; }
         if (ba) {
-            sum += alp ? alp[i0 - sB] : 1.0;
-            if (aa) sum += alp ? alp[i0 - sA - sB] : 1.0;
+            sum += alp ? alp[chk(g, i0 - sB)] : 1.0;
+            if (aa) sum += alp ? alp[chk(g, i0 - sA - sB)] : 1.0;
             w *= 0.5;
         }
         ale = (T)(sum * w);
         double cab[2];
-        edge_speeds(psi, alp, i0, aa, ba, sA, sB, cab);
+        edge_speeds(g, psi, alp, i0, aa, ba, sA, sB, cab);
         ca = (T)cab[0];
         cb = (T)cab[1];
     }
@@ -620,12 +620,12 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
         T ale = T(1), ca = T(1), cb = T(1);
         if (alp || psi) {
             double sum = alp ? alp[i0] : 1.0;
-            sum += alp ? alp[i0 - sA] : 1.0;
-            sum += alp ? alp[i0 - sB] : 1.0;
-            sum += alp ? alp[i0 - sA - sB] : 1.0;
+            sum += alp ? alp[chk(g, i0 - sA)] : 1.0;
+            sum += alp ? alp[chk(g, i0 - sB)] : 1.0;
+            sum += alp ? alp[chk(g, i0 - sA - sB)] : 1.0;
             ale = (T)(sum * 0.25);
             double cab[2];
-            edge_speeds(psi, alp, i0, true, true, sA, sB, cab);
+            edge_speeds(g, psi, alp, i0, true, true, sA, sB, cab);
             ca = (T)cab[0];
             cb = (T)cab[1];
         }
@@ -714,7 +714,7 @@ __device__ __forceinline__ void emf_ideal_item(const Dims& g, const CP8& prim, c
     double ca = 1.0, cb = 1.0;
     if (alp || psi) {
         double cab[2];
-        edge_speeds(psi, alp, i0, aa, ba, sA, sB, cab);
+        edge_speeds(g, psi, alp, i0, aa, ba, sA, sB, cab);
         ca = cab[0];
         cb = cab[1];
     }
@@ -777,7 +777,7 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
         int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
         cp[d] += 1;
         cm[d] -= 1;
-        double sp = psi ? psi[o + g.st[d]] : 1.0, sm = psi ? psi[o - g.st[d]] : 1.0;
+        double sp = psi ? psi[chk(g, o + g.st[d])] : 1.0, sm = psi ? psi[chk(g, o - g.st[d])] : 1.0;
         sp = sp * sp;
         sm = sm * sm;
         const double qp = sp * sp * sp * prim[5 + d][cell_at(g, cp)];
@@ -814,8 +814,8 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             if (!g.act[i]) continue;
-            const double ap = alp ? alp[o + g.st[i]] : 1.0, am = alp ? alp[o - g.st[i]] : 1.0;
-            const double pp = psi ? psi[o + g.st[i]] : 1.0, pm = psi ? psi[o - g.st[i]] : 1.0;
+            const double ap = alp ? alp[chk(g, o + g.st[i])] : 1.0, am = alp ? alp[chk(g, o - g.st[i])] : 1.0;
+            const double pp = psi ? psi[chk(g, o + g.st[i])] : 1.0, pm = psi ? psi[chk(g, o - g.st[i])] : 1.0;
             const double dal = (ap - am) * (0.5 * g.idx[i]);
             const double dps = (pp - pm) * (0.5 * g.idx[i]);
             Lc[1 + i] += p6 * (-tauD * dal + 2.0 * al * (dps * ips) * tr);
@@ -847,7 +847,7 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             if (!g.act[d]) continue;
-            const long long o1 = o + g.st[d];
+            const long long o1 = chk(g, o + g.st[d]);
             const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
 #pragma unroll
             for (int v = 0; v < 8; v++) {
@@ -874,8 +874,8 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
         double r = 0.0;
         const double* __restrict__ Ec = a.Eh[fc];
         const double* __restrict__ Eb = a.Eh[fb];
-        if (g.act[fb]) r -= (Ec[o + g.st[fb]] - Ec[o]) * g.idx[fb];
-        if (g.act[fc]) r += (Eb[o + g.st[fc]] - Eb[o]) * g.idx[fc];
+        if (g.act[fb]) r -= (Ec[chk(g, o + g.st[fb])] - Ec[o]) * g.idx[fb];
+        if (g.act[fc]) r += (Eb[chk(g, o + g.st[fc])] - Eb[o]) * g.idx[fc];
         out_value(a, 8 + fa, o, r, false);
     }
 }

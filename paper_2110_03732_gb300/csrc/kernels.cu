@@ -148,8 +148,8 @@ __global__ void k_curlA(Dims g, CP3 A, P3 bf)
             const int fb = (fa + 1) % 3, fc = (fa + 2) % 3;
             if ((g.act[fb] && c[fb] + 1 >= g.N[fb]) || (g.act[fc] && c[fc] + 1 >= g.N[fc])) continue;
             double r = 0.0;
-            if (g.act[fb]) r += (A.p[fc][t + g.st[fb]] - A.p[fc][t]) * g.idx[fb];
-            if (g.act[fc]) r -= (A.p[fb][t + g.st[fc]] - A.p[fb][t]) * g.idx[fc];
+            if (g.act[fb]) r += (A.p[fc][chk(g, t + g.st[fb])] - A.p[fc][t]) * g.idx[fb];
+            if (g.act[fc]) r -= (A.p[fb][chk(g, t + g.st[fc])] - A.p[fb][t]) * g.idx[fc];
             bf.p[fa][t] = r;
         }
     }
@@ -193,8 +193,8 @@ __global__ void k_curlA_cc(Dims g, CP3 A, P3 qB)
         for (int a = 0; a < 3; a++) {
             const int b = (a + 1) % 3, c = (a + 2) % 3;
             double r = 0.0;
-            if (g.act[b]) r += (A.p[c][o + g.st[b]] - A.p[c][o - g.st[b]]) * (0.5 * g.idx[b]);
-            if (g.act[c]) r -= (A.p[b][o + g.st[c]] - A.p[b][o - g.st[c]]) * (0.5 * g.idx[c]);
+            if (g.act[b]) r += (A.p[c][chk(g, o + g.st[b])] - A.p[c][chk(g, o - g.st[b])]) * (0.5 * g.idx[b]);
+            if (g.act[c]) r -= (A.p[b][chk(g, o + g.st[c])] - A.p[b][chk(g, o - g.st[c])]) * (0.5 * g.idx[c]);
             qB.p[a][o] = r;
         }
     }
@@ -668,5 +668,7 @@ cudaError_t launch_diag_cc(const Dims& g, CP3 qB, CP8 q, double dV, double* part
     k_fold<<<1, 256, 0, st>>>(part, nblk, 11, nullptr, 1u << 2, out);
     return cudaGetLastError();
 }
+
+GRMHD_OOB_READER(oob_kernels)
 
 }  // namespace grmhd

@@ -167,4 +167,12 @@ cudaError_t launch_prim2con_cc(const Dims& g, CP8 prim, CP3 qB, const double* ps
 cudaError_t launch_diag_cc(const Dims& g, CP3 qB, CP8 q, double dV, double* part, int nblk, double* out,
                            cudaStream_t st);
 
+// index-bounds violations counted by each translation unit's kernels in a checked
+// build (GRMHD_CHECK_BOUNDS; 0 otherwise, ~0 if the counter could not be read)
+unsigned long long oob_kernels(bool reset);
+unsigned long long oob_glm(bool reset);
+unsigned long long oob_elliptic(bool reset);
+unsigned long long oob_batch(bool reset);
+unsigned long long oob_noalloc(bool reset);
+
 }  // namespace grmhd

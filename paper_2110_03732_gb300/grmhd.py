@@ -97,6 +97,7 @@ def lib():
     L.grmhd_save_start.argtypes = [vp, vp, C.c_size_t, vp]
     L.grmhd_load_start.argtypes = [vp, vp, C.c_size_t, vp]
     L.grmhd_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), vp]
+    L.grmhd_bounds_violations.argtypes = [C.POINTER(C.c_longlong), C.c_int]
     L.grmhd_last_error.restype = C.c_char_p
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
                  "grmhd_set_metric", "grmhd_set_eta", "grmhd_set_dynamo", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
@@ -105,7 +106,7 @@ def lib():
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
                  "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
                  "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start",
-                 "grmhd_fp64_fma_rate"):
+                 "grmhd_fp64_fma_rate", "grmhd_bounds_violations"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -139,6 +140,16 @@ def make_grid(ndim, n, lo, hi, bc):
         b = bc[d]
         g.bc[d] = BC[b] if isinstance(b, str) else int(b)
     return g
+
+
+def bounds_violations(reset=False):
+    """Array-index bounds violations counted since the last reset (synchronises the
+    device); -1 when the loaded library is the normal build, which has no checks.
+    Load the checked copy by pointing build.LIB at build.LIB_CHECKED before the
+    first use of the library."""
+    n = C.c_longlong(0)
+    check(lib().grmhd_bounds_violations(C.byref(n), int(bool(reset))), "bounds_violations")
+    return n.value
 
 
 def fp64_fma_rate(stream=None):

@@ -287,3 +287,16 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_normal_build_reports_no_bounds_checks():
+    """The normal build has no index checks: grmhd_bounds_violations reports -1 (and
+    needs no device for that)."""
+    import ctypes as C
+    from paper_2110_03732_gb300 import build as _b
+    L = C.CDLL(_b.build())
+    L.grmhd_bounds_violations.argtypes = [C.POINTER(C.c_longlong), C.c_int]
+    L.grmhd_bounds_violations.restype = C.c_int
+    n = C.c_longlong(7)
+    assert L.grmhd_bounds_violations(C.byref(n), 0) == 0 and n.value == -1
+    assert L.grmhd_bounds_violations(None, 0) == -1
