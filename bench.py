@@ -585,13 +585,68 @@ def bench_batched(grmhd, P, dev, args):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     ms = float(np.mean(times))
+    # the same boxes through the persistent launch: k steps in one cooperative launch
+    B.step_persistent(1)
+    torch.cuda.synchronize()
+    e0.record()
+    B.step_persistent(k, synchronize=False)
+    e1.record()
+    e1.synchronize()
+    assert B.persistent_status() == 0
+    ms_p = e0.elapsed_time(e1) / k
     nfail = sum(s.diagnostics()[2] for s in solvers[:8])
     out = {"workload": "256 Orszag-Tang boxes, sides U{64,128,256,512}, eta 10^U[-6,0], seed 0",
            "boxes": len(probs), "cells": cells, "precision": "mixed", "value": cells * STAGES / (ms / 1e3),
            "unit": UNIT, "ms_per_step": ms, "steps": k, "graph_captured": True,
-           "launch_config": {kk: list(vv) for kk, vv in cfg.items()}, "newton_failures_first8": nfail}
+           "launch_config": {kk: list(vv) for kk, vv in cfg.items()}, "newton_failures_first8": nfail,
+           "persistent": {"value": cells * STAGES / (ms_p / 1e3), "ms_per_step": ms_p,
+                          "launch": f"{k} steps in one cooperative launch (phases separated by grid barriers)"}}
     del graph, B, solvers
     torch.cuda.synchronize()
+    out["small_problems"] = bench_small_batch(grmhd, P, dev)
+    return out
+
+
+def bench_small_batch(grmhd, P, dev, n_tubes=32, steps=200):
+    """Many small problems, where launches dominate: 32 1-D shock tubes of 400-4096
+    cells (seeded) in mixed precision, `steps` steps by the per-kind batched kernels
+    (replayed from a CUDA graph of one step) and by the persistent launch (all steps in
+    one cooperative launch)."""
+    import torch
+    rng = np.random.default_rng(5)
+    probs = [P.shock_tube(int(n), eta=10.0 ** rng.uniform(-6, 0)) for n in rng.integers(400, 4097, n_tubes)]
+    out = {"workload": f"{n_tubes} shock tubes of 400-4096 cells, eta 10^U[-6,0], seed 5, mixed precision",
+           "cells": int(sum(p.cells for p in probs)), "steps": steps}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for mode in ("per_kind_graph", "persistent"):
+        solvers = [grmhd.Solver.from_problem(pr, device=dev, precision="mixed") for pr in probs]
+        B = grmhd.Batch(solvers)
+        B.set_dt([s.compute_dt() for s in solvers])
+        B.step()
+        torch.cuda.synchronize()
+        if mode == "per_kind_graph":
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(side):
+                with torch.cuda.graph(graph, stream=side):
+                    B.step(stream=side)
+            torch.cuda.current_stream().wait_stream(side)
+            e0.record()
+            for _ in range(steps):
+                graph.replay()
+            e1.record()
+        else:
+            e0.record()
+            B.step_persistent(steps, synchronize=False)
+            e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[mode] = {"ms_per_step": ms, "value": out["cells"] * STAGES / (ms / 1e3),
+                     "newton_failures": sum(s.diagnostics()[2] for s in solvers)}
+        del B, solvers
+    out["unit"] = UNIT
     return out
 
 

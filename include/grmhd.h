@@ -51,6 +51,7 @@ typedef enum {
     GRMHD_ERR_ARG = -1,        /* invalid argument (message in grmhd_last_error) */
     GRMHD_ERR_CUDA = -2,       /* a CUDA call failed */
     GRMHD_ERR_SCRATCH = -3,    /* scratch buffer too small or misaligned */
+    GRMHD_ERR_TIMEOUT = -4,    /* a bounded device-side wait ran out (persistent batched launch) */
     GRMHD_ERR_STATE = -5       /* call out of order (e.g. step before bind) */
 } grmhd_status;
 
@@ -333,6 +334,30 @@ grmhd_status grmhd_batch_autotune(grmhd_batch* b, int reps, grmhd_stream_t strea
 /* Chosen launch shape per kernel kind (8 entries: implicit, flux x/y/z, emf x/y/z,
  * update). */
 grmhd_status grmhd_batch_config(const grmhd_batch* b, int* threads, int* items);
+
+/* Persistent launch: nsteps IMEX steps of every problem in ONE cooperative launch
+ * (blocks co-resident, at most the device holds).  Per stage it runs the phases of
+ * grmhd_batch_step -- the implicit solves; the face fluxes and edge EMFs; the update
+ * (after the FIXED-boundary face copy at the start of each step) -- over the same work
+ * lists and per-item bodies, with a grid-wide barrier between phases.  A problem's
+ * results are bitwise the same alone and in any batch, and for any split of its steps
+ * into launches; against grmhd_batch_step they agree to round-off (the compiler may
+ * contract the bodies inlined into this one kernel differently).  Every barrier wait
+ * is bounded: a
+ * block that waits longer than the batch's wait limit (grmhd_batch_set_wait_limit,
+ * 1 s by default) sets the batch's error flag, and all blocks then leave the kernel;
+ * the problems' states are then partly advanced and must be restored by the caller.
+ * synchronize != 0: the call waits for the launch and returns GRMHD_ERR_TIMEOUT if a
+ * wait ran out; synchronize == 0: launches only (a memset and a kernel: capturable in
+ * a CUDA graph), and grmhd_batch_persistent_status reports later.  Uses the dts of the
+ * last grmhd_batch_set_dt for every step.  GRMHD_ERR_CUDA if the device cannot make a
+ * cooperative launch. */
+grmhd_status grmhd_batch_step_persistent(grmhd_batch* b, int nsteps, int synchronize, grmhd_stream_t stream);
+/* Limit of each grid-barrier wait of the persistent launch, in seconds (0..60). */
+grmhd_status grmhd_batch_set_wait_limit(grmhd_batch* b, double seconds);
+/* Synchronises the stream; GRMHD_ERR_TIMEOUT if a wait of the last persistent launch
+ * ran out, GRMHD_OK otherwise. */
+grmhd_status grmhd_batch_persistent_status(grmhd_batch* b, grmhd_stream_t stream);
 grmhd_status grmhd_batch_destroy(grmhd_batch* b);
 
 /* div B norms of caller-owned face fields without allocating anything.  The paper

@@ -35,6 +35,16 @@ struct ProbStage {
     double* Eh64[3];
     double* fe64[3][3];   // [D][C]: edge EMFs written by the D-flux kernel (flat 1-D / 2-D)
     UpdateArgs upd;
+    int fixed;            // FIXED boundaries: the later bases take the face fields each step
+};
+
+// grid-wide barrier of the persistent launch (device memory in the batch scratch):
+// arrivals, generation, and the error flag a wait that ran out sets
+struct BarrierState {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
 };
 
 // faces (edges) per item of the batched flux (EMF) kernels: each item marches K of them
@@ -119,6 +129,150 @@ __global__ void __launch_bounds__(256) kb_update(const ProbStage* __restrict__ P
     }
 }
 
+// ---------------------------------------------------------------------------
+// persistent launch: every phase of nsteps steps in one cooperative launch
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier (all blocks are co-resident: cooperative launch).  Each block's
+// writes are fenced before it arrives; the last arrival resets the count and advances
+// the generation; the others wait for the generation to change, for at most limit_ns
+// of the global timer.  A wait that runs out sets the batch's error flag; every block
+// that sees the flag (waiting, or at its next barrier) returns false and leaves the
+// kernel, so the launch ends within about one limit and the host reads the flag.
+__device__ bool grid_barrier(BarrierState* bs, unsigned nblocks, unsigned long long limit_ns)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &bs->gen;
+        volatile int* err = &bs->err;
+        int good = *err == 0;
+        if (good) {
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(&bs->count, 1u) == nblocks - 1) {
+                atomicExch(&bs->count, 0u);
+                __threadfence();
+                atomicAdd(&bs->gen, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                while (*gen == g) {
+                    if (*err) {
+                        good = 0;
+                        break;
+                    }
+                    if (global_ns() - t0 > limit_ns) {
+                        atomicExch(&bs->err, 1);
+                        good = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+            if (*err) good = 0;
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+struct PersistLists {
+    const Chunk* ch;
+    int off[WL_KINDS][2], cnt[WL_KINDS][2];
+};
+
+// the items of one work-list kind and metric flag, chunks spread over the blocks
+#define PERSIST_ITEMS(KIND, MM, BODY)                                                   \
+    {                                                                                   \
+        const Chunk* ch_ = L.ch + L.off[KIND][MM];                                      \
+        const int n_ = L.cnt[KIND][MM];                                                 \
+        for (int i_ = blockIdx.x; i_ < n_; i_ += gridDim.x) {                           \
+            const Chunk k_ = ch_[i_];                                                   \
+            const ProbStage& ps = P[k_.prob * s + stage];                               \
+            for (long long t = k_.begin + threadIdx.x; t < k_.end; t += blockDim.x) {   \
+                BODY;                                                                   \
+            }                                                                           \
+        }                                                                               \
+    }
+
+template <int C, bool M, typename T>
+__device__ __forceinline__ void emf_any_item(const ProbStage& ps, long long t)
+{
+    if (ps.g.act[(C + 1) % 3] && ps.g.act[(C + 2) % 3])
+        emf_march_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t);
+    else
+        emf_item<C, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.Eh64[C], t);
+}
+
+// nsteps IMEX steps of every problem: per stage the implicit solves, then the face
+// fluxes and edge EMFs (which read the same stage primitives and write separate
+// arrays), then the update, with a grid barrier after each phase; FIXED-boundary
+// problems first copy their face fields into the later-stage bases, as
+// grmhd_batch_step does.  The per-item bodies are those of the per-kind kernels.
+template <typename T>
+__global__ void __launch_bounds__(128) kb_persistent(const ProbStage* __restrict__ P, int n, int s, PersistLists L,
+                                                     BarrierState* bs, int nsteps, unsigned long long limit_ns,
+                                                     int any_fixed)
+{
+    const unsigned nb = gridDim.x;
+    for (int step = 0; step < nsteps; step++) {
+        if (any_fixed) {
+            for (int p = 0; p < n; p++) {
+                const ProbStage& ps = P[p * s];
+                if (!ps.fixed) continue;
+                const long long nc = ps.g.ncell;
+                for (int k = 1; k < s; k++)
+                    for (int v = 0; v < 3; v++) {
+                        const double* __restrict__ src = ps.upd.qn[8 + v];
+                        double* __restrict__ dst = ps.upd.base[k][8 + v];
+                        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nc;
+                             t += (long long)gridDim.x * blockDim.x)
+                            dst[t] = src[t];
+                    }
+            }
+            if (!grid_barrier(bs, nb, limit_ns)) return;
+        }
+        for (int stage = 0; stage < s; stage++) {
+            PERSIST_ITEMS(WL_IMP, 0, implicit_item<false>(ps.g, ps.imp, t))
+            PERSIST_ITEMS(WL_IMP, 1, implicit_item<true>(ps.g, ps.imp, t))
+            if (!grid_barrier(bs, nb, limit_ns)) return;
+            PERSIST_ITEMS(WL_FLUX + 0, 0, (flux_march_item<0, false, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
+                                                                       ps.F64[0], nullptr, ps.fe64[0], t)))
+            PERSIST_ITEMS(WL_FLUX + 0, 1, (flux_march_item<0, true, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
+                                                                      ps.F64[0], nullptr, ps.fe64[0], t)))
+            PERSIST_ITEMS(WL_FLUX + 1, 0, (flux_march_item<1, false, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
+                                                                       ps.F64[1], nullptr, ps.fe64[1], t)))
+            PERSIST_ITEMS(WL_FLUX + 1, 1, (flux_march_item<1, true, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
+                                                                      ps.F64[1], nullptr, ps.fe64[1], t)))
+            PERSIST_ITEMS(WL_FLUX + 2, 0, (flux_march_item<2, false, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
+                                                                       ps.F64[2], nullptr, ps.fe64[2], t)))
+            PERSIST_ITEMS(WL_FLUX + 2, 1, (flux_march_item<2, true, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
+                                                                      ps.F64[2], nullptr, ps.fe64[2], t)))
+            PERSIST_ITEMS(WL_EMF + 0, 0, (emf_any_item<0, false, T>(ps, t)))
+            PERSIST_ITEMS(WL_EMF + 0, 1, (emf_any_item<0, true, T>(ps, t)))
+            PERSIST_ITEMS(WL_EMF + 1, 0, (emf_any_item<1, false, T>(ps, t)))
+            PERSIST_ITEMS(WL_EMF + 1, 1, (emf_any_item<1, true, T>(ps, t)))
+            PERSIST_ITEMS(WL_EMF + 2, 0, (emf_any_item<2, false, T>(ps, t)))
+            PERSIST_ITEMS(WL_EMF + 2, 1, (emf_any_item<2, true, T>(ps, t)))
+            if (!grid_barrier(bs, nb, limit_ns)) return;
+            PERSIST_ITEMS(WL_UPD, 0, update_item<false>(ps.g, ps.upd, t))
+            PERSIST_ITEMS(WL_UPD, 1, update_item<true>(ps.g, ps.upd, t))
+            if (step + 1 < nsteps || stage + 1 < s)
+                if (!grid_barrier(bs, nb, limit_ns)) return;
+        }
+    }
+}
+#undef PERSIST_ITEMS
+
 // items of one problem for a work-list kind (0 = not run)
 long long items_of(const grmhd_ctx* cx, int kind)
 {
@@ -161,6 +315,9 @@ struct grmhd_batch_s {
     Cfg cfg[WL_KINDS];
     int nsm;
     std::vector<int> fixed_probs;       // problems with FIXED boundaries
+    BarrierState* d_bar;                // persistent launch: grid barrier (device)
+    double wait_limit_s;                // persistent launch: limit of each barrier wait
+    int persist_blocks;                 // persistent launch: co-resident blocks (0: not yet known)
 };
 
 namespace {
@@ -224,6 +381,7 @@ void fill_desc(grmhd_batch* b, int p, double dt)
         for (int k = 0; k < 3; k++) ps.upd.bf[k] = ps.bfs.p[k];
         ps.upd.psi = ps.psi;
         ps.upd.alp = ps.alp;
+        ps.fixed = ctx_any_fixed(c) ? 1 : 0;
     }
 }
 
@@ -315,7 +473,8 @@ grmhd_status grmhd_batch_scratch_bytes(grmhd_ctx* const* ctxs, int n, size_t* by
             return batch_fail(GRMHD_ERR_ARG, "batched execution takes the MC reconstruction only");
         s = ctx_stages(ctxs[p]);
     }
-    *bytes = rup(sizeof(ProbStage) * (size_t)n * s) + rup(sizeof(Chunk) * chunk_capacity(ctxs, n));
+    *bytes = rup(sizeof(ProbStage) * (size_t)n * s) + rup(sizeof(Chunk) * chunk_capacity(ctxs, n)) +
+             rup(sizeof(BarrierState));
     return GRMHD_OK;
 }
 
@@ -343,6 +502,9 @@ grmhd_status grmhd_batch_create(grmhd_ctx* const* ctxs, int n, void* scratch, si
     b->d_desc = (ProbStage*)scratch;
     b->d_chunks = (Chunk*)((char*)scratch + rup(sizeof(ProbStage) * (size_t)n * b->s));
     b->chunk_cap = chunk_capacity(ctxs, n);
+    b->d_bar = (BarrierState*)((char*)b->d_chunks + rup(sizeof(Chunk) * b->chunk_cap));
+    b->wait_limit_s = 1.0;
+    b->persist_blocks = 0;
     b->nsm = ctx_nsm(ctxs[0]);
     for (int k = 0; k < WL_KINDS; k++) b->cfg[k] = kCands[1];
     for (int p = 0; p < n; p++) {
@@ -446,6 +608,69 @@ grmhd_status grmhd_batch_autotune(grmhd_batch* b, int reps, grmhd_stream_t strea
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return res;
+}
+
+grmhd_status grmhd_batch_set_wait_limit(grmhd_batch* b, double seconds)
+{
+    if (!b || !(seconds >= 0.0) || !(seconds <= 60.0))
+        return batch_fail(GRMHD_ERR_ARG, "grmhd_batch_set_wait_limit: a limit in [0, 60] seconds");
+    b->wait_limit_s = seconds;
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_batch_persistent_status(grmhd_batch* b, grmhd_stream_t stream)
+{
+    if (!b) return batch_fail(GRMHD_ERR_ARG, "batch is NULL");
+    BarrierState h;
+    cudaError_t e = cudaMemcpyAsync(&h, b->d_bar, sizeof h, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return batch_fail(GRMHD_ERR_CUDA, "reading the persistent launch's status failed");
+    if (h.err) return batch_fail(GRMHD_ERR_TIMEOUT, "a grid barrier wait of the persistent launch ran out of time");
+    return GRMHD_OK;
+}
+
+grmhd_status grmhd_batch_step_persistent(grmhd_batch* b, int nsteps, int synchronize, grmhd_stream_t stream)
+{
+    NvtxRange nv("grmhd_batch_step_persistent");
+    if (!b || nsteps < 1) return batch_fail(GRMHD_ERR_ARG, "grmhd_batch_step_persistent: bad arguments");
+    for (int p = 0; p < b->n; p++)
+        if (!(b->dt[p] > 0.0)) return batch_fail(GRMHD_ERR_STATE, "call grmhd_batch_set_dt before stepping");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool mixed = b->mixed;
+    const void* fn = mixed ? (const void*)kb_persistent<float> : (const void*)kb_persistent<double>;
+    if (b->persist_blocks < 1) {
+        int dev = 0, coop = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (e == cudaSuccess && coop)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0);
+        if (e != cudaSuccess || !coop || per_sm < 1)
+            return batch_fail(GRMHD_ERR_CUDA, "the device cannot run the persistent (cooperative) launch");
+        b->persist_blocks = per_sm * b->nsm;
+    }
+    // the barrier starts at zero; a memset node, so the call can be graph-captured
+    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(BarrierState), st);
+    if (e != cudaSuccess) return batch_fail(GRMHD_ERR_CUDA, "barrier reset failed");
+    PersistLists L;
+    L.ch = b->d_chunks;
+    int total = 0;
+    for (int k = 0; k < WL_KINDS; k++)
+        for (int m = 0; m < 2; m++) {
+            L.off[k][m] = b->off[k][m];
+            L.cnt[k][m] = b->cnt[k][m];
+            total += b->cnt[k][m];
+        }
+    const ProbStage* P = b->d_desc;
+    int n = b->n, s = b->s, any_fixed = b->fixed_probs.empty() ? 0 : 1;
+    BarrierState* bar = b->d_bar;
+    unsigned long long limit = (unsigned long long)(b->wait_limit_s * 1e9);
+    // no more blocks than co-resident ones (the barrier needs them all), nor than chunks
+    const int blocks = std::max(1, std::min(b->persist_blocks, total));
+    void* args[] = {(void*)&P, (void*)&n, (void*)&s, (void*)&L, (void*)&bar, (void*)&nsteps, (void*)&limit,
+                    (void*)&any_fixed};
+    e = cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(128), args, 0, st);
+    if (e != cudaSuccess) return batch_fail(GRMHD_ERR_CUDA, "persistent launch failed");
+    return synchronize ? grmhd_batch_persistent_status(b, stream) : GRMHD_OK;
 }
 
 grmhd_status grmhd_batch_config(const grmhd_batch* b, int* threads, int* items)

@@ -18,6 +18,7 @@ _lib = None
 
 GRMHD_OK = 0
 GRMHD_WARN_C2P_FAILED = 1
+GRMHD_ERR_TIMEOUT = -4
 BC = {"periodic": 0, "outflow": 1, "fixed": 2}
 
 
@@ -91,6 +92,9 @@ def lib():
     L.grmhd_batch_autotune.argtypes = [vp, C.c_int, vp]
     L.grmhd_batch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.grmhd_batch_destroy.argtypes = [vp]
+    L.grmhd_batch_step_persistent.argtypes = [vp, C.c_int, C.c_int, vp]
+    L.grmhd_batch_set_wait_limit.argtypes = [vp, C.c_double]
+    L.grmhd_batch_persistent_status.argtypes = [vp, vp]
     L.grmhd_launch_count.argtypes = [vp]
     L.grmhd_launch_count.restype = C.c_longlong
     L.grmhd_start_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
@@ -106,7 +110,8 @@ def lib():
                  "grmhd_batch_set_dt", "grmhd_batch_step", "grmhd_batch_autotune", "grmhd_batch_config",
                  "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
                  "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start",
-                 "grmhd_fp64_fma_rate", "grmhd_bounds_violations"):
+                 "grmhd_fp64_fma_rate", "grmhd_bounds_violations", "grmhd_batch_step_persistent",
+                 "grmhd_batch_set_wait_limit", "grmhd_batch_persistent_status"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -459,3 +464,18 @@ class Batch:
         it = (C.c_int * 8)()
         check(self.L.grmhd_batch_config(self.b, th, it), "batch_config")
         return {k: (th[i], it[i]) for i, k in enumerate(self.KINDS)}
+
+    def step_persistent(self, nsteps=1, synchronize=True, stream=None):
+        """nsteps steps of every problem in one cooperative launch (bitwise the same
+        results as step()); with synchronize, raises GrmhdError on a wait that ran out
+        (status GRMHD_ERR_TIMEOUT)."""
+        return check(self.L.grmhd_batch_step_persistent(self.b, int(nsteps), int(bool(synchronize)),
+                                                        _stream(stream)), "batch_step_persistent")
+
+    def set_wait_limit(self, seconds):
+        check(self.L.grmhd_batch_set_wait_limit(self.b, float(seconds)), "batch_set_wait_limit")
+
+    def persistent_status(self, stream=None):
+        """GRMHD_OK, or GRMHD_ERR_TIMEOUT if a barrier wait of the last persistent launch
+        ran out (synchronises; does not raise)."""
+        return int(self.L.grmhd_batch_persistent_status(self.b, _stream(stream)))
