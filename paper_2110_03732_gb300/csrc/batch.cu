@@ -218,8 +218,14 @@ __device__ __forceinline__ void emf_any_item(const ProbStage& ps, long long t)
 // arrays), then the update, with a grid barrier after each phase; FIXED-boundary
 // problems first copy their face fields into the later-stage bases, as
 // grmhd_batch_step does.  The per-item bodies are those of the per-kind kernels.
+//
+// Registers: the fused kernel takes the largest need of its phases (255 unbounded).
+// The mixed-precision instantiation is bounded to four 128-thread blocks per SM: on
+// the 256-box batch that ran 38.4 ms per step against 50.7 ms at two blocks (spills of
+// ~1.7 KB cost less than the lost occupancy); the FP64 one stays at two (four would
+// spill 4.6 KB).
 template <typename T>
-__global__ void __launch_bounds__(128) kb_persistent(const ProbStage* __restrict__ P, int n, int s, PersistLists L,
+__global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2)) kb_persistent(const ProbStage* __restrict__ P, int n, int s, PersistLists L,
                                                      BarrierState* bs, int nsteps, unsigned long long limit_ns,
                                                      int any_fixed)
 {
