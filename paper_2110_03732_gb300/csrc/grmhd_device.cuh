@@ -334,17 +334,45 @@ __device__ __forceinline__ T ppm_iface(T am, T a0, T ap, T app)
     return ppm_iface_s<T>(a0, ap, ppm_slope<T>(am, a0, ap), ppm_slope<T>(a0, ap, app));
 }
 
+// signs of a product from the IEEE bit patterns (an FP64 multiply and compare would
+// take two FP64 issue slots): x y > 0 when both are nonzero with equal signs, x y < 0
+// when both are nonzero with opposite signs
+template <typename T>
+__device__ __forceinline__ bool prod_pos(T x, T y)
+{
+    using I = typename Bits<T>::I;
+    const I bx = Bits<T>::to(x), by = Bits<T>::to(y);
+    return (bx ^ by) >= 0 && (bx & Bits<T>::MAG) != 0 && (by & Bits<T>::MAG) != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool prod_neg(T x, T y)
+{
+    using I = typename Bits<T>::I;
+    const I bx = Bits<T>::to(x), by = Bits<T>::to(y);
+    return (bx ^ by) < 0 && (bx & Bits<T>::MAG) != 0 && (by & Bits<T>::MAG) != 0;
+}
+
+// Colella & Woodward's monotonicity limits of the parabola through aL, a0, aR: flat
+// at a local extremum ((aR - a0)(a0 - aL) <= 0), else the edge whose overshoot the
+// parabola would take past the other is moved (dd m6 > dd^2, or -dd^2 > dd m6, with
+// dd = aR - aL and m6 = 6 (a0 - (aL + aR)/2)).  The comparisons are decided as signs:
+// dd m6 - dd^2 = 2 dd t1 and dd m6 + dd^2 = 2 dd t2 with t1 = 3 a0 - aL - 2 aR and
+// t2 = 3 a0 - 2 aL - aR, and the moved edges are 3 a0 - 2 aR = t1 + aL and
+// 3 a0 - 2 aL = t2 + aR.  Where rounding could flip a decision the two outcomes
+// coincide (t1 = 0 moves aL onto itself), so the limiter stays continuous.
 template <typename T>
 __device__ __forceinline__ void ppm_limit(T a0, T& aL, T& aR)
 {
-    if ((aR - a0) * (a0 - aL) <= T(0)) {
+    if (!prod_pos(aR - a0, a0 - aL)) {
         aL = a0;
         aR = a0;
         return;
     }
-    const T dd = aR - aL, m6 = T(6) * (a0 - T(0.5) * (aL + aR));
-    if (dd * m6 > dd * dd) aL = T(3) * a0 - T(2) * aR;
-    else if (-dd * dd > dd * m6) aR = T(3) * a0 - T(2) * aL;
+    const T dd = aR - aL;
+    const T t1 = T(3) * a0 - aL - T(2) * aR, t2 = T(3) * a0 - T(2) * aL - aR;
+    if (prod_pos(dd, t1)) aL = t1 + aL;
+    else if (prod_neg(dd, t2)) aR = t2 + aR;
 }
 
 template <typename T>
