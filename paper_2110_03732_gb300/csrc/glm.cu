@@ -45,7 +45,7 @@ __device__ __forceinline__ void glm_face_flux(const Dims& g, const GlmFluxArgs& 
     face_state<double>(prR, BR, D, psf, alf, g.gh, sR);
     // HLL with c+ = c- = alpha sqrt(gamma^DD) (Sec. 2.5, maximal diffusivity); with equal
     // speeds (c f_L + c f_R - c^2 (q_R - q_L)) / 2c = (f_L + f_R - c (q_R - q_L)) / 2
-    const double cs = alf / pf2;
+    const double cs = psi ? alf * rcp_pos(pf2) : alf;
     const long long o = r0;
 #pragma unroll
     for (int v = 0; v < 8; v++) a.F[v][o] = sL.f[v] + sR.f[v] - cs * (sR.q[v] - sL.q[v]);
@@ -93,7 +93,7 @@ __device__ __forceinline__ void glm_flux_march_item(const Dims& g, const GlmFlux
         double ip6 = 1.0;
         if (psi) {
             const double ps = psi[lin(g, cs[0], cs[1], cs[2])], p2 = ps * ps;
-            ip6 = 1.0 / (p2 * p2 * p2);
+            ip6 = rcp_pos(p2 * p2 * p2);
         }
 #pragma unroll
         for (int e = 0; e < 3; e++) x[8 + e] = a.qB[e][mi] * ip6;
@@ -201,7 +201,7 @@ __device__ __forceinline__ void glm_update_item(const Dims& g, const GlmUpdateAr
         double sp = psi ? psi[chk(g, o + g.st[d])] : 1.0, sm = psi ? psi[chk(g, o - g.st[d])] : 1.0;
         sp = sp * sp;
         sm = sm * sm;
-        const double sp3 = sp * sp * sp, sm3 = sm * sm * sm, r = 1.0 / (sp3 * sm3);
+        const double sp3 = sp * sp * sp, sm3 = sm * sm * sm, r = rcp_pos(sp3 * sm3);
         const double php = a.qphi[cell_at(g, cp)] * (sm3 * r);   // q_Phi / psi^6
         const double phm = a.qphi[cell_at(g, cm)] * (sp3 * r);
         Lc[8 + d] -= al * p2 * ((php - phm) * (0.5 * g.idx[d]));

@@ -574,6 +574,11 @@ __device__ __forceinline__ double rcp_pos(double x)
     return fma(y, fma(e, e, e), y);
 }
 
+// 1/x for a positive x of moderate size in the stencil precision T (metric factors,
+// speed products): rcp_pos in FP64, the division in FP32
+__device__ __forceinline__ double rcp_t(double x) { return rcp_pos(x); }
+__device__ __forceinline__ float rcp_t(float x) { return 1.0f / x; }
+
 // ---------------------------------------------------------------------------
 // implicit electric field + velocity solve (Sec. 2.4), xi = 0, orthonormal frame
 // ---------------------------------------------------------------------------

@@ -36,7 +36,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     const long long id = lin(g, c[0], c[1], c[2]);
     const double ps = psi ? psi[id] : 1.0;
     const double al = alp ? alp[id] : 1.0;
-    const double p2 = ps * ps, p4 = p2 * p2, ip2 = 1.0 / p2, ip4 = ip2 * ip2, ip6 = ip4 * ip2;
+    const double p2 = ps * ps, p4 = p2 * p2, ip2 = M ? rcp_pos(p2) : 1.0, ip4 = ip2 * ip2, ip6 = ip4 * ip2;
     CellIn ci;
     ci.gh = g.gh;
     ci.igh = g.igh;
@@ -57,7 +57,7 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
     }
     const double et = eta ? eta[id] : eta_u;
     // flat: eta / (a_ii dt) with the host's reciprocal, no division
-    ci.etat = a.stiff ? (M ? et / (al * a_dt) : et * a.ia_dt) : -1.0;
+    ci.etat = a.stiff ? (M ? et * rcp_pos(al) * a.ia_dt : et * a.ia_dt) : -1.0;
     cell_derive(ci);
     double u[3];
     Eval e;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
     const T psf = psi ? (T)(0.5 * (psi[rm] + psi[r0])) : T(1);
     const T alf = alp ? (T)(0.5 * (alp[rm] + alp[r0])) : T(1);
-    const T pf2 = psf * psf, ipf2 = T(1) / pf2;
+    const T pf2 = psf * psf, ipf2 = psi ? rcp_t(pf2) : T(1);
     // orthonormal-frame states at the face: u_hat = psi^2 u, E_hat = psi^2 E,
     // B_hat = psi^2 B (normal: q_B / psi^4)
     BL[D] = BR[D] = (T)bf.p[D][face_at(g, D, c)] * (ipf2 * ipf2);
@@ -361,7 +361,7 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
         T ip6 = T(1);
         if (psi) {
             const T ps = (T)psi[lin(g, cs[0], cs[1], cs[2])], p2 = ps * ps;
-            ip6 = T(1) / (p2 * p2 * p2);
+            ip6 = rcp_t(p2 * p2 * p2);
         }
         x[8] = (T)cell_qB_in(g, prim, bf, T1, cs, mi) * ip6;
         x[9] = (T)cell_qB_in(g, prim, bf, T2, cs, mi) * ip6;
@@ -427,7 +427,7 @@ __device__ __forceinline__ void edge_speeds(const Dims& g, const double* __restr
             }
         }
     }
-    const double r = 1.0 / (den[0] * den[1]);
+    const double r = rcp_pos(den[0] * den[1]);
     cab[0] = num[0] * den[1] * r;
     cab[1] = num[1] * den[0] * r;
 }
@@ -792,7 +792,7 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
         //   s_S_i = psi^6 [-(tau + D) d_i alpha + 2 alpha (d_i psi / psi)(rho h W^2 v^2 + 3p + U)]
         //   s_tau = -psi^4 S_hat_i d_i alpha
         const double rho = prim[0][o], p = prim[4][o];
-        const double ip4 = 1.0 / p4, ips = ps * p2 * ip4;   // psi^-4, psi^-1
+        const double ip4 = rcp_pos(p4), ips = ps * p2 * ip4;   // psi^-4, psi^-1
         double uh[3], Eh[3], Bh[3];
 #pragma unroll
         for (int i = 0; i < 3; i++) {
