@@ -135,13 +135,14 @@ def peaks():
 
 # Algorithmic bytes per 512^2 launch of the mixed-precision stencil kernels (each datum
 # once, flat 2-D grid): a flux launch reads the 10 FP32 values each face state needs
-# per cell (8 primitives and the 2 transverse cell q_B, 40 B) and writes 8 FP64 fluxes
-# and the one degenerate edge EMF it owns per face (72 B); the edge-EMF launch reads E_z
-# (FP32) and the two face q_B (FP64) per edge and writes its FP64 EMF (28 B); the update
-# reads per cell q^n or the running sum (11), the fluxes (16), the primitives its sources
-# use (u^1..3, E^1..2: 5), R (3) and the edge EMFs (3), and writes the later-stage base
-# and the running sum (22, stage 0) or q^{n+1} (11, stage 1): 55.5 doubles on average.
-MIXED_ALG_BYTES_PER_CELL = {"flux": 112.0, "emf": 28.0, "update": 55.5 * 8}
+# per cell (8 primitives and the 2 transverse cell q_B, 40 B) and writes 8 FP32 fluxes
+# and the one degenerate FP64 edge EMF it owns per face (40 B); the edge-EMF launch
+# reads E_z (FP32) and the two face q_B (FP64) per edge and writes its FP64 EMF (28 B);
+# the update reads per cell the 16 FP32 fluxes (64 B) and, in doubles, q^n or the
+# running sum (11), the primitives its sources use (u^1..3, E^1..2: 5), R (3) and the
+# edge EMFs (3), and writes the later-stage base and the running sum (22, stage 0) or
+# q^{n+1} (11, stage 1): 64 B + 39.5 doubles on average.
+MIXED_ALG_BYTES_PER_CELL = {"flux": 80.0, "emf": 28.0, "update": 64.0 + 39.5 * 8}
 
 
 class ClockSampler:

@@ -101,13 +101,19 @@ typedef struct {
     double cfl;        /* Courant number for grmhd_compute_dt */
     double newton_tol; /* Newton residual tolerance, relative to the momentum terms of
                           f_i (Sec. 2.4); 0 -> 1e-13 (FP64) or 1e-10
-                          (mixed, whose FP32 fluxes err near 1e-7) */
+                          (mixed, whose FP32 fluxes err near 1e-7).  The FP64 path
+                          accepts a root by its FP64 residual; the mixed path by its
+                          double-word residual (~1e-14 of the momentum scale) and so
+                          needs newton_tol >= 1e-11 (else GRMHD_ERR_ARG) */
     int newton_kmax;   /* Newton iteration cap; 0 -> 50 */
     int precision;     /* GRMHD_PREC_FP64: every step in FP64.  GRMHD_PREC_MIXED: MC
-                          reconstruction, HLL fluxes and the edge EMF in FP32; the
-                          implicit solve / con2prim, sources, CT face update and stage
-                          combination stay FP64 (div B stays at FP64 round-off because
-                          each FP32 edge EMF is shared by the faces around it) */
+                          reconstruction, HLL fluxes and the edge EMF in FP32, the
+                          flux divergence in double-word arithmetic from the FP32
+                          fluxes; the implicit solve / con2prim (its root accepted by
+                          a double-word residual, its outputs FP64), sources, CT face
+                          update and stage combination stay FP64 (div B stays at FP64
+                          round-off because each FP32 edge EMF is shared by the faces
+                          around it) */
     double rho_atm;    /* atmosphere (not in the paper): a cell with D < 10 rho_atm, or
                           whose solve fails, is set to rest at (rho_atm, p_atm) with E
                           kept; 0 disables it (failures then keep their primitives) */
@@ -287,6 +293,50 @@ grmhd_status grmhd_set_launch_overlap(grmhd_ctx* ctx, int enable);
  * measures the denominator that FP64-bound kernels are compared with and changes no
  * device setting.  GRMHD_ERR_CUDA without a device. */
 grmhd_status grmhd_fp64_fma_rate(double* tflops, grmhd_stream_t stream);
+
+/* The library's own device arithmetic helpers, evaluated elementwise (testing only,
+ * not part of the paper's method), so that they can be held to their definitions.
+ * Per element, `in` holds 1, 2 or 3 doubles (the arity below, interleaved) and `out`
+ * receives 1 or 2; a double-word result is written as hi, lo (each a binary32 value
+ * widened exactly).
+ *   RSQRT_GE1   1/sqrt(x) for 1 <= x < 2^127 (FP32 estimate + one step of order 3)
+ *   RCP_POS     1/x for x > 0 of moderate size (likewise)
+ *   D2F         binary64 -> binary32 on the integer pipe (round half away from zero;
+ *               below the normal binary32 range a signed zero, above it infinity)
+ *   F2D         binary32 -> binary64 on the integer pipe of the binary32 nearest x
+ *               (exact; binary32 subnormals become a signed zero)
+ *   DW_SPLIT    the double-word hi + lo of x (2 out)
+ *   DW_ADD, DW_MUL   double-word sum / product of a, b (2 in, 2 out)
+ *   DW_RCP, DW_SQRT  double-word 1/x and sqrt(x) (1 in, 2 out)
+ *   QUARTER, TWICE   x/4 and 2x by an exponent move (exact in the normal range)
+ *   MINMOD3     minmod(a, b, c) decided on the bit patterns (3 in); MINMOD3_F32 the
+ *               same in binary32 of the nearest binary32 inputs
+ *   PROD_SIGN   sign of a b decided on the bit patterns: 1, -1, or 0 (2 in)
+ *   PPM_LIMIT   the limited parabola edges (aL, aR) of the cell a0 (3 in: a0, aL, aR;
+ *               2 out)
+ *   TESTS       finite(x) + 2 (x > 0, finite) + 4 (|x| < 1e10 by its high word)
+ * Asynchronous on `stream`.  GRMHD_ERR_ARG for an unknown op, n < 0, or NULL arrays
+ * with n > 0; n = 0 launches nothing. */
+typedef enum {
+    GRMHD_NUM_RSQRT_GE1 = 0,
+    GRMHD_NUM_RCP_POS = 1,
+    GRMHD_NUM_D2F = 2,
+    GRMHD_NUM_F2D = 3,
+    GRMHD_NUM_DW_SPLIT = 4,
+    GRMHD_NUM_DW_ADD = 5,
+    GRMHD_NUM_DW_MUL = 6,
+    GRMHD_NUM_DW_RCP = 7,
+    GRMHD_NUM_DW_SQRT = 8,
+    GRMHD_NUM_QUARTER = 9,
+    GRMHD_NUM_TWICE = 10,
+    GRMHD_NUM_MINMOD3 = 11,
+    GRMHD_NUM_MINMOD3_F32 = 12,
+    GRMHD_NUM_PROD_SIGN = 13,
+    GRMHD_NUM_PPM_LIMIT = 14,
+    GRMHD_NUM_TESTS = 15,
+    GRMHD_NUM_COUNT = 16
+} grmhd_numeric_op;
+grmhd_status grmhd_numerics_eval(int op, const double* in, double* out, long long n, grmhd_stream_t stream);
 
 /* Index-bounds violations (diagnostic build only; not part of the paper's method).
  * The library is also built as a checked copy (compiled with GRMHD_CHECK_BOUNDS, in

@@ -31,7 +31,7 @@ struct ProbStage {
     CP3 bfs;
     const double* psi;
     const double* alp;
-    FluxOut<double> F64[3];   // fluxes and edge EMFs: FP64 for both precisions
+    FluxOut<double> F64[3];   // fluxes: FP64, or FP32 in the same arrays (mixed precision)
     double* Eh64[3];
     double* fe64[3][3];   // [D][C]: edge EMFs written by the D-flux kernel (flat 1-D / 2-D)
     UpdateArgs upd;
@@ -74,20 +74,32 @@ constexpr int kMinItems = 128;   // smallest chunk of any candidate (scratch siz
 // batched kernels
 // ---------------------------------------------------------------------------
 
-template <bool M>
+template <bool M, bool ACC>
 __global__ void __launch_bounds__(256) kb_implicit(const ProbStage* __restrict__ P, int s, int stage,
                                                   const Chunk* __restrict__ ch, int nch)
 {
     for (int i = blockIdx.x; i < nch; i += gridDim.x) {
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
-        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) implicit_item<M>(ps.g, ps.imp, t);
+        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x)
+            implicit_item<M, false, ACC>(ps.g, ps.imp, t);
     }
 }
 
 template <typename T> __device__ __forceinline__ const PrimIn<T>& prim_of(const ProbStage& ps);
 template <> __device__ __forceinline__ const PrimIn<double>& prim_of<double>(const ProbStage& ps) { return ps.p64; }
 template <> __device__ __forceinline__ const PrimIn<float>& prim_of<float>(const ProbStage& ps) { return ps.p32; }
+// the D-fluxes in the stencil precision: the FP32 fluxes of the mixed path occupy the
+// first half of the same arrays
+template <typename T> __device__ __forceinline__ FluxOut<T> flux_of(const ProbStage& ps, int d);
+template <> __device__ __forceinline__ FluxOut<double> flux_of<double>(const ProbStage& ps, int d) { return ps.F64[d]; }
+template <> __device__ __forceinline__ FluxOut<float> flux_of<float>(const ProbStage& ps, int d)
+{
+    FluxOut<float> f;
+#pragma unroll
+    for (int v = 0; v < 8; v++) f.p[v] = reinterpret_cast<float*>(ps.F64[d].p[v]);
+    return f;
+}
 // item t: kMarch consecutive D-faces (flux_march_item)
 template <int D, bool M, typename T>
 __global__ void __launch_bounds__(256) kb_flux(const ProbStage* __restrict__ P, int s, int stage,
@@ -97,7 +109,8 @@ __global__ void __launch_bounds__(256) kb_flux(const ProbStage* __restrict__ P, 
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
         for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x)
-            flux_march_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, ps.F64[D], nullptr, ps.fe64[D], t);
+            flux_march_item<D, M, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp, flux_of<T>(ps, D), nullptr,
+                                     ps.fe64[D], t);
     }
 }
 
@@ -118,14 +131,14 @@ __global__ void __launch_bounds__(256) kb_emf(const ProbStage* __restrict__ P, i
     }
 }
 
-template <bool M>
+template <bool M, bool F32>
 __global__ void __launch_bounds__(256) kb_update(const ProbStage* __restrict__ P, int s, int stage,
                                                 const Chunk* __restrict__ ch, int nch)
 {
     for (int i = blockIdx.x; i < nch; i += gridDim.x) {
         const Chunk k = ch[i];
         const ProbStage& ps = P[k.prob * s + stage];
-        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) update_item<M>(ps.g, ps.upd, t);
+        for (long long t = k.begin + threadIdx.x; t < k.end; t += blockDim.x) update_item<M, F32>(ps.g, ps.upd, t);
     }
 }
 
@@ -248,21 +261,21 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2)) kb_persistent(c
             if (!grid_barrier(bs, nb, limit_ns)) return;
         }
         for (int stage = 0; stage < s; stage++) {
-            PERSIST_ITEMS(WL_IMP, 0, implicit_item<false>(ps.g, ps.imp, t))
-            PERSIST_ITEMS(WL_IMP, 1, implicit_item<true>(ps.g, ps.imp, t))
+            PERSIST_ITEMS(WL_IMP, 0, (implicit_item<false, false, sizeof(T) == 4>(ps.g, ps.imp, t)))
+            PERSIST_ITEMS(WL_IMP, 1, (implicit_item<true, false, sizeof(T) == 4>(ps.g, ps.imp, t)))
             if (!grid_barrier(bs, nb, limit_ns)) return;
             PERSIST_ITEMS(WL_FLUX + 0, 0, (flux_march_item<0, false, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
-                                                                       ps.F64[0], nullptr, ps.fe64[0], t)))
+                                                                       flux_of<T>(ps, 0), nullptr, ps.fe64[0], t)))
             PERSIST_ITEMS(WL_FLUX + 0, 1, (flux_march_item<0, true, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
-                                                                      ps.F64[0], nullptr, ps.fe64[0], t)))
+                                                                      flux_of<T>(ps, 0), nullptr, ps.fe64[0], t)))
             PERSIST_ITEMS(WL_FLUX + 1, 0, (flux_march_item<1, false, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
-                                                                       ps.F64[1], nullptr, ps.fe64[1], t)))
+                                                                       flux_of<T>(ps, 1), nullptr, ps.fe64[1], t)))
             PERSIST_ITEMS(WL_FLUX + 1, 1, (flux_march_item<1, true, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
-                                                                      ps.F64[1], nullptr, ps.fe64[1], t)))
+                                                                      flux_of<T>(ps, 1), nullptr, ps.fe64[1], t)))
             PERSIST_ITEMS(WL_FLUX + 2, 0, (flux_march_item<2, false, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
-                                                                       ps.F64[2], nullptr, ps.fe64[2], t)))
+                                                                       flux_of<T>(ps, 2), nullptr, ps.fe64[2], t)))
             PERSIST_ITEMS(WL_FLUX + 2, 1, (flux_march_item<2, true, T>(ps.g, prim_of<T>(ps), ps.bfs, ps.psi, ps.alp,
-                                                                      ps.F64[2], nullptr, ps.fe64[2], t)))
+                                                                      flux_of<T>(ps, 2), nullptr, ps.fe64[2], t)))
             PERSIST_ITEMS(WL_EMF + 0, 0, (emf_any_item<0, false, T>(ps, t)))
             PERSIST_ITEMS(WL_EMF + 0, 1, (emf_any_item<0, true, T>(ps, t)))
             PERSIST_ITEMS(WL_EMF + 1, 0, (emf_any_item<1, false, T>(ps, t)))
@@ -270,8 +283,8 @@ __global__ void __launch_bounds__(128, (sizeof(T) == 4 ? 4 : 2)) kb_persistent(c
             PERSIST_ITEMS(WL_EMF + 2, 0, (emf_any_item<2, false, T>(ps, t)))
             PERSIST_ITEMS(WL_EMF + 2, 1, (emf_any_item<2, true, T>(ps, t)))
             if (!grid_barrier(bs, nb, limit_ns)) return;
-            PERSIST_ITEMS(WL_UPD, 0, update_item<false>(ps.g, ps.upd, t))
-            PERSIST_ITEMS(WL_UPD, 1, update_item<true>(ps.g, ps.upd, t))
+            PERSIST_ITEMS(WL_UPD, 0, (update_item<false, sizeof(T) == 4>(ps.g, ps.upd, t)))
+            PERSIST_ITEMS(WL_UPD, 1, (update_item<true, sizeof(T) == 4>(ps.g, ps.upd, t)))
             if (step + 1 < nsteps || stage + 1 < s)
                 if (!grid_barrier(bs, nb, limit_ns)) return;
         }
@@ -382,6 +395,7 @@ void fill_desc(grmhd_batch* b, int p, double dt)
         for (int d = 0; d < 3; d++)
             for (int v = 0; v < 8; v++)
                 ps.upd.F[d][v] = !ps.g.act[d] ? nullptr : ps.F64[d].p[v];
+        ps.upd.f32 = ctx_mixed(c) ? 1 : 0;
         for (int k = 0; k < 3; k++) ps.upd.Eh[k] = ps.Eh64[k];
         for (int v = 0; v < 8; v++) ps.upd.prim[v] = ps.imp.prim.p[v];
         for (int k = 0; k < 3; k++) ps.upd.bf[k] = ps.bfs.p[k];
@@ -408,8 +422,13 @@ cudaError_t launch_stage(grmhd_batch* b, int stage, cudaStream_t st, unsigned ma
         if (!(mask >> kind & 1u) || !b->cnt[kind][m]) continue;
         const Chunk* ch = b->d_chunks + b->off[kind][m];
         const int nch = b->cnt[kind][m], th = b->cfg[kind].threads, gr = grid_of(b, kind, m);
-        if (m) kb_implicit<true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
-        else kb_implicit<false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        if (b->mixed) {
+            if (m) kb_implicit<true, true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+            else kb_implicit<false, true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        } else {
+            if (m) kb_implicit<true, false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+            else kb_implicit<false, false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        }
     }
     for (int d = 0; d < 3; d++)
         for (int m = 0; m < 2; m++) {
@@ -444,8 +463,13 @@ cudaError_t launch_stage(grmhd_batch* b, int stage, cudaStream_t st, unsigned ma
         if (!(mask >> kind & 1u) || !b->cnt[kind][m]) continue;
         const Chunk* ch = b->d_chunks + b->off[kind][m];
         const int nch = b->cnt[kind][m], th = b->cfg[kind].threads, gr = grid_of(b, kind, m);
-        if (m) kb_update<true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
-        else kb_update<false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        if (b->mixed) {
+            if (m) kb_update<true, true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+            else kb_update<false, true><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        } else {
+            if (m) kb_update<true, false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+            else kb_update<false, false><<<gr, th, 0, st>>>(P, s, stage, ch, nch);
+        }
     }
     return cudaGetLastError();
 }

@@ -278,6 +278,7 @@ ImpArgs imp_args(grmhd_ctx* c, CP8 qb, CP3 bf, double a_dt, P8 prim, P3 R, P3 qE
     a.kmax = c->par.newton_kmax;
     a.tol = c->par.newton_tol;
     a.tolf = (float)c->par.newton_tol;
+    a.dwacc = c->mixed ? 1 : 0;
     a.stiff = a_dt > 0.0;
     a.rho_atm = c->par.rho_atm;
     a.p_atm = c->par.p_atm;
@@ -340,9 +341,9 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         for (int k = 0; k < 3; k++)
             if (fused_emf_dir(c, k) == d) eh64[k] = c->Eh[k];
         if (c->mixed) {
-            // FP32 arithmetic, FP64 results (widened once when stored)
-            FluxOut<double> fo;
-            for (int v = 0; v < 8; v++) fo.p[v] = c->F[d][v];
+            // FP32 arithmetic and FP32 fluxes (in the first half of each flux array)
+            FluxOut<float> fo;
+            for (int v = 0; v < 8; v++) fo.p[v] = reinterpret_cast<float*>(c->F[d][v]);
             e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm, eh64);
         } else {
             e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
@@ -364,6 +365,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     }
     for (int d = 0; d < 3; d++)
         for (int v = 0; v < 8; v++) a.F[d][v] = !g.act[d] ? nullptr : c->F[d][v];
+    a.f32 = c->mixed ? 1 : 0;
     for (int k = 0; k < 3; k++) a.Eh[k] = c->Eh[k];
     for (int v = 0; v < 8; v++) a.prim[v] = prim.p[v];
     for (int k = 0; k < 3; k++) a.bf[k] = bfs.p[k];
@@ -498,6 +500,10 @@ grmhd_status grmhd_create(const grmhd_grid* grid, const grmhd_params* par, const
         return fail(GRMHD_ERR_ARG, "precision must be GRMHD_PREC_FP64 or GRMHD_PREC_MIXED");
     if (par->divb != GRMHD_DIVB_CT && par->divb != GRMHD_DIVB_GLM)
         return fail(GRMHD_ERR_ARG, "divb must be GRMHD_DIVB_CT or GRMHD_DIVB_GLM");
+    // the mixed path accepts the root by its double-word residual (~1e-14 of the
+    // momentum scale), which bounds the exact residual for tolerances from 1e-11 up
+    if (par->precision == GRMHD_PREC_MIXED && par->newton_tol > 0.0 && par->newton_tol < 1e-11)
+        return fail(GRMHD_ERR_ARG, "mixed precision needs newton_tol >= 1e-11 (or 0 for the default 1e-10)");
     if (par->divb == GRMHD_DIVB_GLM && par->precision != GRMHD_PREC_FP64)
         return fail(GRMHD_ERR_ARG, "GLM cleaning runs in FP64 only");
     if (par->divb == GRMHD_DIVB_GLM && !(par->kappa_b >= 0.0))

@@ -63,6 +63,7 @@ struct Dims {
     FastDiv dvp[2];        // division by n[d] + 1 (1 where inactive): face and edge indices
     int mk[3];             // march length along d (faces or edges per thread)
     FastDiv dq[3];         // division by the chunks per line along d, (n[d] + mk[d]) / mk[d]
+    float hix[3][2];       // 1/(2 dx) as a double-word hi + lo (the FP32 flux divergence)
 };
 
 // set the march length along d (and its chunk divisor) of a launch's copy of the grid
@@ -72,14 +73,20 @@ inline void set_march(Dims& g, int d, int K)
     g.dq[d] = make_fastdiv((unsigned)((g.n[d] + K) / K));
 }
 
-// the divisors of a grid whose extents n, act are set (march length 1 everywhere)
+// the divisors of a grid whose extents n, act and idx are set (march length 1
+// everywhere), and the double-word split of 1/(2 dx)
 inline void set_divisors(Dims& g)
 {
     for (int d = 0; d < 2; d++) {
         g.dv[d] = make_fastdiv((unsigned)g.n[d]);
         g.dvp[d] = make_fastdiv((unsigned)(g.act[d] ? g.n[d] + 1 : 1));
     }
-    for (int d = 0; d < 3; d++) set_march(g, d, 1);
+    for (int d = 0; d < 3; d++) {
+        set_march(g, d, 1);
+        const double h = 0.5 * g.idx[d];
+        g.hix[d][0] = (float)h;
+        g.hix[d][1] = (float)(h - (double)g.hix[d][0]);
+    }
 }
 
 // (i0, i1, i2) of index t over an x-fastest box whose first two extents have the
@@ -307,7 +314,9 @@ __device__ __forceinline__ void mc_face(T a0, T a1, T a2, T a3, T& L, T& R)
     R = a2 - minmod3<T>(d0, scale_pow2<T, -2>(a3 - a1), dp);
 }
 
-// 1/sqrt(x) through CUDA's reciprocal square root, in the precision of x
+// 1/sqrt(x) through CUDA's reciprocal square root, in the precision of x (for the
+// stencil kernels' 1 + u^2 the FP64 form counts as many FP64 instructions as
+// rsqrt_ge1 below)
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 
@@ -552,19 +561,20 @@ __device__ __forceinline__ bool mag_below_int(double x, unsigned bound_hi)
     return ((unsigned)__double2hiint(x) & 0x7fffffffu) < bound_hi;
 }
 
-// 1/sqrt(x) for x >= 1 and 1/x for x > 0 in FP64 from an FP32 estimate: rsqrt takes
-// two Newton steps y + y (1/2 - x y^2 / 2), each squaring the relative error (2^-22
-// -> 2^-43 -> 2^-86); the reciprocal takes one step of order three, y (1 + e + e^2)
-// with e = 1 - x y (2^-22 -> 2^-66).  Both end within an ulp or so of the exact
-// value, without the special-value branches of the library routines (their callers
-// only pass moderate positive values; the FP64 residual decides the root either way).
+// 1/sqrt(x) for 1 <= x < 2^127 and 1/x for x > 0 in FP64 from an FP32 estimate y,
+// each with one correction step of order three (the truncated binomial series).
+// rsqrt: e = 1 - x y^2, 1/sqrt(x) = y (1 - e)^(-1/2) = y (1 + e/2 + 3e^2/8 + ...);
+// reciprocal: e = 1 - x y, 1/x = y / (1 - e) = y (1 + e + e^2 + ...).  The estimate
+// is good to about 2^-21 (rsqrtf / __fdividef and the rounding of x to FP32), so the
+// dropped terms are near 2^-63 and the result is within an ulp or so of the exact
+// value: 5 FP64 instructions for rsqrt, 3 for the reciprocal, and none of the
+// special-value branches of the library routines (their callers pass moderate
+// positive values only).
 __device__ __forceinline__ double rsqrt_ge1(double x)
 {
-    double y = f2d_int(rsqrtf(d2f_int(x)));
-    const double h = 0.5 * x;
-    y = fma(y, fma(-h, y * y, 0.5), y);
-    y = fma(y, fma(-h, y * y, 0.5), y);
-    return y;
+    const double y = f2d_int(rsqrtf(d2f_int(x)));
+    const double e = fma(-x, y * y, 1.0);
+    return fma(y, e * fma(0.375, e, 0.5), y);
 }
 
 __device__ __forceinline__ double rcp_pos(double x)
@@ -1053,7 +1063,14 @@ struct EvalDW {
     float f[3], wt, base, M;
 };
 
-__device__ __forceinline__ void evaluate_dw(const CellIn& c, const dw* u, EvalDW& o)
+// W, E(u) and w_t of the last double-word evaluation, kept when the residual there
+// accepts the root (double-word acceptance)
+struct DwRoot {
+    dw W, wt, E[3];
+};
+
+template <bool KEEP = false>
+__device__ __forceinline__ void evaluate_dw(const CellIn& c, const dw* u, EvalDW& o, DwRoot* r = nullptr)
 {
     dw S[3], B[3], E[3];
 #pragma unroll
@@ -1094,6 +1111,12 @@ __device__ __forceinline__ void evaluate_dw(const CellIn& c, const dw* u, EvalDW
     o.wt = wt.hi;
     o.base = base.hi;
     o.M = M;
+    if (KEEP) {
+        r->W = W;
+        r->wt = wt;
+#pragma unroll
+        for (int i = 0; i < 3; i++) r->E[i] = E[i];
+    }
 }
 
 // Newton corrections from the double-word residual with the FP32 Jacobian (the
@@ -1104,10 +1127,20 @@ __device__ __forceinline__ void evaluate_dw(const CellIn& c, const dw* u, EvalDW
 // is already below the tolerance and the FP64 residual can accept it directly.  Steps
 // are taken only when finite and within the step bound; u (FP64) receives the result
 // only if it is finite.
+//
+// ACC (double-word acceptance, for tolerances of 1e-11 and above): the double-word
+// residual itself accepts the root.  It is accurate to ~1e-14 of the momentum scale,
+// a few hundred times below tol M / 4 there, so |f| <= tol M / 4 in double-word
+// arithmetic bounds the exact residual by the tolerance.  The small-step exit is then
+// skipped (the next evaluation decides), and on acceptance u, W, 1/W, w_t and E(u)
+// are written to e from the double-word values; the return value says whether that
+// happened (else the FP64 residual decides, as without ACC).
 constexpr int kDwEvals = 4;   // most double-word residual evaluations per solve
 constexpr unsigned kHi1e10 = 0x4202A05Fu;   // high word of 1e10 (the bound on W)
 
-__device__ __forceinline__ void newton_refine_dw(const CellIn& c, const CellF& cf, double* u, float tol, int nit)
+template <bool ACC>
+__device__ __forceinline__ bool newton_refine_dw(const CellIn& c, const CellF& cf, double* u, float tol, int nit,
+                                                 Eval* e)
 {
     dw ud[3];
 #pragma unroll
@@ -1115,10 +1148,25 @@ __device__ __forceinline__ void newton_refine_dw(const CellIn& c, const CellF& c
     bool moved = false;
     for (int k = 0; k < nit; k++) {
         EvalDW ed;
-        evaluate_dw(c, ud, ed);
+        DwRoot rt;
+        evaluate_dw<ACC>(c, ud, ed, &rt);
         if (!(ed.M > 0.0f) || !(ed.M < 1e30f) || !(ed.wt > 0.0f)) break;
         const float fm = fmaxf(fabsf(ed.f[0]), fmaxf(fabsf(ed.f[1]), fabsf(ed.f[2])));
-        if (fm <= 0.25f * tol * ed.M) break;   // also false for NaN
+        if (fm <= 0.25f * tol * ed.M) {   // also false for NaN
+            if (ACC && rt.W.hi < 1e10f) {
+                const dw iW = dw_rcp(rt.W);
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    u[i] = dw_to_double(ud[i]);
+                    e->E[i] = dw_to_double(rt.E[i]);
+                }
+                e->W = dw_to_double(rt.W);
+                e->iW = dw_to_double(iW);
+                e->wt = dw_to_double(rt.wt);
+                return true;
+            }
+            break;
+        }
         const float uf[3] = {ud[0].hi, ud[1].hi, ud[2].hi};
         const float uu = uf[0] * uf[0] + uf[1] * uf[1] + uf[2] * uf[2];
         const float Wf = sqrtf(1.0f + uu), iWf = 1.0f / Wf;
@@ -1134,7 +1182,7 @@ __device__ __forceinline__ void newton_refine_dw(const CellIn& c, const CellF& c
 #pragma unroll
         for (int i = 0; i < 3; i++) ud[i] = dw_add_f(ud[i], dx[i]);
         moved = true;
-        if (nx2 <= 0.01f * tol * fmaxf(1.0f, uu)) break;
+        if (!ACC && nx2 <= 0.01f * tol * fmaxf(1.0f, uu)) break;
     }
     if (moved) {
         const double v[3] = {dw_to_double(ud[0]), dw_to_double(ud[1]), dw_to_double(ud[2])};
@@ -1144,13 +1192,16 @@ __device__ __forceinline__ void newton_refine_dw(const CellIn& c, const CellF& c
             u[2] = v[2];
         }
     }
+    return false;
 }
 
 // Globally convergent Newton (backtracking on |f|^2 with the Armijo condition and a
 // bounded step).  u: in = initial guess, out = solution.  Converged when |f| is at
 // `tol` against its own momentum scale M, or when the step no longer moves u.
 // Returns iterations, or -1.  uin: the FP32 value of the start when the caller has it
-// (has_uin; the start is then exactly that value).
+// (has_uin; the start is then exactly that value).  ACC: double-word acceptance (the
+// mixed-precision path, whose tolerance is at least 1e-11; see newton_refine_dw).
+template <bool ACC = false>
 __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e, int kmax, double tol, float tolf,
                                             bool has_uin, const F3& uin)
 {
@@ -1162,8 +1213,9 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
     bool has1 = has_uin;
     if (c.emode != 2) {
         // Newton corrections from the double-word residual; the FP64 residual below
-        // then accepts the root, or the FP64 iteration continues from there
-        newton_refine_dw(c, cf, u, tolf, kDwEvals);
+        // then accepts the root (or, with ACC, the double-word one already did), or the
+        // FP64 iteration continues from there
+        if (newton_refine_dw<ACC>(c, cf, u, tolf, kDwEvals, &e)) return 0;
         has1 = false;
     } else if (tol < 1e-11) {
         F3 un;

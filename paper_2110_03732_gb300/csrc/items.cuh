@@ -14,8 +14,9 @@ namespace grmhd {
 // ---------------------------------------------------------------------------
 
 // CC: the magnetic field is cell-centred (a.bf holds cell q_B, GLM variant) instead of
-// staggered on faces
-template <bool M, bool CC = false>
+// staggered on faces.  ACC: the mixed-precision path, whose double-word residual
+// accepts the root (newton_refine_dw)
+template <bool M, bool CC = false, bool ACC = false>
 __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, long long t)
 {
     // flat metric: alpha = psi = 1 known at compile time
@@ -84,10 +85,10 @@ __device__ __forceinline__ void implicit_item(const Dims& g, const ImpArgs& a, l
             if (!mag_below_int(u[i], kHi1e30)) fin = false;   // also NaN
         }
         if (!fin) u[0] = u[1] = u[2] = 0.0;
-        int it = newton_solve(ci, u, e, kmax, tol, a.tolf, hist && fin, ust);
+        int it = newton_solve<ACC>(ci, u, e, kmax, tol, a.tolf, hist && fin, ust);
         if (it < 0 && fin) {
             u[0] = u[1] = u[2] = 0.0;
-            it = newton_solve(ci, u, e, kmax, tol, a.tolf, false, ust);
+            it = newton_solve<ACC>(ci, u, e, kmax, tol, a.tolf, false, ust);
         }
         if (it < 0) {
             atomicAdd(nfail, 1ull);
@@ -187,7 +188,7 @@ __device__ __forceinline__ T uct_edge(T hLL, T hLR, T hRL, T hRR, T ca, T cb, T 
 template <int D, bool M, typename T>
 __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const double* psi_in, const double* alp_in,
                                           const int* c, long long rm, long long r0, T* prL, T* prR, T* BL, T* BR,
-                                          const FluxOut<double>& F, double* const* vbar, double* const* Eh = nullptr)
+                                          const FluxOut<T>& F, double* const* vbar, double* const* Eh = nullptr)
 {
     const double* __restrict__ psi = M ? psi_in : nullptr;
     const double* __restrict__ alp = M ? alp_in : nullptr;
@@ -234,7 +235,7 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
 #pragma unroll
     for (int v = 0; v < 8; v++) {
         const T hv = v == 0 || v == 4 ? h4 : (v < 4 ? h6 : h2);
-        F.p[v][o] = to_f64((gL[v] + gR[v]) * hv);
+        F.p[v][o] = (gL[v] + gR[v]) * hv;
     }
     if (vbar && vbar[0]) {
         // App. A steps (i)-(ii): vhat^j = alpha v^j (beta = 0) of the L and R states,
@@ -341,7 +342,7 @@ __device__ __forceinline__ void march_coords(const Dims& g, long long t, int* c,
 // themselves run along x).
 template <int D, bool M, typename T, bool P = false>
 __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& prim, const CP3& bf,
-                                                const double* psi_in, const double* alp_in, const FluxOut<double>& F,
+                                                const double* psi_in, const double* alp_in, const FluxOut<T>& F,
                                                 double* const* vbar, double* const* Eh, long long t)
 {
     using Rec = LineRec<T, P>;
@@ -824,7 +825,12 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
     }
 }
 
-template <bool M>
+// F32: the fluxes are FP32 arrays (mixed precision).  Each difference of two FP32
+// values is then exact as a double-word, and the divergence sum_d (F[o + e_d] - F[o])
+// / (2 dx_d) is formed in double-word arithmetic on the FP32 pipe (about 2^-46 of its
+// terms, far below the FP32 fluxes' own error) and widened by one FP64 add, in place
+// of two FP64 instructions per flux.
+template <bool M, bool F32 = false>
 __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, long long t)
 {
     // flat metric: alpha = psi = 1 known at compile time
@@ -842,17 +848,39 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
     const long long o = lin(g, c[0], c[1], c[2]);
     if (interior) {
         double Lc[8];
+        if (F32) {
+            dw acc[8];
+            bool first = true;
 #pragma unroll
-        for (int v = 0; v < 8; v++) Lc[v] = 0.0;
+            for (int v = 0; v < 8; v++) acc[v] = dw_make(0.0f);
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            if (!g.act[d]) continue;
-            const long long o1 = chk(g, o + g.st[d]);
-            const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
+            for (int d = 0; d < 3; d++) {
+                if (!g.act[d]) continue;
+                const long long o1 = chk(g, o + g.st[d]);
+                const dw h = {g.hix[d][0], g.hix[d][1]};   // F holds twice the flux
 #pragma unroll
-            for (int v = 0; v < 8; v++) {
-                const double* __restrict__ Fv = a.F[d][v];
-                Lc[v] -= (Fv[o1] - Fv[o]) * hidx;
+                for (int v = 0; v < 8; v++) {
+                    const float* __restrict__ Fv = reinterpret_cast<const float*>(a.F[d][v]);
+                    const dw term = dw_mul(two_sum(Fv[o1], -Fv[o]), h);
+                    acc[v] = first ? term : dw_add(acc[v], term);
+                }
+                first = false;
+            }
+#pragma unroll
+            for (int v = 0; v < 8; v++) Lc[v] = -dw_to_double(acc[v]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < 8; v++) Lc[v] = 0.0;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                if (!g.act[d]) continue;
+                const long long o1 = chk(g, o + g.st[d]);
+                const double hidx = 0.5 * g.idx[d];   // F holds twice the flux
+#pragma unroll
+                for (int v = 0; v < 8; v++) {
+                    const double* __restrict__ Fv = a.F[d][v];
+                    Lc[v] -= (Fv[o1] - Fv[o]) * hidx;
+                }
             }
         }
         cell_sources<false>(g, a.prim, a.bf, psi, alp, c, o, Lc);

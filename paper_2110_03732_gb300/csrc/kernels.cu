@@ -27,14 +27,14 @@ thread_local bool launch_overlap = false;
 // implicit step
 // ---------------------------------------------------------------------------
 
-template <bool M>
+template <bool M, bool ACC>
 __global__ void __launch_bounds__(128, 4) k_implicit(Dims g, ImpArgs a)
 {
     grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        implicit_item<M>(g, a, t);
+        implicit_item<M, false, ACC>(g, a, t);
 }
 
 // the same solve with cell-centred q_B (GLM variant, Sec. 3.1)
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) k_emf_ideal(Dims g, EmfArgs<double> a, Vb
 // update: cell-centred L (flux divergence + non-stiff sources) and face L_B (CT)
 // ---------------------------------------------------------------------------
 
-template <bool M>
+template <bool M, bool F32>
 __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
 {
     grid_dep_sync();
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
     for (int d = 0; d < 3; d++) tot *= g.act[d] ? g.n[d] + 1 : 1;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
-        update_item<M>(g, a, t);
+        update_item<M, F32>(g, a, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -398,7 +398,9 @@ static int grid_for(long long work, int threads, int nsm)
 cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st)
 {
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
-    launch_k(a.psi || a.alp ? k_implicit<true> : k_implicit<false>, grid_for(work, 128, nsm), 128, st, g, a);
+    const bool m = a.psi || a.alp;
+    if (a.dwacc) launch_k(m ? k_implicit<true, true> : k_implicit<false, true>, grid_for(work, 128, nsm), 128, st, g, a);
+    else launch_k(m ? k_implicit<true, false> : k_implicit<false, false>, grid_for(work, 128, nsm), 128, st, g, a);
     return cudaGetLastError();
 }
 
@@ -425,6 +427,7 @@ cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, 
 cudaError_t launch_implicit_cc(const Dims& g, const ImpArgs& a, int nsm, cudaStream_t st)
 {
     const long long work = (long long)g.n[0] * g.n[1] * g.n[2];
+    // GLM contexts are FP64 only: the FP64 residual accepts the root
     launch_k(a.psi || a.alp ? k_implicit_cc<true> : k_implicit_cc<false>, grid_for(work, 128, nsm), 128, st, g,
              a);
     return cudaGetLastError();
@@ -542,7 +545,7 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
 }
 
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<double> F, int nsm, cudaStream_t st, bool ppm, double* const* Eh)
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm, double* const* Eh)
 {
     FluxArgs<float> a;
     for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !(psi || alp) ? Eh[k] : nullptr;
@@ -610,7 +613,9 @@ cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStrea
     long long work = 1;
     for (int d = 0; d < 3; d++) work *= g.act[d] ? g.n[d] + 1 : 1;
     const int b = grid_for(work, 128, nsm);
-    launch_k(a.psi || a.alp ? k_update<true> : k_update<false>, b, 128, st, g, a);
+    const bool m = a.psi || a.alp;
+    if (a.f32) launch_k(m ? k_update<true, true> : k_update<false, true>, b, 128, st, g, a);
+    else launch_k(m ? k_update<true, false> : k_update<false, false>, b, 128, st, g, a);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,8 @@ struct ImpArgs {
     int kmax;
     double tol, rho_atm, p_atm;
     float tolf;             // tol in FP32 (for the double-word corrections)
+    int dwacc;              // mixed precision (tol >= 1e-11): the double-word residual
+                            // accepts the root (the ACC instantiations)
     int stiff;              // a_dt > 0 (else E is held fixed)
     int atm;                // rho_atm > 0 (an atmosphere is set)
     double d_atm;           // 10 rho_atm: cells with D below it are atmosphere
@@ -55,7 +57,7 @@ struct FluxArgs {
     CP3 bf;
     const double* psi;
     const double* alp;
-    FluxOut<double> F;
+    FluxOut<T> F;           // twice the face fluxes (FP32 values in mixed precision)
     double* vbar[2];        // ideal-limit EMF: transverse transport velocities (or NULL)
     double* Eh[3];          // edge EMFs written by the flux kernel (flat 1-D / 2-D grids,
                             // see face_flux), NULL for those the EMF kernels compute
@@ -79,7 +81,8 @@ struct UpdateArgs {
     double At[4][4], A[4][4], wt[4], w[4];
     double cL[4], cR[4];    // dt At[k][stage], dt A[k][stage]: this stage's terms in base k
     double cwL, cwR;        // dt wt[stage], dt w[stage]: its terms in the final combination
-    const double* F[3][8];  // twice the face fluxes per active direction
+    const double* F[3][8];  // twice the face fluxes per active direction (float arrays when f32)
+    int f32;                // the fluxes are FP32 (the mixed-precision flux kernels)
     const double* Eh[3];    // edge EMFs
     const double* prim[8];  // stage primitives (padded)
     const double* bf[3];    // stage face fields
@@ -98,7 +101,7 @@ cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream
 cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, const double* u3, const double* psi,
                              P3f hs, P3f hd, int nsm, cudaStream_t st);
 cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<double> F, int nsm, cudaStream_t st, bool ppm = false,
+                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false,
                           double* const* Eh = nullptr);
 cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
                          const double* alp, double* Eh, int nsm, cudaStream_t st, bool ppm = false);

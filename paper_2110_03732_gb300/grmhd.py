@@ -18,6 +18,7 @@ _lib = None
 
 GRMHD_OK = 0
 GRMHD_WARN_C2P_FAILED = 1
+GRMHD_ERR_ARG = -1
 GRMHD_ERR_TIMEOUT = -4
 BC = {"periodic": 0, "outflow": 1, "fixed": 2}
 
@@ -102,6 +103,7 @@ def lib():
     L.grmhd_load_start.argtypes = [vp, vp, C.c_size_t, vp]
     L.grmhd_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), vp]
     L.grmhd_bounds_violations.argtypes = [C.POINTER(C.c_longlong), C.c_int]
+    L.grmhd_numerics_eval.argtypes = [C.c_int, vp, vp, C.c_longlong, vp]
     L.grmhd_last_error.restype = C.c_char_p
     for name in ("grmhd_tableau_ssp2", "grmhd_scratch_bytes", "grmhd_create", "grmhd_destroy", "grmhd_bind",
                  "grmhd_set_metric", "grmhd_set_eta", "grmhd_set_dynamo", "grmhd_init_from_prims", "grmhd_compute_dt", "grmhd_stage",
@@ -111,7 +113,7 @@ def lib():
                  "grmhd_batch_destroy", "grmhd_explicit_L_glm", "grmhd_bind_phi", "grmhd_clean_scratch_bytes",
                  "grmhd_clean_divb", "grmhd_start_bytes", "grmhd_save_start", "grmhd_load_start",
                  "grmhd_fp64_fma_rate", "grmhd_bounds_violations", "grmhd_batch_step_persistent",
-                 "grmhd_batch_set_wait_limit", "grmhd_batch_persistent_status"):
+                 "grmhd_batch_set_wait_limit", "grmhd_batch_persistent_status", "grmhd_numerics_eval"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -163,6 +165,30 @@ def fp64_fma_rate(stream=None):
     r = C.c_double(0.0)
     check(lib().grmhd_fp64_fma_rate(C.byref(r), _stream(stream)), "fp64_fma_rate")
     return r.value
+
+
+# ops of grmhd_numerics_eval: (value, inputs per element, outputs per element)
+NUMERIC_OPS = {
+    "rsqrt_ge1": (0, 1, 1), "rcp_pos": (1, 1, 1), "d2f": (2, 1, 1), "f2d": (3, 1, 1),
+    "dw_split": (4, 1, 2), "dw_add": (5, 2, 2), "dw_mul": (6, 2, 2), "dw_rcp": (7, 1, 2),
+    "dw_sqrt": (8, 1, 2), "quarter": (9, 1, 1), "twice": (10, 1, 1), "minmod3": (11, 3, 1),
+    "minmod3_f32": (12, 3, 1), "prod_sign": (13, 2, 1), "ppm_limit": (14, 3, 2), "tests": (15, 1, 1),
+}
+
+
+def numerics_eval(name, x, stream=None):
+    """The library's device arithmetic helper `name` (NUMERIC_OPS) on the float64 CUDA
+    tensor x of shape (n,) or (n, arity); returns (n,) or (n, 2) (testing only)."""
+    import torch
+    op, ar, no = NUMERIC_OPS[name]
+    x = x.to(torch.float64).contiguous()
+    n = x.shape[0]
+    if x.numel() != n * ar:
+        raise GrmhdError(f"numerics_eval {name}: expected {ar} inputs per element")
+    out = torch.empty((n, no) if no > 1 else (n,), dtype=torch.float64, device=x.device)
+    check(lib().grmhd_numerics_eval(op, x.data_ptr() if n else None, out.data_ptr() if n else None, n,
+                                    _stream(stream)), "numerics_eval")
+    return out
 
 
 def ssp2():

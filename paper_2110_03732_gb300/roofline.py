@@ -7,19 +7,24 @@ live CUDA-event launch times.  A count taken on other kernel sources than the on
 built is reported as stale (``sources_digest`` differs), and its traffic is then not
 reported.
 
-Refresh (one GPU, the 512^2 case of bench.py, one launch list per precision):
+Refresh (one GPU, the 512^2 case of bench.py; one capture per precision and kernel
+kind, each of one kernel name pattern and two launches, taken after the three warm-up
+steps have run the same kernels):
 
     python bench.py --case ot --case-n 512 --steps 1 --warmup 3 > gpurun_out/plain.log 2>&1 &&
-    ncu --metrics <METRICS> --clock-control none --print-units base \\
-        -k "regex:^(k_implicit|k_flux_march|k_emf|k_update)" -s 30 -c 10 --csv \\
-        --log-file gpurun_out/counts_fp64.csv \\
-        python bench.py --case ot --case-n 512 --steps 1 --warmup 3
-    (the same with --case ot_mixed into counts_mixed.csv)
-    python -m paper_2110_03732_gb300.roofline gpurun_out/counts_fp64.csv gpurun_out/counts_mixed.csv \\
-        > profiles/roofline_counts.json
+    for k in k_implicit k_flux_march k_emf_march k_update; do
+      ncu --metrics <METRICS> --clock-control none --print-units base \
+          -k "regex:^$k" -s <S> -c 2 --csv --log-file gpurun_out/counts_fp64_$k.csv \
+          python bench.py --case ot --case-n 512 --steps 1 --warmup 3 || break
+    done
+    (the same with --case ot_mixed into counts_mixed_$k.csv)
+    python -m paper_2110_03732_gb300.roofline --fp64 gpurun_out/counts_fp64_*.csv \
+        --mixed gpurun_out/counts_mixed_*.csv > profiles/roofline_counts.json
 
-with <METRICS> the comma-joined ``METRICS`` below.  The three warm-up steps are 30
-launches of these kernels; the 10 captured are the two stages of the next step.
+with <METRICS> the comma-joined ``METRICS`` below and <S> the launches of that kernel
+pattern in the warm-up steps (2 per step for the implicit solve, the edge EMF and the
+update, 4 for the two flux directions): the two captured launches are the first of the
+next step (for the flux, its two directions of the first stage).
 """
 from __future__ import annotations
 
@@ -86,19 +91,20 @@ def _num(x, unit=""):
     return float(str(x).replace(",", "")) * _SCALE.get(unit, 1.0)
 
 
-def counts_from_ncu_csv(path: str, cells: int):
+def counts_from_ncu_csv(paths, cells: int):
     """Per kernel kind: launches, and per launch the mean duration, FP64 flop
     (2 DFMA + DADD + DMUL), FP64-pipe instructions (thread level), FP64-pipe busy
-    fraction and DRAM bytes; per-kernel-name rows kept beside them."""
+    fraction and DRAM bytes; per-kernel-name rows kept beside them.  ``paths``: one
+    ncu CSV or a list of them (one capture per kernel kind)."""
     rows = {}
-    with open(path) as fh:
-        lines = [ln for ln in fh if ln.startswith('"')]
-    rd = csv.DictReader(lines)
-    for r in rd:
-        key = (r["ID"], r["Kernel Name"])
-        rows.setdefault(key, {})[r["Metric Name"]] = _num(r["Metric Value"], r.get("Metric Unit", ""))
+    for path in ([paths] if isinstance(paths, str) else list(paths)):
+        with open(path) as fh:
+            lines = [ln for ln in fh if ln.startswith('"')]
+        for r in csv.DictReader(lines):
+            key = (path, r["ID"], r["Kernel Name"])
+            rows.setdefault(key, {})[r["Metric Name"]] = _num(r["Metric Value"], r.get("Metric Unit", ""))
     per_name = {}
-    for (_, name), m in rows.items():
+    for (_, _, name), m in rows.items():
         kind = kind_of(name)
         if kind is None:
             continue
@@ -142,7 +148,8 @@ def _head():
         return None
 
 
-def build_counts(fp64_csv: str, mixed_csv: str | None = None, n: int = 512):
+def build_counts(fp64_csv, mixed_csv=None, n: int = 512):
+    """The stored counts from the FP64 and mixed captures (a path or a list each)."""
     cells = n * n
     out = {"workload": f"orszag_tang_2d_{n}x{n}", "cells": cells, "sources_digest": sources_digest(),
            "head_when_counted": _head(), "metrics": METRICS,
@@ -204,8 +211,9 @@ def hbm_entry(counts, prec: str, kind: str, avg_launch_ms: float, alg_bytes_per_
 
 
 if __name__ == "__main__":
-    args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    if not args:
-        print(__doc__)
-        sys.exit(2)
-    print(json.dumps(build_counts(args[0], args[1] if len(args) > 1 else None), indent=1))
+    import argparse
+    ap = argparse.ArgumentParser(description="roofline counts from ncu captures (see the module docstring)")
+    ap.add_argument("--fp64", nargs="+", required=True, help="ncu CSV captures of the FP64 512^2 step")
+    ap.add_argument("--mixed", nargs="+", default=None, help="ncu CSV captures of the mixed 512^2 step")
+    a = ap.parse_args()
+    print(json.dumps(build_counts(a.fp64, a.mixed), indent=1))

@@ -81,6 +81,12 @@ def test_roofline_counts_from_ncu_csv(tmp_path):
     assert k["dram_bytes"] == pytest.approx(30e6)
     assert k["fp64_pipe_inst"] == pytest.approx(32 * 2e6)
     assert k["fp64_flop_per_cell"] == pytest.approx(66e6 / 262144)
+    # one capture per kernel kind: launches of the same ID in two files are two launches
+    g = tmp_path / "counts2.csv"
+    g.write_text(NCU_CSV)
+    kinds2, _ = RL.counts_from_ncu_csv([str(f), str(g)], 512 * 512)
+    assert kinds2["flux"]["launches"] == 2
+    assert kinds2["flux"]["fp64_flop"] == pytest.approx(k["fp64_flop"])
 
 
 def test_roofline_alu_entry_arithmetic_and_staleness(tmp_path, monkeypatch):

@@ -300,3 +300,40 @@ def test_normal_build_reports_no_bounds_checks():
     n = C.c_longlong(7)
     assert L.grmhd_bounds_violations(C.byref(n), 0) == 0 and n.value == -1
     assert L.grmhd_bounds_violations(None, 0) == -1
+
+
+def test_numerics_eval_checks_arguments_on_the_host():
+    """grmhd_numerics_eval refuses an unknown op, a negative count and NULL arrays, and
+    launches nothing for n = 0 -- all before any device call."""
+    import ctypes as C
+    from paper_2110_03732_gb300 import build as _b
+    L = C.CDLL(_b.build())
+    f = L.grmhd_numerics_eval
+    f.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]
+    f.restype = C.c_int
+    assert f(-1, None, None, 0, None) == -1
+    assert f(16, None, None, 0, None) == -1
+    assert f(0, None, None, -1, None) == -1
+    assert f(0, None, None, 4, None) == -1
+    assert f(0, None, None, 0, None) == 0
+
+
+def test_mixed_precision_refuses_a_tolerance_below_1e_11():
+    """The mixed path accepts Newton roots by a double-word residual (~1e-14 of the
+    momentum scale): grmhd_create refuses newton_tol in (0, 1e-11) for it, before any
+    device call; FP64 takes any tolerance."""
+    import ctypes as C
+    from paper_2110_03732_gb300 import build as _b
+    from paper_2110_03732_gb300.grmhd import Params, Tableau
+    L = C.CDLL(_b.build())
+    L.grmhd_create.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.grmhd_create.restype = C.c_int
+    L.grmhd_tableau_ssp2.argtypes = [C.c_void_p]
+    L.grmhd_last_error.restype = C.c_char_p
+    t = Tableau()
+    L.grmhd_tableau_ssp2(C.byref(t))
+    g = _grid(2, (8, 8, 1))
+    p = Params(4.0 / 3.0, 0.4, 1e-12, 0, 1, 0.0, 0.0, 0, 0.0, 0, 0)
+    ctx = C.c_void_p()
+    assert L.grmhd_create(C.byref(g), C.byref(p), C.byref(t), C.byref(ctx)) == -1
+    assert b"newton_tol" in L.grmhd_last_error()
