@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched and serving measurements")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--n", type=int, default=N_OT, help=argparse.SUPPRESS)
-    ap.add_argument("--case", choices=["star", "clean", "ot", "ot_mixed"], default=None,
-                    help="run one workload alone (for profiling) and print its timings: the 3-D star with "
+    ap.add_argument("--case", choices=["star", "star_mixed", "clean", "ot", "ot_mixed"], default=None,
+                    help="run one workload alone (for profiling) and print its timings: the 3-D star (FP64 or mixed) with "
                          "--case-n cells a side, the multigrid cleaning of the --case-n^2 Orszag-Tang problem, "
                          "or the --case-n^2 Orszag-Tang step in FP64 or mixed precision")
     ap.add_argument("--case-n", type=int, default=96)
@@ -67,10 +67,11 @@ def run_case(args, grmhd, P, dev):
     n = args.case_n
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if args.case in ("star", "ot", "ot_mixed"):
-        if args.case == "star":
-            S = grmhd.Solver.from_problem(P.star(n), device=dev)
-            name = f"star_3d_{n}^3_fp64"
+    if args.case in ("star", "star_mixed", "ot", "ot_mixed"):
+        if args.case.startswith("star"):
+            prec = "mixed" if args.case == "star_mixed" else "fp64"
+            S = grmhd.Solver.from_problem(P.star(n), device=dev, precision=prec)
+            name = f"star_3d_{n}^3_{prec}"
         else:
             prec = "mixed" if args.case == "ot_mixed" else "fp64"
             S = grmhd.Solver.from_problem(P.orszag_tang(n), device=dev, precision=prec)
@@ -138,11 +139,11 @@ def peaks():
 # per cell (8 primitives and the 2 transverse cell q_B, 40 B) and writes 8 FP32 fluxes
 # and the one degenerate FP64 edge EMF it owns per face (40 B); the edge-EMF launch
 # reads E_z (FP32) and the two face q_B (FP64) per edge and writes its FP64 EMF (28 B);
-# the update reads per cell the 16 FP32 fluxes (64 B) and, in doubles, q^n or the
-# running sum (11), the primitives its sources use (u^1..3, E^1..2: 5), R (3) and the
-# edge EMFs (3), and writes the later-stage base and the running sum (22, stage 0) or
-# q^{n+1} (11, stage 1): 64 B + 39.5 doubles on average.
-MIXED_ALG_BYTES_PER_CELL = {"flux": 80.0, "emf": 28.0, "update": 64.0 + 39.5 * 8}
+# the update reads per cell the 16 FP32 fluxes and the FP32 primitives its sources use
+# (u^1..3, E^1..2: 21 floats, 84 B) and, in doubles, q^n or the running sum (11), R (3)
+# and the edge EMFs (3), and writes the later-stage base and the running sum (22,
+# stage 0) or q^{n+1} (11, stage 1): 84 B + 33.5 doubles on average.
+MIXED_ALG_BYTES_PER_CELL = {"flux": 80.0, "emf": 28.0, "update": 84.0 + 33.5 * 8}
 
 
 class ClockSampler:

@@ -107,13 +107,13 @@ typedef struct {
                           needs newton_tol >= 1e-11 (else GRMHD_ERR_ARG) */
     int newton_kmax;   /* Newton iteration cap; 0 -> 50 */
     int precision;     /* GRMHD_PREC_FP64: every step in FP64.  GRMHD_PREC_MIXED: MC
-                          reconstruction, HLL fluxes and the edge EMF in FP32, the
-                          flux divergence in double-word arithmetic from the FP32
-                          fluxes; the implicit solve / con2prim (its root accepted by
-                          a double-word residual, its outputs FP64), sources, CT face
-                          update and stage combination stay FP64 (div B stays at FP64
-                          round-off because each FP32 edge EMF is shared by the faces
-                          around it) */
+                          reconstruction, HLL fluxes, the edge EMF and the non-stiff
+                          sources in FP32, the flux divergence in double-word
+                          arithmetic from the FP32 fluxes; the implicit solve /
+                          con2prim (its root accepted by a double-word residual, its
+                          outputs FP64), CT face update and stage combination stay FP64
+                          (div B stays at FP64 round-off because each FP32 edge EMF is
+                          shared by the faces around it) */
     double rho_atm;    /* atmosphere (not in the paper): a cell with D < 10 rho_atm, or
                           whose solve fails, is set to rest at (rho_atm, p_atm) with E
                           kept; 0 disables it (failures then keep their primitives) */

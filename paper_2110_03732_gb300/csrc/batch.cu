@@ -398,6 +398,7 @@ void fill_desc(grmhd_batch* b, int p, double dt)
         ps.upd.f32 = ctx_mixed(c) ? 1 : 0;
         for (int k = 0; k < 3; k++) ps.upd.Eh[k] = ps.Eh64[k];
         for (int v = 0; v < 8; v++) ps.upd.prim[v] = ps.imp.prim.p[v];
+        for (int v = 0; v < 11; v++) ps.upd.p32[v] = ps.p32.p[v];
         for (int k = 0; k < 3; k++) ps.upd.bf[k] = ps.bfs.p[k];
         ps.upd.psi = ps.psi;
         ps.upd.alp = ps.alp;

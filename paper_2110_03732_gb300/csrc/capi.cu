@@ -368,6 +368,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     a.f32 = c->mixed ? 1 : 0;
     for (int k = 0; k < 3; k++) a.Eh[k] = c->Eh[k];
     for (int v = 0; v < 8; v++) a.prim[v] = prim.p[v];
+    for (int v = 0; v < 11; v++) a.p32[v] = c->mixed ? c->p32[v] : nullptr;
     for (int k = 0; k < 3; k++) a.bf[k] = bfs.p[k];
     a.psi = c->psi;
     a.alp = c->alp;

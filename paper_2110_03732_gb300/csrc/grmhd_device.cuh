@@ -545,6 +545,22 @@ __device__ __forceinline__ double f2d_int(float v)
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f2d_int(x); }
 
+// an FP64 metric factor (psi, alpha) in the stencil precision T: itself, or rounded to
+// binary32 on the integer pipe (a metric stencil converts tens of them per face or
+// edge, and a hardware conversion would issue each on the FP64 pipe); mean2 = (a + b)/2
+// in T (FP64: the sum first; FP32: of the two rounded values, no FP64 instruction).
+// Face fields and constants, a few per face, keep the hardware conversion: the FP32
+// kernels leave the FP64 pipe idle, and it is fewer instructions.
+template <typename T> __device__ __forceinline__ T met_t(double x);
+template <> __device__ __forceinline__ double met_t<double>(double x) { return x; }
+template <> __device__ __forceinline__ float met_t<float>(double x) { return d2f_int(x); }
+template <typename T> __device__ __forceinline__ T mean2(double a, double b);
+template <> __device__ __forceinline__ double mean2<double>(double a, double b) { return 0.5 * (a + b); }
+template <> __device__ __forceinline__ float mean2<float>(double a, double b)
+{
+    return 0.5f * (d2f_int(a) + d2f_int(b));
+}
+
 constexpr unsigned kHi1e30 = 0x46293E59u;   // high word of 1e30 (a start beyond is discarded)
 
 // FP64 tests on the integer pipe (an FP64 compare also issues on the FP64 pipe):

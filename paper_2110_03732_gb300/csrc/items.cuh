@@ -193,8 +193,8 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     const double* __restrict__ psi = M ? psi_in : nullptr;
     const double* __restrict__ alp = M ? alp_in : nullptr;
     constexpr int T1 = (D + 1) % 3, T2 = (D + 2) % 3;
-    const T psf = psi ? (T)(0.5 * (psi[rm] + psi[r0])) : T(1);
-    const T alf = alp ? (T)(0.5 * (alp[rm] + alp[r0])) : T(1);
+    const T psf = psi ? mean2<T>(psi[rm], psi[r0]) : T(1);
+    const T alf = alp ? mean2<T>(alp[rm], alp[r0]) : T(1);
     const T pf2 = psf * psf, ipf2 = psi ? rcp_t(pf2) : T(1);
     // orthonormal-frame states at the face: u_hat = psi^2 u, E_hat = psi^2 E,
     // B_hat = psi^2 B (normal: q_B / psi^4)
@@ -361,7 +361,7 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
         for (int v = 0; v < 8; v++) x[v] = prim.p[v][mi];
         T ip6 = T(1);
         if (psi) {
-            const T ps = (T)psi[lin(g, cs[0], cs[1], cs[2])], p2 = ps * ps;
+            const T ps = met_t<T>(psi[lin(g, cs[0], cs[1], cs[2])]), p2 = ps * ps;
             ip6 = rcp_t(p2 * p2 * p2);
         }
         x[8] = (T)cell_qB_in(g, prim, bf, T1, cs, mi) * ip6;
@@ -407,11 +407,12 @@ __device__ __forceinline__ void flux_march_item(const Dims& g, const PrimIn<T>& 
 // the (up to two) A-faces touching the edge, cab[1] likewise for the B-faces; 1 in an
 // inactive direction.  The larger of a0/q0 and a1/q1 is picked by comparing a0 q1 with
 // a1 q0, and both quotients come from one reciprocal.
+template <typename T>
 __device__ __forceinline__ void edge_speeds(const Dims& g, const double* __restrict__ psi,
                                             const double* __restrict__ alp, long long i0, bool aa, bool ba,
-                                            long long sA, long long sB, double* cab)
+                                            long long sA, long long sB, T* cab)
 {
-    double num[2] = {1.0, 1.0}, den[2] = {1.0, 1.0};
+    T num[2] = {T(1), T(1)}, den[2] = {T(1), T(1)};
 #pragma unroll
     for (int k = 0; k < 2; k++) {
         const bool act = k == 0 ? aa : ba, oth = k == 0 ? ba : aa;
@@ -419,16 +420,16 @@ __device__ __forceinline__ void edge_speeds(const Dims& g, const double* __restr
         const long long sn = k == 0 ? sA : sB, so = k == 0 ? sB : sA;
         for (int tt = 0; tt < (oth ? 2 : 1); tt++) {
             const long long cf = chk(g, i0 - tt * so), cfm = chk(g, cf - sn);
-            const double psf = psi ? 0.5 * (psi[cfm] + psi[cf]) : 1.0;
-            const double alf = alp ? 0.5 * (alp[cfm] + alp[cf]) : 1.0;
-            const double q = psf * psf;
+            const T psf = psi ? mean2<T>(psi[cfm], psi[cf]) : T(1);
+            const T alf = alp ? mean2<T>(alp[cfm], alp[cf]) : T(1);
+            const T q = psf * psf;
             if (tt == 0 || alf * den[k] > num[k] * q) {
                 num[k] = alf;
                 den[k] = q;
             }
         }
     }
-    const double r = rcp_pos(den[0] * den[1]);
+    const T r = rcp_t(den[0] * den[1]);
     cab[0] = num[0] * den[1] * r;
     cab[1] = num[1] * den[0] * r;
 }
@@ -461,14 +462,14 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
             for (int sa = 0; sa < NS; sa++) {
                 int cs[3] = {cb[0], cb[1], cb[2]};
                 cs[A] = P ? ext_cell(g, A, cb[A] + sa - OFF) : cb[A] + sa - OFF;
-                const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
+                const T ps = psi ? met_t<T>(psi[lin(g, cs[0], cs[1], cs[2])]) : T(1);
                 const T p2 = ps * ps;
                 v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
             }
             if (P) ppm_face<T>(v, s[0][ob], s[1][ob]);
             else mc_face<T>(v[0], v[1], v[2], v[NS - 1], s[0][ob], s[1][ob]);
         } else {
-            const T ps = psi ? (T)psi[lin(g, cb[0], cb[1], cb[2])] : T(1);
+            const T ps = psi ? met_t<T>(psi[lin(g, cb[0], cb[1], cb[2])]) : T(1);
             const T p2 = ps * ps;
             s[0][ob] = s[1][ob] = p2 * p2 * Ec[cell_at(g, cb)];
         }
@@ -514,18 +515,18 @@ __device__ __forceinline__ void emf_item(const Dims& g, const PrimIn<T>& prim, c
     T ale = T(1), ca = T(1), cb = T(1);
     if (alp || psi) {
         // mean of the 1, 2 or 4 cells around the edge
-        double sum = alp ? alp[i0] : 1.0, w = 1.0;
-        if (aa) { sum += alp ? alp[chk(g, i0 - sA)] : 1.0; w = 0.5; }
+        T sum = alp ? met_t<T>(alp[i0]) : T(1), w = T(1);
+        if (aa) { sum += alp ? met_t<T>(alp[chk(g, i0 - sA)]) : T(1); w = T(0.5); }
         if (ba) {
-            sum += alp ? alp[chk(g, i0 - sB)] : 1.0;
-            if (aa) sum += alp ? alp[chk(g, i0 - sA - sB)] : 1.0;
-            w *= 0.5;
+            sum += alp ? met_t<T>(alp[chk(g, i0 - sB)]) : T(1);
+            if (aa) sum += alp ? met_t<T>(alp[chk(g, i0 - sA - sB)]) : T(1);
+            w *= T(0.5);
         }
-        ale = (T)(sum * w);
-        double cab[2];
-        edge_speeds(g, psi, alp, i0, aa, ba, sA, sB, cab);
-        ca = (T)cab[0];
-        cb = (T)cab[1];
+        ale = sum * w;
+        T cab[2];
+        edge_speeds<T>(g, psi, alp, i0, aa, ba, sA, sB, cab);
+        ca = cab[0];
+        cb = cab[1];
     }
     // steps (v)-(vii): hat{E}^{XY} = alpha E_C^{XY}; Londrillo & Del Zanna (2004) with
     // c+ = c- in each direction, where the four-state weights are all 1/4 and the
@@ -575,7 +576,7 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
             int cs[3] = {c[0], c[1], c[2]};
             cs[B] = mb;
             cs[A] = P ? ext_cell(g, A, c[A] + sa - OFF) : c[A] + sa - OFF;
-            const T ps = psi ? (T)psi[lin(g, cs[0], cs[1], cs[2])] : T(1);
+            const T ps = psi ? met_t<T>(psi[lin(g, cs[0], cs[1], cs[2])]) : T(1);
             const T p2 = ps * ps;
             v[sa] = p2 * p2 * Ec[cell_at(g, cs)];
         }
@@ -620,15 +621,15 @@ __device__ __forceinline__ void emf_march_item(const Dims& g, const PrimIn<T>& p
         const long long sA = g.st[A], sB = g.st[B];
         T ale = T(1), ca = T(1), cb = T(1);
         if (alp || psi) {
-            double sum = alp ? alp[i0] : 1.0;
-            sum += alp ? alp[chk(g, i0 - sA)] : 1.0;
-            sum += alp ? alp[chk(g, i0 - sB)] : 1.0;
-            sum += alp ? alp[chk(g, i0 - sA - sB)] : 1.0;
-            ale = (T)(sum * 0.25);
-            double cab[2];
-            edge_speeds(g, psi, alp, i0, true, true, sA, sB, cab);
-            ca = (T)cab[0];
-            cb = (T)cab[1];
+            T sum = alp ? met_t<T>(alp[i0]) : T(1);
+            sum += alp ? met_t<T>(alp[chk(g, i0 - sA)]) : T(1);
+            sum += alp ? met_t<T>(alp[chk(g, i0 - sB)]) : T(1);
+            sum += alp ? met_t<T>(alp[chk(g, i0 - sA - sB)]) : T(1);
+            ale = sum * T(0.25);
+            T cab[2];
+            edge_speeds<T>(g, psi, alp, i0, true, true, sA, sB, cab);
+            ca = cab[0];
+            cb = cab[1];
         }
         // EXY[X][Y]: X the A side (the row's L / R), Y the B side (L = this edge's
         // lower-B state)
@@ -830,6 +831,74 @@ __device__ __forceinline__ void cell_sources(const Dims& g, const double* const*
 // / (2 dx_d) is formed in double-word arithmetic on the FP32 pipe (about 2^-46 of its
 // terms, far below the FP32 fluxes' own error) and widened by one FP64 add, in place
 // of two FP64 instructions per flux.
+// The same sources on the mixed-precision path, in FP32 from the stage's FP32
+// primitives and cell q_B (the values its FP32 fluxes were built from), each term
+// widened and added to Lc in FP64.  The metric differences d_i alpha, d_i psi are
+// taken in FP64 before rounding (a slowly varying alpha would otherwise lose digits to
+// cancellation); the rest carries FP32 rounding, below the FP32 fluxes' own error.
+__device__ __forceinline__ void cell_sources_f32(const Dims& g, const float* const* p32,
+                                                 const double* __restrict__ psi, const double* __restrict__ alp,
+                                                 const int* c, long long o, double* Lc)
+{
+    const float ps = psi ? d2f_int(psi[o]) : 1.0f;
+    const float al = alp ? d2f_int(alp[o]) : 1.0f;
+    const float p2 = ps * ps, p4 = p2 * p2, p6 = p4 * p2;
+    float u[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) u[i] = p32[1 + i][o];
+    const float xw = 1.0f + p4 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const float iW = rsqrtf(xw);
+    const float W = xw * iW;
+    float divqE = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (!g.act[d]) continue;
+        int cp[3] = {c[0], c[1], c[2]}, cm[3] = {c[0], c[1], c[2]};
+        cp[d] += 1;
+        cm[d] -= 1;
+        float sp = psi ? d2f_int(psi[chk(g, o + g.st[d])]) : 1.0f, sm = psi ? d2f_int(psi[chk(g, o - g.st[d])]) : 1.0f;
+        sp = sp * sp;
+        sm = sm * sm;
+        const float qp = sp * sp * sp * p32[5 + d][cell_at(g, cp)];
+        const float qm = sm * sm * sm * p32[5 + d][cell_at(g, cm)];
+        divqE += (qp - qm) * (0.5f * d2f_int(g.idx[d]));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) Lc[5 + i] -= f2d_int(al * divqE * (u[i] * iW));
+    if (psi || alp) {
+        const float rho = p32[0][o], p = p32[4][o];
+        const float ip4 = 1.0f / p4, ips = ps * p2 * ip4;   // psi^-4, psi^-1
+        float uh[3], Eh[3], Bh[3];
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            uh[i] = p2 * u[i];
+            Eh[i] = p2 * p32[5 + i][o];
+            Bh[i] = p32[8 + i][o] * ip4;   // psi^2 q_B / psi^6
+        }
+        const float rhoh = rho + d2f_int(g.gh) * p;
+        const float U = 0.5f * (Eh[0] * Eh[0] + Eh[1] * Eh[1] + Eh[2] * Eh[2] + Bh[0] * Bh[0] + Bh[1] * Bh[1] +
+                                Bh[2] * Bh[2]);
+        const float tauD = rhoh * W * W - p + U;   // tau + D
+        float S[3];
+        S[0] = rhoh * W * uh[0] + (Eh[1] * Bh[2] - Eh[2] * Bh[1]);
+        S[1] = rhoh * W * uh[1] + (Eh[2] * Bh[0] - Eh[0] * Bh[2]);
+        S[2] = rhoh * W * uh[2] + (Eh[0] * Bh[1] - Eh[1] * Bh[0]);
+        const float tr = rhoh * (uh[0] * uh[0] + uh[1] * uh[1] + uh[2] * uh[2]) + 3.0f * p + U;
+        float s4 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            if (!g.act[i]) continue;
+            const long long op = chk(g, o + g.st[i]), om = chk(g, o - g.st[i]);
+            const float hi = 0.5f * d2f_int(g.idx[i]);
+            const float dal = alp ? d2f_int(alp[op] - alp[om]) * hi : 0.0f;
+            const float dps = psi ? d2f_int(psi[op] - psi[om]) * hi : 0.0f;
+            Lc[1 + i] += f2d_int(p6 * (-tauD * dal + 2.0f * al * (dps * ips) * tr));
+            s4 += S[i] * dal;
+        }
+        Lc[4] -= f2d_int(p4 * s4);
+    }
+}
+
 template <bool M, bool F32 = false>
 __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, long long t)
 {
@@ -883,7 +952,8 @@ __device__ __forceinline__ void update_item(const Dims& g, const UpdateArgs& a, 
                 }
             }
         }
-        cell_sources<false>(g, a.prim, a.bf, psi, alp, c, o, Lc);
+        if (F32) cell_sources_f32(g, a.p32, psi, alp, c, o, Lc);
+        else cell_sources<false>(g, a.prim, a.bf, psi, alp, c, o, Lc);
 #pragma unroll
         for (int v = 0; v < 8; v++) out_value(a, v, o, Lc[v], v >= 5);
     }

@@ -14,9 +14,8 @@ enum { UPD_WRITE_L = 0, UPD_STAGE = 1 };
 template <typename T> struct PrimIn;
 template <> struct PrimIn<double> { const double* p[8]; };
 template <> struct PrimIn<float> { const float* p[11]; };
-// face fluxes of the 8 cell-centred variables, stored in FP64 as twice the HLL flux
-// (the update kernel folds the 1/2 into its 1/dx); the mixed path's FP32 fluxes are
-// widened once, when stored
+// face fluxes of the 8 cell-centred variables, stored as twice the HLL flux (the
+// update kernel folds the 1/2 into its 1/dx): FP64, or FP32 on the mixed path
 template <typename T> struct FluxOut { T* p[8]; };
 struct F11 { float* p[11]; };
 
@@ -85,6 +84,7 @@ struct UpdateArgs {
     int f32;                // the fluxes are FP32 (the mixed-precision flux kernels)
     const double* Eh[3];    // edge EMFs
     const double* prim[8];  // stage primitives (padded)
+    const float* p32[11];   // their FP32 copy with the cell q_B (mixed precision: the sources)
     const double* bf[3];    // stage face fields
     const double* psi;
     const double* alp;

@@ -1,6 +1,7 @@
-"""Mixed precision (MC reconstruction, HLL fluxes and the UCT edge EMF in FP32; the
-implicit E + velocity solve, sources, CT face update and stage combination in
-FP64) against the FP64 oracle.  Bounds (the targets for the mixed path): relative
+"""Mixed precision (MC reconstruction, HLL fluxes, the UCT edge EMF and the non-stiff
+sources in FP32, the flux divergence in double-word arithmetic; the implicit E +
+velocity solve, CT face update and stage combination in FP64) against the FP64
+oracle.  Bounds (the targets for the mixed path): relative
 L1 error of the density <= 1e-5 after 100 steps, div B at FP64 round-off
 (<= 1e-12), conservation of the periodic totals at FP64 round-off (each FP32 face
 flux and edge EMF value is shared by both sides)."""
