@@ -334,30 +334,39 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     // FP32 primitives; the update (sources, CT, stage folds) stays FP64
     PrimIn<float> p32;
     for (int v = 0; v < 11; v++) p32.p[v] = c->p32[v];
-    for (int d = 0; d < 3; d++) {
+    if (c->mixed) {
+        // FP32 arithmetic and FP32 fluxes (in the first half of each flux array): the
+        // fluxes of every direction and the edge EMFs in one launch
+        FluxOut<float> fo[3];
+        double* fe[3][3];
+        double* eh[3];
+        for (int d = 0; d < 3; d++)
+            for (int v = 0; v < 8; v++) fo[d].p[v] = reinterpret_cast<float*>(c->F[d][v]);
+        for (int d = 0; d < 3; d++)
+            for (int k = 0; k < 3; k++) fe[d][k] = fused_emf_dir(c, k) == d ? c->Eh[k] : nullptr;
+        for (int k = 0; k < 3; k++) eh[k] = emf_needed(g, k) && fused_emf_dir(c, k) < 0 ? c->Eh[k] : nullptr;
+        const int tk = tbegin(c, KIND_FLUX, st);
+        e = launch_stencil32(g, p32, bfs, c->psi, c->alp, fo, fe, eh, c->nsm, st, c->ppm);
+        tend(c, tk, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "stencil kernel");
+    }
+    for (int d = 0; d < 3 && !c->mixed; d++) {
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
         double* eh64[3] = {nullptr, nullptr, nullptr};
         for (int k = 0; k < 3; k++)
             if (fused_emf_dir(c, k) == d) eh64[k] = c->Eh[k];
-        if (c->mixed) {
-            // FP32 arithmetic and FP32 fluxes (in the first half of each flux array)
-            FluxOut<float> fo;
-            for (int v = 0; v < 8; v++) fo.p[v] = reinterpret_cast<float*>(c->F[d][v]);
-            e = launch_flux32(g, d, p32, bfs, c->psi, c->alp, fo, c->nsm, st, c->ppm, eh64);
-        } else {
-            e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
-                            c->ppm, eh64);
-        }
+        e = launch_flux(g, d, prim, bfs, c->psi, c->alp, p8(c->F[d]), c->nsm, st, c->ideal ? c->vbar[d] : nullptr,
+                        c->ppm, eh64);
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "flux kernel");
     }
-    for (int k = 0; k < 3; k++) {
+    for (int k = 0; k < 3 && !c->mixed; k++) {
         if (!emf_needed(g, k) || fused_emf_dir(c, k) >= 0) continue;
         const int tk = tbegin(c, KIND_EMF, st);
-        if (c->mixed) e = launch_emf32(g, k, p32, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
-        else if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
+        if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
         else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
         tend(c, tk, st);
         c->launches++;

@@ -14,6 +14,8 @@
 //   k_prim2con, k_curlA (Sec. 4), k_dt (Sec. 2.5), k_divb, k_totals: set-up and
 //   diagnostics; k_implicit_cc, k_curlA_cc, k_prim2con_cc, k_diag_cc: the same for the
 //   cell-centred fields of the GLM variant (its flux and update kernels: glm.cu)
+#include <cstring>
+
 #include "grmhd_device.cuh"
 #include "items.cuh"
 #include "kernels.h"
@@ -93,6 +95,72 @@ __global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a)
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x)
         emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+}
+
+// Mixed precision: the face fluxes of every active direction and the edge EMFs the
+// flux kernels do not write, in one launch.  Block ranges select the task (the same
+// items, march lengths and grid copies as the separate launches, so every face and
+// edge is bitwise the same); one launch keeps the SMs filled across what were three to
+// six latency-bound single-wave kernels with their tails.
+struct Stencil32 {
+    int b0[7];                 // first block of task s (flux x, y, z; EMF x, y, z); b0[6] = grid
+    int emarch[3];             // EMF task C marches along C + 2 (both transverse directions active)
+    Dims g[6];                 // each task's copy of the grid, with its march length
+    FluxArgs<float> fa[3];
+    EmfArgs<float> ea[3];
+};
+
+template <int D, bool M, bool P>
+__device__ __forceinline__ void stencil_flux32(const Dims& g, const FluxArgs<float>& a, long long t0, long long nt)
+{
+    const long long tot = g.dq[D].d * (D == 0 ? (long long)g.n[1] * g.n[2]
+                                              : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
+    for (long long t = t0; t < tot; t += nt)
+        flux_march_item<D, M, float, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, nullptr, a.Eh, t);
+}
+
+template <int C, bool M, bool P>
+__device__ __forceinline__ void stencil_emf32(const Dims& g, const EmfArgs<float>& a, int march, long long t0,
+                                              long long nt)
+{
+    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
+    if (march) {
+        const long long tot = (long long)g.dq[B].d * g.n[C] * (g.n[A] + 1);
+        for (long long t = t0; t < tot; t += nt) emf_march_item<C, M, float, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+    } else {
+        long long tot = 1;
+#pragma unroll
+        for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
+        for (long long t = t0; t < tot; t += nt) emf_item<C, M, float, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+    }
+}
+
+template <bool M, bool P>
+__global__ void __launch_bounds__(128) k_stencil32(Stencil32 L)
+{
+    grid_dep_sync();
+    const int b = blockIdx.x;
+    int s = 0;
+#pragma unroll
+    for (int i = 1; i < 6; i++)
+        if (b >= L.b0[i]) s = i;   // empty tasks have b0[i] == b0[i + 1]
+    switch (s) {
+#define GRMHD_STENCIL_CASE(S, CALL)                                                   \
+    case S: {                                                                         \
+        const long long nt = (long long)(L.b0[S + 1] - L.b0[S]) * blockDim.x;        \
+        const long long t0 = (long long)(b - L.b0[S]) * blockDim.x + threadIdx.x;    \
+        CALL;                                                                         \
+        break;                                                                        \
+    }
+        GRMHD_STENCIL_CASE(0, (stencil_flux32<0, M, P>(L.g[0], L.fa[0], t0, nt)))
+        GRMHD_STENCIL_CASE(1, (stencil_flux32<1, M, P>(L.g[1], L.fa[1], t0, nt)))
+        GRMHD_STENCIL_CASE(2, (stencil_flux32<2, M, P>(L.g[2], L.fa[2], t0, nt)))
+        GRMHD_STENCIL_CASE(3, (stencil_emf32<0, M, P>(L.g[3], L.ea[0], L.emarch[0], t0, nt)))
+        GRMHD_STENCIL_CASE(4, (stencil_emf32<1, M, P>(L.g[4], L.ea[1], L.emarch[1], t0, nt)))
+        GRMHD_STENCIL_CASE(5, (stencil_emf32<2, M, P>(L.g[5], L.ea[2], L.emarch[2], t0, nt)))
+#undef GRMHD_STENCIL_CASE
+    default: break;
+    }
 }
 
 // ideal-limit edge EMF (App. A) from the stored transport velocities
@@ -544,19 +612,69 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
     return cudaGetLastError();
 }
 
-cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm, double* const* Eh)
+template <bool M, bool P>
+static int stencil32_blocks_per_sm()
 {
-    FluxArgs<float> a;
-    for (int k = 0; k < 3; k++) a.Eh[k] = Eh && !(psi || alp) ? Eh[k] : nullptr;
-    a.vbar[0] = a.vbar[1] = nullptr;
-    a.prim = prim;
-    a.bf = bf;
-    a.psi = psi;
-    a.alp = alp;
-    a.F = F;
-    if (ppm) flux_dispatch<float, true>(g, d, psi || alp, nsm, st, a);
-    else flux_dispatch<float, false>(g, d, psi || alp, nsm, st, a);
+    static int nb = 0;
+    if (nb < 1) {
+        int q = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_stencil32<M, P>, 128, 0) != cudaSuccess || q < 1) q = 1;
+        nb = q;
+    }
+    return nb;
+}
+
+cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, const double* psi, const double* alp,
+                             const FluxOut<float>* F, double* const (*fe)[3], double* const* Eh, int nsm,
+                             cudaStream_t st, bool ppm)
+{
+    const bool m = psi || alp;
+    const int bps = ppm ? (m ? stencil32_blocks_per_sm<true, true>() : stencil32_blocks_per_sm<false, true>())
+                        : (m ? stencil32_blocks_per_sm<true, false>() : stencil32_blocks_per_sm<false, false>());
+    const double c0 = ppm ? 1.0 : 0.6;
+    Stencil32 L;
+    memset(&L, 0, sizeof L);
+    int nb = 0;
+    for (int d = 0; d < 3; d++) {
+        L.b0[d] = nb;
+        L.g[d] = g;
+        FluxArgs<float>& a = L.fa[d];
+        a.prim = prim;
+        a.bf = bf;
+        a.psi = psi;
+        a.alp = alp;
+        if (!g.act[d]) continue;
+        a.F = F[d];
+        for (int k = 0; k < 3; k++) a.Eh[k] = fe && !m ? fe[d][k] : nullptr;
+        const long long other = d == 0 ? (long long)g.n[1] * g.n[2]
+                                       : (d == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]);
+        set_march(L.g[d], d, march_len(g.n[d], other, nsm, bps, c0));
+        nb += grid_for((long long)L.g[d].dq[d].d * other, 128, nsm);
+    }
+    for (int c = 0; c < 3; c++) {
+        L.b0[3 + c] = nb;
+        L.g[3 + c] = g;
+        EmfArgs<float>& a = L.ea[c];
+        a.prim = prim;
+        a.bf = bf;
+        a.psi = psi;
+        a.alp = alp;
+        if (!Eh || !Eh[c]) continue;
+        a.Eh = Eh[c];
+        const int A = (c + 1) % 3, B = (c + 2) % 3;
+        if (g.act[A] && g.act[B]) {
+            const long long other = (long long)g.n[c] * (g.n[A] + 1);
+            set_march(L.g[3 + c], B, march_len(g.n[B], other, nsm, bps, c0));
+            L.emarch[c] = 1;
+            nb += grid_for((long long)L.g[3 + c].dq[B].d * other, 128, nsm);
+        } else {
+            nb += grid_for(emf_work(g, c), 128, nsm);
+        }
+    }
+    L.b0[6] = nb;
+    if (nb == 0) return cudaSuccess;
+    if (ppm) launch_k(m ? k_stencil32<true, true> : k_stencil32<false, true>, nb, 128, st, L);
+    else launch_k(m ? k_stencil32<true, false> : k_stencil32<false, false>, nb, 128, st, L);
     return cudaGetLastError();
 }
 
@@ -591,20 +709,6 @@ cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const doubl
     if (c == 0) launch_k(m ? k_emf_ideal<0, true> : k_emf_ideal<0, false>, b, 128, st, g, a, v);
     else if (c == 1) launch_k(m ? k_emf_ideal<1, true> : k_emf_ideal<1, false>, b, 128, st, g, a, v);
     else launch_k(m ? k_emf_ideal<2, true> : k_emf_ideal<2, false>, b, 128, st, g, a, v);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                         const double* alp, double* Eh, int nsm, cudaStream_t st, bool ppm)
-{
-    EmfArgs<float> a;
-    a.prim = prim;
-    a.bf = bf;
-    a.psi = psi;
-    a.alp = alp;
-    a.Eh = Eh;
-    if (ppm) emf_dispatch<float, true>(g, c, psi || alp, nsm, st, a);
-    else emf_dispatch<float, false>(g, c, psi || alp, nsm, st, a);
     return cudaGetLastError();
 }
 

@@ -100,11 +100,12 @@ cudaError_t launch_implicit(const Dims& g, const ImpArgs& a, int nsm, cudaStream
 // coordinate u1..u3), hd = 0, on every cell
 cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, const double* u3, const double* psi,
                              P3f hs, P3f hd, int nsm, cudaStream_t st);
-cudaError_t launch_flux32(const Dims& g, int d, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                          const double* alp, FluxOut<float> F, int nsm, cudaStream_t st, bool ppm = false,
-                          double* const* Eh = nullptr);
-cudaError_t launch_emf32(const Dims& g, int c, const PrimIn<float>& prim, CP3 bf, const double* psi,
-                         const double* alp, double* Eh, int nsm, cudaStream_t st, bool ppm = false);
+// mixed precision: the fluxes of every active direction (F[d]; fe[d][k]: the edge EMFs
+// the d-flux writes on a flat 1-D / 2-D grid, or NULL) and the edge EMFs Eh[c] (NULL
+// for those not computed here) in one launch of k_stencil32
+cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, const double* psi, const double* alp,
+                             const FluxOut<float>* F, double* const (*fe)[3], double* const* Eh, int nsm,
+                             cudaStream_t st, bool ppm = false);
 cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
 // ppm: PPM reconstruction instead of MC (FP64 only)
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,

@@ -11,20 +11,22 @@ Refresh (one GPU, the 512^2 case of bench.py; one capture per precision and kern
 kind, each of one kernel name pattern and two launches, taken after the three warm-up
 steps have run the same kernels):
 
+    M=$(python -c "from paper_2110_03732_gb300 import roofline as R; print(','.join(R.METRICS))")
     python bench.py --case ot --case-n 512 --steps 1 --warmup 3 > gpurun_out/plain.log 2>&1 &&
-    for k in k_implicit k_flux_march k_emf_march k_update; do
-      ncu --metrics <METRICS> --clock-control none --print-units base \
-          -k "regex:^$k" -s <S> -c 2 --csv --log-file gpurun_out/counts_fp64_$k.csv \
+    for k in k_implicit:6 k_flux_march:12 k_emf_march:6 k_update:6; do
+      ncu --metrics $M --clock-control none --print-units base \
+          -k "regex:^${k%%:*}" -s ${k##*:} -c 2 --csv --log-file gpurun_out/counts_fp64_${k%%:*}.csv \
           python bench.py --case ot --case-n 512 --steps 1 --warmup 3 || break
     done
-    (the same with --case ot_mixed into counts_mixed_$k.csv)
+    (the same with --case ot_mixed into counts_mixed_*.csv, for k_implicit:6,
+    k_stencil32:6 and k_update:6: the mixed path runs its fluxes and edge EMFs in
+    one launch per stage)
     python -m paper_2110_03732_gb300.roofline --fp64 gpurun_out/counts_fp64_*.csv \
         --mixed gpurun_out/counts_mixed_*.csv > profiles/roofline_counts.json
 
-with <METRICS> the comma-joined ``METRICS`` below and <S> the launches of that kernel
-pattern in the warm-up steps (2 per step for the implicit solve, the edge EMF and the
-update, 4 for the two flux directions): the two captured launches are the first of the
-next step (for the flux, its two directions of the first stage).
+The skip counts are the launches of that kernel pattern in the warm-up steps (2 per
+step, 4 for the two flux directions): the two captured launches are the first of the
+next step (for the FP64 flux, its two directions of the first stage).
 """
 from __future__ import annotations
 
@@ -49,6 +51,7 @@ METRICS = [
     "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active",
     "dram__bytes_read.sum",
     "dram__bytes_write.sum",
+    "smsp__inst_executed.sum",
 ]
 
 # FP64 issue rate of GB300 from its unit counts and clock: 2 FP64 lanes per SM per
@@ -59,6 +62,10 @@ N_SM = 152
 SM_GHZ = 2.07
 FP64_INST_PEAK_PER_S = FP64_LANES_PER_SM_CYCLE * N_SM * SM_GHZ * 1e9        # 6.29e11
 FP64_PEAK_TFLOPS = 2 * FP64_INST_PEAK_PER_S / 1e12                          # 1.26 (nominal 1.25)
+# instruction issue rate: 4 schedulers per SM, each issuing one warp instruction (32
+# thread instructions) per cycle, 152 SMs, 2.07 GHz -- the bound of a kernel whose
+# instructions spread over the FP32, integer and FP64 pipes with none of them saturated
+ISSUE_PEAK_TINST = 4 * 32 * N_SM * SM_GHZ * 1e9 / 1e12                     # 40.3 T thread inst/s
 
 
 def sources_digest() -> str:
@@ -74,8 +81,8 @@ def sources_digest() -> str:
 
 
 def kind_of(kernel_name: str):
-    for pre, kind in (("k_implicit", "implicit"), ("k_flux_march", "flux"), ("k_emf", "emf"),
-                      ("k_update", "update")):
+    for pre, kind in (("k_implicit", "implicit"), ("k_flux_march", "flux"), ("k_stencil32", "flux"),
+                      ("k_emf", "emf"), ("k_update", "update")):
         if kernel_name.startswith(pre) or kernel_name.startswith("void " + pre):
             return kind
     return None
@@ -112,28 +119,32 @@ def counts_from_ncu_csv(paths, cells: int):
                 + m["smsp__sass_thread_inst_executed_op_dadd_pred_on.sum"]
                 + m["smsp__sass_thread_inst_executed_op_dmul_pred_on.sum"])
         e = per_name.setdefault(name, {"kind": kind, "launches": 0, "dur_us": 0.0, "fp64_flop": 0.0,
-                                       "fp64_pipe_inst": 0.0, "fp64_pipe_busy": 0.0, "dram_bytes": 0.0})
+                                       "fp64_pipe_inst": 0.0, "fp64_pipe_busy": 0.0, "dram_bytes": 0.0,
+                                       "inst": 0.0})
         e["launches"] += 1
         e["dur_us"] += m["gpu__time_duration.sum"]
         e["fp64_flop"] += flop
         e["fp64_pipe_inst"] += 32 * m["sm__inst_executed_pipe_fp64.sum"]
         e["fp64_pipe_busy"] += m["sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active"] / 100
         e["dram_bytes"] += m["dram__bytes_read.sum"] + m["dram__bytes_write.sum"]
+        e["inst"] += 32 * m.get("smsp__inst_executed.sum", 0.0)   # thread instructions (full warps)
+    F = ("dur_us", "fp64_flop", "fp64_pipe_inst", "fp64_pipe_busy", "dram_bytes", "inst")
     for e in per_name.values():
         n = e["launches"]
-        for k in ("dur_us", "fp64_flop", "fp64_pipe_inst", "fp64_pipe_busy", "dram_bytes"):
+        for k in F:
             e[k] /= n
     kinds = {}
     for name, e in per_name.items():
         k = kinds.setdefault(e["kind"], {"launches": 0, "kernels": []})
         k["kernels"].append(name)
-        for f in ("dur_us", "fp64_flop", "fp64_pipe_inst", "fp64_pipe_busy", "dram_bytes"):
+        for f in F:
             k[f] = k.get(f, 0.0) + e[f] * e["launches"]
         k["launches"] += e["launches"]
     for k in kinds.values():
         n = k["launches"]
-        for f in ("dur_us", "fp64_flop", "fp64_pipe_inst", "fp64_pipe_busy", "dram_bytes"):
+        for f in F:
             k[f] /= n
+        k["inst_per_cell"] = k["inst"] / cells
         k["fp64_flop_per_cell"] = k["fp64_flop"] / cells
         k["fp64_pipe_inst_per_cell"] = k["fp64_pipe_inst"] / cells
         k["dram_bytes_per_cell"] = k["dram_bytes"] / cells
@@ -177,9 +188,9 @@ def alu_entry(counts, prec: str, kind: str, avg_launch_ms: float, peak_probe_tfl
     mean launch time: achieved FP64 flop/s against the nominal FP64 rate, and the
     FP64-pipe issue fraction beside it (a DADD or DMUL takes an issue slot like a DFMA
     but counts one flop)."""
-    if not counts or prec not in counts or kind not in counts[prec]["kinds"]:
+    if not counts or prec not in counts or kind not in counts[prec]["kinds"] or not avg_launch_ms > 0:
         return {"bound": "alu", "kernel": kind, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "note": "no stored counts for this kernel"}
+                "frac": None, "traffic": None, "note": "no stored counts or no launches for this kernel"}
     k = counts[prec]["kinds"][kind]
     stale = counts["stale"]
     s = avg_launch_ms / 1e3
@@ -193,6 +204,28 @@ def alu_entry(counts, prec: str, kind: str, avg_launch_ms: float, peak_probe_tfl
             "peak_probe_tflops": peak_probe_tflops,
             "counts": {"head_when_counted": counts.get("head_when_counted"),
                        "sources_digest": counts.get("sources_digest"), "stale": stale}}
+
+
+def issue_entry(counts, prec: str, kind: str, avg_launch_ms: float):
+    """Roofline entry of a kernel bound by instruction issue (its instructions spread
+    over the FP32, integer and FP64 pipes): executed thread instructions per launch
+    over the live launch time, against the issue rate of the SMs; the FP64 figures of
+    alu_entry beside it."""
+    base = alu_entry(counts, prec, kind, avg_launch_ms)
+    k = (counts or {}).get(prec, {}).get("kinds", {}).get(kind)
+    if not k or not k.get("inst") or not avg_launch_ms > 0:
+        return {"bound": "alu", "kernel": kind, "achieved": None, "peak": ISSUE_PEAK_TINST, "unit": "Tinst/s",
+                "frac": None, "traffic": None, "note": "no stored instruction counts for this kernel"}
+    s = avg_launch_ms / 1e3
+    ach = k["inst"] / s / 1e12
+    out = {"bound": "alu", "kernel": kind, "achieved": ach, "peak": ISSUE_PEAK_TINST, "unit": "Tinst/s",
+           "frac": ach / ISSUE_PEAK_TINST, "traffic": base["traffic"], "avg_launch_ms": avg_launch_ms,
+           "inst_per_cell": k["inst_per_cell"],
+           "peak_source": "instruction issue of GB300 from its unit counts and clock (4 schedulers x 32 lanes "
+                          "per SM per cycle x 152 SMs x 2.07 GHz)",
+           "fp64_tflops": base["achieved"], "fp64_flop_frac": base["frac"],
+           "fp64_issue_frac": base.get("fp64_issue_frac"), "counts": base.get("counts")}
+    return out
 
 
 def hbm_entry(counts, prec: str, kind: str, avg_launch_ms: float, alg_bytes_per_launch: float, hbm_gbs: float):

@@ -126,6 +126,29 @@ def test_roofline_alu_entry_arithmetic_and_staleness(tmp_path, monkeypatch):
     assert r2["traffic"] is None and r2["counts"]["stale"] is True
 
 
+def test_issue_entry_arithmetic(tmp_path):
+    """The instruction-issue roofline: 32 x warp instructions per launch over the live
+    launch time, against 4 schedulers x 32 lanes x 152 SMs x 2.07 GHz."""
+    import json
+    from paper_2110_03732_gb300 import roofline as RL
+    f = tmp_path / "counts.csv"
+    row = ('"0","1","python3","h","void k_flux_march<0, 0, double, 0>(Dims, FluxArgs<double>)","1","7",'
+           '"(128, 1, 1)","(296, 1, 1)","0","10.3","Command line profiler metrics","smsp__inst_executed.sum",'
+           '"inst","1,000,000"')
+    lines = NCU_CSV.splitlines()
+    f.write_text("\n".join(lines[:3] + [row] + lines[3:]) + "\n")
+    counts = RL.build_counts(str(f))
+    p = tmp_path / "c.json"
+    p.write_text(json.dumps(counts))
+    c = RL.load_counts(str(p))
+    r = RL.issue_entry(c, "fp64", "flux", 0.1)
+    assert RL.ISSUE_PEAK_TINST == pytest.approx(4 * 32 * 152 * 2.07e9 / 1e12)
+    assert r["unit"] == "Tinst/s" and r["achieved"] == pytest.approx(32e6 / 1e-4 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / RL.ISSUE_PEAK_TINST)
+    assert r["fp64_flop_frac"] == pytest.approx(RL.alu_entry(c, "fp64", "flux", 0.1)["frac"])
+    assert RL.issue_entry(c, "fp64", "update", 0.1)["achieved"] is None
+
+
 def test_hbm_entry_arithmetic():
     from paper_2110_03732_gb300 import roofline as RL
     r = RL.hbm_entry(None, "mixed", "flux", 0.02, 112.0 * 262144, 6780.4)
