@@ -270,7 +270,9 @@ grmhd_status grmhd_load_start(grmhd_ctx* ctx, const void* src, size_t bytes, grm
  * stage kernel (at most 64 launches between two grmhd_kernel_times calls; later
  * ones go untimed).  grmhd_kernel_times waits for the recorded events and returns
  * the cumulative milliseconds and launch counts per kind: [0] implicit solve,
- * [1] face fluxes, [2] edge EMFs, [3] update.  grmhd_set_timing(ctx, 0) stops the
+ * [1] face fluxes, [2] edge EMFs, [3] update.  With the resistive edge EMF (CT) the
+ * fluxes of every direction and the edge EMFs run in one stencil launch per stage,
+ * counted under [1]; [2] then stays empty.  grmhd_set_timing(ctx, 0) stops the
  * recording; what was recorded stays readable, and enabling again restarts the
  * totals from zero.  grmhd_kernel_times fails with GRMHD_ERR_STATE if timing was
  * never enabled. */

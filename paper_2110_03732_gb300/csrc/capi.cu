@@ -351,7 +351,23 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "stencil kernel");
     }
-    for (int d = 0; d < 3 && !c->mixed; d++) {
+    // FP64, resistive UCT: likewise one launch
+    const bool fused = c->mixed || !c->ideal;
+    if (!c->mixed && fused) {
+        P8 fo[3];
+        double* fe[3][3];
+        double* eh[3];
+        for (int d = 0; d < 3; d++) fo[d] = p8(c->F[d]);
+        for (int d = 0; d < 3; d++)
+            for (int k = 0; k < 3; k++) fe[d][k] = fused_emf_dir(c, k) == d ? c->Eh[k] : nullptr;
+        for (int k = 0; k < 3; k++) eh[k] = emf_needed(g, k) && fused_emf_dir(c, k) < 0 ? c->Eh[k] : nullptr;
+        const int tk = tbegin(c, KIND_FLUX, st);
+        e = launch_stencil64(g, prim, bfs, c->psi, c->alp, fo, fe, eh, c->nsm, st, c->ppm);
+        tend(c, tk, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "stencil kernel");
+    }
+    for (int d = 0; d < 3 && !fused; d++) {
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
         double* eh64[3] = {nullptr, nullptr, nullptr};
@@ -363,7 +379,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "flux kernel");
     }
-    for (int k = 0; k < 3 && !c->mixed; k++) {
+    for (int k = 0; k < 3 && !fused; k++) {
         if (!emf_needed(g, k) || fused_emf_dir(c, k) >= 0) continue;
         const int tk = tbegin(c, KIND_EMF, st);
         if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);

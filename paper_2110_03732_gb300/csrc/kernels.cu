@@ -97,46 +97,47 @@ __global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a)
         emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
 }
 
-// Mixed precision: the face fluxes of every active direction and the edge EMFs the
-// flux kernels do not write, in one launch.  Block ranges select the task (the same
+// The face fluxes of every active direction and the edge EMFs the flux kernels do not
+// write, in one launch (resistive UCT, FP64 or mixed precision).  Block ranges select the task (the same
 // items, march lengths and grid copies as the separate launches, so every face and
 // edge is bitwise the same); one launch keeps the SMs filled across what were three to
 // six latency-bound single-wave kernels with their tails.
-struct Stencil32 {
+template <typename T>
+struct StencilTasks {
     int b0[7];                 // first block of task s (flux x, y, z; EMF x, y, z); b0[6] = grid
     int emarch[3];             // EMF task C marches along C + 2 (both transverse directions active)
     Dims g[6];                 // each task's copy of the grid, with its march length
-    FluxArgs<float> fa[3];
-    EmfArgs<float> ea[3];
+    FluxArgs<T> fa[3];
+    EmfArgs<T> ea[3];
 };
 
-template <int D, bool M, bool P>
-__device__ __forceinline__ void stencil_flux32(const Dims& g, const FluxArgs<float>& a, long long t0, long long nt)
+template <int D, bool M, typename T, bool P>
+__device__ __forceinline__ void stencil_flux(const Dims& g, const FluxArgs<T>& a, long long t0, long long nt)
 {
     const long long tot = g.dq[D].d * (D == 0 ? (long long)g.n[1] * g.n[2]
                                               : (D == 1 ? (long long)g.n[0] * g.n[2] : (long long)g.n[0] * g.n[1]));
     for (long long t = t0; t < tot; t += nt)
-        flux_march_item<D, M, float, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, nullptr, a.Eh, t);
+        flux_march_item<D, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.F, nullptr, a.Eh, t);
 }
 
-template <int C, bool M, bool P>
-__device__ __forceinline__ void stencil_emf32(const Dims& g, const EmfArgs<float>& a, int march, long long t0,
-                                              long long nt)
+template <int C, bool M, typename T, bool P>
+__device__ __forceinline__ void stencil_emf(const Dims& g, const EmfArgs<T>& a, int march, long long t0,
+                                            long long nt)
 {
     constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
     if (march) {
         const long long tot = (long long)g.dq[B].d * g.n[C] * (g.n[A] + 1);
-        for (long long t = t0; t < tot; t += nt) emf_march_item<C, M, float, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+        for (long long t = t0; t < tot; t += nt) emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
     } else {
         long long tot = 1;
 #pragma unroll
         for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
-        for (long long t = t0; t < tot; t += nt) emf_item<C, M, float, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
+        for (long long t = t0; t < tot; t += nt) emf_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
     }
 }
 
-template <bool M, bool P>
-__global__ void __launch_bounds__(128) k_stencil32(Stencil32 L)
+template <bool M, typename T, bool P>
+__global__ void __launch_bounds__(128) k_stencil(StencilTasks<T> L)
 {
     grid_dep_sync();
     const int b = blockIdx.x;
@@ -152,12 +153,12 @@ __global__ void __launch_bounds__(128) k_stencil32(Stencil32 L)
         CALL;                                                                         \
         break;                                                                        \
     }
-        GRMHD_STENCIL_CASE(0, (stencil_flux32<0, M, P>(L.g[0], L.fa[0], t0, nt)))
-        GRMHD_STENCIL_CASE(1, (stencil_flux32<1, M, P>(L.g[1], L.fa[1], t0, nt)))
-        GRMHD_STENCIL_CASE(2, (stencil_flux32<2, M, P>(L.g[2], L.fa[2], t0, nt)))
-        GRMHD_STENCIL_CASE(3, (stencil_emf32<0, M, P>(L.g[3], L.ea[0], L.emarch[0], t0, nt)))
-        GRMHD_STENCIL_CASE(4, (stencil_emf32<1, M, P>(L.g[4], L.ea[1], L.emarch[1], t0, nt)))
-        GRMHD_STENCIL_CASE(5, (stencil_emf32<2, M, P>(L.g[5], L.ea[2], L.emarch[2], t0, nt)))
+        GRMHD_STENCIL_CASE(0, (stencil_flux<0, M, T, P>(L.g[0], L.fa[0], t0, nt)))
+        GRMHD_STENCIL_CASE(1, (stencil_flux<1, M, T, P>(L.g[1], L.fa[1], t0, nt)))
+        GRMHD_STENCIL_CASE(2, (stencil_flux<2, M, T, P>(L.g[2], L.fa[2], t0, nt)))
+        GRMHD_STENCIL_CASE(3, (stencil_emf<0, M, T, P>(L.g[3], L.ea[0], L.emarch[0], t0, nt)))
+        GRMHD_STENCIL_CASE(4, (stencil_emf<1, M, T, P>(L.g[4], L.ea[1], L.emarch[1], t0, nt)))
+        GRMHD_STENCIL_CASE(5, (stencil_emf<2, M, T, P>(L.g[5], L.ea[2], L.emarch[2], t0, nt)))
 #undef GRMHD_STENCIL_CASE
     default: break;
     }
@@ -612,33 +613,35 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
     return cudaGetLastError();
 }
 
-template <bool M, bool P>
-static int stencil32_blocks_per_sm()
+template <bool M, typename T, bool P>
+static int stencil_blocks_per_sm()
 {
     static int nb = 0;
     if (nb < 1) {
         int q = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_stencil32<M, P>, 128, 0) != cudaSuccess || q < 1) q = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_stencil<M, T, P>, 128, 0) != cudaSuccess || q < 1)
+            q = 1;
         nb = q;
     }
     return nb;
 }
 
-cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, const double* psi, const double* alp,
-                             const FluxOut<float>* F, double* const (*fe)[3], double* const* Eh, int nsm,
-                             cudaStream_t st, bool ppm)
+template <typename T>
+static cudaError_t stencil_launch(const Dims& g, const PrimIn<T>& prim, CP3 bf, const double* psi, const double* alp,
+                                  const FluxOut<T>* F, double* const (*fe)[3], double* const* Eh, int nsm,
+                                  cudaStream_t st, bool ppm)
 {
     const bool m = psi || alp;
-    const int bps = ppm ? (m ? stencil32_blocks_per_sm<true, true>() : stencil32_blocks_per_sm<false, true>())
-                        : (m ? stencil32_blocks_per_sm<true, false>() : stencil32_blocks_per_sm<false, false>());
+    const int bps = ppm ? (m ? stencil_blocks_per_sm<true, T, true>() : stencil_blocks_per_sm<false, T, true>())
+                        : (m ? stencil_blocks_per_sm<true, T, false>() : stencil_blocks_per_sm<false, T, false>());
     const double c0 = ppm ? 1.0 : 0.6;
-    Stencil32 L;
+    StencilTasks<T> L;
     memset(&L, 0, sizeof L);
     int nb = 0;
     for (int d = 0; d < 3; d++) {
         L.b0[d] = nb;
         L.g[d] = g;
-        FluxArgs<float>& a = L.fa[d];
+        FluxArgs<T>& a = L.fa[d];
         a.prim = prim;
         a.bf = bf;
         a.psi = psi;
@@ -654,7 +657,7 @@ cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, c
     for (int c = 0; c < 3; c++) {
         L.b0[3 + c] = nb;
         L.g[3 + c] = g;
-        EmfArgs<float>& a = L.ea[c];
+        EmfArgs<T>& a = L.ea[c];
         a.prim = prim;
         a.bf = bf;
         a.psi = psi;
@@ -673,9 +676,27 @@ cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, c
     }
     L.b0[6] = nb;
     if (nb == 0) return cudaSuccess;
-    if (ppm) launch_k(m ? k_stencil32<true, true> : k_stencil32<false, true>, nb, 128, st, L);
-    else launch_k(m ? k_stencil32<true, false> : k_stencil32<false, false>, nb, 128, st, L);
+    if (ppm) launch_k(m ? k_stencil<true, T, true> : k_stencil<false, T, true>, nb, 128, st, L);
+    else launch_k(m ? k_stencil<true, T, false> : k_stencil<false, T, false>, nb, 128, st, L);
     return cudaGetLastError();
+}
+
+cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, const double* psi, const double* alp,
+                             const FluxOut<float>* F, double* const (*fe)[3], double* const* Eh, int nsm,
+                             cudaStream_t st, bool ppm)
+{
+    return stencil_launch<float>(g, prim, bf, psi, alp, F, fe, Eh, nsm, st, ppm);
+}
+
+cudaError_t launch_stencil64(const Dims& g, CP8 prim, CP3 bf, const double* psi, const double* alp, const P8* F,
+                             double* const (*fe)[3], double* const* Eh, int nsm, cudaStream_t st, bool ppm)
+{
+    PrimIn<double> p;
+    FluxOut<double> fo[3];
+    for (int v = 0; v < 8; v++) p.p[v] = prim.p[v];
+    for (int d = 0; d < 3; d++)
+        for (int v = 0; v < 8; v++) fo[d].p[v] = F[d].p[v];
+    return stencil_launch<double>(g, p, bf, psi, alp, fo, fe, Eh, nsm, st, ppm);
 }
 
 cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,

@@ -106,6 +106,9 @@ cudaError_t launch_hist_init(const Dims& g, const double* u1, const double* u2, 
 cudaError_t launch_stencil32(const Dims& g, const PrimIn<float>& prim, CP3 bf, const double* psi, const double* alp,
                              const FluxOut<float>* F, double* const (*fe)[3], double* const* Eh, int nsm,
                              cudaStream_t st, bool ppm = false);
+// the same for the FP64 path (resistive UCT; the ideal-limit EMF keeps its own launches)
+cudaError_t launch_stencil64(const Dims& g, CP8 prim, CP3 bf, const double* psi, const double* alp, const P8* F,
+                             double* const (*fe)[3], double* const* Eh, int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_prim_to32(const Dims& g, CP8 prim, CP3 bf, F11 p32, int nsm, cudaStream_t st);
 // ppm: PPM reconstruction instead of MC (FP64 only)
 cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* psi, const double* alp, P8 F, int nsm,
