@@ -13,20 +13,19 @@ steps have run the same kernels):
 
     M=$(python -c "from paper_2110_03732_gb300 import roofline as R; print(','.join(R.METRICS))")
     python bench.py --case ot --case-n 512 --steps 1 --warmup 3 > gpurun_out/plain.log 2>&1 &&
-    for k in k_implicit:6 k_flux_march:12 k_emf_march:6 k_update:6; do
+    for k in k_implicit k_stencil k_update; do
       ncu --metrics $M --clock-control none --print-units base \
-          -k "regex:^${k%%:*}" -s ${k##*:} -c 2 --csv --log-file gpurun_out/counts_fp64_${k%%:*}.csv \
+          -k "regex:^$k" -s 6 -c 2 --csv --log-file gpurun_out/counts_fp64_$k.csv \
           python bench.py --case ot --case-n 512 --steps 1 --warmup 3 || break
     done
-    (the same with --case ot_mixed into counts_mixed_*.csv, for k_implicit:6,
-    k_stencil32:6 and k_update:6: the mixed path runs its fluxes and edge EMFs in
-    one launch per stage)
+    (the same with --case ot_mixed into counts_mixed_$k.csv)
     python -m paper_2110_03732_gb300.roofline --fp64 gpurun_out/counts_fp64_*.csv \
         --mixed gpurun_out/counts_mixed_*.csv > profiles/roofline_counts.json
 
-The skip counts are the launches of that kernel pattern in the warm-up steps (2 per
-step, 4 for the two flux directions): the two captured launches are the first of the
-next step (for the FP64 flux, its two directions of the first stage).
+k_stencil is the one launch per stage of the face fluxes of every direction and the
+resistive edge EMFs; it is counted as the flux kind.  The three warm-up steps run 6
+launches of each pattern (2 per step): the two captured are the two stages of the
+next step.
 """
 from __future__ import annotations
 
@@ -81,7 +80,7 @@ def sources_digest() -> str:
 
 
 def kind_of(kernel_name: str):
-    for pre, kind in (("k_implicit", "implicit"), ("k_flux_march", "flux"), ("k_stencil32", "flux"),
+    for pre, kind in (("k_implicit", "implicit"), ("k_flux_march", "flux"), ("k_stencil", "flux"),
                       ("k_emf", "emf"), ("k_update", "update")):
         if kernel_name.startswith(pre) or kernel_name.startswith("void " + pre):
             return kind
