@@ -367,6 +367,8 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "stencil kernel");
     }
+    // the ideal-limit EMF: the flux launches (which also write the transport velocities),
+    // then one EMF launch per edge direction
     for (int d = 0; d < 3 && !fused; d++) {
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
@@ -382,8 +384,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
     for (int k = 0; k < 3 && !fused; k++) {
         if (!emf_needed(g, k) || fused_emf_dir(c, k) >= 0) continue;
         const int tk = tbegin(c, KIND_EMF, st);
-        if (c->ideal) e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
-        else e = launch_emf(g, k, prim, bfs, c->psi, c->alp, c->Eh[k], c->nsm, st, c->ppm);
+        e = launch_emf_ideal(g, k, prim, bfs, c->psi, c->alp, c->vbar, c->Eh[k], c->nsm, st);
         tend(c, tk, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "emf kernel");

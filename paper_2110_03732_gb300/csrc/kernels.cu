@@ -1,13 +1,19 @@
 // CUDA kernels of one IMEX-RK stage of resistive (GR)MHD with staggered
-// constrained transport (arXiv 2110.03732), sm_103a, FP64.
+// constrained transport (arXiv 2110.03732), sm_103a, FP64 and mixed precision.
 //
 //   k_implicit   Sec. 2.4: per-cell Newton on u coupled to the implicit E update;
 //                writes stage primitives and the stiff rate R = (q_E - q_E,base)/(a_ii dt)
-//   k_flux_march<D>  Sec. 2.1 + Sec. 5 defaults: MC (or PPM) reconstruction to the
-//                D-faces, marched along D, and the HLL flux with the maximal-diffusivity
-//                speeds of Sec. 2.5 (on flat 1-D / 2-D grids also the degenerate edge EMFs)
-//   k_emf_march<C>, k_emf<C>  Sec. 3.2 steps (i)-(vii): upwind (UCT-HLL) edge EMF
-//                hat{E}_C, marched along C + 2 when both transverse directions are active
+//   k_stencil<M, T, P>  one launch per stage of
+//                - the flux tasks, Sec. 2.1 + Sec. 5 defaults: MC (or PPM)
+//                  reconstruction to the D-faces, marched along D, and the HLL flux with
+//                  the maximal-diffusivity speeds of Sec. 2.5 (on flat 1-D / 2-D grids
+//                  also the degenerate edge EMFs), and
+//                - the edge-EMF tasks, Sec. 3.2 steps (i)-(vii): the upwind (UCT-HLL)
+//                  edge EMF hat{E}_C, marched along C + 2 when both transverse
+//                  directions are active
+//                in FP64 or (T = float) mixed precision
+//   k_flux_march<D>, k_emf_ideal<C>  the fluxes and App. A edge EMF of the ideal-limit
+//                variant (separate launches: the flux writes the transport velocities)
 //   k_update<M>  flux divergence + non-stiff sources (Sec. 2.1) and the CT face update
 //                (Sec. 3.2); writes L, or folds it straight into the IMEX stage bases and
 //                the final combination (Sec. 2.3)
@@ -68,40 +74,16 @@ __global__ void __launch_bounds__(128) k_flux_march(Dims g, FluxArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// upwind constrained transport: hat{E}_C on the edges along C, stored at the corner
-// index that is lower in a = C+1 and b = C+2
+// the explicit stencil of a stage: face fluxes and upwind constrained transport
+// (hat{E}_C on the edges along C, stored at the corner index that is lower in
+// a = C+1 and b = C+2)
 // ---------------------------------------------------------------------------
 
-template <int C, bool M, typename T, bool P = false>
-__global__ void __launch_bounds__(128) k_emf(Dims g, EmfArgs<T> a)
-{
-    grid_dep_sync();
-    long long tot = 1;
-#pragma unroll
-    for (int d = 0; d < 3; d++) tot *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x)
-        emf_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
-}
-
-// MC (or PPM) edge EMFs, K consecutive edges along B = C + 2 per thread
-// (emf_march_item; A and B active)
-template <int C, bool M, typename T, bool P = false>
-__global__ void __launch_bounds__(128) k_emf_march(Dims g, EmfArgs<T> a)
-{
-    grid_dep_sync();
-    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
-    const long long tot = (long long)g.dq[B].d * g.n[C] * (g.n[A] + 1);   // chunks of g.mk[B] edges
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x)
-        emf_march_item<C, M, T, P>(g, a.prim, a.bf, a.psi, a.alp, a.Eh, t);
-}
-
-// The face fluxes of every active direction and the edge EMFs the flux kernels do not
-// write, in one launch (resistive UCT, FP64 or mixed precision).  Block ranges select the task (the same
-// items, march lengths and grid copies as the separate launches, so every face and
-// edge is bitwise the same); one launch keeps the SMs filled across what were three to
-// six latency-bound single-wave kernels with their tails.
+// The face fluxes of every active direction and the edge EMFs the flux tasks do not
+// write, in one launch (resistive UCT, FP64 or mixed precision).  Block ranges select
+// the task (the same items, march lengths and grid copies as separate launches would
+// take, so every face and edge is bitwise the same); one launch keeps the SMs filled
+// across what would be three to six single-wave kernels with their tails.
 template <typename T>
 struct StencilTasks {
     int b0[7];                 // first block of task s (flux x, y, z; EMF x, y, z); b0[6] = grid
@@ -546,47 +528,7 @@ static void flux_dispatch(const Dims& g, int d, bool m, int nsm, cudaStream_t st
     else m ? flux_march_launch<2, true, T, P>(g, nsm, st, a) : flux_march_launch<2, false, T, P>(g, nsm, st, a);
 }
 
-template <int C, bool M, typename T, bool P>
-static int emf_march_blocks_per_sm()
-{
-    static int nb = 0;
-    if (nb < 1) {
-        int q = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k_emf_march<C, M, T, P>, 128, 0) != cudaSuccess ||
-            q < 1)
-            q = 1;
-        nb = q;
-    }
-    return nb;
-}
-
-// edges of direction C: marched along B when A and B are both active (K chosen as for
-// the flux kernels), one per thread otherwise
-template <int C, bool M, typename T, bool P>
-static void emf_launch(const Dims& g, int nsm, cudaStream_t st, const EmfArgs<T>& a)
-{
-    constexpr int A = (C + 1) % 3, B = (C + 2) % 3;
-    if (!g.act[A] || !g.act[B]) {
-        long long work = 1;
-        for (int d = 0; d < 3; d++) work *= (d == C) ? g.n[d] : (g.act[d] ? g.n[d] + 1 : 1);
-        launch_k(k_emf<C, M, T, P>, grid_for(work, 128, nsm), 128, st, g, a);
-        return;
-    }
-    const long long other = (long long)g.n[C] * (g.n[A] + 1);
-    const int K = march_len(g.n[B], other, nsm, emf_march_blocks_per_sm<C, M, T, P>(), P ? 1.0 : 0.6);
-    Dims gl = g;
-    set_march(gl, B, K);
-    launch_k(k_emf_march<C, M, T, P>, grid_for((long long)gl.dq[B].d * other, 128, nsm), 128, st, gl, a);
-}
-
-template <typename T, bool P>
-static void emf_dispatch(const Dims& g, int c, bool m, int nsm, cudaStream_t st, const EmfArgs<T>& a)
-{
-    if (c == 0) m ? emf_launch<0, true, T, P>(g, nsm, st, a) : emf_launch<0, false, T, P>(g, nsm, st, a);
-    else if (c == 1) m ? emf_launch<1, true, T, P>(g, nsm, st, a) : emf_launch<1, false, T, P>(g, nsm, st, a);
-    else m ? emf_launch<2, true, T, P>(g, nsm, st, a) : emf_launch<2, false, T, P>(g, nsm, st, a);
-}
-
+// edges of direction C (one per thread when A or B is inactive)
 static long long emf_work(const Dims& g, int c)
 {
     long long work = 1;
@@ -697,20 +639,6 @@ cudaError_t launch_stencil64(const Dims& g, CP8 prim, CP3 bf, const double* psi,
     for (int d = 0; d < 3; d++)
         for (int v = 0; v < 8; v++) fo[d].p[v] = F[d].p[v];
     return stencil_launch<double>(g, p, bf, psi, alp, fo, fe, Eh, nsm, st, ppm);
-}
-
-cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
-                       int nsm, cudaStream_t st, bool ppm)
-{
-    EmfArgs<double> a;
-    for (int v = 0; v < 8; v++) a.prim.p[v] = prim.p[v];
-    a.bf = bf;
-    a.psi = psi;
-    a.alp = alp;
-    a.Eh = Eh;
-    if (ppm) emf_dispatch<double, true>(g, c, psi || alp, nsm, st, a);
-    else emf_dispatch<double, false>(g, c, psi || alp, nsm, st, a);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp,

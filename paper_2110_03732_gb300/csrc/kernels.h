@@ -120,8 +120,6 @@ cudaError_t launch_flux(const Dims& g, int d, CP8 prim, CP3 bf, const double* ps
 // component (d + 1 + k) % 3 (NULL for inactive directions)
 cudaError_t launch_emf_ideal(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp,
                              const double* const (*vb)[2], double* Eh, int nsm, cudaStream_t st);
-cudaError_t launch_emf(const Dims& g, int c, CP8 prim, CP3 bf, const double* psi, const double* alp, double* Eh,
-                       int nsm, cudaStream_t st, bool ppm = false);
 cudaError_t launch_update(const Dims& g, const UpdateArgs& a, int nsm, cudaStream_t st);
 cudaError_t launch_curlA(const Dims& g, CP3 A, P3 bf, int nsm, cudaStream_t st);
 cudaError_t launch_prim2con(const Dims& g, CP8 prim, CP3 bf, const double* psi, P8 q, int nsm, cudaStream_t st);
