@@ -351,8 +351,12 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "stencil kernel");
     }
-    // FP64, resistive UCT: likewise one launch
-    const bool fused = c->mixed || !c->ideal;
+    // FP64, resistive UCT: likewise one launch, unless the flux of a single direction is
+    // the only task (a flat 1-D grid), where the plain flux kernel launches faster
+    int ntask = 0;
+    for (int d = 0; d < 3; d++) ntask += g.act[d] ? 1 : 0;
+    for (int k = 0; k < 3; k++) ntask += emf_needed(g, k) && fused_emf_dir(c, k) < 0 ? 1 : 0;
+    const bool fused = c->mixed || (!c->ideal && ntask > 1);
     if (!c->mixed && fused) {
         P8 fo[3];
         double* fe[3][3];
@@ -368,7 +372,7 @@ grmhd_status explicit_part(grmhd_ctx* c, CP8 prim, CP3 bfs, UpdateArgs& a, cudaS
         if (e != cudaSuccess) return cuda_fail(e, "stencil kernel");
     }
     // the ideal-limit EMF: the flux launches (which also write the transport velocities),
-    // then one EMF launch per edge direction
+    // then one EMF launch per edge direction; or the one flux launch of a flat 1-D grid
     for (int d = 0; d < 3 && !fused; d++) {
         if (!g.act[d]) continue;
         const int tk = tbegin(c, KIND_FLUX, st);
