@@ -9,18 +9,18 @@ reported.
 
 Refresh (one GPU, the 512^2 case of bench.py; one capture per precision and kernel
 kind, each of one kernel name pattern and two launches, taken after the three warm-up
-steps have run the same kernels):
+steps have run the same kernels; OUT is any scratch folder):
 
     M=$(python -c "from paper_2110_03732_gb300 import roofline as R; print(','.join(R.METRICS))")
-    python bench.py --case ot --case-n 512 --steps 1 --warmup 3 > gpurun_out/plain.log 2>&1 &&
+    python bench.py --case ot --case-n 512 --steps 1 --warmup 3 > $OUT/plain.log 2>&1 &&
     for k in k_implicit k_stencil k_update; do
       ncu --metrics $M --clock-control none --print-units base \
-          -k "regex:^$k" -s 6 -c 2 --csv --log-file gpurun_out/counts_fp64_$k.csv \
+          -k "regex:^$k" -s 6 -c 2 --csv --log-file $OUT/counts_fp64_$k.csv \
           python bench.py --case ot --case-n 512 --steps 1 --warmup 3 || break
     done
     (the same with --case ot_mixed into counts_mixed_$k.csv)
-    python -m paper_2110_03732_gb300.roofline --fp64 gpurun_out/counts_fp64_*.csv \
-        --mixed gpurun_out/counts_mixed_*.csv > profiles/roofline_counts.json
+    python -m paper_2110_03732_gb300.roofline --fp64 $OUT/counts_fp64_*.csv \
+        --mixed $OUT/counts_mixed_*.csv > profiles/roofline_counts.json
 
 k_stencil is the one launch per stage of the face fluxes of every direction and the
 resistive edge EMFs; it is counted as the flux kind.  The three warm-up steps run 6
