@@ -98,3 +98,11 @@ def test_ideal_emf_rejected_where_unsupported(G):
     S = G.Solver.from_problem(pr, emf="ideal")
     with pytest.raises(G.GrmhdError):
         G.Batch([S])
+
+
+def test_ideal_emf_orszag_tang_full_size_two_steps(G):
+    """The ideal-limit UCT on the 512^2 Orszag-Tang workload in the launch configuration
+    the benchmark times: two steps against the oracle."""
+    S = _steps(G, P.orszag_tang(512), 2)
+    divb, _, _ = S.diagnostics()
+    assert divb[2] < 1e-12

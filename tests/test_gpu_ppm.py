@@ -145,3 +145,27 @@ def test_ppm_mixed_vs_fp64(G):
     scale = max(abs(x) for x in tot0[:5])
     for v in range(5):
         assert abs(tot1[v] - tot0[v]) <= 1e-12 * scale
+
+
+def test_ppm_orszag_tang_full_size_two_steps(G):
+    """PPM on the 512^2 Orszag-Tang workload in the launch configuration the benchmark
+    times: two steps against the oracle, FP64 bounds; then the mixed-precision PPM path
+    on the same workload against the same oracle (relative L1 of D and tau <= 1e-5)."""
+    pr = P.orszag_tang(512)
+    st = oracle.from_problem(pr, rec="ppm")
+    S = G.Solver.from_problem(pr, rec="ppm")
+    Sm = G.Solver.from_problem(pr, rec="ppm", precision="mixed")
+    dt = oracle.cfl_dt(st.grid, pr.cfl)
+    I = st.grid.interior()
+    for k in range(2):
+        st.step(dt)
+        S.step(dt)
+        Sm.step(dt)
+        torch.cuda.synchronize()
+        for v in range(8):
+            check(cpu(S.q[v])[I], st.q[v][I], ("ppm 512^2", k, v))
+        for d in range(3):
+            check(cpu(S.bf[d])[I], st.bf[d][I], ("ppm 512^2", k, "B", d))
+        for v in (0, 4):
+            assert rel_l1(cpu(Sm.q[v])[I], st.q[v][I]) <= 1e-5, ("ppm mixed 512^2", k, v)
+    assert S.diagnostics()[2] == 0 and Sm.diagnostics()[2] == 0 and st.fails == 0
