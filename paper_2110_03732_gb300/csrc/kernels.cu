@@ -35,8 +35,12 @@ thread_local bool launch_overlap = false;
 // implicit step
 // ---------------------------------------------------------------------------
 
+// Five blocks per SM (96 registers, about 1 KB of spills): against four (128 registers)
+// the mixed-precision and metric instances ran 1.5-4 % faster (512^2 vortex mixed 58.1 ->
+// 57.3 us, 128^3 star mixed 398 -> 381 us, FP64 455 -> 442 us per launch); the flat FP64
+// instance is unchanged (79.3 us).
 template <bool M, bool ACC>
-__global__ void __launch_bounds__(128, 4) k_implicit(Dims g, ImpArgs a)
+__global__ void __launch_bounds__(128, 5) k_implicit(Dims g, ImpArgs a)
 {
     grid_dep_sync();
     const long long tot = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -172,8 +176,13 @@ __global__ void __launch_bounds__(128) k_emf_ideal(Dims g, EmfArgs<double> a, Vb
 // update: cell-centred L (flux divergence + non-stiff sources) and face L_B (CT)
 // ---------------------------------------------------------------------------
 
+// The FP32-flux instances are held to 32 registers (16 blocks per SM, 300-570 B of
+// spills): the 513^2 items of a 512^2 stage then fit one wave instead of 1.5 and the
+// 128^3 star's mixed update ran 454 -> 421 us per launch (512^2: 42.8 -> 41.7 us).  The
+// FP64 instances keep the compiler's choice (64-78 registers): bound by the FP64 pipe,
+// they only lost from more blocks.
 template <bool M, bool F32>
-__global__ void __launch_bounds__(128) k_update(Dims g, UpdateArgs a)
+__global__ void __launch_bounds__(128, F32 ? 16 : 0) k_update(Dims g, UpdateArgs a)
 {
     grid_dep_sync();
     long long tot = 1;
