@@ -409,6 +409,10 @@ __device__ __forceinline__ int ext_cell(const Dims& g, int d, int m)
     return m < 0 ? 0 : g.N[d] - 1;
 }
 
+// fused multiply-add in the precision of its operands
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 // ---------------------------------------------------------------------------
 // physical state at a face in the orthonormal frame (Sec. 2.1)
 // ---------------------------------------------------------------------------
@@ -485,6 +489,7 @@ __device__ __forceinline__ void face_hll_half(const T* pr, const T* B, int d, T 
     const T rho = pr[0], p = pr[4];
     const T u[3] = {pr[1], pr[2], pr[3]};
     const T E[3] = {pr[5], pr[6], pr[7]};
+    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
     const T x = T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     iW = rsqrt_t(x);
     const T W = x * iW;
@@ -492,16 +497,25 @@ __device__ __forceinline__ void face_hll_half(const T* pr, const T* B, int d, T 
     const T hW = rhoh * W;
     // 2U = |E|^2 + |B|^2; p + U and U - p each as one fused multiply-add
     const T U2 = E[0] * E[0] + E[1] * E[1] + E[2] * E[2] + B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-    const T X[3] = {E[1] * B[2] - E[2] * B[1], E[2] * B[0] - E[0] * B[2], E[0] * B[1] - E[1] * B[0]};
+    const T Xd = E[d1] * B[d2] - E[d2] * B[d1];   // (E x B)_d, used twice
     const T a = u[d] + s * W;
     const T K = rhoh * a;
     g[0] = rho * a;
+    // S_j halves, j != d: the component (E x B)_j = E^{j+1} B^{j+2} - E^{j+2} B^{j+1} is
+    // used once, so it enters the chain of fused multiply-adds directly
 #pragma unroll
-    for (int j = 0; j < 3; j++) g[1 + j] = K * u[j] - E[d] * E[j] - B[d] * B[j] + s * X[j];
-    g[1 + d] += T(0.5) * U2 + p;
-    const T Sd = hW * u[d] + X[d];
-    g[4] = (Sd - rho * u[d]) + s * (W * (hW - rho) + (T(0.5) * U2 - p));
-    const int d1 = (d + 1) % 3, d2 = (d + 2) % 3;
+    for (int j = 0; j < 3; j++) {
+        if (j == d) continue;
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        g[1 + j] = fma_t(K, u[j], fma_t(-E[d], E[j], fma_t(-B[d], B[j], fma_t(s * E[j1], B[j2], -(s * E[j2]) * B[j1]))));
+    }
+    // S_d: K u^d + (p + U - E^d E^d - B^d B^d) + SG (E x B)_d
+    g[1 + d] = fma_t(K, u[d], fma_t(-E[d], E[d], fma_t(-B[d], B[d], fma_t(T(0.5), U2, p))) + s * Xd);
+    // tau: S_d - rho u^d + SG (rho h W^2 - p + U - rho W)
+    //    = S_d + SG (h W W + U - p) - rho a,  and rho a is g[0]
+    const T Sd = fma_t(hW, u[d], Xd);
+    const T Tq = fma_t(W, hW, fma_t(T(0.5), U2, -p));
+    g[4] = (Sd + s * Tq) - g[0];
     g[5 + d] = s * E[d];
     g[5 + d1] = B[d2] + s * E[d1];
     g[5 + d2] = s * E[d2] - B[d1];

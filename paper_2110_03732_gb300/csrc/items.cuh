@@ -183,8 +183,9 @@ __device__ __forceinline__ T uct_edge(T hLL, T hLR, T hRL, T hRR, T ca, T cb, T 
 // Eh (flat metric only, else NULL): Eh[C] set for an edge direction C != D whose
 // third direction is inactive (a 1-D or 2-D grid).  Its edges then coincide with the
 // D-faces, and the UCT EMF there needs only reconstructions along D of E_C and of the
-// transverse q_B, which are this face's states: the face writes hat{E}_C, bitwise what
-// emf_item computes (the same MC or PPM values, the same edge formula).
+// transverse q_B, which are this face's states: the face writes hat{E}_C, what emf_item
+// computes from the same MC or PPM values (to round-off: the edge formula here is
+// reduced for the coinciding states).
 template <int D, bool M, typename T>
 __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const double* psi_in, const double* alp_in,
                                           const int* c, long long rm, long long r0, T* prL, T* prR, T* BL, T* BR,
@@ -201,12 +202,12 @@ __device__ __forceinline__ void face_flux(const Dims& g, const CP3& bf, const do
     BL[D] = BR[D] = (T)bf.p[D][face_at(g, D, c)] * (ipf2 * ipf2);
     if (!M && Eh) {
         // C = D + 1: A = D + 2 (inactive), B = D; C = D + 2: A = D, B = D + 1 (inactive)
-        if (Eh[T1])
-            Eh[T1][r0] = to_f64(uct_edge<T>(prL[5 + T1], prR[5 + T1], prL[5 + T1], prR[5 + T1], T(1), T(1), BL[D],
-                                             BR[D], BL[T2], BR[T2]));
-        if (Eh[T2])
-            Eh[T2][r0] = to_f64(uct_edge<T>(prL[5 + T2], prL[5 + T2], prR[5 + T2], prR[5 + T2], T(1), T(1),
-                                             BL[T1], BR[T1], BL[D], BR[D]));
+        // uct_edge with the inactive side's two states equal: the four-state mean is
+        // the mean of the two D states, the normal field's jump across the inactive
+        // side is zero, and the unit speeds leave (E_L + E_R -/+ jump of the transverse
+        // q_B along D) / 2
+        if (Eh[T1]) Eh[T1][r0] = to_f64(scale_pow2<T, -1>((prL[5 + T1] + prR[5 + T1]) - (BR[T2] - BL[T2])));
+        if (Eh[T2]) Eh[T2][r0] = to_f64(scale_pow2<T, -1>((prL[5 + T2] + prR[5 + T2]) + (BR[T1] - BL[T1])));
     }
     if (psi) {
 #pragma unroll
