@@ -230,9 +230,13 @@ __device__ __forceinline__ double cell_divb(const Dims& g, const double* const* 
     return dv;
 }
 
+template <typename T, int K>
+__device__ __forceinline__ T scale_pow2(T v);
+
 // cell-centred q_B^e of the cell at padded coordinates c: the cell is mapped first,
 // then the mean of its two e-faces (the lower face alone where the upper one lies
-// outside a fixed-boundary array); an inactive e stores the cell value itself
+// outside a fixed-boundary array; the halving on the integer pipe); an inactive e
+// stores the cell value itself
 __device__ __forceinline__ double cell_qB(const Dims& g, const double* __restrict__ bf, int e, const int* c)
 {
     int m[3];
@@ -244,7 +248,7 @@ __device__ __forceinline__ double cell_qB(const Dims& g, const double* __restric
     if (g.bc[e] == BC_PERIODIC && h == g.ng[e] + g.n[e]) h = g.ng[e];
     if (h >= g.N[e]) return bf[i0];
     const long long i1 = chk(g, i0 + (long long)(h - m[e]) * g.st[e]);
-    return 0.5 * (bf[i0] + bf[i1]);
+    return scale_pow2<double, -1>(bf[i0] + bf[i1]);
 }
 
 // ---------------------------------------------------------------------------
@@ -717,7 +721,7 @@ __device__ __forceinline__ unsigned mag_hi(double x) { return (unsigned)__double
 __device__ __forceinline__ double from_hi(unsigned h) { return __hiloint2double((int)h, 0); }
 
 struct Eval {
-    double W, iW, E[3], wt, U, A1, iWe, iden, Esu, f[3], g;
+    double W, iW, E[3], wt, U, A1, iWe, iden, Esu, f[3];
     double fm;   // max |f_i| (high-word maximum: within 2^-20 below the exact one)
     double M;    // momentum scale of f: max(|S_i|, |(E x B)_i|, |w_t u_i|), likewise
 };
@@ -775,11 +779,13 @@ __device__ __forceinline__ void evaluate(const CellIn& c, const double* u, Eval&
     e.f[0] = w0 - c.S[0] + x0;
     e.f[1] = w1 - c.S[1] + x1;
     e.f[2] = w2 - c.S[2] + x2;
-    e.g = e.f[0] * e.f[0] + e.f[1] * e.f[1] + e.f[2] * e.f[2];
     e.fm = from_hi(max(mag_hi(e.f[0]), max(mag_hi(e.f[1]), mag_hi(e.f[2]))));
     e.M = from_hi(max(max(max(mag_hi(c.S[0]), mag_hi(c.S[1])), max(mag_hi(c.S[2]), mag_hi(x0))),
                       max(max(mag_hi(x1), mag_hi(x2)), max(mag_hi(w0), max(mag_hi(w1), mag_hi(w2))))));
 }
+
+// |f|^2 of an evaluated residual
+__device__ __forceinline__ double fnorm2(const Eval& e) { return e.f[0] * e.f[0] + e.f[1] * e.f[1] + e.f[2] * e.f[2]; }
 
 // Jacobian J_ij = w_t delta_ij + u_i dw_t/du_j + (dE/du_j x B)_i
 __device__ __forceinline__ void jacobian(const CellIn& c, const double* u, const Eval& e, double J[3][3])
@@ -1275,15 +1281,17 @@ __device__ __forceinline__ int newton_solve(const CellIn& c, double* u, Eval& e,
             const double s = sqrt(1e4 * nu2 / nx2);
             dx[0] *= s; dx[1] *= s; dx[2] *= s;
         }
-        // slope of |f|^2 along the Newton direction is -2|f|^2
-        const double g0 = e.g;
+        // slope of |f|^2 along the Newton direction is -2|f|^2 (|f|^2 is formed here,
+        // not in evaluate: a residual accepted at once never needs it)
+        const double g0 = fnorm2(e);
         double lam = 1.0, ut[3];
         Eval et;
         for (int ls = 0; ls < 30; ls++) {
             ut[0] = u[0] + lam * dx[0]; ut[1] = u[1] + lam * dx[1]; ut[2] = u[2] + lam * dx[2];
             evaluate(c, ut, et);
-            if (et.g <= g0 * (1.0 - 2e-4 * lam) || !(g0 > 0.0)) break;
-            double lq = g0 * lam * lam / (et.g - g0 + 2.0 * g0 * lam);
+            const double gt = fnorm2(et);
+            if (gt <= g0 * (1.0 - 2e-4 * lam) || !(g0 > 0.0)) break;
+            double lq = g0 * lam * lam / (gt - g0 + 2.0 * g0 * lam);
             if (!(lq == lq)) lq = 0.5 * lam;
             lam = fmin(fmax(lq, 0.1 * lam), 0.5 * lam);
         }
