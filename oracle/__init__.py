@@ -32,23 +32,34 @@ BC = {"periodic": 0, "outflow": 1, "fixed": 2}
 GAMMA_SSP2 = 1.0 - 1.0 / np.sqrt(2.0)
 
 
+def compile_library(src: str, out: str) -> None:
+    """gcc, plain C99, FP64, no fused multiply-add contraction."""
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", src, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with gcc (no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
+        compile_library(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
 
 
 def lib():
+    """The loaded oracle library.  ``GRMHD_ORACLE_LIB`` names another build of the oracle
+    source to load instead (tests/test_oracle_mutations.py loads copies with planted
+    mistakes that way); it is then loaded as it is, never rebuilt."""
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            L = C.CDLL(_LIB)
+            path = os.environ.get("GRMHD_ORACLE_LIB")
+            if not path:
+                build()
+                path = _LIB
+            L = C.CDLL(path)
             dp = C.POINTER(C.c_double)
             dpp = C.POINTER(dp)
             ip = C.POINTER(C.c_int)

@@ -211,3 +211,48 @@ def test_totals_of_uniform_state_with_conformal_factor(psi):
     powers = np.array([6, 8, 8, 8, 6, 4, 4, 4])
     vol = 4 * 0.5 * 3 * 0.25 * 5 * 0.2
     np.testing.assert_allclose(oracle.totals(g, q), vol * psi ** powers * flat, rtol=1e-13, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# the CFL time step (Sec. 2.5: characteristic speeds alpha sqrt(gamma^dd) with beta = 0;
+# the multi-dimensional rule of reading c14: dt = CFL / max over cells of sum_d c_d / dx_d)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ndim,n,dx", [(1, [16], [0.1]), (2, [12, 9], [0.1, 0.25]), (3, [6, 5, 7], [0.5, 0.2, 0.125])])
+def test_cfl_dt_flat_is_the_light_crossing_bound(ndim, n, dx):
+    """Flat space: light moves at 1 in every direction, and the bound for a
+    dimensionally unsplit step is CFL / sum_d (1 / dx_d)."""
+    g = oracle.Grid(ndim, n, dx, ["periodic"] * 3, 4.0 / 3.0)
+    want = 0.4 / sum(1.0 / dx[d] for d in range(ndim))
+    assert abs(oracle.cfl_dt(g, 0.4) - want) <= 1e-15 * want
+
+
+@pytest.mark.parametrize("alpha,psi", [(0.5, 2.0), (0.8, 1.25), (1.0, 0.5)])
+def test_cfl_dt_constant_metric_is_a_rescaling(alpha, psi):
+    """On a constant lapse alpha and conformal factor psi (gamma_ij = psi^4 delta_ij) the
+    coordinate light speed is alpha / psi^2, so the step is the flat one times
+    psi^2 / alpha.  The ghost cells carry extreme metric values that must be ignored."""
+    g = oracle.Grid(2, [10, 7], [0.1, 0.3], ["outflow"] * 3, 4.0 / 3.0)
+    a = np.full(g.shape, alpha)
+    p = np.full(g.shape, psi)
+    I = g.interior()
+    ghost = np.ones(g.shape, dtype=bool)
+    ghost[I] = False
+    a[ghost] = 1e6
+    p[ghost] = 1e-3
+    flat = oracle.cfl_dt(g, 0.4)
+    assert abs(oracle.cfl_dt(g, 0.4, a, p) - flat * psi * psi / alpha) <= 1e-14 * flat * psi * psi / alpha
+
+
+def test_cfl_dt_takes_the_fastest_cell():
+    """One interior cell with twice the lapse (light twice as fast there) halves the
+    step; the same cell with psi = 2 instead slows light four-fold and leaves the step
+    to the other cells."""
+    g = oracle.Grid(3, [5, 4, 6], [0.2, 0.2, 0.4], ["outflow"] * 3, 5.0 / 3.0)
+    flat = oracle.cfl_dt(g, 0.4)
+    a = np.ones(g.shape)
+    a[3, 4, 5] = 2.0   # an interior cell (padded indices, two ghosts each side)
+    assert abs(oracle.cfl_dt(g, 0.4, a, None) - flat / 2.0) <= 1e-15 * flat
+    p = np.ones(g.shape)
+    p[3, 4, 5] = 2.0
+    assert abs(oracle.cfl_dt(g, 0.4, None, p) - flat) <= 1e-15 * flat
