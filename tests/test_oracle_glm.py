@@ -15,9 +15,12 @@ the mathematics, not by the oracle itself:
 * a constant metric (alpha, psi) is a rescaling of flat space: the metric run on
   dx / psi^2 with dt / alpha reproduces the flat run, variable by variable, with
   the powers of psi that the densitisation gives (for the CT scheme as well);
-* the reflection x -> -x of a 1-D line with a metric.
-All 14 mistakes planted in a scratch copy of the GLM code (signs, metric factors,
-densitisation, indices, one-sided face states, stage folds) fail one of these."""
+* the reflection x -> -x of a 1-D line with a metric;
+* Phi stays at rest for a uniform field in a linear lapse (its flux and its lapse
+  source cancel exactly).
+tests/test_oracle_mutations.py plants mistakes in the GLM code (signs, metric factors,
+densitisation, a flux along the wrong axis, the damping, the HLL diffusion) and checks
+that one of these fails for each."""
 import math
 
 import numpy as np
@@ -261,3 +264,28 @@ def test_glm_reflection_1d():
     for v in range(12):
         np.testing.assert_allclose(sg[v] * rv(L[v])[I], LR[v][I], rtol=1e-12, atol=1e-12 * np.abs(L[v]).max(),
                                    err_msg=str(v))
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+def test_glm_phi_balances_a_uniform_field_in_a_lapse_gradient(ndim):
+    """Sec. 3.1: with Phi = 0, the Phi equation's flux alpha q_B^i and its source
+    q_B^i d_i alpha cancel for a uniform q_B in a linear lapse: the flux divergence
+    (alpha_{i+1/2} - alpha_{i-1/2}) q_B / dx with face means of a linear alpha is the
+    central difference of alpha times q_B, exactly the source.  So a static uniform
+    state with a field along the lapse gradient has d q_Phi / dt = 0 to round-off,
+    while each of the two terms alone is of order q_B d alpha.  (Flat conformal
+    factor, E = 0, v = 0.)"""
+    n = [24, 10][:ndim]
+    dx = [0.05, 0.08][:ndim]
+    g = oracle.Grid(ndim, n, dx, ["outflow"] * 3, 4.0 / 3.0)
+    shp = g.shape
+    X = (np.arange(shp[2]) - 2 + 0.5) * dx[0]
+    alpha = np.broadcast_to(0.6 + 0.5 * X, shp).copy()   # d alpha / dx = 0.5
+    prim = [np.full(shp, 1.0), np.zeros(shp), np.zeros(shp), np.zeros(shp), np.full(shp, 0.3),
+            np.zeros(shp), np.zeros(shp), np.zeros(shp)]
+    qB = [np.full(shp, 0.7), np.full(shp, 0.2 if ndim > 1 else 0.0), np.zeros(shp)]
+    qphi = np.zeros(shp)
+    L = oracle.explicit_L_glm(g, 1.0, prim, qB, qphi, alpha, None)
+    I = g.interior()
+    source_alone = 0.7 * 0.5
+    assert np.abs(L[11][I]).max() <= 1e-12 * source_alone

@@ -8,7 +8,8 @@ fail: a mistake of that kind anywhere in these parts of the oracle would not go
 unnoticed.  The pins are the closed forms, paper tables, exact solutions, invariants
 and symmetries of test_oracle_cell.py, test_oracle_physics.py,
 test_oracle_diagnostics.py, test_oracle_ppm.py and test_oracle_ideal_emf.py (its two
-slowest convergence runs left out here)."""
+slowest convergence runs left out, except for mistakes in the ideal-limit EMF, which
+run that file whole); mistakes in the GLM variant run test_oracle_glm.py."""
 import concurrent.futures as cf
 import os
 import subprocess
@@ -23,7 +24,11 @@ PINS = ["tests/test_oracle_cell.py", "tests/test_oracle_diagnostics.py", "tests/
 SKIP = ["tests/test_oracle_ideal_emf.py::test_ideal_and_resistive_emf_agree_in_the_stiff_limit",
         "tests/test_oracle_ideal_emf.py::test_ideal_emf_advects_the_loop_at_second_order"]
 
-# (name, expression in the oracle, the mistake put in its place)
+# the pins of the GLM variant and of the ideal-limit EMF (all of them)
+GLM_PINS = ["tests/test_oracle_glm.py"]
+IDEAL_PINS = ["tests/test_oracle_ideal_emf.py"]
+
+# (name, expression in the oracle, the mistake put in its place[, pins if not PINS])
 MUTATIONS = [
     # prim2con (Sec. 2.1): tau without -D; the sign of the Poynting term in S
     ("tau_without_D",
@@ -100,13 +105,51 @@ MUTATIONS = [
     ("dt_psi_power",
      "if (G.act[d]) s += alp_at(alp, c) * sqrt(1.0 / pow(ps, 4)) / G.dx[d];",
      "if (G.act[d]) s += alp_at(alp, c) * sqrt(1.0 / pow(ps, 2)) / G.dx[d];"),
+    # GLM cleaning (Sec. 3.1): fluxes of q_B and q_Phi, their sources, densitisation
+    ("glm_phi_flux_axis",
+     "F[NQ + 3] = alp * sg * B[d];",
+     "F[NQ + 3] = alp * sg * B[(d + 1) % 3];", GLM_PINS),
+    ("glm_B_flux_sign",
+     "for (int k = 0; k < 3; k++) s += levi(j, d, k) * alp * g * pr[5 + k];",
+     "for (int k = 0; k < 3; k++) s -= levi(j, d, k) * alp * g * pr[5 + k];", GLM_PINS),
+    ("glm_phi_densitisation",
+     "q[NQ + 3] = sg * Phi;",
+     "q[NQ + 3] = Phi;", GLM_PINS),
+    ("glm_hll_diffusion_sign",
+     "for (int v = 0; v < NGLM; v++)\n                F[d][v][c] = (cp * FL[v] + cm * FR[v] - cp * cm * (qR[v] - qL[v]))",
+     "for (int v = 0; v < NGLM; v++)\n                F[d][v][c] = (cp * FL[v] + cm * FR[v] + cp * cm * (qR[v] - qL[v]))", GLM_PINS),
+    ("glm_damping_sign",
+     "Lc[NQ + 3] += -al * kappa * qPhi[c];",
+     "Lc[NQ + 3] += al * kappa * qPhi[c];", GLM_PINS),
+    ("glm_sB_without_inverse_metric",
+     "Lc[NQ + i] += -sg * al * (1.0 / gg) * dPhi;",
+     "Lc[NQ + i] += -sg * al * dPhi;", GLM_PINS),
+    ("glm_dphi_factor",
+     "double dPhi = (rec[NPR + 3][cp1] - rec[NPR + 3][cm1]) / (2.0 * g->dx[i]);",
+     "double dPhi = (rec[NPR + 3][cp1] - rec[NPR + 3][cm1]) / (g->dx[i]);", GLM_PINS),
+    ("glm_sphi_lapse_sign",
+     "Lc[NQ + 3] += qB[i][c] * dal;",
+     "Lc[NQ + 3] -= qB[i][c] * dal;", GLM_PINS),
+    # ideal-limit edge EMF (App. A)
+    ("ideal_diffusion_sign",
+     "- cam * cap * (qBbR - qBbL)) / (cam + cap)",
+     "+ cam * cap * (qBbR - qBbL)) / (cam + cap)", IDEAL_PINS),
+    ("ideal_second_term_sign",
+     "+ (cbm * vbR * qBaR + cbp * vbL * qBaL - cbm * cbp * (qBaR - qBaL)) / (cbm + cbp);",
+     "- (cbm * vbR * qBaR + cbp * vbL * qBaL - cbm * cbp * (qBaR - qBaL)) / (cbm + cbp);", IDEAL_PINS),
+    ("ideal_vbar_wrong_W",
+     "double vL = alf * recL[1 + j] / WL, vR = alf * recR[1 + j] / WR;",
+     "double vL = alf * recL[1 + j] / WL, vR = alf * recR[1 + j] / WL;", IDEAL_PINS),
+    ("ideal_vhat_without_lapse",
+     "vbar[d][j][c] = alp_at(X->alp, c) * prim[1 + j][c] / sqrt(1.0 + uu);",
+     "vbar[d][j][c] = prim[1 + j][c] / sqrt(1.0 + uu);", IDEAL_PINS),
 ]
 
 
 def test_every_mistake_applies_to_exactly_one_place():
     with open(SRC) as fh:
         src = fh.read()
-    for name, old, new in MUTATIONS:
+    for name, old, new, *_ in MUTATIONS:
         assert src.count(old) == 1, name
         assert old != new, name
 
@@ -114,7 +157,8 @@ def test_every_mistake_applies_to_exactly_one_place():
 def _survives(case, tmpdir):
     """Compile the oracle with one planted mistake and run the pins against it;
     returns None when a pin fails, else the pins' output."""
-    name, old, new = case
+    name, old, new = case[:3]
+    pins = case[3] if len(case) > 3 else PINS
     with open(SRC) as fh:
         src = fh.read()
     mut = os.path.join(tmpdir, f"{name}.c")
@@ -123,8 +167,8 @@ def _survives(case, tmpdir):
     lib = os.path.join(tmpdir, f"lib{name}.so")
     oracle.compile_library(mut, lib)
     env = dict(os.environ, GRMHD_ORACLE_LIB=lib)
-    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS,
-           *[f"--deselect={s}" for s in SKIP]]
+    cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *pins,
+           *[f"--deselect={s}" for s in SKIP if pins is PINS]]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     # 1: some pin failed.  0 would be a mistake no pin sees; other codes are crashes or
     # collection errors, which do not count as being caught
