@@ -105,6 +105,27 @@ MUTATIONS = [
     ("dt_psi_power",
      "if (G.act[d]) s += alp_at(alp, c) * sqrt(1.0 / pow(ps, 4)) / G.dx[d];",
      "if (G.act[d]) s += alp_at(alp, c) * sqrt(1.0 / pow(ps, 2)) / G.dx[d];"),
+    # implicit stage (Sec. 2.4, reading c2): eta_t without the lapse; R without 1/(a_ii dt)
+    ("etat_without_lapse",
+     "cl.etat = a_dt > 0 ? et / (alp_at(alp, c) * a_dt) : -1.0;",
+     "cl.etat = a_dt > 0 ? et / a_dt : -1.0;"),
+    ("R_without_a_dt",
+     "if (R) R[i][c] = a_dt > 0 ? (qEn - q[5 + i][c]) / a_dt : 0.0;",
+     "if (R) R[i][c] = a_dt > 0 ? (qEn - q[5 + i][c]) : 0.0;"),
+    # cell-centred B (reading c11), the initial curl (Sec. 4), the tau source, the final
+    # combination of the face fields
+    ("cell_B_lower_face_only",
+     "qBc[d][c] = 0.5 * (bf[d][c] + bf[d][shift(g, c, d, 1)]);",
+     "qBc[d][c] = bf[d][c];"),
+    ("curl_sign",
+     "if (G.act[fb]) r += (A[fc][shift(&G, c, fb, 1)] - A[fc][c]) / G.dx[fb];",
+     "if (G.act[fb]) r -= (A[fc][shift(&G, c, fb, 1)] - A[fc][c]) / G.dx[fb];"),
+    ("tau_source_sign",
+     "Lc[4] += al * sg * (-(S_lo[i] / gg) / al * dal);",
+     "Lc[4] += al * sg * ((S_lo[i] / gg) / al * dal);"),
+    ("face_combination_weight",
+     "for (int d = 0; d < 3; d++) bf[d][c] += dt * wt[i] * Ls[i][NQ + d][c];",
+     "for (int d = 0; d < 3; d++) bf[d][c] += dt * Ls[i][NQ + d][c];"),
     # GLM cleaning (Sec. 3.1): fluxes of q_B and q_Phi, their sources, densitisation
     ("glm_phi_flux_axis",
      "F[NQ + 3] = alp * sg * B[d];",
