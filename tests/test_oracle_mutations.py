@@ -126,6 +126,34 @@ MUTATIONS = [
     ("face_combination_weight",
      "for (int d = 0; d < 3; d++) bf[d][c] += dt * wt[i] * Ls[i][NQ + d][c];",
      "for (int d = 0; d < 3; d++) bf[d][c] += dt * Ls[i][NQ + d][c];"),
+    # metric factors (Sec. 2.1, Sec. 2.5, Sec. 3.2): the edge lapse as a sum, not a mean;
+    # the tau flux without gamma^dd on S_d; d gamma_jj with the wrong power; rho_e not
+    # undensitised; the E densitisation; the charge-current source's sign
+    ("edge_lapse_sum",
+     "ale /= nce;",
+     "(void)nce;"),
+    ("tau_flux_without_inverse_metric",
+     "F[4] = sg * alp * (ginv * S_lo[d] - v[d] * D);",
+     "F[4] = sg * alp * (S_lo[d] - v[d] * D);"),
+    ("dgamma_factor",
+     "double dgam = 4.0 * ps * ps * ps * dps;",
+     "double dgam = 2.0 * ps * ps * ps * dps;"),
+    ("rho_e_densitised",
+     "double rhoe = divqE / sg;",
+     "double rhoe = divqE;"),
+    ("E_undensitised",
+     "for (int j = 0; j < 3; j++) q[5 + j] = sg * pr[5 + j];",
+     "for (int j = 0; j < 3; j++) q[5 + j] = pr[5 + j];"),
+    ("charge_current_sign",
+     "Lc[5 + i] += -sg * al * rhoe * v_up[i];",
+     "Lc[5 + i] += sg * al * rhoe * v_up[i];"),
+    # reconstruction: the left state's slope sign; PPM's second monotonicity branch
+    ("mc_left_state_sign",
+     "*L = a[m1] + 0.5 * mc_slope(a[m2], a[m1], a[c]);",
+     "*L = a[m1] - 0.5 * mc_slope(a[m2], a[m1], a[c]);"),
+    ("ppm_second_limit",
+     "else if (-dd * dd > dd * m6) *aR = 3.0 * a0 - 2.0 * *aL;",
+     "else if (-dd * dd > dd * m6) *aR = 3.0 * a0 - 2.0 * *aR;"),
     # GLM cleaning (Sec. 3.1): fluxes of q_B and q_Phi, their sources, densitisation
     ("glm_phi_flux_axis",
      "F[NQ + 3] = alp * sg * B[d];",
