@@ -41,6 +41,22 @@ MUTATIONS = [
     ("A5_sign",
      "double A5 = -1.0 - x2 * W / p;",
      "double A5 = 1.0 - x2 * W / p;"),
+    # the dynamo terms of the A_k (Sec. 2.4 with xi != 0)
+    ("A0_dynamo_term",
+     "double A0 = W + et + x2 * (W * W - 1.0) / p;",
+     "double A0 = W + et + x2 * (W * W + 1.0) / p;"),
+    ("A1_dynamo_term",
+     "double A1 = et / q + x2 * et * W / (p * q);",
+     "double A1 = et / q - x2 * et * W / (p * q);"),
+    ("A2_sign",
+     "double A2 = -xi * et / p;",
+     "double A2 = xi * et / p;"),
+    ("A3_swapped",
+     "double A3 = xi * q / p;",
+     "double A3 = xi * p / q;"),
+    ("A4_eta_sign",
+     "double A4 = xi * (1.0 - et * et + x2) / (p * q);",
+     "double A4 = xi * (1.0 + et * et + x2) / (p * q);"),
     ("residual_ExB_sign",
      "f[i] = wt * u_lo[i] - (c->S[i] - eEB[i]);",
      "f[i] = wt * u_lo[i] - (c->S[i] + eEB[i]);"),
